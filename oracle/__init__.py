@@ -1,0 +1,359 @@
+"""FP64 CPU oracle for the FCBM-EC peridynamic operators (arXiv 2105.06055).
+
+TEST INFRASTRUCTURE. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package. The GPU library never imports, links or calls it, and the two share
+no code: this package computes the model constants, the horizon and every sum
+on its own, from the paper.
+
+Contents
+  * ``pd_oracle.c`` (built into ``_build/liboracle.so``): the direct O(N |H|)
+    neighbour sums of the one-point quadrature (Eq. 55 first line, §4.1.1) for
+    the linearized bond model (Eq. 17-18, 75, 100), its strain energy density
+    (Eq. 47, 102), damage counts (Eq. 12, 44, reading R11), the linearized
+    state-based solid (Eq. 33-39, 92-94), the node-weight gradient of the bond
+    operator, and the periodic Fourier symbol (Eq. 57).
+  * Python drivers written step by step in the paper's order: velocity-Verlet
+    with embedded constraint and energy-based bond breaking (Eq. 63, 83-84),
+    FP64 conjugate gradient on the EC static residual (Eq. 89), and model
+    constants (§5.1, §5.2).
+
+Every function here is FP64. Parity status of each function is listed in the
+``PINS`` table at the bottom, which the pin tests import.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pd_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compile ``pd_oracle.c`` with gcc (-O2, OpenMP). Returns the .so path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            P = ctypes.c_void_p
+            I, D = ctypes.c_int, ctypes.c_double
+            lib.or_num_threads.restype = I
+            lib.or_set_threads.argtypes = [I]
+            lib.or_horizon.argtypes = [I, P, D, I, P, P]
+            lib.or_horizon.restype = I
+            lib.or_force_bond.argtypes = [I, P, P, D, D, P, P, P, P]
+            lib.or_energy_bond.argtypes = [I, P, P, D, D, P, P, P, P]
+            lib.or_damage.argtypes = [I, P, P, D, P, P, P, P, P]
+            lib.or_force_lps.argtypes = [P, P, D, D, D, P, P, P, P, P]
+            lib.or_force_bond_grad_s.argtypes = [I, P, P, D, D, P, P, P, P, P]
+            lib.or_symbol_bond.argtypes = [I, P, P, D, D, P, P]
+            _lib = lib
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _grid(shape):
+    """shape is (n2, n1) in 2D or (n3, n2, n1) in 3D (C order, x1 fastest)."""
+    if len(shape) == 2:
+        return 2, np.array([shape[1], shape[0], 1], dtype=np.int32)
+    return 3, np.array([shape[2], shape[1], shape[0]], dtype=np.int32)
+
+
+def _dx(dim, dx):
+    d = np.ones(3, dtype=np.float64)
+    a = np.atleast_1d(np.asarray(dx, dtype=np.float64))
+    d[:dim] = a[0] if a.size == 1 else a[:dim]
+    return d
+
+
+def num_threads() -> int:
+    return _load().or_num_threads()
+
+
+def set_threads(t: int) -> None:
+    _load().or_set_threads(int(t))
+
+
+# ----------------------------------------------------------------------------
+# Model constants (§3.1, §3.3, §5.1, §5.2)
+# ----------------------------------------------------------------------------
+
+def horizon(dim: int, dx, delta: float):
+    """Integer offsets o (|H| x 3) and lengths |xi| of the horizon (R1, R2)."""
+    lib = _load()
+    d = _dx(dim, dx)
+    cap = 1
+    for a in range(dim):
+        cap *= 2 * int(math.floor(delta / d[a] + 1e-9)) + 1
+    off = np.zeros((cap, 3), dtype=np.int32)
+    ln = np.zeros(cap, dtype=np.float64)
+    cnt = lib.or_horizon(dim, _p(d), float(delta), cap, _p(off), _p(ln))
+    return off[:cnt].copy(), ln[:cnt].copy()
+
+
+def alpha_bond(dim: int, E: float, delta: float) -> float:
+    """Bond constant for omega = 1/|xi|.
+
+    2D plane stress: 9E/(pi delta^3) (§5.2, with nu = 1/3).
+    3D: 12E/(pi delta^4) (reading R7, nu = 1/4): equate the bond energy of an
+    isotropic stretch, 1/4 int alpha omega |xi|^2 s^2 dV = pi alpha delta^4 s^2/4,
+    with the classical 9 kappa s^2 / 2 = 3 E s^2.
+    """
+    if dim == 2:
+        return 9.0 * E / (math.pi * delta ** 3)
+    return 12.0 * E / (math.pi * delta ** 4)
+
+
+def lps_constants(E: float, nu: float, dx, delta: float):
+    """(ka, cb, m0) of the linearized state-based solid (Eq. 37; reading R5).
+
+    kappa = E / (3 (1 - 2 nu)), mu = E / (2 (1 + nu)),
+    m0 = Σ_H omega |xi|^2 dV over a full horizon (Eq. 35, omega = 1/|xi|),
+    ka = (3 kappa - 5 mu)/m0, cb = 30 mu/m0.
+    """
+    d = _dx(3, dx)
+    _, ln = horizon(3, d, delta)
+    dV = float(d[0] * d[1] * d[2])
+    m0 = float(np.sum(ln)) * dV  # omega |xi|^2 = |xi|
+    kappa = E / (3.0 * (1.0 - 2.0 * nu))
+    mu = E / (2.0 * (1.0 + nu))
+    return (3.0 * kappa - 5.0 * mu) / m0, 30.0 * mu / m0, m0
+
+
+def wc_from_stretch(dim: int, dx, delta: float, alpha: float, s0: float) -> float:
+    """Critical energy density for a critical stretch s0 (reading R10).
+
+    W_c is the Eq. 47 energy density of a fully bonded node under the isotropic
+    stretch u = s0 x: each bond has eta = s0 xi, so eta.C.eta = alpha s0^2 |xi|
+    for omega = 1/|xi|, and W_c = 1/2 alpha s0^2 dV Σ_H |xi|.
+    """
+    d = _dx(dim, dx)
+    _, ln = horizon(dim, d, delta)
+    dV = float(np.prod(d[:dim]))
+    return 0.5 * alpha * s0 * s0 * dV * float(np.sum(ln))
+
+
+# ----------------------------------------------------------------------------
+# Direct sums (C)
+# ----------------------------------------------------------------------------
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _u8(a):
+    return np.ascontiguousarray(a, dtype=np.uint8)
+
+
+def force_bond(u, chi, dx, delta, alpha, s=None):
+    """L = chi s Σ chi' s' C (u' - u) dV (Eq. 17-18, 75, 100). u: (d, *shape)."""
+    chi = _u8(chi)
+    dim, n = _grid(chi.shape)
+    u = _f64(u)
+    assert u.shape == (dim,) + chi.shape
+    s = None if s is None else _f64(s)
+    L = np.empty_like(u)
+    _load().or_force_bond(dim, _p(n), _p(_dx(dim, dx)), float(delta), float(alpha),
+                          _p(chi), _p(s), _p(u), _p(L))
+    return L
+
+
+def energy_bond(u, chi, dx, delta, alpha, lam=None):
+    """W = 1/2 chi lam Σ chi' lam' eta.C.eta dV (Eq. 47, 102)."""
+    chi = _u8(chi)
+    dim, n = _grid(chi.shape)
+    u = _f64(u)
+    lam = None if lam is None else _u8(lam)
+    W = np.empty(chi.shape, dtype=np.float64)
+    _load().or_energy_bond(dim, _p(n), _p(_dx(dim, dx)), float(delta), float(alpha),
+                           _p(chi), _p(lam), _p(u), _p(W))
+    return W
+
+
+def damage(chi, lam, dx, delta):
+    """(nb, beta, d): broken in-body bonds, initial in-body bonds, damage index
+    (Eq. 12 with mu = lam lam', Eq. 44; reading R11)."""
+    chi = _u8(chi)
+    lam = _u8(lam)
+    dim, n = _grid(chi.shape)
+    nb = np.empty(chi.shape, dtype=np.int32)
+    beta = np.empty(chi.shape, dtype=np.int32)
+    d = np.empty(chi.shape, dtype=np.float64)
+    _load().or_damage(dim, _p(n), _p(_dx(dim, dx)), float(delta), _p(chi), _p(lam),
+                      _p(nb), _p(beta), _p(d))
+    return nb, beta, d
+
+
+def force_lps(u, chi, dx, delta, ka, cb, return_aux=False):
+    """Linearized state-based force with EC (Eq. 33-39, 92-94), 3D only."""
+    chi = _u8(chi)
+    dim, n = _grid(chi.shape)
+    assert dim == 3
+    u = _f64(u)
+    L = np.empty_like(u)
+    th = np.empty(chi.shape, dtype=np.float64)
+    m = np.empty(chi.shape, dtype=np.float64)
+    _load().or_force_lps(_p(n), _p(_dx(3, dx)), float(delta), float(ka), float(cb),
+                         _p(chi), _p(u), _p(L), _p(th), _p(m))
+    if return_aux:
+        return L, th, m
+    return L
+
+
+def force_bond_grad_s(u, p, chi, dx, delta, alpha, s=None):
+    """d(Σ p.L)/ds for the bond operator with node weight s."""
+    chi = _u8(chi)
+    dim, n = _grid(chi.shape)
+    u = _f64(u)
+    p = _f64(p)
+    s = None if s is None else _f64(s)
+    g = np.empty(chi.shape, dtype=np.float64)
+    _load().or_force_bond_grad_s(dim, _p(n), _p(_dx(dim, dx)), float(delta), float(alpha),
+                                 _p(chi), _p(s), _p(u), _p(p), _p(g))
+    return g
+
+
+def symbol_bond(shape, dx, delta, alpha, k):
+    """M(k) with L = -M(k) u for a single periodic mode (Eq. 57, chi = 1)."""
+    dim = len(shape)
+    n = np.array(list(shape[::-1]) + [1] * (3 - dim), dtype=np.int32)
+    kk = np.zeros(3, dtype=np.float64)
+    kk[:dim] = k
+    M = np.zeros(9, dtype=np.float64)
+    _load().or_symbol_bond(dim, _p(n), _p(_dx(dim, dx)), float(delta), float(alpha),
+                           _p(kk), _p(M))
+    return M.reshape(3, 3)[:dim, :dim].copy()
+
+
+# ----------------------------------------------------------------------------
+# Drivers in the paper's order
+# ----------------------------------------------------------------------------
+
+def verlet_damage(u, v, lam, chi, chi_omega, b, w, dx, delta, alpha, rho, dt, wc, nsteps):
+    """Velocity-Verlet with embedded constraint and energy-based bond breaking.
+
+    Order per step n -> n+1 (Eq. 83-84 for the kinematics, Eq. 63 and reading R8
+    for the integrity index, Eq. 100-102 for L and W with lambda):
+        a^n      = L(u^n, lam^n) + b
+        u^{n+1}  = chi_O { u^n + dt [v^n + dt/(2 rho) a^n] } + (1 - chi_O) w
+        lam^{n+1} = lam^n [ W(u^n, lam^n) <= wc ]          (irreversible)
+        a^{n+1}  = L(u^{n+1}, lam^{n+1}) + b
+        v^{n+1}  = chi_O { v^n + dt/(2 rho) (a^n + a^{n+1}) }
+    chi_omega has shape (d, *grid); w and b have shape (d, *grid).
+    Returns (u, v, lam, flips) with flips = nodes whose lam went 1 -> 0.
+    """
+    u = _f64(u).copy()
+    v = _f64(v).copy()
+    lam = _u8(lam).copy()
+    co = np.asarray(chi_omega, dtype=np.float64)
+    b = _f64(b)
+    w = _f64(w)
+    L = force_bond(u, chi, dx, delta, alpha, s=lam.astype(np.float64))
+    W = energy_bond(u, chi, dx, delta, alpha, lam=lam)
+    flips = 0
+    for _ in range(nsteps):
+        a0 = L + b
+        u = co * (u + dt * (v + dt / (2.0 * rho) * a0)) + (1.0 - co) * w
+        new_lam = (lam.astype(bool) & (W <= wc)).astype(np.uint8)
+        flips += int(np.sum(lam.astype(np.int64) - new_lam.astype(np.int64)))
+        lam = new_lam
+        L = force_bond(u, chi, dx, delta, alpha, s=lam.astype(np.float64))
+        W = energy_bond(u, chi, dx, delta, alpha, lam=lam)
+        v = co * (v + dt / (2.0 * rho) * (a0 + L + b))
+    return u, v, lam, flips
+
+
+def static_residual(u, chi, chi_omega, b, dx, delta, op):
+    """R = chi_O (L(u) + b) (Eq. 89); ``op`` is 'bond' with alpha or 'lps' with (ka, cb)."""
+    L = _apply(op, u, chi, dx, delta)
+    return np.asarray(chi_omega, dtype=np.float64) * (L + _f64(b))
+
+
+def _apply(op, u, chi, dx, delta):
+    kind = op[0]
+    if kind == "bond":
+        return force_bond(u, chi, dx, delta, op[1])
+    if kind == "lps":
+        return force_lps(u, chi, dx, delta, op[1], op[2])
+    raise ValueError(kind)
+
+
+def cg_static(chi, chi_omega, b, w, dx, delta, op, rtol=1e-12, max_iter=100000):
+    """FP64 conjugate gradient for the EC static problem (Eq. 85-89, §5.1).
+
+    Unknowns are u on Omega (chi_O = 1); u = w on Gamma (reading R14/R15).
+    The system chi_O (L(u) + b) = 0 with u = e + w, e = 0 off Omega, is
+    A e = r0 with A e = -chi_O L(chi_O e) (symmetric positive definite on Omega)
+    and r0 = chi_O (b + L(w)). Unpreconditioned CG from e = 0 [50].
+    Returns (u, iterations, relative residual ||chi_O(L(u)+b)|| / ||chi_O b||).
+    """
+    co = np.asarray(chi_omega, dtype=np.float64)
+    w = _f64(w)
+    b = _f64(b)
+
+    def A(e):
+        return -co * _apply(op, co * e, chi, dx, delta)
+
+    r = co * (b + _apply(op, w, chi, dx, delta))
+    e = np.zeros_like(r)
+    p = r.copy()
+    rr = float(np.vdot(r, r))
+    bn = math.sqrt(float(np.vdot(co * b, co * b)))
+    it = 0
+    while it < max_iter and math.sqrt(rr) > rtol * bn:
+        q = A(p)
+        alpha = rr / float(np.vdot(p, q))
+        e += alpha * p
+        r -= alpha * q
+        rr_new = float(np.vdot(r, r))
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+        it += 1
+    u = co * e + (1.0 - co) * w
+    res = static_residual(u, chi, chi_omega, b, dx, delta, op)
+    return u, it, math.sqrt(float(np.vdot(res, res))) / bn
+
+
+# Parity status of each oracle function: the pin tests that tie it to the
+# paper or to mathematics (tests/test_oracle_pins.py).
+PINS = {
+    "horizon": "brute-force lattice count; |H| = 28/48/80 (2D d=3,4,5), 122 (3D d=3)",
+    "alpha_bond": "energy of isotropic stretch vs classical elasticity; symbol vs Navier-Cauchy",
+    "force_bond": "translation/rotation null space, affine interior, symbol, reciprocity, "
+                  "all-pairs brute force, dense operator spectrum",
+    "energy_bond": "energy identity Σ W dV = -<u, L u> dV; isotropic-stretch closed form",
+    "damage": "integer counts vs brute force; intact body d = 0",
+    "force_lps": "translation/rotation null space, affine 2-delta interior, dilatation of "
+                 "isotropic stretch = 3 s, nu = 1/4 reduces to bond form, reciprocity",
+    "force_bond_grad_s": "central finite differences of force_bond",
+    "symbol_bond": "single-mode displacement through force_bond",
+    "verlet_damage": "energy conservation without damage, time reversibility",
+    "cg_static": "FP64 residual of the returned solution",
+}

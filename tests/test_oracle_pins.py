@@ -1,0 +1,464 @@
+"""Pins of the FP64 oracle against the paper and mathematics (CPU only).
+
+Each test ties one oracle function to something other than itself: a value the
+paper prints, a closed form, an invariant, classical elasticity, or brute
+force on a tiny grid. A plausible slip in the oracle (a dropped term, a wrong
+sign or index, a transposed operand, a wrong constant) fails at least one.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2105_06055_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    vals = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, v = line.split()[:2]
+            vals[k] = float(v)
+    return vals
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+# --------------------------------------------------------------------------
+# Horizon and constants
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim,delta,count", [(2, 3.0, 28), (2, 4.0, 48), (2, 5.0, 80),
+                                             (3, 3.0, 122)])
+def test_horizon_counts(oracle, dim, delta, count):
+    off, ln = oracle.horizon(dim, 1.0, delta)
+    assert len(off) == count
+    # brute force lattice count
+    r = int(delta)
+    rng3 = range(-r, r + 1) if dim == 3 else [0]
+    bf = sum(1 for i in range(-r, r + 1) for j in range(-r, r + 1) for k in rng3
+             if 0 < i * i + j * j + k * k <= delta * delta)
+    assert bf == count
+    assert np.allclose(ln, np.sqrt((off.astype(float) ** 2).sum(1)))
+
+
+def test_paper_grid_values():
+    """Eq. 52 grid spacing on the delta-grown box reproduces the printed m-factors."""
+    g = _golden("paper_grid_values.txt")
+    m1 = g["s51_delta_cm"] / (g["s51_L1_cm"] / g["s51_N1"])
+    assert abs(m1 - g["s51_m1"]) < 0.005
+    L1 = g["s52_plate_L1_cm"] + 2 * g["s52_delta_cm"]
+    L2 = g["s52_plate_L2_cm"] + 2 * g["s52_delta_cm"]
+    assert abs(g["s52_delta_cm"] / (L1 / g["s52_N1"]) - g["s52_m1"]) < 0.005
+    assert abs(g["s52_delta_cm"] / (L2 / g["s52_N2"]) - g["s52_m2"]) < 0.005
+
+
+def test_paper_time_step_is_stable(oracle):
+    """§5.2 states dt = 5e-8 s is stable for the glass plate. With the 2D bond
+    constant 9E/(pi delta^3) and the grid of §5.2, the largest eigenvalue of the
+    discrete periodic symbol bounds the Verlet stability limit dt < 2 sqrt(rho/l_max).
+    The printed dt must lie below it, and not absurdly far below (a constant off
+    by a large factor would break one side)."""
+    g = _golden("paper_grid_values.txt")
+    delta = g["s52_delta_cm"] * 1e-2
+    dx1 = (g["s52_plate_L1_cm"] + 2 * g["s52_delta_cm"]) * 1e-2 / g["s52_N1"]
+    dx2 = (g["s52_plate_L2_cm"] + 2 * g["s52_delta_cm"]) * 1e-2 / g["s52_N2"]
+    alpha = oracle.alpha_bond(2, g["s52_E_Pa"], delta)
+    shape = (int(g["s52_N2"]), int(g["s52_N1"]))
+    lmax = 0.0
+    for k1 in range(0, shape[1] // 2 + 1, 8):
+        for k2 in range(0, shape[0] // 2 + 1, 8):
+            M = oracle.symbol_bond(shape, (dx1, dx2), delta, alpha, (k1, k2))
+            lmax = max(lmax, float(np.linalg.eigvalsh(M).max()))
+    dt_crit = 2.0 * math.sqrt(g["s52_rho"] / lmax)
+    assert g["s52_dt_s"] < dt_crit < 10 * g["s52_dt_s"]
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_bond_symbol_long_wave_is_navier(oracle, dim):
+    """Long-wave limit of the discrete bond operator = Navier-Cauchy elasticity.
+
+    With omega = 1/|xi| and alpha = 9E/(pi delta^3) (2D plane stress, nu = 1/3)
+    or 12E/(pi delta^4) (3D, nu = 1/4), the symbol M(k) -> mu |kappa|^2 I +
+    (lam + mu) kappa kappa^T with lam = mu = 3E/8 (2D) or 2E/5 (3D). The
+    discrete horizon sum converges to the integral as delta/dx grows; at
+    delta = 10 dx the quadrature error is a few percent."""
+    E = 1.0
+    delta = 10.0 if dim == 2 else 7.0
+    n = 1024 if dim == 2 else 256
+    shape = (n,) * dim
+    alpha = oracle.alpha_bond(dim, E, delta)
+    lam = mu = (3.0 * E / 8.0) if dim == 2 else (2.0 * E / 5.0)
+    for kvec in ([1, 0, 0], [1, 1, 0], [2, -1, 1]):
+        k = np.array(kvec[:dim], dtype=float)
+        kap = 2 * math.pi * k / n
+        M = oracle.symbol_bond(shape, 1.0, delta, alpha, k)
+        Mn = mu * kap.dot(kap) * np.eye(dim) + (lam + mu) * np.outer(kap, kap)
+        assert _rel(M, Mn) < 0.06, (kvec, M, Mn)
+
+
+def test_wc_closed_form(oracle):
+    """W of a fully bonded node under u = s0 x equals 1/2 alpha s0^2 dV Σ|xi| (R10)."""
+    shape = (40, 40)
+    delta, s0 = 4.0, 1e-3
+    alpha = oracle.alpha_bond(2, 1.0, delta)
+    chi = inputs.box_mask(shape, (4, 4), (36, 36))
+    x1, x2 = inputs.coords(shape)
+    u = np.stack([s0 * x1, s0 * x2])
+    W = oracle.energy_bond(u, chi, 1.0, delta, alpha)
+    wc = oracle.wc_from_stretch(2, 1.0, delta, alpha, s0)
+    assert abs(W[20, 20] / wc - 1.0) < 1e-12
+    _, ln = oracle.horizon(2, 1.0, delta)
+    assert abs(np.sum(ln) - 129.0) < 0.01  # Σ|xi| for 2D delta = 4
+
+
+# --------------------------------------------------------------------------
+# Bond operator
+# --------------------------------------------------------------------------
+
+def _blob(shape, seed):
+    """Seeded irregular body inside the box, at least 4 nodes from its edges."""
+    g = inputs.rng(seed)
+    dim = len(shape)
+    chi = inputs.box_mask(shape, (4,) * dim, tuple(s - 4 for s in shape[::-1]))
+    holes = g.random(shape) < 0.08
+    chi[holes] = 0
+    return chi
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_bond_rigid_motions_give_zero_force(oracle, dim):
+    shape = (24,) * dim if dim == 2 else (14,) * 3
+    chi = _blob(shape, 1)
+    delta = 3.0
+    alpha = oracle.alpha_bond(dim, 1.0, delta)
+    x = inputs.coords(shape)
+    t = np.stack([np.full(shape, 0.3 + 0.1 * i) for i in range(dim)])
+    assert np.max(np.abs(oracle.force_bond(t, chi, 1.0, delta, alpha))) < 1e-13
+    Wm = np.zeros((dim, dim))
+    Wm[0, 1], Wm[1, 0] = 0.01, -0.01
+    if dim == 3:
+        Wm[0, 2], Wm[2, 0] = -0.02, 0.02
+    rot = np.stack([sum(Wm[i, j] * x[j] for j in range(dim)) for i in range(dim)])
+    assert np.max(np.abs(oracle.force_bond(rot, chi, 1.0, delta, alpha))) < 1e-13
+
+
+def test_bond_affine_interior_zero_and_boundary_nonzero(oracle):
+    cfg = inputs.plate_2d_single_eval(n=64, margin=12, seed=3)
+    delta = 3.0
+    alpha = oracle.alpha_bond(2, 1.0, delta)
+    ua, A, t = inputs.affine_field(cfg["shape"], 1.0, 1e-3, 7)
+    L = oracle.force_bond(ua, cfg["chi"], 1.0, delta, alpha)
+    inner = inputs.box_mask(cfg["shape"], (15, 15), (49, 49)).astype(bool)
+    assert np.max(np.abs(L[:, inner])) < 1e-15
+    ring = cfg["chi"].astype(bool) & ~inner
+    assert np.max(np.abs(L[:, ring])) > 1e-5
+
+
+def test_bond_single_mode_symbol(oracle):
+    """chi = 1 (periodic): u = a cos(2 pi k.x/N + phi) gives L = -M(k) u (Eq. 57)."""
+    shape = (32, 48)
+    delta = 3.5
+    alpha = oracle.alpha_bond(2, 2.0, delta)
+    chi = np.ones(shape, dtype=np.uint8)
+    i1, i2 = inputs.coords(shape)
+    k = (5, -3)
+    ph = 2 * math.pi * (k[0] * i1 / 48 + k[1] * i2 / 32) + 0.4
+    a = np.array([0.7, -1.3])
+    u = np.stack([a[0] * np.cos(ph), a[1] * np.cos(ph)])
+    L = oracle.force_bond(u, chi, 1.0, delta, alpha)
+    M = oracle.symbol_bond(shape, 1.0, delta, alpha, k)
+    ref = -np.einsum("ij,j...->i...", M, u)
+    assert _rel(L, ref) < 1e-12
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_bond_reciprocity_and_sign(oracle, dim):
+    shape = (20, 22) if dim == 2 else (12, 13, 14)
+    chi = _blob(shape, 5)
+    s = 0.5 + inputs.rng(9).random(shape)
+    delta = 2.5
+    alpha = oracle.alpha_bond(dim, 1.0, delta)
+    g = inputs.rng(11)
+    u = g.normal(size=(dim,) + shape)
+    v = g.normal(size=(dim,) + shape)
+    Lu = oracle.force_bond(u, chi, 1.0, delta, alpha, s=s)
+    Lv = oracle.force_bond(v, chi, 1.0, delta, alpha, s=s)
+    a, b = float(np.sum(v * Lu)), float(np.sum(u * Lv))
+    assert abs(a - b) < 1e-12 * max(abs(a), 1.0)
+    assert float(np.sum(u * Lu)) < 0
+
+
+def test_bond_matches_all_pairs_brute_force(oracle):
+    """Pure-Python all-pairs sum with minimum-image distances on a tiny grid."""
+    shape = (9, 11)  # n2, n1
+    delta = 2.2
+    dx = (1.0, 0.9)
+    alpha = 0.37
+    g = inputs.rng(2)
+    chi = (g.random(shape) < 0.8).astype(np.uint8)
+    s = 0.5 + g.random(shape)
+    u = g.normal(size=(2,) + shape)
+    L = oracle.force_bond(u, chi, dx, delta, alpha, s=s)
+    n2, n1 = shape
+    ref = np.zeros_like(u)
+    for a2 in range(n2):
+        for a1 in range(n1):
+            if not chi[a2, a1]:
+                continue
+            for b2 in range(n2):
+                for b1 in range(n1):
+                    d1 = (b1 - a1 + n1 // 2) % n1 - n1 // 2
+                    d2 = (b2 - a2 + n2 // 2) % n2 - n2 // 2
+                    xi = np.array([d1 * dx[0], d2 * dx[1]])
+                    r = math.hypot(*xi)
+                    if r == 0 or r > delta or not chi[b2, b1]:
+                        continue
+                    eta = u[:, b2, b1] - u[:, a2, a1]
+                    f = alpha / r * np.outer(xi, xi) / r ** 2 @ eta
+                    ref[:, a2, a1] += s[a2, a1] * s[b2, b1] * f * dx[0] * dx[1]
+    assert _rel(L, ref) < 1e-13
+
+
+def test_bond_dense_operator_spectrum(oracle):
+    """Assemble the operator on a tiny body: symmetric, negative semi-definite,
+    null space = the 3 rigid motions of a connected 2D body."""
+    shape = (10, 10)
+    chi = inputs.box_mask(shape, (2, 2), (8, 8))
+    delta = 2.0
+    alpha = oracle.alpha_bond(2, 1.0, delta)
+    idx = np.flatnonzero(chi)
+    n = len(idx)
+    Nn = chi.size
+    Amat = np.zeros((2 * n, 2 * n))
+    for c in range(2):
+        for jj, p in enumerate(idx):
+            e = np.zeros((2, Nn))
+            e[c, p] = 1.0
+            L = oracle.force_bond(e.reshape((2,) + shape), chi, 1.0, delta, alpha).reshape(2, Nn)
+            Amat[:, c * n + jj] = np.concatenate([L[0, idx], L[1, idx]])
+    assert np.max(np.abs(Amat - Amat.T)) < 1e-14
+    ev = np.linalg.eigvalsh(Amat)
+    assert ev.max() < 1e-12
+    assert int(np.sum(np.abs(ev) < 1e-10)) == 3
+
+
+def test_energy_identity(oracle):
+    """Σ_x W(x) = -Σ_x u.L(x) with W of Eq. 47 and the same lambda (R9)."""
+    shape = (30, 26)
+    chi = _blob(shape, 4)
+    g = inputs.rng(21)
+    lam = (g.random(shape) < 0.9).astype(np.uint8)
+    u = g.normal(size=(2,) + shape)
+    delta = 3.0
+    alpha = oracle.alpha_bond(2, 1.0, delta)
+    W = oracle.energy_bond(u, chi, 1.0, delta, alpha, lam=lam)
+    L = oracle.force_bond(u, chi, 1.0, delta, alpha, s=lam.astype(float))
+    assert abs(W.sum() + np.sum(u * L)) < 1e-12 * W.sum()
+
+
+def test_damage_counts_brute_force(oracle):
+    shape = (16, 18)
+    g = inputs.rng(8)
+    chi = _blob(shape, 6)
+    lam = chi.copy()
+    lam[g.random(shape) < 0.15] = 0
+    delta = 3.0
+    nb, beta, d = oracle.damage(chi, lam, 1.0, delta)
+    off, _ = oracle.horizon(2, 1.0, delta)
+    n2, n1 = shape
+    for a2 in range(n2):
+        for a1 in range(n1):
+            b = k = 0
+            if chi[a2, a1]:
+                for o in off:
+                    q2, q1 = (a2 + o[1]) % n2, (a1 + o[0]) % n1
+                    if chi[q2, q1]:
+                        b += 1
+                        k += int(not (lam[a2, a1] and lam[q2, q1]))
+            assert beta[a2, a1] == b and nb[a2, a1] == k
+    nb0, _, d0 = oracle.damage(chi, chi, 1.0, delta)
+    assert nb0.max() == 0 and d0.max() == 0.0
+
+
+# --------------------------------------------------------------------------
+# State-based solid
+# --------------------------------------------------------------------------
+
+def test_lps_rigid_affine_and_dilatation(oracle):
+    shape = (20, 20, 20)
+    delta = 2.0
+    chi = inputs.box_mask(shape, (3, 3, 3), (17, 17, 17))
+    ka, cb, m0 = oracle.lps_constants(1.0, 0.4, 1.0, delta)
+    x = inputs.coords(shape)
+    t = np.stack([np.full(shape, 0.1 * (i + 1)) for i in range(3)])
+    assert np.max(np.abs(oracle.force_lps(t, chi, 1.0, delta, ka, cb))) < 1e-13
+    Wm = np.array([[0, 0.01, -0.02], [-0.01, 0, 0.03], [0.02, -0.03, 0]])
+    rot = np.stack([sum(Wm[i, j] * x[j] for j in range(3)) for i in range(3)])
+    assert np.max(np.abs(oracle.force_lps(rot, chi, 1.0, delta, ka, cb))) < 1e-13
+    s = 1e-3
+    iso = np.stack([s * x[i] for i in range(3)])
+    L, th, m = oracle.force_lps(iso, chi, 1.0, delta, ka, cb, return_aux=True)
+    inner1 = inputs.box_mask(shape, (5, 5, 5), (15, 15, 15)).astype(bool)  # delta interior
+    inner2 = inputs.box_mask(shape, (7, 7, 7), (13, 13, 13)).astype(bool)  # 2 delta interior
+    assert np.allclose(th[inner1], 3 * s, rtol=1e-12)
+    assert np.allclose(m[inner1], m0, rtol=1e-12)
+    ua, _, _ = inputs.affine_field(shape, 1.0, 1e-3, 5)
+    La = oracle.force_lps(ua, chi, 1.0, delta, ka, cb)
+    assert np.max(np.abs(La[:, inner2])) < 1e-15
+    assert np.max(np.abs(La[:, ~inner1 & chi.astype(bool)])) > 1e-6
+
+
+def test_lps_reduces_to_bond_at_quarter_poisson(oracle):
+    """At nu = 1/4, 3 kappa - 5 mu = 0 and the state-based force equals the bond
+    form with constant 30 mu / m0 (Eq. 37)."""
+    shape = (12, 12, 12)
+    delta = 2.0
+    chi = _blob(shape, 3)
+    ka, cb, _ = oracle.lps_constants(1.0, 0.25, 1.0, delta)
+    assert abs(ka) < 1e-15
+    u = inputs.rng(4).normal(size=(3,) + shape)
+    L1 = oracle.force_lps(u, chi, 1.0, delta, ka, cb)
+    L2 = oracle.force_bond(u, chi, 1.0, delta, cb)
+    assert _rel(L1, L2) < 1e-13
+    # and cb equals the 3D bond constant of classical calibration at nu = 1/4
+    # in the continuum limit (m0 -> 4 pi delta^4 / 4 = pi delta^4 for omega = 1/|xi|)
+    E = 1.0
+    mu = E / 2.5
+    assert abs(30 * mu / (math.pi * delta ** 4) / oracle.alpha_bond(3, E, delta) - 1) < 1e-12
+
+
+def test_lps_reciprocity(oracle):
+    shape = (11, 12, 13)
+    delta = 2.0
+    chi = _blob(shape, 7)
+    ka, cb, _ = oracle.lps_constants(1.0, 0.4, 1.0, delta)
+    g = inputs.rng(3)
+    u = g.normal(size=(3,) + shape)
+    v = g.normal(size=(3,) + shape)
+    a = float(np.sum(v * oracle.force_lps(u, chi, 1.0, delta, ka, cb)))
+    b = float(np.sum(u * oracle.force_lps(v, chi, 1.0, delta, ka, cb)))
+    assert abs(a - b) < 1e-12 * abs(a)
+    assert float(np.sum(u * oracle.force_lps(u, chi, 1.0, delta, ka, cb))) < 0
+
+
+def test_lps_long_wave_is_navier(oracle):
+    """Periodic single mode through the state-based operator: the long-wave limit
+    is Navier-Cauchy with kappa, mu of (E, nu) (here nu = 0.4)."""
+    n = 48
+    shape = (n, n, n)
+    delta = 5.0
+    E, nu = 1.0, 0.4
+    ka, cb, _ = oracle.lps_constants(E, nu, 1.0, delta)
+    chi = np.ones(shape, dtype=np.uint8)
+    i1, i2, i3 = inputs.coords(shape)
+    k = np.array([1.0, 1.0, 0.0])
+    kap = 2 * math.pi * k / n
+    ph = kap[0] * i1 + kap[1] * i2 + kap[2] * i3
+    mu = E / (2 * (1 + nu))
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    Mn = mu * kap.dot(kap) * np.eye(3) + (lam + mu) * np.outer(kap, kap)
+    for a in (np.array([1.0, 0, 0]), np.array([0, 0, 1.0])):
+        u = np.stack([a[i] * np.cos(ph) for i in range(3)])
+        L = oracle.force_lps(u, chi, 1.0, delta, ka, cb)
+        ref = -np.einsum("ij,j...->i...", Mn, u)
+        assert _rel(L, ref) < 0.08
+
+
+# --------------------------------------------------------------------------
+# Gradient, dynamics, statics
+# --------------------------------------------------------------------------
+
+def test_grad_s_matches_finite_differences(oracle):
+    shape = (14, 15)
+    chi = _blob(shape, 2)
+    g = inputs.rng(31)
+    s = 0.8 + 0.4 * g.random(shape)
+    u = g.normal(size=(2,) + shape)
+    p = g.normal(size=(2,) + shape)
+    delta = 2.5
+    alpha = oracle.alpha_bond(2, 1.0, delta)
+    gs = oracle.force_bond_grad_s(u, p, chi, 1.0, delta, alpha, s=s)
+    h = 1e-6
+    for _ in range(5):
+        dirn = g.normal(size=shape)
+        jp = np.sum(p * oracle.force_bond(u, chi, 1.0, delta, alpha, s=s + h * dirn))
+        jm = np.sum(p * oracle.force_bond(u, chi, 1.0, delta, alpha, s=s - h * dirn))
+        fd = (jp - jm) / (2 * h)
+        an = float(np.sum(gs * dirn))
+        assert abs(fd - an) < 1e-7 * max(1.0, abs(an))
+
+
+def test_verlet_energy_and_reversibility(oracle):
+    shape = (24, 24)
+    chi = inputs.box_mask(shape, (4, 4), (20, 20))
+    delta, rho = 3.0, 1.0
+    alpha = oracle.alpha_bond(2, 1.0, delta)
+    co = np.stack([chi, chi])
+    u0 = inputs.sine_modes(shape, 3, 1e-3, 2, 5) * chi
+    v0 = np.zeros_like(u0)
+    b = np.zeros_like(u0)
+    lam = chi.copy()
+    M = oracle.symbol_bond(shape, 1.0, delta, alpha, (12, 12))
+    dt = 0.2 * 2 * math.sqrt(rho / np.linalg.eigvalsh(M).max())
+
+    def energy(u, v):
+        W = oracle.energy_bond(u, chi, 1.0, delta, alpha)
+        return 0.5 * rho * np.sum(v * v) + 0.5 * W.sum()
+
+    e0 = energy(u0, v0)
+    # energy error of velocity-Verlet is O(dt^2): halving dt over the same
+    # time span divides it by ~4; a wrong energy normalisation would not
+    errs = []
+    for k in (1, 2):
+        uk, vk, _, fl = oracle.verlet_damage(u0, v0, lam, chi, co, b, b, 1.0, delta, alpha,
+                                             rho, dt / k, 1e300, 40 * k)
+        assert fl == 0
+        errs.append(abs(energy(uk, vk) / e0 - 1))
+    assert 3.0 < errs[0] / errs[1] < 5.0 and errs[1] < 5e-3
+    u1, v1, _, _ = oracle.verlet_damage(u0, v0, lam, chi, co, b, b, 1.0, delta, alpha,
+                                        rho, dt, 1e300, 40)
+    u2, v2, _, _ = oracle.verlet_damage(u1, -v1, lam, chi, co, b, b, 1.0, delta, alpha,
+                                        rho, dt, 1e300, 40)
+    assert np.max(np.abs(u2 - u0)) < 1e-12 * np.max(np.abs(u0)) * 1e3
+    assert np.max(np.abs(v2 + v0)) < 1e-9
+
+
+def test_verlet_breaks_only_above_wc(oracle):
+    shape = (20, 20)
+    chi = inputs.box_mask(shape, (3, 3), (17, 17))
+    delta = 3.0
+    alpha = oracle.alpha_bond(2, 1.0, delta)
+    u = inputs.rng(3).normal(size=(2,) + shape) * 1e-3 * chi
+    W = oracle.energy_bond(u, chi, 1.0, delta, alpha)
+    wc = float(np.median(W[chi.astype(bool)]))
+    z = np.zeros_like(u)
+    _, _, lam, fl = oracle.verlet_damage(u, z, chi, chi, np.stack([chi, chi]), z, z, 1.0,
+                                         delta, alpha, 1.0, 1e-3, wc, 1)
+    assert np.array_equal(lam.astype(bool), chi.astype(bool) & (W <= wc))
+    assert fl == int(np.sum(chi.astype(bool) & (W > wc)))
+
+
+def test_cg_static_residual(oracle):
+    shape = (24, 24)
+    cfgm = inputs.box_mask(shape, (3, 3), (21, 21))
+    x1, _ = inputs.coords(shape)
+    co = cfgm.copy()
+    co[(x1 >= 3) & (x1 < 6)] = 0
+    b = np.zeros((2,) + shape)
+    b[0][(x1 >= 18) & (x1 < 21) & (cfgm == 1)] = 1e-3 / 3
+    delta = 3.0
+    alpha = oracle.alpha_bond(2, 1.0, delta)
+    u, it, rel = oracle.cg_static(cfgm, np.stack([co, co]), b, np.zeros_like(b), 1.0, delta,
+                                  ("bond", alpha), rtol=1e-12)
+    assert rel < 1e-11 and it > 10
+    # the body is pulled along +x1 at the loaded end
+    assert u[0][12, 19] > 0
