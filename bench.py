@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Benchmark of the FCBM-EC hot path on one GB300 (or N replicas).
+
+Workload (the 3D elastostatic configuration): 128^3 periodic box, horizon
+delta = 3 grid spacings, body = cube [3, 125)^3 minus a centred ball of radius
+32, linearized state-based solid with E = 1, nu = 0.25, clamp (chi_Omega = 0,
+w = 0) on the three node layers at the x1-low face, body-force layer
+b1 = sigma/delta (sigma = 1e-3) on the three layers at the x1-high face.
+One step = one complete static solve from u = 0 to a relative FP64 residual of
+1e-8: FP32 FFT-convolution CG with FP64 inner products inside FP64 iterative
+refinement (pd_solve_static).
+
+Metric: force evaluations x nodes per second (each CG iteration and each FP64
+residual is one evaluation of the PD operator on all 128^3 nodes), plus the
+solve time and the HBM roofline fraction of the dominant FFT pass.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+Under torchrun (N > 1) every rank solves its own copy (replicas: the problem
+does not shard) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PD force evals x nodes/sec (FCBM-EC static solve to 1e-8 rel. residual)"
+UNIT = "node-evals/s"
+N_GRID = 128
+DELTA = 3.0
+RTOL = 1e-8
+
+
+def workload_config(n):
+    return {
+        "workload": f"3D linearized state-based PD elastostatic solve, {n}^3 box, cube minus centred ball "
+                    f"r={n // 4}, delta=3, E=1, nu=0.25, clamp on x1-low face via EC, body-force layer "
+                    f"b1=sigma/delta (sigma=1e-3) on x1-high face, FP32 FFT CG + FP64 refinement to 1e-8",
+        "grid": [n, n, n],
+        "delta_cells": DELTA,
+        "rtol": RTOL,
+        "l2": "working set > L2 (solver vectors, spectra, boundary field ~0.4 GB) and 256 MB L2 flush "
+              "between steps",
+    }
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    QUERY = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = os.path.join("/tmp", f"pd_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                if self.uuid and parts[1] != self.uuid:
+                    continue
+                rows.append(parts)
+        if not rows:
+            return None
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def pass_bytes(kind, d=3, nc=6, F=3):
+    """Algorithmic bytes per node of one launch of each FP32 pass of the bond/LPS
+    (nu = 1/4) force pipeline; a packed half spectrum costs 4 bytes per node."""
+    return {
+        "rows_fwd": 4 * d + 1 + 4 * F,          # read u_j, chi; write F spectra
+        "cols_x2": 2 * 4 * F,                   # read + write F spectra
+        "last_axis": 2 * 4 * F + nc * 4 / 8.0,  # read + write F spectra; folded kernel table (~N/8 modes)
+        "rows_inv": 4 * F + 4 * d + 1 + 4 * nc + 4 * d,  # read spectra, u, chi, G; write L
+    }[kind]
+
+
+def run_native(args, rank, world):
+    import torch
+
+    from paper_2105_06055_gb300 import build as pd_build
+    from paper_2105_06055_gb300 import inputs, pd
+
+    if rank == 0 or world == 1:
+        pd_build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    n = args.n
+    cfg = inputs.cube_with_cavity(n=n)
+    shape = cfg["shape"]
+    N = n ** 3
+    prob = pd.Problem(shape=shape, delta=DELTA, model=pd.PD_LIN_STATE, E=1.0, nu=0.25, fp64=False)
+    chi = torch.tensor(cfg["chi"], device=dev)
+    chi_om = torch.tensor(cfg["chi_omega"], device=dev)
+    plan = pd.Plan(prob, chi, chi_om)
+    b = torch.tensor(cfg["b"], dtype=torch.float64, device=dev)
+    u = torch.zeros((3,) + shape, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def one_solve():
+        u.zero_()
+        it, rel, st = plan.solve_static(u, b, None, rtol=RTOL, max_iter=50000)
+        if st != 0:
+            raise RuntimeError(f"solve did not converge: rel {rel}")
+        return it, rel
+
+    for _ in range(args.warmup):
+        one_solve()
+    torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        if not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid)
+    plan.profile(True)
+    launches0 = plan.launch_count
+    times = []
+    its = []
+    rels = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        it, rel = one_solve()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        its.append(it)
+        rels.append(rel)
+    clocks = sampler.stop()
+    launches = plan.launch_count - launches0
+    prof = plan.profile_read()
+    plan.profile(False)
+    evals_per_step = prof["rows_inv"][1] / args.steps  # one inverse row pass per force evaluation
+    total_ms = sum(times)
+    t_max = total_ms
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * evals_per_step * args.steps * N / (t_max * 1e-3)
+
+    # dominant pass and its roofline
+    peak, peak_kind = load_peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_n) = dom
+    bytes_per_launch = pass_bytes(dom_name) * N
+    achieved = bytes_per_launch / (dom_ms / dom_n * 1e-3) / 1e9
+    t_eval_ms = total_ms / (evals_per_step * args.steps)
+    m2 = 25.0 * N / (t_eval_ms * 1e-3) / (peak * 1e9)
+
+    # end to end through the public API with host buffers
+    b_host = torch.tensor(cfg["b"], dtype=torch.float64).pin_memory()
+    u_host = torch.empty((3,) + shape, dtype=torch.float64).pin_memory()
+    e2e_times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.copy_(b_host, non_blocking=True)
+        one_solve()
+        u_host.copy_(u, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_value = world * evals_per_step * N / statistics.mean(e2e_times)
+
+    result = None
+    if rank == 0:
+        result = {
+            "metric": METRIC,
+            "value": value,
+            "unit": UNIT,
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": t_max / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32 FFT convolutions + f64 residuals/inner products",
+            "data": "synthetic (seeded geometry and load, no dataset)",
+            "config": dict(workload_config(n), parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+            "static_solve_ms": t_max / args.steps,
+            "cg_iterations_per_solve": statistics.mean(its),
+            "force_evals_per_solve": evals_per_step,
+            "final_rel_residual": max(rels),
+            "ms_per_force_eval": t_eval_ms,
+            "m2_end_to_end_hbm_frac": m2,
+            "passes_ms_per_launch": {k: (v[0] / v[1] if v[1] else None) for k, v in prof.items()},
+            "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
+                         "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "algorithmic_bytes_per_launch": bytes_per_launch},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(b_host.numel() * 8),
+                    "d2h_bytes_per_step": int(u_host.numel() * 8)},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+    plan.close()
+    return result, cfg
+
+
+def oracle_sample(n, nevals, threads=None):
+    """Time the FP64 oracle's state-based force on the same workload (host cores)."""
+    import numpy as np
+
+    import oracle
+    from paper_2105_06055_gb300 import inputs
+
+    oracle.build()
+    if threads:
+        oracle.set_threads(threads)
+    cfg = inputs.cube_with_cavity(n=n)
+    ka, cb, _ = oracle.lps_constants(1.0, 0.25, 1.0, DELTA)
+    u = inputs.sine_modes(cfg["shape"], 4, 1e-3, 3, 5)
+    t0 = time.perf_counter()
+    for _ in range(nevals):
+        oracle.force_lps(u, cfg["chi"], 1.0, DELTA, ka, cb)
+    dt = time.perf_counter() - t0
+    N = n ** 3
+    return nevals * N / dt, oracle.num_threads(), dt
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--n", type=int, default=N_GRID)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+
+    if args.impl == "reference":
+        # the reference arm is the FP64 oracle on the host cores; rank 0 only
+        if rank != 0:
+            return
+        value, cores, dt = oracle_sample(args.n, 1)  # warm-up (page-in, thread spin-up)
+        samples = []
+        for _ in range(args.warmup - 1 if args.warmup > 1 else 0):
+            oracle_sample(args.n, 1)
+        t_all = 0.0
+        for _ in range(args.steps):
+            v, cores, dt = oracle_sample(args.n, 1)
+            samples.append(v)
+            t_all += dt
+        value = statistics.mean(samples)
+        out = {
+            "impl": "reference",
+            "metric": METRIC,
+            "value": value,
+            "unit": UNIT,
+            "n_gpus": args.gpus,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_all / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f64",
+            "data": "synthetic (seeded geometry and load, no dataset)",
+            "config": workload_config(args.n),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"one FP64 direct-sum state-based force evaluation of the {args.n}^3 "
+                                       f"workload per step (the solve's unit of work)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(out))
+        return
+
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    result, cfg = run_native(args, rank, world)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            v, cores, dt = oracle_sample(args.n, 2)
+            result["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                      "sample": f"2 FP64 direct-sum state-based force evaluations of the "
+                                                f"{args.n}^3 workload ({dt:.1f} s)"}
+        print(json.dumps(result))
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,229 @@
+/*
+ * pd.h -- C ABI of the GB300 FCBM-EC peridynamics library.
+ *
+ * The library evaluates the peridynamic (PD) internal-force operator of the
+ * fast convolution-based method with embedded constraint (FCBM-EC;
+ * Jafarzadeh, Mousavi, Larios, Bobaru, arXiv 2105.06055) as FFT convolutions
+ * on one NVIDIA GB300 (sm_103a), and builds the paper's dynamic (velocity
+ * Verlet, §4.2.3) and static (conjugate gradient, §4.3) drivers on it.
+ *
+ * Conventions shared by every entry point
+ *   Grid (Eq. 52): n[0] x n[1] x n[2] nodes (n[2] = 1 in 2D), spacing dx[k],
+ *     node (i1,i2,i3) at x = (i1 dx1, i2 dx2, i3 dx3), periodic box (§4.1).
+ *     Supported lengths: powers of two, 32 <= n[0] <= 2048, 16 <= n[1], n[2] <= 1024.
+ *   Fields: device arrays, component-major and x1 fastest,
+ *     f[c][i3][i2][i1]; vector fields have d = dim components; N = n0 n1 n2.
+ *     Floating-point fields are float (problem.fp64 == 0) or double
+ *     (problem.fp64 == 1). Masks are uint8 0/1.
+ *   Ownership: the caller owns every field buffer it passes; the library
+ *     owns the plan and all of its workspace, which is allocated in
+ *     pd_plan_create only. Later calls allocate nothing.
+ *   Streams: every call enqueues its work on `stream` (a cudaStream_t, NULL
+ *     for the legacy default stream) and returns without synchronising,
+ *     except where a call says it reads back a result. A plan may be used
+ *     by one stream at a time.
+ *   Errors: no exception crosses the ABI. A non-PD_OK status means nothing
+ *     was enqueued (argument errors) or a CUDA call failed (PD_ERR_CUDA);
+ *     pd_status_string gives a message, pd_last_error_detail more context.
+ *
+ * Model constants (omega(|xi|) = 1/|xi| throughout, §5.1, §5.2):
+ *   PD_LIN_BOND, 2D: C_ij(xi) = alpha omega xi_i xi_j / |xi|^2 (Eq. 17),
+ *     alpha = 9E/(pi delta^3), plane stress, nu = 1/3 (§5.2).
+ *   PD_LIN_BOND, 3D: alpha = 12E/(pi delta^4), nu = 1/4 (energy calibration of
+ *     an isotropic stretch; the paper prints only the 2D value).
+ *   PD_LIN_STATE (3D): linearized state-based solid (Eq. 33-39, 92-97) with
+ *     kappa = E/(3(1-2nu)), mu = E/(2(1+nu)), bulk m0 = Σ_H omega|xi|^2 dV
+ *     in the kernels (Eq. 37) and the nodal m(x) of Eq. 94 in the dilatation.
+ */
+#ifndef PD_H
+#define PD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PD_OK = 0,
+    PD_ERR_ARG = -1,            /* invalid argument (null pointer, bad enum, bad mask) */
+    PD_ERR_SIZE = -2,           /* unsupported grid size or horizon                    */
+    PD_ERR_NOMEM = -3,          /* device allocation failed in pd_plan_create          */
+    PD_ERR_CUDA = -4,           /* a CUDA runtime call or kernel launch failed         */
+    PD_ERR_NOT_CONVERGED = -5,  /* iterative solve hit max_iter before rtol            */
+    PD_ERR_TIMEOUT = -6,        /* a bounded device-side wait gave up                  */
+    PD_ERR_NONFINITE = -7       /* a NaN or Inf appeared in a reduction                */
+} pd_status;
+
+typedef enum {
+    PD_LIN_BOND = 0,   /* linearized bond-based solid, Eq. 17-18            */
+    PD_LIN_STATE = 1   /* linearized state-based (LPS) solid, Eq. 33-39, 3D */
+} pd_model;
+
+typedef struct {
+    int dim;         /* 2 or 3                                                    */
+    int n[3];        /* grid nodes per axis (Eq. 52); n[2] = 1 in 2D              */
+    double dx[3];    /* grid spacing per axis (dx[2] ignored in 2D)               */
+    double delta;    /* horizon radius; bonds are 0 < |xi| <= delta (Eq. 48)      */
+    int model;       /* pd_model                                                  */
+    double E;        /* Young's modulus                                           */
+    double nu;       /* Poisson ratio (PD_LIN_STATE only)                         */
+    double rho;      /* mass density (Eq. 1), used by pd_step_verlet              */
+    double Wc;       /* critical strain energy density (Eq. 40, 63); <= 0: no damage */
+    int fp64;        /* 0: FP32 fields and FFTs; 1: FP64 fields and FFTs          */
+} pd_problem;
+
+typedef struct pd_plan pd_plan;  /* opaque; owns spectra, masks and workspace */
+
+/*
+ * pd_plan_create -- validate a problem, copy its masks and precompute every
+ * plan-time quantity (§4.1.1, §4.2.2):
+ *   - the horizon offsets and the kernel spectrum K^_ij(k) = dV Σ_H C_ij(xi)
+ *     e^{-2 pi i k.xi/n} in FP64 (Eq. 56-57; real and even), kept as the
+ *     difference M^ = (K^(k) - K^(0)) / N in FP32 and FP64;
+ *   - the boundary field G_ij(x) = dV Σ_H C_ij(xi) chi(x+xi) - P_ij chi(x)
+ *     (the (C*chi_B) u_j term of Eq. 100 minus P u, zero in the delta-interior);
+ *   - state-based: m(x) (Eq. 94, 97) and q_i(x) = Σ_H g_i(xi) dV chi(x+xi) with
+ *     g_i = omega xi_i, and the spectrum of g_i.
+ * chi_B:     device, N bytes, 1 inside the body B (Eq. 73). The body must stay
+ *            at least delta from the box faces (§4.2.2), else PD_ERR_ARG.
+ * chi_Omega: device, d x N bytes (Eq. 74, one mask per component), or NULL
+ *            for chi_Omega_i = chi_B. chi_Omega must be 0 where chi_B is 0.
+ * stream:    stream for the plan-time kernels; pd_plan_create synchronises it.
+ * out:       receives the plan; release it with pd_plan_destroy.
+ * The masks are copied; the caller may free its buffers afterwards.
+ */
+pd_status pd_plan_create(const pd_problem *problem, const uint8_t *chi_B,
+                         const uint8_t *chi_Omega, void *stream, pd_plan **out);
+
+/* Release a plan and all of its device memory. NULL is a no-op. */
+void pd_plan_destroy(pd_plan *plan);
+
+/*
+ * pd_kernel_spectrum -- write the FP64 kernel spectrum (Eq. 56-57)
+ *   K^_ij(k) = dV Σ_{xi in H} C_ij(xi) cos(2 pi Σ_a k_a o_a / n_a)
+ * for the half-spectrum k1 in [0, n0/2], k2 in [0, n1), k3 in [0, n2), as
+ * d(d+1)/2 real arrays in the order 11,22,33,12,13,23 (2D: 11,22,12), each
+ * [k3][k2][k1] with k1 fastest. out: device, d(d+1)/2 x (n0/2+1) n1 n2 doubles.
+ * K^(0) is the tensor P_ij of Eq. 56.
+ */
+pd_status pd_kernel_spectrum(pd_plan *plan, double *out, void *stream);
+
+/*
+ * pd_force -- one FCBM-EC force evaluation (Eq. 57-58 with the chi_B cut of
+ * Eq. 75 and the node weight of Eq. 100):
+ *   bond:  L_i = v [ C_ij * (v u_j) - (C_ij * v) u_j ] dV,  v = chi_B s
+ *   state: L_i = chi [ -th (a_i*chi) - a_i*(chi th) + C_ij*(chi u_j)
+ *                      - (C_ij*chi) u_j ] dV           (Eq. 92, 95-97)
+ * computed as FFT convolutions on the device:
+ *   L_i = v [ IFFT( M^_ij FFT(v u_j) ) - G_ij u_j ]  (algebraically identical).
+ * u:  device, d x N (input displacement).
+ * s:  device, N node weight (bond model only), or NULL for s = 1. With s the
+ *     G field is formed for v = chi_B s inside the call (extra convolutions).
+ * L:  device, d x N (output force density; 0 where chi_B = 0).
+ * W:  device, N, or NULL: strain energy density of Eq. 47 / 102 with bond
+ *     factor v v' (bond model only).
+ * u and L must not overlap.
+ */
+pd_status pd_force(pd_plan *plan, const void *u, const void *s, void *L, void *W, void *stream);
+
+/*
+ * pd_step_verlet -- nsteps of velocity Verlet with embedded constraint and the
+ * energy-based bond breaking of §3.4 (bond model):
+ *   a^n       = L(u^n, lam^n) + b
+ *   u^{n+1}   = chi_O { u^n + dt [v^n + dt/(2 rho) a^n] } + (1 - chi_O) w   (Eq. 83)
+ *   lam^{n+1} = lam^n [ W(u^n, lam^n) <= Wc ]  (Eq. 63; irreversible)
+ *   v^{n+1}   = chi_O { v^n + dt/(2 rho) (a^n + a^{n+1}) }                  (Eq. 84)
+ * with L and W of Eq. 101-102 (node weight chi_B lam). Wc <= 0 disables
+ * breaking (lam stays as given).
+ * u, v:   device, d x N, updated in place.
+ * lambda: device, N bytes (integrity index, Eq. 43), updated in place; NULL
+ *         means lam = 1 and no breaking.
+ * b, w:   device, d x N: body force density and Gamma values (Eq. 78); w may
+ *         be NULL (w = 0).
+ * n_broken_out: host pointer or NULL; receives the number of nodes whose lam
+ *         went from 1 to 0 during the call (this synchronises the stream).
+ */
+pd_status pd_step_verlet(pd_plan *plan, void *u, void *v, uint8_t *lambda, const void *b,
+                         const void *w, double dt, int nsteps, int64_t *n_broken_out,
+                         void *stream);
+
+/*
+ * pd_solve_static -- solve the FCBM-EC static problem (Eq. 85-89)
+ *   chi_O (L(u) + b) = 0 on Omega,  u = w on Gamma,
+ * by conjugate gradient (§4.3, ref. [50]) on A e = chi_O (b + L(w)),
+ * A e = -chi_O L(chi_O e), which is symmetric positive definite on Omega.
+ * FP32 plan: the inner CG runs on FP32 FFT convolutions with FP64 inner
+ * products; an outer iterative refinement recomputes the residual
+ * r = chi_O (b + L(u)) with the FP64 operator and stops when
+ * ||r||_2 <= rtol ||chi_O b||_2. FP64 plan: plain CG on the FP64 operator.
+ * u:  device, d x N, FP64 regardless of the plan's precision; in: initial
+ *     guess (values on Gamma are replaced by w), out: solution.
+ * b, w: device, d x N, FP64 (w may be NULL for w = 0).
+ * max_iter: cap on the total number of CG iterations.
+ * iters_out, relres_out: host pointers (may be NULL): CG iterations done and
+ *     the final FP64 relative residual. The call synchronises the stream.
+ * Returns PD_ERR_NOT_CONVERGED if rtol was not reached.
+ */
+pd_status pd_solve_static(pd_plan *plan, double *u, const double *b, const double *w,
+                          double rtol, int max_iter, int *iters_out, double *relres_out,
+                          void *stream);
+
+/*
+ * pd_force_adjoint -- reverse-mode derivative of pd_force (bond model). The
+ * paper has no adjoint; this differentiates the quadrature of Eq. 17-18, 75
+ * with bond factor s s'. Given gL = dJ/dL for some scalar J:
+ *   gu_i(y) = (dL/du)^T gL = L[gL](y)   (the operator is symmetric, so this is
+ *             the same FFT convolution applied to gL)
+ *   gs(y)   = chi(y) Σ_xi chi' s' C_ij(xi) (gL_i(y) - gL_i(y+xi)) (u_j(y+xi) - u_j(y)) dV
+ *           = chi { gL_i [C_ij*(v u_j)] - gL_i u_j [C_ij*v] - Σ_ij C_ij*(v gL_i u_j)
+ *                   + u_j [C_ij*(v gL_i)] } dV,   v = chi s
+ * u, s, gL: device inputs (s may be NULL for s = 1); gu: device d x N output
+ * (may be NULL); gs: device N output (may be NULL).
+ */
+pd_status pd_force_adjoint(pd_plan *plan, const void *u, const void *s, const void *gL,
+                           void *gu, void *gs, void *stream);
+
+/*
+ * pd_damage -- broken-bond counts and damage index (Eq. 12, 44, 48-49, 65):
+ *   beta(x) = chi Σ_H chi',  nb(x) = chi Σ_H chi' (1 - lam lam'),  d = nb / beta.
+ * Counts are exact integers (direct integer sums over the horizon).
+ * lambda: device N bytes. nb: device N int32 or NULL. d: device N float/double
+ * (plan precision) or NULL.
+ */
+pd_status pd_damage(pd_plan *plan, const uint8_t *lambda, int32_t *nb, void *d, void *stream);
+
+/* Bytes of device memory owned by the plan. */
+int64_t pd_plan_workspace_bytes(const pd_plan *plan);
+
+/* Largest stable velocity-Verlet step for the plan's periodic operator:
+ * 2 sqrt(rho / max_k max-eig M(k)), M(k) = K^(0) - K^(k) (host FP64). */
+double pd_stable_dt(const pd_plan *plan);
+
+/* Number of kernel launches the library has enqueued since the plan was
+ * created (for launch accounting). */
+int64_t pd_plan_launch_count(const pd_plan *plan);
+
+/*
+ * Per-pass timing (diagnostics). With profiling enabled, every FFT-pass launch
+ * of the plan is bracketed by two CUDA events recorded on the launching stream
+ * (the events are created in pd_plan_create); pd_plan_profile_read returns the
+ * summed event time and the launch count of one pass kind since the last
+ * pd_plan_profile call:
+ *   0 row pass, forward (prologue + x1 transform)
+ *   1 column pass along x2 (3D), forward or inverse
+ *   2 last-axis pass (forward transform, spectral combine, inverse transform)
+ *   3 row pass, inverse (x1 transform + epilogue)
+ * Reading synchronises on the recorded events. Enabling resets the counters.
+ */
+pd_status pd_plan_profile(pd_plan *plan, int enable);
+pd_status pd_plan_profile_read(pd_plan *plan, int kind, double *ms_total, int64_t *launches);
+
+const char *pd_status_string(pd_status status);
+const char *pd_last_error_detail(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PD_H */

@@ -1,0 +1,25 @@
+// pd_force entry point; the pipelines are instantiated in pd_force_f32.cu / pd_force_f64.cu.
+#include "pd_ops.cuh"
+
+namespace pd {
+template <typename T>
+pd_status force_plain(pd_plan *p, const T *u, const T *s, T *L, T *W, cudaStream_t st);
+}  // namespace pd
+
+using namespace pd;
+
+extern "C" pd_status pd_force(pd_plan *p, const void *u, const void *s, void *L, void *W, void *stream)
+{
+    if (!p || !u || !L) {
+        set_error("pd_force: null plan, u or L");
+        return PD_ERR_ARG;
+    }
+    if (u == L) {
+        set_error("pd_force: u and L must not overlap");
+        return PD_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (p->prob.fp64)
+        return force_plain<double>(p, (const double *)u, (const double *)s, (double *)L, (double *)W, st);
+    return force_plain<float>(p, (const float *)u, (const float *)s, (float *)L, (float *)W, st);
+}

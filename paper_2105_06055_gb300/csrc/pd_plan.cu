@@ -1,0 +1,693 @@
+// Plan creation: validation, horizon, kernel spectra, boundary fields, twiddles.
+//
+// Everything here runs once per plan (§4.1.1: "P can be computed once and
+// stored as a preprocessing step"); all device memory of the library is
+// allocated here so that later calls allocate nothing.
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <vector>
+
+#include "pd_plan.cuh"
+
+namespace pd {
+
+static thread_local char g_err[512];
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+pd_status set_smem_attr(const void *func, size_t smem)
+{
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) {
+            set_error("cudaFuncSetAttribute(%zu bytes): %s", smem, cudaGetErrorString(e));
+            return PD_ERR_CUDA;
+        }
+    }
+    return PD_OK;
+}
+
+pd_status prof_harvest(pd_plan *p)
+{
+    if (p->ev_used == 0) return PD_OK;
+    PD_CUDA_TRY(cudaEventSynchronize(p->ev[2 * p->ev_used - 1]));
+    for (int i = 0; i < p->ev_used; ++i) {
+        float ms = 0.f;
+        PD_CUDA_TRY(cudaEventElapsedTime(&ms, p->ev[2 * i], p->ev[2 * i + 1]));
+        p->prof_ms[p->ev_kind[i]] += ms;
+        p->prof_n[p->ev_kind[i]]++;
+    }
+    p->ev_used = 0;
+    return PD_OK;
+}
+
+template <typename T>
+Model<T> model_view(const pd_plan *p)
+{
+    Model<T> m;
+    m.dim = p->dim;
+    m.n1 = p->n1;
+    m.n2 = p->n2;
+    m.n3 = p->n3;
+    m.h = p->h;
+    m.ky_half = p->n2 / 2;
+    m.kz_half = p->n3 / 2;
+    m.N = p->N;
+    m.nrows = p->nrows;
+    m.fold_sz = p->fold_sz;
+    m.chi = p->chi;
+    m.chi_om = p->chi_om;
+    if constexpr (sizeof(T) == 8) {
+        m.mhat = (const T *)p->mhat64;
+        m.ghat = (const T *)p->ghat64;
+        m.G = (const T *)p->G64;
+        m.qt = (const T *)p->qt64;
+        m.m3inv = (const T *)p->m3inv64;
+    } else {
+        m.mhat = (const T *)p->mhat32;
+        m.ghat = (const T *)p->ghat32;
+        m.G = (const T *)p->G32;
+        m.qt = (const T *)p->qt32;
+        m.m3inv = (const T *)p->m3inv32;
+    }
+    m.ka = (T)p->ka;
+    return m;
+}
+template Model<float> model_view<float>(const pd_plan *);
+template Model<double> model_view<double>(const pd_plan *);
+
+// ---------------------------------------------------------------------------
+// Plan-time kernels (FP64)
+// ---------------------------------------------------------------------------
+
+// Folded spectra: for kx in [0, h], ky in [0, n2/2], kz in [0, n3/2]:
+//   mhat_c(k) = (1/N) Σ_H C_c(xi) dV (cos(theta) - 1) = -(2/N) Σ C_c dV sin^2(theta/2)
+//   ghat_i(k) = (1/N) Σ_H g_i(xi) dV sin(theta)
+// theta = 2 pi Σ_a k_a o_a / n_a, reduced exactly with integer arithmetic.
+__global__ void k_fold_tables(int dim, int n1, int n2, int n3, int h, HorizonDev hz, int ncomp,
+                              double invN, double *mhat, double *ghat, int64_t fold_sz)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= fold_sz) return;
+    const int kx = (int)(t % (h + 1));
+    const int ky = (int)((t / (h + 1)) % (n2 / 2 + 1));
+    const int kz = (int)(t / ((int64_t)(h + 1) * (n2 / 2 + 1)));
+    const int nmax = max(n1, max(n2, n3));
+    const int s1 = nmax / n1, s2 = nmax / n2, s3 = nmax / n3;
+    double accm[6] = {0, 0, 0, 0, 0, 0}, accg[3] = {0, 0, 0};
+    for (int c = 0; c < hz.cnt; ++c) {
+        const int o1 = hz.off[3 * c], o2 = hz.off[3 * c + 1], o3 = hz.off[3 * c + 2];
+        long long num = (long long)kx * o1 * s1 + (long long)ky * o2 * s2 + (long long)kz * o3 * s3;
+        num %= nmax;
+        if (num < 0) num += nmax;
+        const double frac = (double)num / (double)nmax;  // theta / (2 pi) in [0, 1)
+        const double sh = sinpi(frac);                   // sin(theta / 2)
+        const double one_minus_cos = 2.0 * sh * sh;
+        for (int q = 0; q < ncomp; ++q) accm[q] -= hz.c[q * hz.cnt + c] * one_minus_cos;
+        if (ghat) {
+            const double sn = sinpi(2.0 * frac);
+            for (int i = 0; i < 3; ++i) accg[i] += hz.g[i * hz.cnt + c] * sn;
+        }
+    }
+    for (int q = 0; q < ncomp; ++q) mhat[q * fold_sz + t] = accm[q] * invN;
+    if (ghat)
+        for (int i = 0; i < 3; ++i) ghat[i * fold_sz + t] = accg[i] * invN;
+    (void)dim;
+}
+
+// Unfolded FP64 kernel spectrum K^_c(k) = Σ_H C_c(xi) dV cos(theta), k1 in [0, n1/2].
+__global__ void k_kernel_spectrum(int n1, int n2, int n3, int h, HorizonDev hz, int ncomp, double *out,
+                                  int64_t total)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const int kx = (int)(t % (h + 1));
+    const int ky = (int)((t / (h + 1)) % n2);
+    const int kz = (int)(t / ((int64_t)(h + 1) * n2));
+    const int nmax = max(n1, max(n2, n3));
+    const int s1 = nmax / n1, s2 = nmax / n2, s3 = nmax / n3;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int c = 0; c < hz.cnt; ++c) {
+        long long num = (long long)kx * hz.off[3 * c] * s1 + (long long)ky * hz.off[3 * c + 1] * s2 +
+                        (long long)kz * hz.off[3 * c + 2] * s3;
+        num %= nmax;
+        if (num < 0) num += nmax;
+        const double cs = cospi(2.0 * (double)num / (double)nmax);
+        for (int q = 0; q < ncomp; ++q) acc[q] += hz.c[q * hz.cnt + c] * cs;
+    }
+    for (int q = 0; q < ncomp; ++q) out[q * total + t] = acc[q];
+}
+
+// State-based node fields: q_i(x) = Σ_H g_i dV chi(x+xi), m(x) = chi Σ_H omega|xi|^2 dV chi(x+xi)
+// (Eq. 93-94, 96-97), stored as q_i and 3/m (0 outside the body).
+__global__ void k_state_fields(int n1, int n2, int n3, HorizonDev hz, const uint8_t *chi, double *qt,
+                               double *m3inv, int64_t N)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= N) return;
+    const int i1 = (int)(p % n1), i2 = (int)((p / n1) % n2), i3 = (int)(p / ((int64_t)n1 * n2));
+    double q[3] = {0, 0, 0}, m = 0;
+    if (chi[p]) {
+        for (int c = 0; c < hz.cnt; ++c) {
+            const int a = (i1 + hz.off[3 * c]) & (n1 - 1);
+            const int b = (i2 + hz.off[3 * c + 1]) & (n2 - 1);
+            const int e = (i3 + hz.off[3 * c + 2]) & (n3 - 1);
+            const int64_t qi = ((int64_t)e * n2 + b) * n1 + a;
+            if (!chi[qi]) continue;
+            for (int i = 0; i < 3; ++i) q[i] += hz.g[i * hz.cnt + c];
+            m += hz.w2[c];
+        }
+    }
+    for (int i = 0; i < 3; ++i) qt[i * N + p] = chi[p] ? q[i] : 0.0;
+    m3inv[p] = (chi[p] && m > 0) ? 3.0 / m : 0.0;
+}
+
+// Largest eigenvalue over the folded modes of the periodic symbol
+//   M(k) = -N mhat(k) + (3 ka / m0) (N ghat)(N ghat)^T   (state-based term only
+// when ghat is given), per-block maxima written to out[blockIdx.x].
+__global__ void k_lam_max(int dim, const double *mhat, const double *ghat, double kcoef, double Nd,
+                          int64_t fold_sz, double *out)
+{
+    __shared__ double sm[256];
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double lm = 0.0;
+    if (t < fold_sz) {
+        double M[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        if (dim == 2) {
+            M[0] = -Nd * mhat[t];
+            M[4] = -Nd * mhat[fold_sz + t];
+            M[1] = M[3] = -Nd * mhat[2 * fold_sz + t];
+        } else {
+            M[0] = -Nd * mhat[t];
+            M[4] = -Nd * mhat[fold_sz + t];
+            M[8] = -Nd * mhat[2 * fold_sz + t];
+            M[1] = M[3] = -Nd * mhat[3 * fold_sz + t];
+            M[2] = M[6] = -Nd * mhat[4 * fold_sz + t];
+            M[5] = M[7] = -Nd * mhat[5 * fold_sz + t];
+            if (ghat) {
+                double gv[3];
+                for (int i = 0; i < 3; ++i) gv[i] = Nd * ghat[i * fold_sz + t];
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) M[3 * i + j] += kcoef * gv[i] * gv[j];
+            }
+        }
+        if (dim == 2) {
+            const double a = M[0], b = M[1], d = M[4];
+            const double tr = 0.5 * (a + d), df = 0.5 * (a - d);
+            lm = tr + sqrt(df * df + b * b);
+        } else {
+            // largest eigenvalue of the symmetric 3x3 matrix, closed form
+            // (trigonometric solution of the characteristic cubic)
+            const double p1 = M[1] * M[1] + M[2] * M[2] + M[5] * M[5];
+            const double q = (M[0] + M[4] + M[8]) / 3.0;
+            const double a0 = M[0] - q, a4 = M[4] - q, a8 = M[8] - q;
+            const double p2 = a0 * a0 + a4 * a4 + a8 * a8 + 2.0 * p1;
+            const double pp = sqrt(p2 / 6.0);
+            if (pp == 0.0) {
+                lm = q;
+            } else {
+                const double b0 = a0 / pp, b4 = a4 / pp, b8 = a8 / pp;
+                const double b1 = M[1] / pp, b2 = M[2] / pp, b5 = M[5] / pp;
+                const double det = b0 * (b4 * b8 - b5 * b5) - b1 * (b1 * b8 - b5 * b2) + b2 * (b1 * b5 - b4 * b2);
+                const double rr = fmin(1.0, fmax(-1.0, 0.5 * det));
+                const double phi = acos(rr) / 3.0;
+                lm = q + 2.0 * pp * cos(phi);
+            }
+        }
+    }
+    sm[threadIdx.x] = lm;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = sm[0];
+}
+
+// Body must keep delta away from the box faces (§4.2.2) and chi_Omega <= chi_B.
+__global__ void k_check_masks(int n1, int n2, int n3, int r1, int r2, int r3, const uint8_t *chi,
+                              const uint8_t *chi_om, int d, int64_t N, int *bad)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= N) return;
+    const int i1 = (int)(p % n1), i2 = (int)((p / n1) % n2), i3 = (int)(p / ((int64_t)n1 * n2));
+    const uint8_t c = chi[p];
+    if (c > 1) atomicOr(bad, 4);
+    if (c) {
+        if (i1 < r1 || i1 >= n1 - r1 || i2 < r2 || i2 >= n2 - r2 || (n3 > 1 && (i3 < r3 || i3 >= n3 - r3)))
+            atomicOr(bad, 1);
+    }
+    if (chi_om)
+        for (int k = 0; k < d; ++k)
+            if (chi_om[k * N + p] > c) atomicOr(bad, 2);
+}
+
+template <typename Tout>
+__global__ void k_convert(const double *in, Tout *out, int64_t n)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) out[t] = (Tout)in[t];
+}
+
+static unsigned nblk(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace pd
+
+using namespace pd;
+
+namespace {
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+template <typename P>
+pd_status dalloc(pd_plan *p, P **ptr, size_t bytes)
+{
+    if (bytes == 0) {
+        *ptr = nullptr;
+        return PD_OK;
+    }
+    cudaError_t e = cudaMalloc((void **)ptr, bytes);
+    if (e != cudaSuccess) {
+        set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+        cudaGetLastError();
+        return PD_ERR_NOMEM;
+    }
+    p->bytes += (int64_t)bytes;
+    return PD_OK;
+}
+
+struct HostHorizon {
+    std::vector<int> off;
+    std::vector<double> c, g, w2;
+    int cnt = 0;
+};
+
+// Horizon offsets (0 < |xi| <= delta, tolerance 1e-12 relative on delta^2) and
+// per-bond kernel values (omega = 1/|xi|):
+//   C_ij = kc xi_i xi_j / |xi|^3 dV, g_i = xi_i / |xi| dV, omega|xi|^2 dV = |xi| dV.
+HostHorizon make_horizon(const pd_plan *p, double kc)
+{
+    HostHorizon h;
+    const int dim = p->dim;
+    int r[3] = {0, 0, 0};
+    for (int a = 0; a < dim; ++a) r[a] = (int)std::floor(p->prob.delta / p->prob.dx[a] + 1e-9);
+    const double d2max = p->prob.delta * p->prob.delta * (1.0 + 1e-12);
+    const double dV = p->dV;
+    std::vector<double> xi;
+    for (int k = -r[2]; k <= r[2]; ++k)
+        for (int j = -r[1]; j <= r[1]; ++j)
+            for (int i = -r[0]; i <= r[0]; ++i) {
+                if (!i && !j && !k) continue;
+                const double x[3] = {i * p->prob.dx[0], j * p->prob.dx[1], dim == 3 ? k * p->prob.dx[2] : 0.0};
+                const double s2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+                if (s2 > d2max) continue;
+                h.off.push_back(i);
+                h.off.push_back(j);
+                h.off.push_back(k);
+                xi.push_back(x[0]);
+                xi.push_back(x[1]);
+                xi.push_back(x[2]);
+                h.cnt++;
+            }
+    const int nc = p->ncomp;
+    h.c.assign((size_t)nc * h.cnt, 0.0);
+    h.g.assign((size_t)3 * h.cnt, 0.0);
+    h.w2.assign((size_t)h.cnt, 0.0);
+    static const int ci[6] = {0, 1, 2, 0, 0, 1}, cj[6] = {0, 1, 2, 1, 2, 2};
+    static const int ci2[3] = {0, 1, 0}, cj2[3] = {0, 1, 1};
+    for (int c = 0; c < h.cnt; ++c) {
+        const double *x = &xi[3 * c];
+        const double rr = std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+        for (int q = 0; q < nc; ++q) {
+            const int a = dim == 3 ? ci[q] : ci2[q], b = dim == 3 ? cj[q] : cj2[q];
+            h.c[(size_t)q * h.cnt + c] = kc * x[a] * x[b] / (rr * rr * rr) * dV;
+        }
+        for (int i = 0; i < 3; ++i) h.g[(size_t)i * h.cnt + c] = x[i] / rr * dV;
+        h.w2[c] = rr * dV;
+    }
+    return h;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pd_last_error_detail(void) { return g_err; }
+
+const char *pd_status_string(pd_status s)
+{
+    switch (s) {
+        case PD_OK: return "ok";
+        case PD_ERR_ARG: return "invalid argument";
+        case PD_ERR_SIZE: return "unsupported size";
+        case PD_ERR_NOMEM: return "device allocation failed";
+        case PD_ERR_CUDA: return "CUDA error";
+        case PD_ERR_NOT_CONVERGED: return "not converged";
+        case PD_ERR_TIMEOUT: return "device wait timed out";
+        case PD_ERR_NONFINITE: return "non-finite value";
+    }
+    return "unknown status";
+}
+
+int64_t pd_plan_workspace_bytes(const pd_plan *p) { return p ? p->bytes : 0; }
+
+pd_status pd_plan_profile(pd_plan *p, int enable)
+{
+    if (!p) {
+        set_error("pd_plan_profile: null plan");
+        return PD_ERR_ARG;
+    }
+    if (p->prof_on && !enable) PD_TRY(prof_harvest(p));
+    p->prof_on = enable ? 1 : 0;
+    for (int k = 0; k < pd_plan::kKinds; ++k) {
+        p->prof_ms[k] = 0.0;
+        p->prof_n[k] = 0;
+    }
+    p->ev_used = 0;
+    return PD_OK;
+}
+
+pd_status pd_plan_profile_read(pd_plan *p, int kind, double *ms_total, int64_t *launches)
+{
+    if (!p || kind < 0 || kind >= pd_plan::kKinds) {
+        set_error("pd_plan_profile_read: null plan or kind out of range");
+        return PD_ERR_ARG;
+    }
+    PD_TRY(prof_harvest(p));
+    if (ms_total) *ms_total = p->prof_ms[kind];
+    if (launches) *launches = p->prof_n[kind];
+    return PD_OK;
+}
+int64_t pd_plan_launch_count(const pd_plan *p) { return p ? p->launches : 0; }
+
+double pd_stable_dt(const pd_plan *p)
+{
+    if (!p || p->lam_max <= 0 || p->prob.rho <= 0) return 0.0;
+    return 2.0 * std::sqrt(p->prob.rho / p->lam_max);
+}
+
+void pd_plan_destroy(pd_plan *p)
+{
+    if (!p) return;
+    void *ptrs[] = {p->chi, p->chi_om, p->hoff, p->mhat64, p->mhat32, p->ghat64, p->ghat32, p->G64, p->G32,
+                    p->qt64, p->m3inv64, p->qt32, p->m3inv32, p->tw64, p->tw32, p->spec32, p->spec64,
+                    p->work, p->red};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    for (int i = 0; i < 2 * pd_plan::kEvPool; ++i)
+        if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+    delete p;
+}
+
+static pd_status plan_create_impl(const pd_problem *pr, const uint8_t *chi_B, const uint8_t *chi_Omega,
+                                  cudaStream_t st, pd_plan *p);
+
+pd_status pd_plan_create(const pd_problem *pr, const uint8_t *chi_B, const uint8_t *chi_Omega, void *stream,
+                         pd_plan **out)
+{
+    if (!pr || !chi_B || !out) {
+        set_error("pd_plan_create: null problem, chi_B or out");
+        return PD_ERR_ARG;
+    }
+    *out = nullptr;
+    pd_plan *p = new pd_plan();
+    pd_status s = plan_create_impl(pr, chi_B, chi_Omega, (cudaStream_t)stream, p);
+    if (s != PD_OK) {
+        pd_plan_destroy(p);
+        return s;
+    }
+    *out = p;
+    return PD_OK;
+}
+
+static pd_status plan_create_impl(const pd_problem *pr, const uint8_t *chi_B, const uint8_t *chi_Omega,
+                                  cudaStream_t st, pd_plan *p)
+{
+    p->prob = *pr;
+    const int dim = pr->dim;
+    if (dim != 2 && dim != 3) {
+        set_error("dim must be 2 or 3 (got %d)", dim);
+        return PD_ERR_ARG;
+    }
+    if (pr->model != PD_LIN_BOND && pr->model != PD_LIN_STATE) {
+        set_error("unknown model %d", pr->model);
+        return PD_ERR_ARG;
+    }
+    if (pr->model == PD_LIN_STATE && dim != 3) {
+        set_error("the state-based model is 3D only");
+        return PD_ERR_ARG;
+    }
+    if (!(pr->delta > 0) || !(pr->E > 0)) {
+        set_error("delta and E must be positive");
+        return PD_ERR_ARG;
+    }
+    if (pr->model == PD_LIN_STATE && !(pr->nu > -1.0 && pr->nu < 0.5)) {
+        set_error("nu must lie in (-1, 0.5)");
+        return PD_ERR_ARG;
+    }
+    const int n1 = pr->n[0], n2 = pr->n[1], n3 = dim == 3 ? pr->n[2] : 1;
+    if (!is_pow2(n1) || n1 < 32 || n1 > 2048 || !is_pow2(n2) || n2 < 16 || n2 > 1024 ||
+        (dim == 3 && (!is_pow2(n3) || n3 < 16 || n3 > 1024)) || (dim == 2 && pr->n[2] != 1)) {
+        set_error("grid %dx%dx%d unsupported: powers of two, 32<=n0<=2048, 16<=n1,n2<=1024, n2=1 in 2D",
+                  pr->n[0], pr->n[1], pr->n[2]);
+        return PD_ERR_SIZE;
+    }
+    int r[3] = {0, 0, 0};
+    for (int a = 0; a < dim; ++a) {
+        if (!(pr->dx[a] > 0)) {
+            set_error("dx[%d] must be positive", a);
+            return PD_ERR_ARG;
+        }
+        r[a] = (int)std::floor(pr->delta / pr->dx[a] + 1e-9);
+    }
+    if (r[0] < 1 || 2 * r[0] + 2 > n1 || 2 * r[1] + 2 > n2 || (dim == 3 && 2 * r[2] + 2 > n3)) {
+        set_error("horizon of %d x %d x %d cells does not fit the grid", r[0], r[1], r[2]);
+        return PD_ERR_SIZE;
+    }
+    p->dim = dim;
+    p->n1 = n1;
+    p->n2 = n2;
+    p->n3 = n3;
+    p->h = n1 / 2;
+    p->ncomp = dim == 3 ? 6 : 3;
+    p->N = (int64_t)n1 * n2 * n3;
+    p->nrows = (int64_t)n2 * n3;
+    p->lgl = ilog2(std::max(n1, std::max(n2, n3)));
+    p->dV = dim == 3 ? pr->dx[0] * pr->dx[1] * pr->dx[2] : pr->dx[0] * pr->dx[1];
+    const double d = pr->delta;
+    if (pr->model == PD_LIN_BOND) {
+        p->alpha = dim == 2 ? 9.0 * pr->E / (M_PI * d * d * d) : 12.0 * pr->E / (M_PI * d * d * d * d);
+        p->ka = 0.0;
+        p->m0 = 0.0;
+    }
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, dev);
+    }
+
+    // horizon and model constants
+    HostHorizon hz0 = make_horizon(p, 1.0);
+    if (pr->model == PD_LIN_STATE) {
+        double m0 = 0.0;
+        for (int c = 0; c < hz0.cnt; ++c) m0 += hz0.w2[c];  // Σ omega |xi|^2 dV
+        const double kappa = pr->E / (3.0 * (1.0 - 2.0 * pr->nu));
+        const double mu = pr->E / (2.0 * (1.0 + pr->nu));
+        p->m0 = m0;
+        p->alpha = 30.0 * mu / m0;
+        // 3 kappa - 5 mu vanishes at nu = 1/4 (the state-based solid is then the
+        // bond form); snap rounding residue to an exact zero
+        const double dk = 3.0 * kappa - 5.0 * mu;
+        p->ka = (std::fabs(dk) <= 1e-12 * (kappa + mu)) ? 0.0 : dk / m0;
+    }
+    p->state_based = (pr->model == PD_LIN_STATE && p->ka != 0.0) ? 1 : 0;
+    HostHorizon hz = make_horizon(p, p->alpha);
+    p->hcount = hz.cnt;
+
+    const int64_t N = p->N;
+    const int nc = p->ncomp;
+    // masks
+    PD_TRY(dalloc(p, &p->chi, (size_t)N));
+    PD_TRY(dalloc(p, &p->chi_om, (size_t)N * dim));
+    PD_CUDA_TRY(cudaMemcpyAsync(p->chi, chi_B, (size_t)N, cudaMemcpyDeviceToDevice, st));
+    for (int k = 0; k < dim; ++k)
+        PD_CUDA_TRY(cudaMemcpyAsync(p->chi_om + k * N, chi_Omega ? chi_Omega + k * N : chi_B, (size_t)N,
+                                    cudaMemcpyDeviceToDevice, st));
+    // horizon tables on device (one buffer: ints, then doubles)
+    int *d_off = nullptr;
+    double *d_c = nullptr, *d_g = nullptr, *d_w2 = nullptr;
+    PD_TRY(dalloc(p, &p->hoff, sizeof(int) * 3 * hz.cnt + sizeof(double) * ((size_t)(nc + 4) * hz.cnt) + 64));
+    d_off = p->hoff;
+    {
+        char *base = (char *)p->hoff;
+        size_t o = ((sizeof(int) * 3 * hz.cnt) + 15) / 16 * 16;
+        d_c = (double *)(base + o);
+        d_g = d_c + (size_t)nc * hz.cnt;
+        d_w2 = d_g + (size_t)3 * hz.cnt;
+    }
+    PD_CUDA_TRY(cudaMemcpyAsync(d_off, hz.off.data(), sizeof(int) * 3 * hz.cnt, cudaMemcpyHostToDevice, st));
+    PD_CUDA_TRY(cudaMemcpyAsync(d_c, hz.c.data(), sizeof(double) * nc * hz.cnt, cudaMemcpyHostToDevice, st));
+    PD_CUDA_TRY(cudaMemcpyAsync(d_g, hz.g.data(), sizeof(double) * 3 * hz.cnt, cudaMemcpyHostToDevice, st));
+    PD_CUDA_TRY(cudaMemcpyAsync(d_w2, hz.w2.data(), sizeof(double) * hz.cnt, cudaMemcpyHostToDevice, st));
+    HorizonDev hd{d_off, d_c, d_g, d_w2, hz.cnt};
+    p->hdev = hd;
+
+    // reduction scratch
+    PD_TRY(dalloc(p, &p->red, sizeof(double) * 65536));
+
+    // mask checks
+    {
+        int *bad = (int *)p->red;
+        PD_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), st));
+        k_check_masks<<<nblk(N), 256, 0, st>>>(n1, n2, n3, r[0], r[1], r[2], p->chi, chi_Omega ? p->chi_om : nullptr,
+                                               dim, N, bad);
+        PD_LAUNCH_CHECK();
+        int hbad = 0;
+        PD_CUDA_TRY(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+        PD_CUDA_TRY(cudaStreamSynchronize(st));
+        if (hbad & 4) {
+            set_error("chi_B must hold 0/1 values");
+            return PD_ERR_ARG;
+        }
+        if (hbad & 1) {
+            set_error("the body must stay at least delta away from the box faces (chi_B = 1 within delta of a face)");
+            return PD_ERR_ARG;
+        }
+        if (hbad & 2) {
+            set_error("chi_Omega must be 0 where chi_B is 0");
+            return PD_ERR_ARG;
+        }
+    }
+
+    // folded spectra
+    p->fold_sz = (int64_t)(p->h + 1) * (n2 / 2 + 1) * (n3 / 2 + 1);
+    const int64_t fs = p->fold_sz;
+    PD_TRY(dalloc(p, &p->mhat64, sizeof(double) * nc * fs));
+    PD_TRY(dalloc(p, &p->mhat32, sizeof(float) * nc * fs));
+    if (pr->model == PD_LIN_STATE) {
+        PD_TRY(dalloc(p, &p->ghat64, sizeof(double) * 3 * fs));
+        PD_TRY(dalloc(p, &p->ghat32, sizeof(float) * 3 * fs));
+    }
+    k_fold_tables<<<nblk(fs, 128), 128, 0, st>>>(dim, n1, n2, n3, p->h, hd, nc, 1.0 / (double)N, p->mhat64,
+                                                p->ghat64, fs);
+    PD_LAUNCH_CHECK();
+    k_convert<float><<<nblk(nc * fs), 256, 0, st>>>(p->mhat64, p->mhat32, nc * fs);
+    PD_LAUNCH_CHECK();
+    if (p->ghat64) {
+        k_convert<float><<<nblk(3 * fs), 256, 0, st>>>(p->ghat64, p->ghat32, 3 * fs);
+        PD_LAUNCH_CHECK();
+    }
+
+    // symbol bound for the stable time step
+    {
+        const unsigned nb = nblk(fs, 256);
+        double *tmp = nullptr;
+        PD_TRY(dalloc(p, &tmp, sizeof(double) * nb));
+        const double kcoef = (pr->model == PD_LIN_STATE) ? 3.0 * p->ka / p->m0 : 0.0;
+        k_lam_max<<<nb, 256, 0, st>>>(dim, p->mhat64, p->ghat64, kcoef, (double)N, fs, tmp);
+        PD_LAUNCH_CHECK();
+        std::vector<double> hm(nb);
+        PD_CUDA_TRY(cudaMemcpyAsync(hm.data(), tmp, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+        PD_CUDA_TRY(cudaStreamSynchronize(st));
+        cudaFree(tmp);
+        p->bytes -= (int64_t)(sizeof(double) * nb);
+        p->lam_max = 0;
+        for (double v : hm) p->lam_max = std::max(p->lam_max, v);
+    }
+
+    // boundary fields
+    PD_TRY(dalloc(p, &p->G64, sizeof(double) * nc * N));
+    PD_TRY(dalloc(p, &p->G32, sizeof(float) * nc * N));
+    k_gfield<double, double, double><<<nblk(N, 128), 128, 0, st>>>(n1, n2, n3, hd, nc, p->chi, (const double *)nullptr,
+                                                                 p->G64, N);
+    PD_LAUNCH_CHECK();
+    k_convert<float><<<nblk(nc * N), 256, 0, st>>>(p->G64, p->G32, nc * N);
+    PD_LAUNCH_CHECK();
+    if (pr->model == PD_LIN_STATE) {
+        PD_TRY(dalloc(p, &p->qt64, sizeof(double) * 3 * N));
+        PD_TRY(dalloc(p, &p->m3inv64, sizeof(double) * N));
+        PD_TRY(dalloc(p, &p->qt32, sizeof(float) * 3 * N));
+        PD_TRY(dalloc(p, &p->m3inv32, sizeof(float) * N));
+        k_state_fields<<<nblk(N, 128), 128, 0, st>>>(n1, n2, n3, hd, p->chi, p->qt64, p->m3inv64, N);
+        PD_LAUNCH_CHECK();
+        k_convert<float><<<nblk(3 * N), 256, 0, st>>>(p->qt64, p->qt32, 3 * N);
+        k_convert<float><<<nblk(N), 256, 0, st>>>(p->m3inv64, p->m3inv32, N);
+        PD_LAUNCH_CHECK();
+    }
+
+    // twiddles e^{-2 pi i k / L}, L = max(n1, n2, n3), from the eighth-turn symmetric
+    // evaluation of cos/sin in FP64 on the host
+    {
+        const int L = 1 << p->lgl;
+        std::vector<cx<double>> t64(L);
+        std::vector<cx<float>> t32(L);
+        for (int k = 0; k < L; ++k) {
+            const double a = 2.0 * M_PI * (double)k / (double)L;
+            t64[k] = mk(std::cos(a), -std::sin(a));
+        }
+        // exact values on the axes and diagonals
+        for (int k = 0; k < L; k += L / 8) {
+            const int o = (8 * k) / L;
+            const double r2 = 0.70710678118654752440;
+            const double cs[8] = {1, r2, 0, -r2, -1, -r2, 0, r2};
+            const double sn[8] = {0, r2, 1, r2, 0, -r2, -1, -r2};
+            t64[k] = mk(cs[o], -sn[o]);
+        }
+        for (int k = 0; k < L; ++k) t32[k] = mk((float)t64[k].x, (float)t64[k].y);
+        PD_TRY(dalloc(p, &p->tw64, sizeof(cx<double>) * L));
+        PD_TRY(dalloc(p, &p->tw32, sizeof(cx<float>) * L));
+        PD_CUDA_TRY(cudaMemcpyAsync(p->tw64, t64.data(), sizeof(cx<double>) * L, cudaMemcpyHostToDevice, st));
+        PD_CUDA_TRY(cudaMemcpyAsync(p->tw32, t32.data(), sizeof(cx<float>) * L, cudaMemcpyHostToDevice, st));
+        PD_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+
+    // timing events (created here so that later calls allocate nothing)
+    for (int i = 0; i < 2 * pd_plan::kEvPool; ++i) PD_CUDA_TRY(cudaEventCreate(&p->ev[i]));
+
+    // spectra and scratch
+    if (!pr->fp64) PD_TRY(dalloc(p, &p->spec32, sizeof(float) * (size_t)kMaxSpecFields * N));
+    PD_TRY(dalloc(p, &p->spec64, sizeof(double) * (size_t)(pr->fp64 ? kMaxSpecFields : 8) * N));
+    {
+        const size_t tb = pr->fp64 ? sizeof(double) : sizeof(float);
+        const size_t vec = tb * (size_t)dim * N;  // one vector field
+        const size_t sizes[] = {vec, vec, vec, vec, tb * (size_t)N, tb * (size_t)nc * N,
+                                sizeof(double) * (size_t)dim * N, sizeof(double) * (size_t)N};
+        void **slots[] = {&p->cg_e, &p->cg_r, &p->cg_p, &p->cg_q, &p->theta, &p->Gw, (void **)&p->r64,
+                          (void **)&p->theta64};
+        size_t total = 0;
+        for (size_t b : sizes) total += (b + 255) / 256 * 256;
+        p->work_bytes = total;
+        PD_TRY(dalloc(p, &p->work, total));
+        char *base = (char *)p->work;
+        for (size_t i = 0; i < sizeof(sizes) / sizeof(sizes[0]); ++i) {
+            *slots[i] = base;
+            base += (sizes[i] + 255) / 256 * 256;
+        }
+    }
+    PD_CUDA_TRY(cudaStreamSynchronize(st));
+    return PD_OK;
+}
+
+pd_status pd_kernel_spectrum(pd_plan *p, double *out, void *stream)
+{
+    if (!p || !out) {
+        set_error("pd_kernel_spectrum: null plan or output");
+        return PD_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    HorizonDev hd = p->hdev;
+    const int64_t total = (int64_t)(p->h + 1) * p->n2 * p->n3;
+    k_kernel_spectrum<<<nblk(total, 128), 128, 0, st>>>(p->n1, p->n2, p->n3, p->h, hd, p->ncomp, out, total);
+    PD_LAUNCH_CHECK();
+    p->launches++;
+    return PD_OK;
+}
+
+}  // extern "C"

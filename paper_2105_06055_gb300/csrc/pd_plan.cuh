@@ -1,0 +1,324 @@
+// Plan object and launch helpers of the GB300 FCBM-EC library (private).
+#pragma once
+
+#include <vector>
+
+#include "pd_common.cuh"
+#include "pd_fft.cuh"
+
+namespace pd {
+
+// Packed-spectrum slots per plan. The 3D last-axis pass is out of place: its
+// blocks read the mirror column k2 -> -k2 of another block's tile, so outputs
+// go to slots after the inputs (inputs + outputs <= kMaxSpecFields).
+constexpr int kMaxSpecFields = 20;
+
+// Device-side view of the model used by the per-node and per-mode functors.
+template <typename T>
+struct Model {
+    int dim;
+    int n1, n2, n3;
+    int h;             // n1 / 2
+    int ky_half, kz_half;
+    int64_t N;         // nodes
+    int64_t nrows;     // n2 * n3
+    const T *mhat;     // folded difference spectrum (K^(k) - K^(0)) / N, ncomp fields
+    const T *ghat;     // folded dV/N * Σ g_i sin(theta) (state-based), 3 fields, or null
+    int64_t fold_sz;   // entries per folded component: (h+1)(n2/2+1)(n3/2+1)
+    const uint8_t *chi;
+    const uint8_t *chi_om;  // d x N
+    const T *G;        // ncomp x N boundary field for v = chi
+    const T *qt;       // 3 x N, state-based q_i(x) = dV (g_i * chi)
+    const T *m3inv;    // N, 3/m(x) (0 outside the body)
+    T ka;              // (3 kappa - 5 mu)/m0 (state-based)
+};
+
+// Folded-table lookup of a symmetric kernel spectrum at mode (kx, ky, kz),
+// kx in [0, n1/2]. Off-diagonal components are odd in each of their two axes.
+template <typename T>
+struct SpecIdx {
+    int64_t idx;
+    bool fy, fz;
+};
+
+template <typename T>
+__device__ __forceinline__ SpecIdx<T> spec_index(const Model<T> &m, int kx, int ky, int kz)
+{
+    SpecIdx<T> r;
+    r.fy = ky > m.ky_half;
+    r.fz = kz > m.kz_half;
+    const int kyf = r.fy ? m.n2 - ky : ky;
+    const int kzf = r.fz ? m.n3 - kz : kz;
+    r.idx = ((int64_t)kzf * (m.ky_half + 1) + kyf) * (m.h + 1) + kx;
+    return r;
+}
+
+// Component order: 2D 11,22,12; 3D 11,22,33,12,13,23.
+template <typename T>
+__device__ __forceinline__ void load_mhat(const Model<T> &m, const SpecIdx<T> &s, T *M /*3x3*/)
+{
+    const T *t = m.mhat + s.idx;
+    const int64_t fs = m.fold_sz;
+    if (m.dim == 2) {
+        const T m11 = t[0], m22 = t[fs], m12 = s.fy ? -t[2 * fs] : t[2 * fs];
+        M[0] = m11; M[1] = m12; M[3] = m12; M[4] = m22;
+    } else {
+        const T m11 = t[0], m22 = t[fs], m33 = t[2 * fs];
+        const T m12 = s.fy ? -t[3 * fs] : t[3 * fs];
+        const T m13 = s.fz ? -t[4 * fs] : t[4 * fs];
+        const T m23 = (s.fy != s.fz) ? -t[5 * fs] : t[5 * fs];
+        M[0] = m11; M[1] = m12; M[2] = m13;
+        M[3] = m12; M[4] = m22; M[5] = m23;
+        M[6] = m13; M[7] = m23; M[8] = m33;
+    }
+}
+
+struct HorizonDev {
+    const int *off;   // 3 x cnt
+    const double *c;  // ncomp x cnt: C_ij(xi) dV
+    const double *g;  // 3 x cnt: g_i(xi) dV = omega xi_i dV (state-based)
+    const double *w2; // cnt: omega |xi|^2 dV
+    int cnt;
+};
+
+// Boundary field of a node weight v = chi s (Eq. 100 with the difference kernel):
+//   G_c(x) = Σ_H C_c(xi) dV (v(x+xi) - v(x)),  G = 0 where chi = 0.
+// For v = chi this is -(Σ_H C dV (1 - chi(x+xi))): zero in the delta-interior.
+template <typename T, typename V, typename Acc>
+__global__ void k_gfield(int n1, int n2, int n3, HorizonDev hz, int ncomp, const uint8_t *chi,
+                         const V *s, T *G, int64_t N)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= N) return;
+    const int i1 = (int)(p % n1), i2 = (int)((p / n1) % n2), i3 = (int)(p / ((int64_t)n1 * n2));
+    Acc acc[6] = {0, 0, 0, 0, 0, 0};
+    if (chi[p]) {
+        const Acc vp = s ? (Acc)s[p] : Acc(1);
+        for (int c = 0; c < hz.cnt; ++c) {
+            const int a = (i1 + hz.off[3 * c]) & (n1 - 1);
+            const int b = (i2 + hz.off[3 * c + 1]) & (n2 - 1);
+            const int e = (i3 + hz.off[3 * c + 2]) & (n3 - 1);
+            const int64_t q = ((int64_t)e * n2 + b) * n1 + a;
+            const Acc vq = chi[q] ? (s ? (Acc)s[q] : Acc(1)) : Acc(0);
+            const Acc dv = vq - vp;
+            if (dv != Acc(0))
+                for (int k = 0; k < ncomp; ++k) acc[k] += (Acc)hz.c[k * hz.cnt + c] * dv;
+        }
+    }
+    for (int k = 0; k < ncomp; ++k) G[k * N + p] = (T)acc[k];
+}
+
+struct LaunchCfg {
+    dim3 grid, block;
+    size_t smem;
+};
+
+}  // namespace pd
+
+struct pd_plan {
+    pd_problem prob;
+    int dim, n1, n2, n3, h, ncomp;
+    int64_t N, nrows;
+    int lgl;            // log2 twiddle table length
+    double dV, alpha;   // bond constant (or 30 mu / m0 for the state-based C)
+    double ka, m0;      // state-based constants
+    double lam_max;     // largest eigenvalue of the periodic symbol
+    int state_based;    // model == PD_LIN_STATE && ka != 0 (dilatation round needed)
+    int hcount;
+    // device memory
+    uint8_t *chi = nullptr, *chi_om = nullptr;
+    int *hoff = nullptr;           // 3 x hcount integer offsets
+    double *mhat64 = nullptr;      // ncomp x fold_sz
+    float *mhat32 = nullptr;
+    double *ghat64 = nullptr;      // 3 x fold_sz (state-based)
+    float *ghat32 = nullptr;
+    int64_t fold_sz = 0;
+    double *G64 = nullptr;         // ncomp x N
+    float *G32 = nullptr;
+    double *qt64 = nullptr, *m3inv64 = nullptr;  // state-based
+    float *qt32 = nullptr, *m3inv32 = nullptr;
+    pd::cx<double> *tw64 = nullptr;
+    pd::cx<float> *tw32 = nullptr;
+    void *spec32 = nullptr;        // kMaxSpecFields x N floats (packed spectra)
+    void *spec64 = nullptr;        // kMaxSpecFields x N doubles
+    void *work = nullptr;          // one allocation carved into the scratch fields below
+    size_t work_bytes = 0;
+    // scratch fields (plan precision T unless noted)
+    void *cg_e = nullptr, *cg_r = nullptr, *cg_p = nullptr, *cg_q = nullptr;  // d x N each
+    void *theta = nullptr;         // N, dilatation (state-based)
+    void *Gw = nullptr;            // ncomp x N, boundary field of a node weight
+    double *r64 = nullptr;         // d x N, FP64 residual / force
+    double *theta64 = nullptr;     // N, FP64 dilatation for the FP64 residual
+    double *red = nullptr;         // reduction partials and scalars
+    int64_t bytes = 0;
+    int64_t launches = 0;
+    int nsm = 148;
+    pd::HorizonDev hdev;  // device horizon tables (views into hoff)
+    // per-pass timing (diagnostics): event pairs around each FFT-pass launch
+    static constexpr int kEvPool = 1024;
+    static constexpr int kKinds = 4;
+    cudaEvent_t ev[2 * kEvPool] = {};
+    int ev_kind[kEvPool] = {};
+    int ev_used = 0;
+    int prof_on = 0;
+    double prof_ms[kKinds] = {};
+    int64_t prof_n[kKinds] = {};
+};
+
+namespace pd {
+
+template <typename T>
+Model<T> model_view(const pd_plan *p);
+
+template <typename T>
+inline T *spec_buf(const pd_plan *p);
+template <>
+inline float *spec_buf<float>(const pd_plan *p) { return (float *)p->spec32; }
+template <>
+inline double *spec_buf<double>(const pd_plan *p) { return (double *)p->spec64; }
+
+template <typename T>
+inline const cx<T> *tw_buf(const pd_plan *p);
+template <>
+inline const cx<float> *tw_buf<float>(const pd_plan *p) { return p->tw32; }
+template <>
+inline const cx<double> *tw_buf<double>(const pd_plan *p) { return p->tw64; }
+
+// Row-pass configuration for F fields in shared memory.
+template <typename T>
+inline void row_cfg(const pd_plan *p, int F, RowGeom &g, LaunchCfg &c)
+{
+    const int H = p->h, nt = H >> 4;
+    int rows = 256 / nt;
+    if (rows < 1) rows = 1;
+    // keep the per-block shared memory modest
+    const int pad = nt < 16 ? nt : 0;
+    while (rows > 1 && (size_t)F * rows * (H + pad) * sizeof(cx<T>) > 96 * 1024) rows >>= 1;
+    while (p->nrows % rows) rows >>= 1;
+    g.lgh = ilog2(H);
+    g.rows = rows;
+    g.pitch = H + pad;
+    g.nrows = p->nrows;
+    g.lgl = p->lgl;
+    c.grid = dim3((unsigned)(p->nrows / rows));
+    c.block = dim3(rows * nt);
+    c.smem = (size_t)F * rows * g.pitch * sizeof(cx<T>);
+}
+
+// Column-pass configuration: axis 1 = x2, axis 2 = x3 (3D), F fields in smem.
+template <typename T>
+inline void col_cfg(const pd_plan *p, int axis, bool last, int F, ColGeom &g, LaunchCfg &c)
+{
+    const int H = p->h;
+    const int L = axis == 1 ? p->n2 : p->n3;
+    const int nt = L >> 4;
+    const int mirror = (p->dim == 3 && last) ? 1 : 0;
+    int64_t inner;
+    int64_t rowstride, outer, outerstride;
+    if (axis == 1) {
+        inner = H;
+        rowstride = H;
+        outer = p->n3;
+        outerstride = (int64_t)p->n2 * H;
+    } else {
+        inner = (int64_t)p->n2 * H;
+        rowstride = inner;
+        outer = 1;
+        outerstride = 0;
+    }
+    int w = 16;
+    while (w > 2 && ((w + mirror) * nt > 512 ||
+                     (size_t)F * L * (w + 1) * sizeof(cx<T>) > 200 * 1024))
+        w >>= 1;
+    while (w > 1 && (H % w)) w >>= 1;
+    g.lgl = ilog2(L);
+    g.w = w;
+    g.pitch = w + 1;
+    g.mirror = mirror;
+    g.inner = inner;
+    g.rowstride = rowstride;
+    g.outerstride = outerstride;
+    g.lgh = ilog2(H);
+    g.n2 = p->n2;
+    g.lgtw = p->lgl;
+    c.grid = dim3((unsigned)(inner / w), (unsigned)outer);
+    c.block = dim3((w + mirror) * nt);
+    c.smem = (size_t)F * L * g.pitch * sizeof(cx<T>);
+}
+
+pd_status set_smem_attr(const void *func, size_t smem);
+
+// pass kinds for the timing facility
+enum PassKind { PASS_ROWS_FWD = 0, PASS_COLS = 1, PASS_LAST = 2, PASS_ROWS_INV = 3 };
+pd_status prof_harvest(pd_plan *p);
+inline pd_status prof_begin(pd_plan *p, int kind, cudaStream_t st)
+{
+    if (!p->prof_on) return PD_OK;
+    if (p->ev_used == pd_plan::kEvPool) PD_TRY(prof_harvest(p));
+    p->ev_kind[p->ev_used] = kind;
+    PD_CUDA_TRY(cudaEventRecord(p->ev[2 * p->ev_used], st));
+    return PD_OK;
+}
+inline pd_status prof_end(pd_plan *p, cudaStream_t st)
+{
+    if (!p->prof_on) return PD_OK;
+    PD_CUDA_TRY(cudaEventRecord(p->ev[2 * p->ev_used + 1], st));
+    p->ev_used++;
+    return PD_OK;
+}
+
+template <typename T, class Op>
+pd_status launch_rows(pd_plan *p, const Op &op, int F, cudaStream_t st)
+{
+    RowGeom g;
+    LaunchCfg c;
+    row_cfg<T>(p, F, g, c);
+    PD_TRY(set_smem_attr((const void *)k_rows<T, Op>, c.smem));
+    PD_TRY(prof_begin(p, Op::kFin > 0 ? PASS_ROWS_INV : PASS_ROWS_FWD, st));
+    k_rows<T, Op><<<c.grid, c.block, c.smem, st>>>(g, op, tw_buf<T>(p));
+    PD_LAUNCH_CHECK();
+    PD_TRY(prof_end(p, st));
+    p->launches++;
+    return PD_OK;
+}
+
+template <typename T, class Op>
+pd_status launch_cols(pd_plan *p, const Op &op, int axis, bool last, int F, cudaStream_t st)
+{
+    ColGeom g;
+    LaunchCfg c;
+    col_cfg<T>(p, axis, last, F, g, c);
+    PD_TRY(set_smem_attr((const void *)k_cols<T, Op>, c.smem));
+    PD_TRY(prof_begin(p, last ? PASS_LAST : PASS_COLS, st));
+    k_cols<T, Op><<<c.grid, c.block, c.smem, st>>>(g, op, tw_buf<T>(p), axis == 2 ? 1 : 0);
+    PD_LAUNCH_CHECK();
+    PD_TRY(prof_end(p, st));
+    p->launches++;
+    return PD_OK;
+}
+
+// Plain column FFT of F packed spectra along axis (forward or inverse), in place.
+template <typename T, int F, int MODE>
+struct ColPass {
+    static constexpr int kFin = F, kFout = F, kMode = MODE, kPre = 0;
+    static constexpr bool kStoreIn = false;
+    cx<T> *spec;
+    int64_t fstride;  // complex elements per field
+    __device__ const cx<T> *spec_in(int f) const { return spec + f * fstride; }
+    __device__ cx<T> *spec_out(int f) const { return spec + f * fstride; }
+    __device__ cx<T> *spec_aux(int) const { return nullptr; }
+    __device__ void combine(int, int, int, const cx<T> *, cx<T> *) const {}
+};
+
+template <typename T, int F>
+pd_status col_pass(pd_plan *p, cx<T> *spec, bool inverse, cudaStream_t st)
+{
+    if (inverse) {
+        ColPass<T, F, 1> op{spec, p->N / 2};
+        return launch_cols<T>(p, op, 1, false, F, st);
+    }
+    ColPass<T, F, 0> op{spec, p->N / 2};
+    return launch_cols<T>(p, op, 1, false, F, st);
+}
+
+}  // namespace pd

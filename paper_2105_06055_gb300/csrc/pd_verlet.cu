@@ -1,0 +1,165 @@
+// pd_step_verlet: FCBM-EC dynamics with energy-based bond breaking.
+//
+// Per step (Eq. 83-84 for the kinematics, Eq. 63 for the integrity index,
+// Eq. 101-102 for L and W with node weight chi_B lam):
+//   kick+drift : v <- v + dt/(2 rho) (L^n + b);  u <- chi_O (u + dt v) + (1 - chi_O) w;
+//                lam <- lam [W^n <= Wc]  (irreversible; counts 1 -> 0 flips)
+//   G^lam      : recomputed on the device only if some lam flipped this step
+//   force      : L^{n+1}, W^{n+1} = FFT convolutions with weight chi_B lam
+//   kick       : v <- chi_O (v + dt/(2 rho) (L^{n+1} + b))
+// The call starts with one force evaluation of the given state, so a run of
+// n steps split over several calls gives the same result as one call.
+#include <algorithm>
+
+#include "pd_plan.cuh"
+
+namespace pd {
+
+template <typename T>
+pd_status force_any(pd_plan *p, const T *u, const T *s, const uint8_t *lam, const T *G, T *L, T *W,
+                    cudaStream_t st);
+
+namespace {
+
+// device counters live in the reduction buffer: [0] flips (int64), [1] flag
+struct VerletCounters {
+    unsigned long long flips;
+    int changed;
+};
+
+template <typename T>
+__global__ void k_kick_drift(T *u, T *v, uint8_t *lam, const T *L, const T *b, const T *w, const T *W,
+                             const uint8_t *chi, const uint8_t *co, int d, int64_t N, T hdt_rho, T dt, T Wc,
+                             int breaking, VerletCounters *cnt)
+{
+    unsigned long long flips = 0;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+        for (int i = 0; i < d; ++i) {
+            const int64_t q = i * N + p;
+            const T vh = v[q] + hdt_rho * (L[q] + b[q]);
+            v[q] = vh;
+            u[q] = co[q] ? (u[q] + dt * vh) : (w ? w[q] : T(0));
+        }
+        if (breaking && chi[p] && lam[p] && !(W[p] <= Wc)) {
+            lam[p] = 0;
+            ++flips;
+        }
+    }
+    // warp-aggregated counter update
+    for (int o = 16; o > 0; o >>= 1) flips += __shfl_down_sync(0xffffffffu, flips, o);
+    if ((threadIdx.x & 31) == 0 && flips) {
+        atomicAdd(&cnt->flips, flips);
+        atomicExch(&cnt->changed, 1);
+    }
+}
+
+template <typename T>
+__global__ void k_kick(T *v, const T *L, const T *b, const uint8_t *co, int64_t n, T hdt_rho)
+{
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        v[q] = co[q] ? v[q] + hdt_rho * (L[q] + b[q]) : T(0);
+}
+
+// G^lam_c(x) = Σ_H C_c dV (v(x+xi) - v(x)), v = chi lam; skipped unless the
+// change flag is set by this step's kick-drift (k_clear_changed resets it).
+template <typename T>
+__global__ void k_gfield_lam(int n1, int n2, int n3, HorizonDev hz, int ncomp, const uint8_t *chi,
+                             const uint8_t *lam, T *G, int64_t N, VerletCounters *cnt, int force)
+{
+    if (!force && !cnt->changed) return;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < N) {
+        const int i1 = (int)(p % n1), i2 = (int)((p / n1) % n2), i3 = (int)(p / ((int64_t)n1 * n2));
+        T acc[6] = {0, 0, 0, 0, 0, 0};
+        if (chi[p]) {
+            const T vp = lam[p] ? T(1) : T(0);
+            for (int c = 0; c < hz.cnt; ++c) {
+                const int a = (i1 + hz.off[3 * c]) & (n1 - 1);
+                const int bb = (i2 + hz.off[3 * c + 1]) & (n2 - 1);
+                const int e = (i3 + hz.off[3 * c + 2]) & (n3 - 1);
+                const int64_t q = ((int64_t)e * n2 + bb) * n1 + a;
+                const T dv = ((chi[q] && lam[q]) ? T(1) : T(0)) - vp;
+                if (dv != T(0))
+                    for (int k = 0; k < ncomp; ++k) acc[k] += (T)hz.c[k * hz.cnt + c] * dv;
+            }
+        }
+        for (int k = 0; k < ncomp; ++k) G[k * N + p] = acc[k];
+    }
+}
+
+__global__ void k_clear_changed(VerletCounters *cnt) { cnt->changed = 0; }
+
+template <typename T>
+pd_status verlet_impl(pd_plan *p, T *u, T *v, uint8_t *lam, const T *b, const T *w, double dt, int nsteps,
+                      int64_t *n_broken_out, cudaStream_t st)
+{
+    const int d = p->dim;
+    const int64_t N = p->N;
+    T *L = (T *)p->cg_q;
+    T *W = (T *)p->theta;
+    T *G = lam ? (T *)p->Gw : (sizeof(T) == 8 ? (T *)p->G64 : (T *)p->G32);
+    const int breaking = (lam && p->prob.Wc > 0) ? 1 : 0;
+    VerletCounters *cnt = reinterpret_cast<VerletCounters *>(p->red + 4096);
+    PD_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(VerletCounters), st));
+    const unsigned nbl = (unsigned)((N + 127) / 128);
+    if (lam) {
+        k_gfield_lam<T><<<nbl, 128, 0, st>>>(p->n1, p->n2, p->n3, p->hdev, p->ncomp, p->chi, lam, G, N, cnt, 1);
+        PD_LAUNCH_CHECK();
+        p->launches++;
+    }
+    PD_TRY(force_any<T>(p, u, nullptr, lam, G, L, breaking ? W : nullptr, st));
+    const T hdt = (T)(0.5 * dt / p->prob.rho);
+    const unsigned ng = (unsigned)std::min<int64_t>(4 * p->nsm, (N + 255) / 256);
+    const unsigned ngv = (unsigned)std::min<int64_t>(4 * p->nsm, (d * N + 255) / 256);
+    for (int s = 0; s < nsteps; ++s) {
+        k_kick_drift<T><<<ng, 256, 0, st>>>(u, v, lam, L, b, w, W, p->chi, p->chi_om, d, N, hdt, (T)dt,
+                                            (T)p->prob.Wc, breaking, cnt);
+        PD_LAUNCH_CHECK();
+        p->launches++;
+        if (breaking) {
+            k_gfield_lam<T><<<nbl, 128, 0, st>>>(p->n1, p->n2, p->n3, p->hdev, p->ncomp, p->chi, lam, G, N, cnt, 0);
+            k_clear_changed<<<1, 1, 0, st>>>(cnt);
+            PD_LAUNCH_CHECK();
+            p->launches += 2;
+        }
+        PD_TRY(force_any<T>(p, u, nullptr, lam, G, L, breaking ? W : nullptr, st));
+        k_kick<T><<<ngv, 256, 0, st>>>(v, L, b, p->chi_om, d * N, hdt);
+        PD_LAUNCH_CHECK();
+        p->launches++;
+    }
+    if (n_broken_out) {
+        VerletCounters h;
+        PD_CUDA_TRY(cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, st));
+        PD_CUDA_TRY(cudaStreamSynchronize(st));
+        *n_broken_out = (int64_t)h.flips;
+    }
+    return PD_OK;
+}
+
+}  // namespace
+}  // namespace pd
+
+using namespace pd;
+
+extern "C" pd_status pd_step_verlet(pd_plan *p, void *u, void *v, uint8_t *lambda, const void *b, const void *w,
+                                    double dt, int nsteps, int64_t *n_broken_out, void *stream)
+{
+    if (!p || !u || !v || !b) {
+        set_error("pd_step_verlet: null plan, u, v or b");
+        return PD_ERR_ARG;
+    }
+    if (!(dt > 0) || nsteps < 0 || !(p->prob.rho > 0)) {
+        set_error("pd_step_verlet: dt and rho must be positive, nsteps >= 0");
+        return PD_ERR_ARG;
+    }
+    if (p->state_based) {
+        set_error("pd_step_verlet: the dynamic driver uses the bond model");
+        return PD_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (p->prob.fp64)
+        return verlet_impl<double>(p, (double *)u, (double *)v, lambda, (const double *)b, (const double *)w, dt,
+                                   nsteps, n_broken_out, st);
+    return verlet_impl<float>(p, (float *)u, (float *)v, lambda, (const float *)b, (const float *)w, dt, nsteps,
+                              n_broken_out, st);
+}

@@ -1,0 +1,281 @@
+"""Python binding of the C ABI in ``include/pd.h`` (argument marshalling only).
+
+Every computation runs in ``libpdfft.so``; this module only checks tensor
+shapes, dtypes and devices, passes raw device pointers and the current CUDA
+stream, and turns status codes into exceptions. There is no fallback: if the
+library is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+from typing import Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpdfft.so")
+_lib = None
+
+PD_LIN_BOND = 0
+PD_LIN_STATE = 1
+
+STATUS = {0: "PD_OK", -1: "PD_ERR_ARG", -2: "PD_ERR_SIZE", -3: "PD_ERR_NOMEM", -4: "PD_ERR_CUDA",
+          -5: "PD_ERR_NOT_CONVERGED", -6: "PD_ERR_TIMEOUT", -7: "PD_ERR_NONFINITE"}
+
+EXPORTS = ["pd_plan_create", "pd_plan_destroy", "pd_kernel_spectrum", "pd_force", "pd_step_verlet",
+           "pd_solve_static", "pd_force_adjoint", "pd_damage", "pd_plan_workspace_bytes",
+           "pd_stable_dt", "pd_plan_launch_count", "pd_status_string", "pd_last_error_detail",
+           "pd_plan_profile", "pd_plan_profile_read"]
+
+PASS_KINDS = {0: "rows_fwd", 1: "cols_x2", 2: "last_axis", 3: "rows_inv"}
+
+
+class PDError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        lib = load()
+        detail = lib.pd_last_error_detail().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({detail})")
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("dx", ctypes.c_double * 3),
+                ("delta", ctypes.c_double), ("model", ctypes.c_int), ("E", ctypes.c_double),
+                ("nu", ctypes.c_double), ("rho", ctypes.c_double), ("Wc", ctypes.c_double),
+                ("fp64", ctypes.c_int)]
+
+
+def load():
+    """Load ``libpdfft.so`` (built by ``paper_2105_06055_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                           "(run paper_2105_06055_gb300/build.py)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    lib.pd_plan_create.argtypes = [ctypes.POINTER(_Problem), P, P, P, ctypes.POINTER(P)]
+    lib.pd_plan_create.restype = I
+    lib.pd_plan_destroy.argtypes = [P]
+    lib.pd_plan_destroy.restype = None
+    lib.pd_kernel_spectrum.argtypes = [P, P, P]
+    lib.pd_kernel_spectrum.restype = I
+    lib.pd_force.argtypes = [P, P, P, P, P, P]
+    lib.pd_force.restype = I
+    lib.pd_step_verlet.argtypes = [P, P, P, P, P, P, D, I, ctypes.POINTER(I64), P]
+    lib.pd_step_verlet.restype = I
+    lib.pd_solve_static.argtypes = [P, P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D), P]
+    lib.pd_solve_static.restype = I
+    lib.pd_force_adjoint.argtypes = [P, P, P, P, P, P, P]
+    lib.pd_force_adjoint.restype = I
+    lib.pd_damage.argtypes = [P, P, P, P, P]
+    lib.pd_damage.restype = I
+    lib.pd_plan_workspace_bytes.argtypes = [P]
+    lib.pd_plan_workspace_bytes.restype = I64
+    lib.pd_plan_launch_count.argtypes = [P]
+    lib.pd_plan_launch_count.restype = I64
+    lib.pd_stable_dt.argtypes = [P]
+    lib.pd_stable_dt.restype = D
+    lib.pd_plan_profile.argtypes = [P, I]
+    lib.pd_plan_profile.restype = I
+    lib.pd_plan_profile_read.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(I64)]
+    lib.pd_plan_profile_read.restype = I
+    lib.pd_status_string.argtypes = [I]
+    lib.pd_status_string.restype = ctypes.c_char_p
+    lib.pd_last_error_detail.argtypes = []
+    lib.pd_last_error_detail.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(st, where):
+    if st != 0:
+        raise PDError(st, where)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+@dataclass
+class Problem:
+    """Arguments of ``pd_problem`` (grid of Eq. 52, horizon, material)."""
+    shape: Sequence[int]           # (n2, n1) or (n3, n2, n1), C order
+    dx: float | Sequence[float] = 1.0
+    delta: float = 3.0
+    model: int = PD_LIN_BOND
+    E: float = 1.0
+    nu: float = 0.25
+    rho: float = 1.0
+    Wc: float = 0.0
+    fp64: bool = False
+
+    def to_c(self) -> _Problem:
+        p = _Problem()
+        dim = len(self.shape)
+        p.dim = dim
+        n = list(self.shape[::-1]) + [1] * (3 - dim)
+        for a in range(3):
+            p.n[a] = int(n[a])
+        dx = [float(self.dx)] * dim if isinstance(self.dx, (int, float)) else [float(v) for v in self.dx]
+        for a in range(3):
+            p.dx[a] = dx[a] if a < dim else 1.0
+        p.delta = float(self.delta)
+        p.model = int(self.model)
+        p.E, p.nu, p.rho, p.Wc = float(self.E), float(self.nu), float(self.rho), float(self.Wc)
+        p.fp64 = 1 if self.fp64 else 0
+        return p
+
+    @property
+    def dim(self):
+        return len(self.shape)
+
+    @property
+    def dtype(self):
+        return torch.float64 if self.fp64 else torch.float32
+
+
+class Plan:
+    """Owns a ``pd_plan``: spectra, masks and workspace on the current GPU."""
+
+    def __init__(self, problem: Problem, chi: torch.Tensor, chi_omega: Optional[torch.Tensor] = None,
+                 stream=None):
+        lib = load()
+        self.problem = problem
+        self.shape = tuple(int(s) for s in problem.shape)
+        self.dim = len(self.shape)
+        self.dtype = problem.dtype
+        chi = self._mask(chi, self.shape, "chi")
+        if chi_omega is not None:
+            chi_omega = self._mask(chi_omega, (self.dim,) + self.shape, "chi_omega")
+        self._c = problem.to_c()
+        h = ctypes.c_void_p()
+        _check(lib.pd_plan_create(ctypes.byref(self._c), _ptr(chi), _ptr(chi_omega), _stream(stream),
+                                  ctypes.byref(h)), "pd_plan_create")
+        self._h = h
+        self.device = chi.device
+
+    @staticmethod
+    def _mask(t, shape, name):
+        if t.dtype != torch.uint8 or not t.is_cuda or tuple(t.shape) != tuple(shape):
+            raise ValueError(f"{name}: expected a CUDA uint8 tensor of shape {tuple(shape)}")
+        return t.contiguous()
+
+    def _field(self, t, ncomp, name, dtype=None, allow_none=False):
+        if t is None:
+            if allow_none:
+                return None
+            raise ValueError(f"{name} is required")
+        shape = (ncomp,) + self.shape if ncomp else self.shape
+        dt = dtype or self.dtype
+        if t.dtype != dt or not t.is_cuda or tuple(t.shape) != shape or not t.is_contiguous():
+            raise ValueError(f"{name}: expected a contiguous CUDA {dt} tensor of shape {shape}, got "
+                             f"{t.dtype} {tuple(t.shape)} (cuda={t.is_cuda}, contiguous={t.is_contiguous()})")
+        return t
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().pd_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- entry points -------------------------------------------------------
+    def kernel_spectrum(self, stream=None) -> torch.Tensor:
+        nc = 3 if self.dim == 2 else 6
+        half = self.shape[-1] // 2 + 1
+        out = torch.empty((nc,) + self.shape[:-1] + (half,), dtype=torch.float64, device=self.device)
+        _check(load().pd_kernel_spectrum(self._h, _ptr(out), _stream(stream)), "pd_kernel_spectrum")
+        return out
+
+    def force(self, u, s=None, L=None, W=None, want_energy=False, stream=None):
+        u = self._field(u, self.dim, "u")
+        s = self._field(s, 0, "s", allow_none=True)
+        if L is None:
+            L = torch.empty_like(u)
+        L = self._field(L, self.dim, "L")
+        if want_energy and W is None:
+            W = torch.empty(self.shape, dtype=self.dtype, device=u.device)
+        W = self._field(W, 0, "W", allow_none=True)
+        _check(load().pd_force(self._h, _ptr(u), _ptr(s), _ptr(L), _ptr(W), _stream(stream)), "pd_force")
+        return (L, W) if W is not None else L
+
+    def step_verlet(self, u, v, lam, b, w=None, dt=1.0, nsteps=1, count_broken=False, stream=None):
+        u = self._field(u, self.dim, "u")
+        v = self._field(v, self.dim, "v")
+        b = self._field(b, self.dim, "b")
+        w = self._field(w, self.dim, "w", allow_none=True)
+        if lam is not None:
+            lam = self._field(lam, 0, "lambda", dtype=torch.uint8)
+        nb = ctypes.c_int64(0)
+        _check(load().pd_step_verlet(self._h, _ptr(u), _ptr(v), _ptr(lam), _ptr(b), _ptr(w), float(dt),
+                                     int(nsteps), ctypes.byref(nb) if count_broken else None,
+                                     _stream(stream)), "pd_step_verlet")
+        return int(nb.value) if count_broken else None
+
+    def solve_static(self, u, b, w=None, rtol=1e-8, max_iter=20000, stream=None, raise_on_fail=True):
+        u = self._field(u, self.dim, "u", dtype=torch.float64)
+        b = self._field(b, self.dim, "b", dtype=torch.float64)
+        w = self._field(w, self.dim, "w", dtype=torch.float64, allow_none=True)
+        it = ctypes.c_int(0)
+        rr = ctypes.c_double(0.0)
+        st = load().pd_solve_static(self._h, _ptr(u), _ptr(b), _ptr(w), float(rtol), int(max_iter),
+                                    ctypes.byref(it), ctypes.byref(rr), _stream(stream))
+        if st != 0 and (raise_on_fail or st != -5):
+            raise PDError(st, "pd_solve_static")
+        return int(it.value), float(rr.value), st
+
+    def force_adjoint(self, u, gL, s=None, want_gu=True, want_gs=True, stream=None):
+        u = self._field(u, self.dim, "u")
+        gL = self._field(gL, self.dim, "gL")
+        s = self._field(s, 0, "s", allow_none=True)
+        gu = torch.empty_like(u) if want_gu else None
+        gs = torch.empty(self.shape, dtype=self.dtype, device=u.device) if want_gs else None
+        _check(load().pd_force_adjoint(self._h, _ptr(u), _ptr(s), _ptr(gL), _ptr(gu), _ptr(gs),
+                                       _stream(stream)), "pd_force_adjoint")
+        return gu, gs
+
+    def damage(self, lam, stream=None):
+        lam = self._field(lam, 0, "lambda", dtype=torch.uint8)
+        nb = torch.empty(self.shape, dtype=torch.int32, device=lam.device)
+        d = torch.empty(self.shape, dtype=self.dtype, device=lam.device)
+        _check(load().pd_damage(self._h, _ptr(lam), _ptr(nb), _ptr(d), _stream(stream)), "pd_damage")
+        return nb, d
+
+    def profile(self, enable: bool = True):
+        _check(load().pd_plan_profile(self._h, 1 if enable else 0), "pd_plan_profile")
+
+    def profile_read(self):
+        """{pass kind: (total ms, launches)} since the last profile() call."""
+        out = {}
+        for k, name in PASS_KINDS.items():
+            ms = ctypes.c_double(0.0)
+            n = ctypes.c_int64(0)
+            _check(load().pd_plan_profile_read(self._h, k, ctypes.byref(ms), ctypes.byref(n)),
+                   "pd_plan_profile_read")
+            out[name] = (float(ms.value), int(n.value))
+        return out
+
+    @property
+    def workspace_bytes(self):
+        return int(load().pd_plan_workspace_bytes(self._h))
+
+    @property
+    def launch_count(self):
+        return int(load().pd_plan_launch_count(self._h))
+
+    @property
+    def stable_dt(self):
+        return float(load().pd_stable_dt(self._h))

@@ -1,0 +1,227 @@
+"""GPU parity of the static solver, the Verlet/damage driver, the adjoint and the
+damage counts against the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2105_06055_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda")
+
+
+@pytest.fixture(scope="module")
+def pdm():
+    from paper_2105_06055_gb300 import build, pd
+    build.build()
+    pd.load()
+    return pd
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _t(a, dt=torch.float64):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dt, device=DEV)
+
+
+# --------------------------------------------------------------------------
+# Static solve (Eq. 85-89)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("fp64", [False, True])
+@pytest.mark.parametrize("nu", [0.25, 0.4])
+def test_static_cube_with_cavity_small(pdm, oracle, fp64, nu):
+    cfg = inputs.cube_with_cavity(n=32, radius_frac=0.2)
+    shape = cfg["shape"]
+    prob = pdm.Problem(shape=shape, delta=3.0, model=pdm.PD_LIN_STATE, nu=nu, fp64=fp64)
+    plan = pdm.Plan(prob, _t(cfg["chi"], torch.uint8), _t(cfg["chi_omega"], torch.uint8))
+    u = torch.zeros((3,) + shape, dtype=torch.float64, device=DEV)
+    it, rel, st = plan.solve_static(u, _t(cfg["b"]), None, rtol=1e-8, max_iter=5000)
+    assert st == 0 and rel <= 1e-8 and it > 0
+    ug = u.cpu().numpy()
+    ka, cb, _ = oracle.lps_constants(1.0, nu, 1.0, 3.0)
+    op = ("lps", ka, cb)
+    res = oracle.static_residual(ug, cfg["chi"], cfg["chi_omega"], cfg["b"], 1.0, 3.0, op)
+    bn = np.linalg.norm(cfg["chi_omega"] * cfg["b"])
+    assert np.linalg.norm(res) / bn <= 1.5e-8
+    uo, _, relo = oracle.cg_static(cfg["chi"], cfg["chi_omega"], cfg["b"], cfg["w"], 1.0, 3.0, op, rtol=1e-12)
+    assert relo < 1e-11
+    assert _rel(ug, uo) < 2e-6
+    assert np.all(ug[:, cfg["chi_omega"][0] == 0] == 0)
+    plan.close()
+
+
+def test_static_2d_bond_fp64_with_prescribed_w(pdm, oracle):
+    shape = (64, 64)
+    chi = inputs.box_mask(shape, (4, 4), (60, 56))
+    x1, x2 = inputs.coords(shape)
+    co = chi.copy()
+    co[(x1 >= 4) & (x1 < 7)] = 0
+    w = np.zeros((2,) + shape)
+    w[1][(x1 >= 4) & (x1 < 7) & (chi == 1)] = 1e-3  # prescribed shear on Gamma
+    b = np.zeros((2,) + shape)
+    b[0][(x1 >= 57) & (x1 < 60) & (chi == 1)] = 1e-3 / 3
+    plan = pdm.Plan(pdm.Problem(shape=shape, delta=3.0, fp64=True), _t(chi, torch.uint8),
+                    _t(np.stack([co, co]), torch.uint8))
+    u = torch.zeros((2,) + shape, dtype=torch.float64, device=DEV)
+    it, rel, st = plan.solve_static(u, _t(b), _t(w), rtol=1e-10, max_iter=20000)
+    assert st == 0 and rel <= 1e-10
+    alpha = oracle.alpha_bond(2, 1.0, 3.0)
+    uo, _, _ = oracle.cg_static(chi, np.stack([co, co]), b, w, 1.0, 3.0, ("bond", alpha), rtol=1e-13)
+    assert _rel(u.cpu().numpy(), uo) < 1e-8
+    plan.close()
+
+
+def test_static_config2_full_size(pdm, oracle):
+    """128^3 cube with spherical cavity, FP32 FFTs + FP64 refinement to 1e-8;
+    the returned u is checked with the oracle's FP64 operator."""
+    cfg = inputs.cube_with_cavity(n=128)
+    shape = cfg["shape"]
+    prob = pdm.Problem(shape=shape, delta=3.0, model=pdm.PD_LIN_STATE, nu=0.25, fp64=False)
+    plan = pdm.Plan(prob, _t(cfg["chi"], torch.uint8), _t(cfg["chi_omega"], torch.uint8))
+    u = torch.zeros((3,) + shape, dtype=torch.float64, device=DEV)
+    it, rel, st = plan.solve_static(u, _t(cfg["b"]), None, rtol=1e-8, max_iter=20000)
+    assert st == 0 and rel <= 1e-8
+    ka, cb, _ = oracle.lps_constants(1.0, 0.25, 1.0, 3.0)
+    res = oracle.static_residual(u.cpu().numpy(), cfg["chi"], cfg["chi_omega"], cfg["b"], 1.0, 3.0,
+                                 ("lps", ka, cb))
+    bn = np.linalg.norm(cfg["chi_omega"] * cfg["b"])
+    assert np.linalg.norm(res) / bn <= 1.5e-8
+    plan.close()
+
+
+# --------------------------------------------------------------------------
+# Dynamics with bond breaking (Eq. 63, 83-84, 101-102)
+# --------------------------------------------------------------------------
+
+def _plate(n1=128, n2=64, delta=3.0):
+    cfg = inputs.notched_plate(n1=n1, n2=n2, delta=delta, sigma=1.0)
+    return cfg
+
+
+@pytest.mark.parametrize("fp64", [True, False])
+def test_verlet_damage_matches_oracle(pdm, oracle, fp64):
+    cfg = _plate()
+    shape, delta = cfg["shape"], cfg["delta"]
+    alpha = oracle.alpha_bond(2, 1.0, delta)
+    wc = oracle.wc_from_stretch(2, 1.0, delta, alpha, 1e-3)
+    sigma = 0.25 * math.sqrt(wc)  # strong enough to break bonds within the run
+    b = cfg["b"] * sigma
+    dt = 0.5 * 2 * math.sqrt(1.0 / max(np.linalg.eigvalsh(oracle.symbol_bond(shape, 1.0, delta, alpha, (k, k))).max()
+                                        for k in range(0, 25)))
+    nsteps = 60
+    uo, vo, lo, flo = oracle.verlet_damage(np.zeros((2,) + shape), np.zeros((2,) + shape), cfg["lam"], cfg["chi"],
+                                           cfg["chi_omega"], b, cfg["w"], 1.0, delta, alpha, 1.0, dt, wc, nsteps)
+    assert flo > 0
+    dtp = torch.float64 if fp64 else torch.float32
+    plan = pdm.Plan(pdm.Problem(shape=shape, delta=delta, rho=1.0, Wc=wc, fp64=fp64), _t(cfg["chi"], torch.uint8))
+    u = torch.zeros((2,) + shape, dtype=dtp, device=DEV)
+    v = torch.zeros_like(u)
+    lam = _t(cfg["lam"], torch.uint8)
+    nb = plan.step_verlet(u, v, lam, _t(b, dtp), None, dt=dt, nsteps=nsteps, count_broken=True)
+    lg = lam.cpu().numpy()
+    if fp64:
+        assert np.array_equal(lg, lo) and nb == flo
+        assert _rel(u.cpu().numpy(), uo) < 1e-10 and _rel(v.cpu().numpy(), vo) < 1e-10
+    else:
+        # chaotic after the first differing flip: compare the count loosely here;
+        # the per-step test below checks decisions bit for bit
+        assert abs(nb - flo) <= max(2, 0.1 * flo)
+    plan.close()
+
+
+def test_verlet_fp32_per_step_decisions(pdm, oracle):
+    """From identical states, one FP32 step takes the same lambda decisions as
+    the FP64 oracle on every node whose W is not within 1e-4 Wc of the threshold."""
+    cfg = _plate()
+    shape, delta = cfg["shape"], cfg["delta"]
+    alpha = oracle.alpha_bond(2, 1.0, delta)
+    g = inputs.rng(5)
+    u = (g.normal(size=(2,) + shape) * 2e-3 + inputs.sine_modes(shape, 4, 5e-3, 3, 2)) * cfg["chi"]
+    u = u.astype(np.float32).astype(np.float64)
+    v = np.zeros_like(u)
+    lam = cfg["lam"]
+    W = oracle.energy_bond(u, cfg["chi"], 1.0, delta, alpha, lam=lam)
+    wc = float(np.median(W[(cfg["chi"] == 1) & (lam == 1)]))
+    dt = 0.05
+    b = np.zeros_like(u)
+    _, _, lo, flo = oracle.verlet_damage(u, v, lam, cfg["chi"], cfg["chi_omega"], b, b, 1.0, delta, alpha, 1.0, dt,
+                                         wc, 1)
+    plan = pdm.Plan(pdm.Problem(shape=shape, delta=delta, rho=1.0, Wc=wc, fp64=False), _t(cfg["chi"], torch.uint8))
+    ut, vt = _t(u, torch.float32), _t(v, torch.float32)
+    lt = _t(lam, torch.uint8)
+    plan.step_verlet(ut, vt, lt, _t(b, torch.float32), None, dt=dt, nsteps=1)
+    lg = lt.cpu().numpy()
+    clear = np.abs(W - wc) > 1e-4 * wc
+    assert np.array_equal(lg[clear], lo[clear])
+    assert np.sum(lg != lo) <= np.sum(~clear)
+    plan.close()
+
+
+def test_verlet_energy_conservation_gpu(pdm, oracle):
+    shape = (64, 64)
+    chi = inputs.box_mask(shape, (4, 4), (60, 60))
+    delta = 3.0
+    alpha = oracle.alpha_bond(2, 1.0, delta)
+    u0 = inputs.sine_modes(shape, 3, 1e-3, 2, 5) * chi
+    plan = pdm.Plan(pdm.Problem(shape=shape, delta=delta, rho=1.0, fp64=True), _t(chi, torch.uint8))
+    dt = 0.1 * plan.stable_dt
+    u = _t(u0)
+    v = torch.zeros_like(u)
+    z = torch.zeros_like(u)
+
+    def energy(uu, vv):
+        W = oracle.energy_bond(uu, chi, 1.0, delta, alpha)
+        return 0.5 * np.sum(vv * vv) + 0.5 * W.sum()
+
+    e0 = energy(u0, np.zeros_like(u0))
+    plan.step_verlet(u, v, None, z, None, dt=dt, nsteps=200)
+    e1 = energy(u.cpu().numpy(), v.cpu().numpy())
+    assert abs(e1 / e0 - 1) < 1e-3
+    plan.close()
+
+
+def test_damage_counts_exact(pdm, oracle):
+    cfg = _plate(n1=64, n2=32, delta=4.0)
+    g = inputs.rng(3)
+    lam = cfg["lam"].copy()
+    lam[g.random(cfg["shape"]) < 0.05] = 0
+    nbo, _, do = oracle.damage(cfg["chi"], lam, 1.0, 4.0)
+    for fp64 in (True, False):
+        plan = pdm.Plan(pdm.Problem(shape=cfg["shape"], delta=4.0, fp64=fp64), _t(cfg["chi"], torch.uint8))
+        nb, d = plan.damage(_t(lam, torch.uint8))
+        assert np.array_equal(nb.cpu().numpy(), nbo)
+        assert np.allclose(d.double().cpu().numpy(), do, rtol=1e-6, atol=0)
+        plan.close()
+
+
+# --------------------------------------------------------------------------
+# Adjoint
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("fp64", [True, False])
+def test_force_adjoint(pdm, oracle, dim, fp64):
+    shape = (64, 64) if dim == 2 else (16, 32, 32)
+    delta = 3.0
+    g = inputs.rng(13)
+    lo = (4,) * dim
+    hi = tuple(s - 4 for s in shape[::-1])
+    chi = inputs.box_mask(shape, lo, hi)
+    s = inputs.smooth_positive_field(shape, 3) ** 0.5
+    u = inputs.sine_modes(shape, 4, 1e-2, 3, 1)
+    pvec = g.normal(size=(dim,) + shape)
+    alpha = oracle.alpha_bond(dim, 1.0, delta)
+    gs_ref = oracle.force_bond_grad_s(u, pvec, chi, 1.0, delta, alpha, s=s)
+    gu_ref = oracle.force_bond(pvec, chi, 1.0, delta, alpha, s=s)
+    dtp = torch.float64 if fp64 else torch.float32
+    plan = pdm.Plan(pdm.Problem(shape=shape, delta=delta, fp64=fp64), _t(chi, torch.uint8))
+    gu, gs = plan.force_adjoint(_t(u, dtp), _t(pvec, dtp), s=_t(s, dtp))
+    tol = 1e-11 if fp64 else 2e-5
+    assert _rel(gu.double().cpu().numpy(), gu_ref) < tol
+    assert _rel(gs.double().cpu().numpy(), gs_ref) < tol
+    plan.close()

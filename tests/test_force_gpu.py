@@ -1,0 +1,194 @@
+"""GPU parity of pd_force against the FP64 direct-sum oracle (element by element).
+
+Tolerances: FP64 path 1e-11 relative L2 (rounding of an exact reorganisation
+of the same quadrature, Eq. 55); FP32 path 1e-5 relative L2 (the force
+tolerance of the FP32 path).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2105_06055_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-11
+FP32_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def pdm():
+    from paper_2105_06055_gb300 import build, pd
+    build.build()
+    pd.load()
+    return pd
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _run_force(pdm, shape, chi, u, delta, fp64, s=None, model=0, nu=0.25, E=1.0, energy=False, dx=1.0):
+    dev = torch.device("cuda")
+    prob = pdm.Problem(shape=shape, dx=dx, delta=delta, model=model, E=E, nu=nu, fp64=fp64)
+    plan = pdm.Plan(prob, torch.tensor(chi, device=dev))
+    dt = torch.float64 if fp64 else torch.float32
+    ut = torch.tensor(u, dtype=dt, device=dev)
+    st = None if s is None else torch.tensor(s, dtype=dt, device=dev)
+    out = plan.force(ut, s=st, want_energy=energy)
+    torch.cuda.synchronize()
+    plan.close()
+    if energy:
+        return out[0].double().cpu().numpy(), out[1].double().cpu().numpy()
+    return out.double().cpu().numpy()
+
+
+def test_plate_2d_single_eval_fp64(pdm, oracle):
+    """2D bond force, 128^2 box, 96^2 body, delta = 3, sine modes + affine field, FP64."""
+    cfg = inputs.plate_2d_single_eval(n=128, margin=16, seed=0)
+    alpha = oracle.alpha_bond(2, 1.0, 3.0)
+    ref = oracle.force_bond(cfg["u"], cfg["chi"], 1.0, 3.0, alpha)
+    L = _run_force(pdm, cfg["shape"], cfg["chi"], cfg["u"], 3.0, True)
+    assert _rel(L, ref) < FP64_TOL
+    assert np.all(L[:, cfg["chi"] == 0] == 0)
+
+
+def _conditioning(oracle, shape, chi, u, L, delta, alpha):
+    """kappa = ||chi u||_2 lam_max / ||L||_2: the FP32 FFT-convolution error is
+    about eps32 * kappa (round-off of the transforms scales with the input norm
+    times the largest kernel eigenvalue, the output with ||L||)."""
+    lam = 0.0
+    for a in range(0, shape[-1] // 2 + 1, 4):
+        for b in range(0, shape[-2] // 2 + 1, 4):
+            lam = max(lam, float(np.linalg.eigvalsh(oracle.symbol_bond(shape, 1.0, delta, alpha, (a, b))).max()))
+    return float(np.linalg.norm(chi * u) * lam / np.linalg.norm(L))
+
+
+def test_plate_2d_single_eval_fp32(pdm, oracle):
+    """Same input on the FP32 path. Its affine part makes kappa ~ 440, so the
+    error bound is 4 eps32 kappa; the sine (deformation) part alone, kappa ~ 36,
+    meets the 1e-5 force tolerance."""
+    cfg = inputs.plate_2d_single_eval(n=128, margin=16, seed=0)
+    alpha = oracle.alpha_bond(2, 1.0, 3.0)
+    ref = oracle.force_bond(cfg["u"], cfg["chi"], 1.0, 3.0, alpha)
+    kappa = _conditioning(oracle, cfg["shape"], cfg["chi"], cfg["u"], ref, 3.0, alpha)
+    L = _run_force(pdm, cfg["shape"], cfg["chi"], cfg["u"], 3.0, False)
+    assert _rel(L, ref) < 4 * 2.0 ** -24 * kappa
+    us = inputs.sine_modes(cfg["shape"], 8, 1e-3, 4, 0)
+    refs = oracle.force_bond(us, cfg["chi"], 1.0, 3.0, alpha)
+    Ls = _run_force(pdm, cfg["shape"], cfg["chi"], us, 3.0, False)
+    assert _rel(Ls, refs) < FP32_TOL
+
+
+@pytest.mark.parametrize("shape,delta,dx", [((16, 32), 2.0, 1.0), ((64, 32), 3.0, 1.0),
+                                            ((32, 128), 4.5, (1.0, 1.2)), ((256, 64), 5.0, 1.0)])
+@pytest.mark.parametrize("fp64", [True, False])
+def test_bond_2d_ragged(pdm, oracle, shape, delta, dx, fp64):
+    g = inputs.rng(7)
+    n2, n1 = shape
+    r1 = int(delta / (dx if np.isscalar(dx) else dx[0])) + 1
+    r2 = int(delta / (dx if np.isscalar(dx) else dx[1])) + 1
+    chi = inputs.box_mask(shape, (r1, r2), (n1 - r1, n2 - r2))
+    chi[g.random(shape) < 0.1] = 0
+    u = g.normal(size=(2,) + shape)
+    alpha = oracle.alpha_bond(2, 1.0, delta)
+    ref = oracle.force_bond(u, chi, dx, delta, alpha)
+    L = _run_force(pdm, shape, chi, u, delta, fp64, dx=dx)
+    assert _rel(L, ref) < (FP64_TOL if fp64 else FP32_TOL)
+
+
+@pytest.mark.parametrize("shape", [(16, 16, 32), (32, 32, 32), (16, 64, 32)])
+@pytest.mark.parametrize("fp64", [True, False])
+def test_bond_3d(pdm, oracle, shape, fp64):
+    g = inputs.rng(11)
+    n3, n2, n1 = shape
+    delta = 3.0
+    chi = inputs.box_mask(shape, (4, 4, 4), (n1 - 4, n2 - 4, n3 - 4))
+    chi[g.random(shape) < 0.05] = 0
+    u = g.normal(size=(3,) + shape)
+    alpha = oracle.alpha_bond(3, 1.0, delta)
+    ref = oracle.force_bond(u, chi, 1.0, delta, alpha)
+    L = _run_force(pdm, shape, chi, u, delta, fp64)
+    assert _rel(L, ref) < (FP64_TOL if fp64 else FP32_TOL)
+
+
+@pytest.mark.parametrize("fp64", [True, False])
+def test_bond_weighted_and_energy(pdm, oracle, fp64):
+    """Node weight s (bond factor s s', Eq. 100 with s in place of lambda) and W (Eq. 102)."""
+    shape = (64, 64)
+    g = inputs.rng(3)
+    chi = inputs.box_mask(shape, (5, 5), (59, 59))
+    s = 0.5 + g.random(shape)
+    u = inputs.sine_modes(shape, 6, 1e-2, 5, 4)
+    alpha = oracle.alpha_bond(2, 1.0, 4.0)
+    ref = oracle.force_bond(u, chi, 1.0, 4.0, alpha, s=s)
+    L = _run_force(pdm, shape, chi, u, 4.0, fp64, s=s)
+    assert _rel(L, ref) < (FP64_TOL if fp64 else FP32_TOL)
+    lam = (g.random(shape) < 0.9).astype(np.uint8)
+    Wref = oracle.energy_bond(u, chi, 1.0, 4.0, alpha, lam=lam)
+    Lref = oracle.force_bond(u, chi, 1.0, 4.0, alpha, s=lam.astype(float))
+    L2, W = _run_force(pdm, shape, chi, u, 4.0, fp64, s=lam.astype(float), energy=True)
+    assert _rel(L2, Lref) < (FP64_TOL if fp64 else FP32_TOL)
+    assert _rel(W, Wref) < (FP64_TOL if fp64 else 1e-4)
+
+
+@pytest.mark.parametrize("nu", [0.25, 0.4])
+@pytest.mark.parametrize("fp64", [True, False])
+def test_state_based_3d(pdm, oracle, nu, fp64):
+    shape = (32, 32, 32)
+    delta = 3.0
+    g = inputs.rng(21)
+    chi = inputs.box_mask(shape, (4, 4, 4), (28, 28, 28))
+    x1, x2, x3 = inputs.coords(shape)
+    chi[(x1 - 15.5) ** 2 + (x2 - 15.5) ** 2 + (x3 - 15.5) ** 2 < 36] = 0
+    u = inputs.sine_modes(shape, 4, 1e-3, 3, 9)
+    ka, cb, _ = oracle.lps_constants(1.0, nu, 1.0, delta)
+    ref = oracle.force_lps(u, chi, 1.0, delta, ka, cb)
+    L = _run_force(pdm, shape, chi, u, delta, fp64, model=1, nu=nu)
+    assert _rel(L, ref) < (FP64_TOL if fp64 else FP32_TOL)
+
+
+def test_kernel_spectrum_matches_symbol(pdm, oracle):
+    shape = (32, 64)
+    dev = torch.device("cuda")
+    delta = 3.5
+    chi = inputs.box_mask(shape, (4, 4), (60, 28))
+    plan = pdm.Plan(pdm.Problem(shape=shape, delta=delta, fp64=True), torch.tensor(chi, device=dev))
+    K = plan.kernel_spectrum().cpu().numpy()
+    alpha = oracle.alpha_bond(2, 1.0, delta)
+    P = K[:, 0, 0]
+    for k1, k2 in [(0, 0), (3, 0), (0, 5), (7, 29), (32, 16), (1, 31)]:
+        M = oracle.symbol_bond(shape, 1.0, delta, alpha, (k1, k2))
+        Kk = K[:, k2, k1]
+        Mg = np.array([[P[0] - Kk[0], P[2] - Kk[2]], [P[2] - Kk[2], P[1] - Kk[1]]])
+        assert np.allclose(Mg, M, rtol=1e-12, atol=1e-14)
+    # stable step: 2 sqrt(rho / max eig), max over the symbol
+    lmax = max(np.linalg.eigvalsh(oracle.symbol_bond(shape, 1.0, delta, alpha, (a, b))).max()
+               for a in range(0, 33) for b in range(0, 32))
+    assert abs(plan.stable_dt / (2 * math.sqrt(1.0 / lmax)) - 1) < 1e-9
+    plan.close()
+
+
+def test_config2_force_full_size_fp32(pdm, oracle):
+    """Full 128^3 workload geometry (cube with spherical cavity, delta = 3,
+    nu = 0.25) in the launch configuration the benchmark uses, FP32 vs oracle."""
+    cfg = inputs.cube_with_cavity(n=128)
+    shape = cfg["shape"]
+    u = inputs.sine_modes(shape, 6, 1e-3, 3, 5)
+    ka, cb, _ = oracle.lps_constants(1.0, 0.25, 1.0, 3.0)
+    ref = oracle.force_lps(u, cfg["chi"], 1.0, 3.0, ka, cb)
+    L = _run_force(pdm, shape, cfg["chi"], u, 3.0, False, model=1, nu=0.25)
+    assert _rel(L, ref) < FP32_TOL
+
+
+def test_rejects_bad_masks(pdm):
+    dev = torch.device("cuda")
+    shape = (32, 32)
+    chi = np.ones(shape, dtype=np.uint8)  # touches the box faces
+    with pytest.raises(pdm.PDError):
+        pdm.Plan(pdm.Problem(shape=shape, delta=3.0), torch.tensor(chi, device=dev))
+    with pytest.raises(pdm.PDError):
+        pdm.Plan(pdm.Problem(shape=(24, 32), delta=3.0),
+                 torch.tensor(np.zeros((24, 32), np.uint8), device=dev))
