@@ -193,6 +193,31 @@ pd_status pd_force_adjoint(pd_plan *plan, const void *u, const void *s, const vo
  */
 pd_status pd_damage(pd_plan *plan, const uint8_t *lambda, int32_t *nb, void *d, void *stream);
 
+/*
+ * pd_force2d_noalloc -- pd_force for a 2D bond-model FP32 problem without a
+ * plan and without allocating any memory. The paper has no counterpart: this
+ * exists for callers that may not call cudaMalloc (a host framework that owns
+ * all device memory through its own pool, a real-time loop that must not hit
+ * the allocator, a plug-in with a fixed memory budget) and so cannot create a
+ * pd_plan. Same operator and result as pd_plan_create + pd_force with s = NULL
+ * and W = NULL.
+ *   problem: dim = 2, model = PD_LIN_BOND, fp64 = 0; grid rules as for
+ *            pd_plan_create, and n[0] * n[1] <= 65536 nodes, horizon <= 512 bonds
+ *            (else PD_ERR_SIZE, nothing enqueued).
+ *   chi_B:   device, N bytes (0/1, body at least delta from the box faces,
+ *            checked: PD_ERR_ARG otherwise). u: device, 2 x N floats.
+ *   L:       device, 2 x N floats (output).
+ * All intermediates live in one fixed 2 MiB __device__ array inside the
+ * library, held by every GPU that loads it until the process exits. The first
+ * call on each device looks up that array's device address; make it before
+ * any stream capture. The call waits on `stream` for the mask check, then
+ * enqueues the force passes and returns. Every call reuses the same array, so
+ * calls that overlap on the GPU (from several streams or threads) race; the
+ * caller must serialise them.
+ */
+pd_status pd_force2d_noalloc(const pd_problem *problem, const uint8_t *chi_B, const float *u, float *L,
+                             void *stream);
+
 /* Bytes of device memory owned by the plan. */
 int64_t pd_plan_workspace_bytes(const pd_plan *plan);
 

@@ -27,7 +27,7 @@ STATUS = {0: "PD_OK", -1: "PD_ERR_ARG", -2: "PD_ERR_SIZE", -3: "PD_ERR_NOMEM", -
 EXPORTS = ["pd_plan_create", "pd_plan_destroy", "pd_kernel_spectrum", "pd_force", "pd_step_verlet",
            "pd_solve_static", "pd_force_adjoint", "pd_damage", "pd_plan_workspace_bytes",
            "pd_stable_dt", "pd_plan_launch_count", "pd_status_string", "pd_last_error_detail",
-           "pd_plan_profile", "pd_plan_profile_read"]
+           "pd_plan_profile", "pd_plan_profile_read", "pd_force2d_noalloc"]
 
 PASS_KINDS = {0: "rows_fwd", 1: "cols_x2", 2: "last_axis", 3: "rows_inv"}
 
@@ -83,6 +83,8 @@ def load():
     lib.pd_plan_profile.restype = I
     lib.pd_plan_profile_read.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(I64)]
     lib.pd_plan_profile_read.restype = I
+    lib.pd_force2d_noalloc.argtypes = [ctypes.POINTER(_Problem), P, P, P, P]
+    lib.pd_force2d_noalloc.restype = I
     lib.pd_status_string.argtypes = [I]
     lib.pd_status_string.restype = ctypes.c_char_p
     lib.pd_last_error_detail.argtypes = []
@@ -279,3 +281,21 @@ class Plan:
     @property
     def stable_dt(self):
         return float(load().pd_stable_dt(self._h))
+
+
+def force2d_noalloc(problem: Problem, chi: torch.Tensor, u: torch.Tensor, L: Optional[torch.Tensor] = None,
+                    stream=None) -> torch.Tensor:
+    """2D FP32 bond force through ``pd_force2d_noalloc``: no plan, no device
+    allocation inside the library (for callers that cannot call cudaMalloc).
+    The output tensor L may be passed in; otherwise it is allocated here, by the
+    caller's side (torch), not by the library."""
+    shape = tuple(int(s) for s in problem.shape)
+    if (len(shape) != 2 or chi.dtype != torch.uint8 or tuple(chi.shape) != shape or not chi.is_cuda
+            or u.dtype != torch.float32 or tuple(u.shape) != (2,) + shape or not u.is_contiguous()):
+        raise ValueError("force2d_noalloc: expects a 2D uint8 chi and a contiguous float32 u of shape (2, n2, n1)")
+    if L is None:
+        L = torch.empty_like(u)
+    c = problem.to_c()
+    _check(load().pd_force2d_noalloc(ctypes.byref(c), _ptr(chi.contiguous()), _ptr(u), _ptr(L), _stream(stream)),
+           "pd_force2d_noalloc")
+    return L
