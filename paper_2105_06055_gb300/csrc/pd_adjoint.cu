@@ -23,7 +23,8 @@ namespace {
 template <typename T, int D>
 struct ProAdj {
     static constexpr int NC = Sym<D>::n;
-    static constexpr int kFin = 0, kFout = 2 * D + NC;
+    static constexpr int kFin = 0, kFout = 2 * D + NC, kNF = 0, kNB = 0, kStage = 0;
+    static constexpr bool kSparse = false;
     const T *u, *pv, *s;
     const uint8_t *chi;
     int64_t N;
@@ -32,7 +33,18 @@ struct ProAdj {
     int64_t fstride;
     __device__ const cx<T> *spec_in(int) const { return nullptr; }
     __device__ cx<T> *spec_out(int f) const { return spec + f * fstride; }
-    __device__ __forceinline__ void node(int64_t row, int i1, const T *, T *out) const
+    __device__ const T *nf_src(int) const { return nullptr; }
+    __device__ const uint8_t *nb_src(int) const { return nullptr; }
+    __device__ void sparse(const RowCtx<T> &, int, int) const {}
+    __device__ void emit(const RowCtx<T> &, int, int, const T *, const T *, DSum &) const {}
+    __device__ void block_done(DSum &) const {}
+    __device__ __forceinline__ void node2(const RowCtx<T> &c, int rl, int i1, const T *, const T *, T *o0,
+                                          T *o1) const
+    {
+        node(c.row0 + rl, i1, o0);
+        node(c.row0 + rl, i1 + 1, o1);
+    }
+    __device__ __forceinline__ void node(int64_t row, int i1, T *out) const
     {
         const int64_t q = row * n1 + i1;
         T v = chi[q] ? T(1) : T(0);
@@ -59,12 +71,10 @@ struct CombAdj {
     static constexpr int kFin = 2 * D + NC, kFout = 2 * D + 1, kMode = 2, kPre = 0;
     static constexpr bool kStoreIn = false;
     Model<T> m;
-    cx<T> *spec;
-    int64_t fstride;
     int obase;  // first output slot (out of place in 3D)
-    __device__ const cx<T> *spec_in(int f) const { return spec + f * fstride; }
-    __device__ cx<T> *spec_out(int f) const { return spec + (obase + f) * fstride; }
-    __device__ cx<T> *spec_aux(int) const { return nullptr; }
+    __device__ int slot_in(int f) const { return f; }
+    __device__ int slot_out(int f) const { return obase + f; }
+    __device__ int slot_aux(int) const { return 0; }
     __device__ __forceinline__ void combine(int kx, int ky, int kz, const cx<T> *in, cx<T> *out) const
     {
         T M[9];
@@ -85,7 +95,8 @@ struct CombAdj {
 template <typename T, int D>
 struct EpiAdj {
     static constexpr int NC = Sym<D>::n;
-    static constexpr int kFin = 2 * D + 1, kFout = 0;
+    static constexpr int kFin = 2 * D + 1, kFout = 0, kNF = 0, kNB = 0, kStage = 0;
+    static constexpr bool kSparse = false;
     const T *u, *pv, *s, *G;
     const uint8_t *chi;
     T *gu, *gs;
@@ -95,7 +106,18 @@ struct EpiAdj {
     int64_t fstride;
     __device__ const cx<T> *spec_in(int f) const { return spec + f * fstride; }
     __device__ cx<T> *spec_out(int) const { return nullptr; }
-    __device__ __forceinline__ void node(int64_t row, int i1, const T *in, T *) const
+    __device__ const T *nf_src(int) const { return nullptr; }
+    __device__ const uint8_t *nb_src(int) const { return nullptr; }
+    __device__ void sparse(const RowCtx<T> &, int, int) const {}
+    __device__ void emit(const RowCtx<T> &, int, int, const T *, const T *, DSum &) const {}
+    __device__ void block_done(DSum &) const {}
+    __device__ __forceinline__ void node2(const RowCtx<T> &c, int rl, int i1, const T *in0, const T *in1, T *,
+                                          T *) const
+    {
+        node(c.row0 + rl, i1, in0);
+        node(c.row0 + rl, i1 + 1, in1);
+    }
+    __device__ __forceinline__ void node(int64_t row, int i1, const T *in) const
     {
         const int64_t q = row * n1 + i1;
         const bool inb = chi[q] != 0;
@@ -142,14 +164,14 @@ pd_status adjoint_pipeline(pd_plan *p, const T *u, const T *s, const T *pv, cons
     const int64_t fs = p->N / 2;
     constexpr int FI = 2 * D + Sym<D>::n, FO = 2 * D + 1;
     ProAdj<T, D> pro{u, pv, s, p->chi, p->N, p->n1, spec, fs};
-    PD_TRY(launch_rows<T>(p, pro, FI, st));
-    if (D == 3) PD_TRY((col_pass<T, FI>(p, spec, false, st)));
+    PD_TRY(launch_rows<T>(p, pro, st));
+    if (D == 3) PD_TRY((col_pass<T, FI>(p, 0, false, st)));
     const int ob = D == 3 ? FI : 0;
-    CombAdj<T, D> cmb{model_view<T>(p), spec, fs, ob};
+    CombAdj<T, D> cmb{model_view<T>(p), ob};
     PD_TRY(launch_cols<T>(p, cmb, D == 3 ? 2 : 1, true, FI, st));
-    if (D == 3) PD_TRY((col_pass<T, FO>(p, spec + ob * fs, true, st)));
+    if (D == 3) PD_TRY((col_pass<T, FO>(p, ob, true, st)));
     EpiAdj<T, D> epi{u, pv, s, G, p->chi, gu, gs, p->N, p->n1, spec + ob * fs, fs};
-    PD_TRY(launch_rows<T>(p, epi, FO, st));
+    PD_TRY(launch_rows<T>(p, epi, st));
     return PD_OK;
 }
 

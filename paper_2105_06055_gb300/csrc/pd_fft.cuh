@@ -28,6 +28,7 @@
 #pragma once
 
 #include "pd_common.cuh"
+#include "pd_tma.cuh"
 
 namespace pd {
 
@@ -90,7 +91,7 @@ __device__ __forceinline__ void dft_reg(cx<T> *v)
 // tw[i] = e^{-2 pi i i / 2^lgl}. Ends with a block-wide barrier.
 template <typename T, int R>
 __device__ __forceinline__ void fft_stage(cx<T> *s, int stride, int n, int ns, int lgnsr, int jt,
-                                          int nt, const cx<T> *__restrict__ tw, int lgl)
+                                          int nt, const cx<T> *__restrict__ tw, int lgl, bool cin, bool cout)
 {
     constexpr int B = 16 / R;
     cx<T> v[16];
@@ -99,7 +100,10 @@ __device__ __forceinline__ void fft_stage(cx<T> *s, int stride, int n, int ns, i
     for (int b = 0; b < B; ++b) {
         const int j = jt + b * nt;
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[b * R + r] = s[(j + r * q) * stride];
+        for (int r = 0; r < R; ++r) {
+            const cx<T> x = s[(j + r * q) * stride];
+            v[b * R + r] = cin ? conjg(x) : x;
+        }
     }
     __syncthreads();
 #pragma unroll
@@ -113,30 +117,70 @@ __device__ __forceinline__ void fft_stage(cx<T> *s, int stride, int n, int ns, i
         dft_reg<T, R>(&v[b * R]);
         const int o = (j - k) * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) s[(o + r * ns) * stride] = v[b * R + r];
+        for (int r = 0; r < R; ++r) s[(o + r * ns) * stride] = cout ? conjg(v[b * R + r]) : v[b * R + r];
     }
     __syncthreads();
 }
 
-// Forward DFT of length 2^lgn (>= 16) in shared memory, in place.
+// Forward DFT of length 2^lgn (>= 16) in shared memory, in place. With cin the
+// input is conjugated as it is read, with cout the output as it is written
+// (IDFT(x) = conj(DFT(conj(x))) costs no extra pass).
 template <typename T>
 __device__ __forceinline__ void fft_smem(cx<T> *s, int stride, int lgn, int jt,
-                                         const cx<T> *__restrict__ tw, int lgl)
+                                         const cx<T> *__restrict__ tw, int lgl, bool cin = false,
+                                         bool cout = false)
 {
     const int n = 1 << lgn, nt = n >> 4;
     int ns = 1, lgns = 0, rem = lgn;
     while (rem > 0) {
         const int lr = rem >= 4 ? 4 : rem;
+        const bool first = (lgns == 0), last = (rem == lr);
+        const bool ci = cin && first, co = cout && last;
         switch (lr) {
-            case 4: fft_stage<T, 16>(s, stride, n, ns, lgns + 4, jt, nt, tw, lgl); break;
-            case 3: fft_stage<T, 8>(s, stride, n, ns, lgns + 3, jt, nt, tw, lgl); break;
-            case 2: fft_stage<T, 4>(s, stride, n, ns, lgns + 2, jt, nt, tw, lgl); break;
-            default: fft_stage<T, 2>(s, stride, n, ns, lgns + 1, jt, nt, tw, lgl); break;
+            case 4: fft_stage<T, 16>(s, stride, n, ns, lgns + 4, jt, nt, tw, lgl, ci, co); break;
+            case 3: fft_stage<T, 8>(s, stride, n, ns, lgns + 3, jt, nt, tw, lgl, ci, co); break;
+            case 2: fft_stage<T, 4>(s, stride, n, ns, lgns + 2, jt, nt, tw, lgl, ci, co); break;
+            default: fft_stage<T, 2>(s, stride, n, ns, lgns + 1, jt, nt, tw, lgl, ci, co); break;
         }
         ns <<= lr;
         lgns += lr;
         rem -= lr;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Compensated FP32 accumulation (Knuth two-sum): sums of FP32 products carried
+// as an unevaluated pair (hi, lo), accurate to about FP32^2, so reductions run
+// on FP32 units and only the block totals are combined in FP64.
+// ---------------------------------------------------------------------------
+struct DSum {
+    float hi = 0.f, lo = 0.f;
+    double d = 0.0;  // FP64 operands accumulate here directly
+    __device__ __forceinline__ void add(float x)
+    {
+        const float s = hi + x;
+        const float bb = s - hi;
+        lo += (hi - (s - bb)) + (x - bb);
+        hi = s;
+    }
+    __device__ __forceinline__ void add(double x) { d += x; }
+    __device__ __forceinline__ double value() const { return d + (double)hi + (double)lo; }
+};
+
+// Sum of one double per thread over the block (all threads must call).
+__device__ __forceinline__ double block_sum_d(double v)
+{
+    __shared__ double sh_bs[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh_bs[wid] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = (threadIdx.x < nw) ? sh_bs[threadIdx.x] : 0.0;
+    if (wid == 0)
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;  // valid in thread 0
 }
 
 // ---------------------------------------------------------------------------
@@ -146,45 +190,92 @@ __device__ __forceinline__ void fft_smem(cx<T> *s, int stride, int lgn, int jt,
 struct RowGeom {
     int lgh;        // log2(n1/2): complex length of a packed row
     int rows;       // rows per block
-    int pitch;      // shared-memory pitch of a row (complex elements)
+    int pitch;      // shared-memory pitch of a packed row (complex elements, even)
     int64_t nrows;  // n2 * n3 (multiple of rows)
-    int lgl;        // log2 of the twiddle table length
+    int lgl;        // log2 of the global twiddle table length
+    int *err;       // device status word (bounded-wait time-outs)
 };
 
-// Op interface (all device):
-//   static constexpr int kFin, kFout;       packed spectra read / written
-//   const cx<T>* spec_in(int f) const;      row-major [row][n1/2] packed spectra
-//   cx<T>*       spec_out(int f) const;
-//   void node(int64_t row, int i1, const T* in, T* out) const;
-//        in:  kFin inverse-transformed values at the node (unnormalised IDFT)
-//        out: kFout real values to transform forward
-// With kFin == 0, node() is a prologue; with kFout == 0, an epilogue.
+// Shared-memory views handed to the row ops.
+template <typename T>
+struct RowCtx {
+    int64_t row0;
+    int rows, n1, pitch;
+    cx<T> *spec;        // [slots][rows][pitch] packed rows (staged outputs after the epilogue)
+    const T *nf;        // [kNF][rows][n1] preloaded node fields
+    const uint8_t *nb;  // [kNB][rows][n1] preloaded byte fields
+    __device__ __forceinline__ T f(int k, int rl, int i1) const { return nf[((size_t)k * rows + rl) * n1 + i1]; }
+    __device__ __forceinline__ uint8_t b(int k, int rl, int i1) const
+    {
+        return nb[((size_t)k * rows + rl) * n1 + i1];
+    }
+    // staged value of field q at node (rl, i1): one half of packed slot i1/2
+    __device__ __forceinline__ T &stage(int q, int rl, int i1) const
+    {
+        cx<T> &c = spec[(q * rows + rl) * pitch + (i1 >> 1)];
+        return (i1 & 1) ? c.y : c.x;
+    }
+};
+
+// Op interface (all device unless noted):
+//   static constexpr int kFin, kFout;  packed spectra read (inverse) / written (forward)
+//   static constexpr int kNF, kNB;     node fields (T / uint8) bulk-loaded for the tile's rows
+//   static constexpr int kStage;       outputs staged in shared memory and written by emit()
+//   static constexpr bool kSparse;     sparse() runs between node2() and emit()
+//   const cx<T>* spec_in(int f); cx<T>* spec_out(int f);   row-major [row][n1/2]
+//   const T* nf_src(int k); const uint8_t* nb_src(int k);  row-major [row][n1]
+//   void node2(ctx, rl, i1, in0, in1, o0, o1): nodes i1 and i1+1 of tile row rl;
+//        in: kFin inverse-transformed values (unnormalised IDFT);
+//        o:  max(kFout, kStage) outputs (forward inputs or staged values)
+//   void sparse(ctx, tid, nthreads); void emit(ctx, rl, i1, s0, s1, acc)
+//   void block_done(acc): called by every thread at the end (block reductions)
+// Data movement: one thread issues bulk async copies (cp.async.bulk) of the
+// tile's spectrum rows and node fields, completing on an mbarrier; twiddles
+// are copied to shared memory; outputs leave through coalesced stores.
 template <typename T, class Op>
 __global__ void __launch_bounds__(256) k_rows(RowGeom g, Op op, const cx<T> *__restrict__ tw)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);
-    constexpr int FI = Op::kFin, FO = Op::kFout;
-    constexpr int FB = FI > FO ? FI : FO;
-    const int H = 1 << g.lgh, nt = H >> 4;
-    const int jt = threadIdx.x % nt, rl = threadIdx.x / nt;
-    const int64_t row = (int64_t)blockIdx.x * g.rows + rl;
-    const int lg1 = g.lgh + 1;  // log2(n1)
-    const int tshift1 = g.lgl - lg1;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    constexpr int FI = Op::kFin, FO = Op::kFout, NF = Op::kNF, NB = Op::kNB, ST = Op::kStage;
+    constexpr int KO = FO > ST ? FO : ST;
+    constexpr int FB = FI > KO ? FI : KO;
+    static_assert(!(FO > 0 && ST > 0), "an op either stages outputs or transforms forward");
+    const int H = 1 << g.lgh, n1 = 2 * H, nt = H >> 4, lg1 = g.lgh + 1;
+    const int rows = g.rows, pitch = g.pitch;
+    const int64_t row0 = (int64_t)blockIdx.x * rows;
+    cx<T> *tws = reinterpret_cast<cx<T> *>(smem_raw);
+    cx<T> *spec = tws + n1;
+    T *nf = reinterpret_cast<T *>(spec + FB * rows * pitch);
+    uint8_t *nb = reinterpret_cast<uint8_t *>(nf + NF * rows * n1);
+    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(nb + ((NB * rows * n1 + 15) & ~15));
+    constexpr bool kLoad = FI > 0 || NF > 0 || NB > 0;
+
+    if (kLoad && threadIdx.x == 0) mbar_init(mbar, 1);
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) tws[i] = tw[i << (g.lgl - lg1)];
+    __syncthreads();
+    if (kLoad && threadIdx.x == 0) {
+        const unsigned bytes = (unsigned)(FI * rows * H * sizeof(cx<T>) + NF * rows * n1 * sizeof(T) + NB * rows * n1);
+        mbar_expect_tx(mbar, bytes);
+#pragma unroll
+        for (int f = 0; f < FI; ++f)
+            for (int r = 0; r < rows; ++r)
+                bulk_load(spec + (f * rows + r) * pitch, op.spec_in(f) + (row0 + r) * H, H * sizeof(cx<T>), mbar);
+#pragma unroll
+        for (int k = 0; k < NF; ++k)
+            bulk_load(nf + k * rows * n1, op.nf_src(k) + row0 * n1, rows * n1 * sizeof(T), mbar);
+#pragma unroll
+        for (int k = 0; k < NB; ++k) bulk_load(nb + k * rows * n1, op.nb_src(k) + row0 * n1, rows * n1, mbar);
+    }
+    if (kLoad && !mbar_wait(mbar, 0, g.err)) return;
+    const RowCtx<T> ctx{row0, rows, n1, pitch, spec, nf, nb};
+    const int jt = threadIdx.x % nt, rf = threadIdx.x / nt;  // FFT mapping: nt threads per row
 
     if constexpr (FI > 0) {
-#pragma unroll
-        for (int f = 0; f < FI; ++f) {
-            const cx<T> *src = op.spec_in(f) + row * H;
-            cx<T> *dst = sm + (f * g.rows + rl) * g.pitch;
-            for (int k = jt; k < H; k += nt) dst[k] = src[k];
-        }
-        __syncthreads();
         // Unpack the half spectrum into Z(k) = E(k) + i O(k) (E, O: DFTs of the
         // even / odd samples, times 2) and store conj(Z) for the inverse.
 #pragma unroll
         for (int f = 0; f < FI; ++f) {
-            cx<T> *z = sm + (f * g.rows + rl) * g.pitch;
+            cx<T> *z = spec + (f * rows + rf) * pitch;
             for (int k = jt; k <= H / 2; k += nt) {
                 if (k == 0) {
                     const cx<T> p = z[0];  // (X(0), X(n1/2))
@@ -192,14 +283,12 @@ __global__ void __launch_bounds__(256) k_rows(RowGeom g, Op op, const cx<T> *__r
                 } else {
                     const int kk = H - k;
                     const cx<T> a = z[k], b = z[kk];
-                    const cx<T> w = tw[k << tshift1];  // W^k, W = e^{-2 pi i / n1}
+                    const cx<T> w = tws[k];  // W^k, W = e^{-2 pi i / n1}
                     // Z(k)  = (a + conj b) + i conj(W^k) (a - conj b)
-                    const cx<T> s1 = a + conjg(b), d1 = a - conjg(b);
-                    const cx<T> zk = s1 + mul_i(cmul(conjg(w), d1));
+                    const cx<T> zk = (a + conjg(b)) + mul_i(cmul(conjg(w), a - conjg(b)));
                     if (kk != k) {
                         // Z(H-k) = (b + conj a) - i W^k (b - conj a)
-                        const cx<T> s2 = b + conjg(a), d2 = b - conjg(a);
-                        const cx<T> zkk = s2 - mul_i(cmul(w, d2));
+                        const cx<T> zkk = (b + conjg(a)) - mul_i(cmul(w, b - conjg(a)));
                         z[kk] = conjg(zkk);
                     }
                     z[k] = conjg(zk);
@@ -208,45 +297,54 @@ __global__ void __launch_bounds__(256) k_rows(RowGeom g, Op op, const cx<T> *__r
         }
         __syncthreads();
 #pragma unroll
-        for (int f = 0; f < FI; ++f)
-            fft_smem<T>(sm + (f * g.rows + rl) * g.pitch, 1, g.lgh, jt, tw, g.lgl);
-        // x[2n] = Re w[n], x[2n+1] = -Im w[n]
-        for (int n = jt; n < H; n += nt) {
-            T in0[FI > 0 ? FI : 1], in1[FI > 0 ? FI : 1];
-            T o0[FO > 0 ? FO : 1], o1[FO > 0 ? FO : 1];
+        for (int f = 0; f < FI; ++f) fft_smem<T>(spec + (f * rows + rf) * pitch, 1, g.lgh, jt, tws, lg1);
+    }
+
+    // per-node work, lanes over consecutive packed slots (2 nodes each)
+    for (int idx = threadIdx.x; idx < rows * H; idx += blockDim.x) {
+        const int rl = idx / H, n = idx - rl * H;
+        T in0[FI > 0 ? FI : 1], in1[FI > 0 ? FI : 1];
+        T o0[KO > 0 ? KO : 1], o1[KO > 0 ? KO : 1];
 #pragma unroll
-            for (int f = 0; f < FI; ++f) {
-                const cx<T> w = sm[(f * g.rows + rl) * g.pitch + n];
-                in0[f] = w.x;
-                in1[f] = -w.y;
-            }
-            op.node(row, 2 * n, in0, o0);
-            op.node(row, 2 * n + 1, in1, o1);
-#pragma unroll
-            for (int f = 0; f < FO; ++f) sm[(f * g.rows + rl) * g.pitch + n] = mk(o0[f], o1[f]);
+        for (int f = 0; f < FI; ++f) {
+            const cx<T> w = spec[(f * rows + rl) * pitch + n];  // x[2n] = Re w, x[2n+1] = -Im w
+            in0[f] = w.x;
+            in1[f] = -w.y;
         }
-        __syncthreads();
-    } else {
-        for (int n = jt; n < H; n += nt) {
-            T o0[FO > 0 ? FO : 1], o1[FO > 0 ? FO : 1];
-            op.node(row, 2 * n, nullptr, o0);
-            op.node(row, 2 * n + 1, nullptr, o1);
+        op.node2(ctx, rl, 2 * n, in0, in1, o0, o1);
 #pragma unroll
-            for (int f = 0; f < FO; ++f) sm[(f * g.rows + rl) * g.pitch + n] = mk(o0[f], o1[f]);
-        }
+        for (int f = 0; f < KO; ++f) spec[(f * rows + rl) * pitch + n] = mk(o0[f], o1[f]);
+    }
+    __syncthreads();
+
+    if constexpr (Op::kSparse) {
+        op.sparse(ctx, threadIdx.x, blockDim.x);
         __syncthreads();
     }
-    (void)FB;
+    DSum acc;
+    if constexpr (ST > 0) {
+        for (int idx = threadIdx.x; idx < rows * H; idx += blockDim.x) {
+            const int rl = idx / H, n = idx - rl * H;
+            T s0[ST], s1[ST];
+#pragma unroll
+            for (int f = 0; f < ST; ++f) {
+                const cx<T> v = spec[(f * rows + rl) * pitch + n];
+                s0[f] = v.x;
+                s1[f] = v.y;
+            }
+            op.emit(ctx, rl, 2 * n, s0, s1, acc);
+        }
+    }
+    op.block_done(acc);
 
     if constexpr (FO > 0) {
 #pragma unroll
-        for (int f = 0; f < FO; ++f)
-            fft_smem<T>(sm + (f * g.rows + rl) * g.pitch, 1, g.lgh, jt, tw, g.lgl);
+        for (int f = 0; f < FO; ++f) fft_smem<T>(spec + (f * rows + rf) * pitch, 1, g.lgh, jt, tws, lg1);
         const T half = T(0.5);
 #pragma unroll
         for (int f = 0; f < FO; ++f) {
-            const cx<T> *z = sm + (f * g.rows + rl) * g.pitch;
-            cx<T> *dst = op.spec_out(f) + row * H;
+            const cx<T> *z = spec + (f * rows + rf) * pitch;
+            cx<T> *dst = op.spec_out(f) + (row0 + rf) * H;
             for (int k = jt; k <= H / 2; k += nt) {
                 if (k == 0) {
                     const cx<T> z0 = z[0];
@@ -254,16 +352,11 @@ __global__ void __launch_bounds__(256) k_rows(RowGeom g, Op op, const cx<T> *__r
                 } else {
                     const int kk = H - k;
                     const cx<T> a = z[k], b = z[kk];
-                    const cx<T> w = tw[k << tshift1];
+                    const cx<T> w = tws[k];
                     // X(k) = 1/2 [(a + conj b) - i W^k (a - conj b)]
-                    const cx<T> xk = scale((a + conjg(b)) - mul_i(cmul(w, a - conjg(b))), half);
-                    dst[k] = xk;
-                    if (kk != k) {
-                        // X(H-k) = 1/2 [(b + conj a) + i conj(W^k) (b - conj a)]
-                        const cx<T> xkk =
-                            scale((b + conjg(a)) + mul_i(cmul(conjg(w), b - conjg(a))), half);
-                        dst[kk] = xkk;
-                    }
+                    dst[k] = scale((a + conjg(b)) - mul_i(cmul(w, a - conjg(b))), half);
+                    // X(H-k) = 1/2 [(b + conj a) + i conj(W^k) (b - conj a)]
+                    if (kk != k) dst[kk] = scale((b + conjg(a)) + mul_i(cmul(conjg(w), b - conjg(a))), half);
                 }
             }
         }
@@ -271,125 +364,134 @@ __global__ void __launch_bounds__(256) k_rows(RowGeom g, Op op, const cx<T> *__r
 }
 
 // ---------------------------------------------------------------------------
-// Column pass
+// Column pass (TMA)
 // ---------------------------------------------------------------------------
 
 struct ColGeom {
-    int lgl;            // log2 of the transform length (axis length)
-    int w;              // tile width (columns, power of two, divides `inner`)
-    int pitch;          // shared-memory pitch of a tile row (>= w + 1)
-    int mirror;         // 1: 3D last-axis pass, load the mirror of column kx = 0
-    int64_t inner;      // number of contiguous columns per outer index
-    int64_t rowstride;  // elements between consecutive positions along the axis
-    int64_t outerstride;
-    int lgh;            // log2(n1/2) (packed row length), for mode coordinates
-    int n2;             // n2 (3D mirror of k2)
-    int lgtw;           // log2 of the twiddle table length
+    int lgl;     // log2 of the transform length L (axis length)
+    int w;       // tile width (columns, power of two, divides the inner extent)
+    int mirror;  // 1: 3D last-axis pass, also loads the mirror of column kx = 0
+    int lgh;     // log2(n1/2) (packed row length), for mode coordinates
+    int n2;      // n2 (3D mirror of k2)
+    int lgtw;    // log2 of the twiddle table length
+    int lb;      // rows per TMA box (<= 256, divides L)
+    int outer;   // outer extent: n3 for the x2 pass, 1 for the last axis
+    int *err;    // device status word (bounded-wait time-outs)
 };
 
 // Op interface:
-//   static constexpr int kFin, kFout;
-//   static constexpr int kMode;   0: forward FFT only, 1: inverse FFT only,
-//                                 2: forward FFT, combine, inverse FFT
-//   static constexpr int kPre;    (kMode 2) leading inputs already transformed
-//                                 along this axis: loaded without an FFT
-//   static constexpr bool kStoreIn; (kMode 2) write the transformed inputs to
-//                                 spec_aux(f) before the combine
-//   cx<T>* spec_aux(int f) const;
-//   const cx<T>* spec_in(int f) const; cx<T>* spec_out(int f) const;
+//   static constexpr int kFin, kFout, kMode, kPre; static constexpr bool kStoreIn;
+//   kMode 0: forward FFT only, 1: inverse FFT only,
+//         2: forward FFT, combine, inverse FFT (kFout <= kFin)
+//   kPre: (kMode 2) leading inputs already transformed along this axis
+//   kStoreIn: (kMode 2) store the transformed inputs to slot_aux(f) first
+//   int slot_in(int f), slot_out(int f), slot_aux(int f): packed-spectrum slots
 //   void combine(int kx, int ky, int kz, const cx<T>* in, cx<T>* out) const;
 //        (kMode 2; called for true modes with kx in [0, n1/2], so both the
 //         kx = 0 and kx = n1/2 halves of the packed column are visited)
-// Shared memory: max(kFin, kFout) x L x pitch complex.
+// Tensor maps: tmt covers all slots of the spectrum buffer as
+// [outer * slots][L][2 * inner] scalars with box (2w, lb, 1); tmm the same with
+// box (4, lb, 1) for the mirror column.
+// Shared memory: [L] twiddles, [max(kFin,kFout)][L][w] tiles, [kFin][L][2] mirror, mbarrier.
 template <typename T, class Op>
-__global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__restrict__ tw,
-                                               int axis_is_z)
+__global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__restrict__ tw, int axis_is_z,
+                                              const __grid_constant__ CUtensorMap tmt,
+                                              const __grid_constant__ CUtensorMap tmm)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     constexpr int FI = Op::kFin, FO = Op::kFout, MODE = Op::kMode;
     constexpr int FB = FI > FO ? FI : FO;
-    const int L = 1 << g.lgl, nt = L >> 4;
-    const int ncol = g.w + g.mirror;
+    static_assert(MODE != 2 || FO <= FI, "combine writes its outputs over its inputs");
+    const int L = 1 << g.lgl;
+    const int w = g.w, ncol = w + g.mirror;
     const int col = threadIdx.x % ncol, jt = threadIdx.x / ncol;
-    const int64_t c0 = (int64_t)blockIdx.x * g.w;
-    const int64_t obase = (int64_t)blockIdx.y * g.outerstride;
+    const int c0 = blockIdx.x * w;
+    const int o = blockIdx.y;
     const int H = 1 << g.lgh;
-    const int nthreads = ncol * nt;
-    const int fsz = L * g.pitch;  // complex elements per field in smem
+    const int nthreads = blockDim.x;
+    const int fsz = L * w;
+    cx<T> *tws = reinterpret_cast<cx<T> *>(smem_raw);  // W_L^i, i < L
+    cx<T> *tile = tws + L;
+    cx<T> *mir = tile + FB * fsz;
+    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(mir + (g.mirror ? FI * L * 2 : 0));
+
     // mirror column (3D last axis): kx = 0 of k2' = (n2 - k2) mod n2
-    int64_t mcol = -1;
-    int ky_tile = 0;
-    if (g.mirror) {
-        ky_tile = (int)(c0 >> g.lgh);
-        if ((c0 & (H - 1)) == 0) mcol = (int64_t)((g.n2 - ky_tile) & (g.n2 - 1)) << g.lgh;
-    }
-    const bool conj_in = (MODE == 1);
+    int mcol = -1;
+    if (g.mirror && (c0 & (H - 1)) == 0) mcol = ((g.n2 - (c0 >> g.lgh)) & (g.n2 - 1)) << g.lgh;
 
-    // ---- load
-#pragma unroll
-    for (int f = 0; f < FI; ++f) {
-        const cx<T> *src = op.spec_in(f) + obase;
-        cx<T> *dst = sm + f * fsz;
-        for (int idx = threadIdx.x; idx < L * g.w; idx += nthreads) {
-            const int r = idx / g.w, c = idx % g.w;
-            cx<T> v = src[(int64_t)r * g.rowstride + c0 + c];
-            dst[r * g.pitch + c] = conj_in ? conjg(v) : v;
-        }
-        if (g.mirror) {
-            for (int r = threadIdx.x; r < L; r += nthreads)
-                dst[r * g.pitch + g.w] = (mcol >= 0) ? src[(int64_t)r * g.rowstride + mcol] : mk(T(0), T(0));
-        }
-    }
+    if (threadIdx.x == 0) mbar_init(mbar, 1);
+    for (int i = threadIdx.x; i < L; i += nthreads) tws[i] = tw[i << (g.lgtw - g.lgl)];
     __syncthreads();
-    constexpr int FPRE = (MODE == 2) ? Op::kPre : 0;
+    if (threadIdx.x == 0) {
+        const unsigned bytes = (unsigned)(FI * fsz * sizeof(cx<T>) + (mcol >= 0 ? FI * L * 2 * sizeof(cx<T>) : 0));
+        mbar_expect_tx(mbar, bytes);
 #pragma unroll
-    for (int f = FPRE; f < FI; ++f) fft_smem<T>(sm + f * fsz + col, g.pitch, g.lgl, jt, tw, g.lgtw);
-
-    if constexpr (MODE == 2 && Op::kStoreIn) {
-#pragma unroll
-        for (int f = FPRE; f < FI; ++f) {
-            cx<T> *dst = op.spec_aux(f) + obase;
-            const cx<T> *srcs = sm + f * fsz;
-            for (int idx = threadIdx.x; idx < L * g.w; idx += nthreads) {
-                const int r = idx / g.w, c = idx % g.w;
-                dst[(int64_t)r * g.rowstride + c0 + c] = srcs[r * g.pitch + c];
+        for (int f = 0; f < FI; ++f) {
+            const int z = o + op.slot_in(f) * g.outer;
+            for (int l0 = 0; l0 < L; l0 += g.lb) {
+                tma_load_3d(tile + f * fsz + l0 * w, &tmt, 2 * c0, l0, z, mbar);
+                if (mcol >= 0) tma_load_3d(mir + f * L * 2 + l0 * 2, &tmm, 2 * mcol, l0, z, mbar);
             }
         }
     }
+    if (!mbar_wait(mbar, 0, g.err)) return;
+
+    // per-thread transform: a tile column, or the mirror column
+    const bool is_m = col >= w;
+    const int cstride = is_m ? 2 : w;
+    auto colbase = [&](int f) -> cx<T> * { return is_m ? (mir + f * L * 2) : (tile + f * fsz + col); };
+
+    constexpr int FPRE = (MODE == 2) ? Op::kPre : 0;
+#pragma unroll
+    for (int f = FPRE; f < FI; ++f)
+        fft_smem<T>(colbase(f), cstride, g.lgl, jt, tws, g.lgl, MODE == 1, MODE == 1);
+
+    if constexpr (MODE == 2 && Op::kStoreIn) {
+        fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int f = FPRE; f < FI; ++f)
+                for (int l0 = 0; l0 < L; l0 += g.lb)
+                    tma_store_3d(&tmt, 2 * c0, l0, o + op.slot_aux(f) * g.outer, tile + f * fsz + l0 * w);
+            bulk_commit();
+            bulk_wait_read_all();
+        }
+        __syncthreads();
+    }
 
     if constexpr (MODE == 2) {
-        // ---- spectral combine, writes conj(output) for the inverse
-        for (int idx = threadIdx.x; idx < L * g.w; idx += nthreads) {
-            const int r = idx / g.w, c = idx % g.w;
-            const int64_t ic = c0 + c;
+        // ---- spectral combine; writes conj(output) for the inverse
+        const bool self_m = (mcol == c0);  // k2 is its own mirror: results parked in mir
+        for (int idx = threadIdx.x; idx < L * w; idx += nthreads) {
+            const int r = idx / w, c = idx % w;
+            const int ic = c0 + c;
             int kx, ky, kz;
             if (axis_is_z) {
                 kz = r;
-                ky = (int)(ic >> g.lgh);
-                kx = (int)(ic & (H - 1));
+                ky = ic >> g.lgh;
+                kx = ic & (H - 1);
             } else {
                 kz = 0;
                 ky = r;
-                kx = (int)ic;
+                kx = ic;
             }
             cx<T> in[FB], out[FB];
             if (kx != 0) {
 #pragma unroll
-                for (int f = 0; f < FI; ++f) in[f] = sm[f * fsz + r * g.pitch + c];
+                for (int f = 0; f < FI; ++f) in[f] = tile[f * fsz + r * w + c];
                 op.combine(kx, ky, kz, in, out);
 #pragma unroll
-                for (int f = 0; f < FO; ++f) sm[f * fsz + r * g.pitch + c] = conjg(out[f]);
+                for (int f = 0; f < FO; ++f) tile[f * fsz + r * w + c] = conjg(out[f]);
             } else if (axis_is_z) {
-                // packed column: mirror (-ky, -kz) is row (L - r) of the extra column
-                // (or of this column when ky is its own mirror)
+                // packed column: mirror (-ky, -kz) is row (L - r) of the mirror
+                // column, or of this column when ky is its own mirror
                 const int rm = (L - r) & (L - 1);
-                const int cm = (mcol == c0 + c) ? c : g.w;  // ky == -ky: same column
                 cx<T> a[FB], b[FB], ya[FB], yb[FB];
 #pragma unroll
                 for (int f = 0; f < FI; ++f) {
-                    const cx<T> z = sm[f * fsz + r * g.pitch + c];
-                    const cx<T> zm = conjg(sm[f * fsz + rm * g.pitch + cm]);
+                    const cx<T> z = tile[f * fsz + r * w + c];
+                    const cx<T> zm = conjg(self_m ? tile[f * fsz + rm * w + c] : mir[f * L * 2 + rm * 2]);
                     a[f] = scale(z + zm, T(0.5));
                     const cx<T> d = scale(z - zm, T(0.5));
                     b[f] = mk(d.y, -d.x);  // d / i
@@ -397,35 +499,24 @@ __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__r
                 op.combine(0, ky, kz, a, ya);
                 op.combine(H, ky, kz, b, yb);
 #pragma unroll
-                for (int f = 0; f < FO; ++f) out[f] = ya[f] + mul_i(yb[f]);
-                // the mirror reads above are from the extra column or from row rm
-                // of this column; rows are rewritten only after the barrier below
-                // when the column is its own mirror (handled by the pair rule)
-                if (cm == g.w) {
-#pragma unroll
-                    for (int f = 0; f < FO; ++f) sm[f * fsz + r * g.pitch + c] = conjg(out[f]);
-                } else {
-                    // self-mirrored column: defer writes through registers + barrier
-                    // is not possible inside this loop; use the pair rule instead
-#pragma unroll
-                    for (int f = 0; f < FO; ++f) in[f] = out[f];
-                    // store to the extra column slot as scratch (its data is unused
-                    // here since cm == c)
-#pragma unroll
-                    for (int f = 0; f < FO; ++f) sm[f * fsz + r * g.pitch + g.w] = conjg(in[f]);
+                for (int f = 0; f < FO; ++f) {
+                    const cx<T> y = conjg(ya[f] + mul_i(yb[f]));
+                    if (self_m)
+                        mir[f * L * 2 + r * 2] = y;
+                    else
+                        tile[f * fsz + r * w + c] = y;
                 }
             } else {
-                // 2D: packed column kx = 0, mirror -ky is row (L - r) of this column.
-                // Pair (r, L - r) is handled by the thread with r <= L - r.
+                // 2D: packed column kx = 0, mirror -ky is row (L - r) of this
+                // column. Pair (r, L - r) is handled by the thread with r <= L - r.
                 const int rm = (L - r) & (L - 1);
                 if (r > rm) continue;
                 cx<T> z[FB], zm[FB], a[FB], b[FB], ya[FB], yb[FB];
 #pragma unroll
                 for (int f = 0; f < FI; ++f) {
-                    z[f] = sm[f * fsz + r * g.pitch + c];
-                    zm[f] = sm[f * fsz + rm * g.pitch + c];
+                    z[f] = tile[f * fsz + r * w + c];
+                    zm[f] = tile[f * fsz + rm * w + c];
                 }
-                // mode r
 #pragma unroll
                 for (int f = 0; f < FI; ++f) {
                     a[f] = scale(z[f] + conjg(zm[f]), T(0.5));
@@ -449,38 +540,35 @@ __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__r
 #pragma unroll
                     for (int f = 0; f < FO; ++f) out2[f] = ya[f] + mul_i(yb[f]);
 #pragma unroll
-                    for (int f = 0; f < FO; ++f) sm[f * fsz + rm * g.pitch + c] = conjg(out2[f]);
+                    for (int f = 0; f < FO; ++f) tile[f * fsz + rm * w + c] = conjg(out2[f]);
                 }
 #pragma unroll
-                for (int f = 0; f < FO; ++f) sm[f * fsz + r * g.pitch + c] = conjg(out[f]);
+                for (int f = 0; f < FO; ++f) tile[f * fsz + r * w + c] = conjg(out[f]);
             }
         }
         __syncthreads();
-        if (g.mirror && mcol == c0) {
-            // self-mirrored packed column (ky = 0 or n2/2): results were parked in
-            // the extra column; move them into place
+        if (self_m) {
             for (int r = threadIdx.x; r < L; r += nthreads) {
 #pragma unroll
-                for (int f = 0; f < FO; ++f) sm[f * fsz + r * g.pitch] = sm[f * fsz + r * g.pitch + g.w];
+                for (int f = 0; f < FO; ++f) tile[f * fsz + r * w] = mir[f * L * 2 + r * 2];
             }
             __syncthreads();
         }
 #pragma unroll
-        for (int f = 0; f < FO; ++f) fft_smem<T>(sm + f * fsz + col, g.pitch, g.lgl, jt, tw, g.lgtw);
+        for (int f = 0; f < FO; ++f) fft_smem<T>(colbase(f), cstride, g.lgl, jt, tws, g.lgl, false, true);
     }
 
-    // ---- store (conj for inverse transforms)
+    // ---- store
     constexpr int FS = (MODE == 2) ? FO : FI;
-    const bool conj_out = (MODE != 0);
+    fence_proxy_async();
+    __syncthreads();
+    if (threadIdx.x == 0) {
 #pragma unroll
-    for (int f = 0; f < FS; ++f) {
-        cx<T> *dst = op.spec_out(f) + obase;
-        const cx<T> *srcs = sm + f * fsz;
-        for (int idx = threadIdx.x; idx < L * g.w; idx += nthreads) {
-            const int r = idx / g.w, c = idx % g.w;
-            const cx<T> v = srcs[r * g.pitch + c];
-            dst[(int64_t)r * g.rowstride + c0 + c] = conj_out ? conjg(v) : v;
-        }
+        for (int f = 0; f < FS; ++f)
+            for (int l0 = 0; l0 < L; l0 += g.lb)
+                tma_store_3d(&tmt, 2 * c0, l0, o + op.slot_out(f) * g.outer, tile + f * fsz + l0 * w);
+        bulk_commit();
+        bulk_wait_read_all();
     }
 }
 

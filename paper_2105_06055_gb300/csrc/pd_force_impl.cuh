@@ -15,22 +15,31 @@ namespace pd {
 
 static inline unsigned nblk_f(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b); }
 
-template <typename T, int D, bool ENERGY>
+// SPARSE: the epilogue takes the plan's boundary-node list of G (weight chi_B);
+// otherwise the dense G passed in (weight chi_B, chi_B s or chi_B lam).
+template <typename T, int D, bool ENERGY, int WM, bool SPARSE = (WM == W_NONE)>
 pd_status force_bond_pipeline(pd_plan *p, const T *u, const T *s, const uint8_t *lam, const T *G, T *L, T *W,
                               cudaStream_t st)
 {
     cx<T> *spec = reinterpret_cast<cx<T> *>(spec_buf<T>(p));
     const int64_t fs = p->N / 2;
     constexpr int FI = D + (ENERGY ? Sym<D>::n : 0), FO = D + (ENERGY ? 1 : 0);
-    ProForce<T, D, ENERGY> pro{u, s, lam, p->chi, p->N, p->n1, spec, fs};
-    PD_TRY(launch_rows<T>(p, pro, FI, st));
-    if (D == 3) PD_TRY((col_pass<T, FI>(p, spec, false, st)));
+    ProForce<T, D, ENERGY, WM> pro{u, s, lam, p->chi, p->N, spec, fs};
+    PD_TRY(launch_rows<T>(p, pro, st));
+    if (D == 3) PD_TRY((col_pass<T, FI>(p, 0, false, st)));
     const int ob = D == 3 ? FI : 0;
-    CombForce<T, D, ENERGY> cmb{model_view<T>(p), spec, fs, ob};
+    CombForce<T, D, ENERGY> cmb{model_view<T>(p), ob};
     PD_TRY(launch_cols<T>(p, cmb, D == 3 ? 2 : 1, true, FI, st));
-    if (D == 3) PD_TRY((col_pass<T, FO>(p, spec + ob * fs, true, st)));
-    EpiForce<T, D, ENERGY> epi{u, s, lam, p->chi, G, L, W, p->N, p->n1, spec + ob * fs, fs};
-    PD_TRY(launch_rows<T>(p, epi, FO, st));
+    if (D == 3) PD_TRY((col_pass<T, FO>(p, ob, true, st)));
+    if constexpr (SPARSE) {
+        static_assert(WM == W_NONE, "the boundary-node list is for the plan weight chi_B");
+        const Model<T> m = model_view<T>(p);
+        EpiForceSparse<T, D, ENERGY> epi{u, p->chi, m.gent, m.goff, L, W, p->N, p->n1, spec + ob * fs, fs};
+        PD_TRY(launch_rows<T>(p, epi, st));
+    } else {
+        EpiForceDense<T, D, ENERGY, WM> epi{u, s, lam, p->chi, G, L, W, p->N, p->n1, spec + ob * fs, fs};
+        PD_TRY(launch_rows<T>(p, epi, st));
+    }
     return PD_OK;
 }
 
@@ -65,11 +74,9 @@ struct CombTheta {
     static constexpr int kFin = 3, kFout = 1, kMode = 2, kPre = 0;
     static constexpr bool kStoreIn = true;
     Model<T> m;
-    cx<T> *spec;
-    int64_t fstride;
-    __device__ const cx<T> *spec_in(int f) const { return spec + f * fstride; }
-    __device__ cx<T> *spec_aux(int f) const { return spec + (5 + f) * fstride; }
-    __device__ cx<T> *spec_out(int) const { return spec + 3 * fstride; }
+    __device__ int slot_in(int f) const { return f; }
+    __device__ int slot_aux(int f) const { return 5 + f; }
+    __device__ int slot_out(int) const { return 3; }
     __device__ __forceinline__ void combine(int kx, int ky, int kz, const cx<T> *in, cx<T> *out) const
     {
         T g[3];
@@ -84,7 +91,8 @@ struct CombTheta {
 // rows: inverse of S, theta at the nodes, forward transform of theta
 template <typename T>
 struct RowTheta {
-    static constexpr int kFin = 1, kFout = 1;
+    static constexpr int kFin = 1, kFout = 1, kNF = 0, kNB = 0, kStage = 0;
+    static constexpr bool kSparse = false;
     Model<T> m;
     const T *u;
     T *theta;
@@ -92,19 +100,31 @@ struct RowTheta {
     int64_t fstride;
     __device__ const cx<T> *spec_in(int) const { return spec + 3 * fstride; }
     __device__ cx<T> *spec_out(int) const { return spec + 4 * fstride; }
-    __device__ __forceinline__ void node(int64_t row, int i1, const T *in, T *out) const
+    __device__ const T *nf_src(int) const { return nullptr; }
+    __device__ const uint8_t *nb_src(int) const { return nullptr; }
+    __device__ __forceinline__ T node1(int64_t p, T in) const
     {
-        const int64_t p = row * m.n1 + i1;
         T th = T(0);
         if (m.chi[p]) {
             T qu = T(0);
 #pragma unroll
             for (int i = 0; i < 3; ++i) qu += m.qt[i * m.N + p] * u[i * m.N + p];
-            th = -m.m3inv[p] * (in[0] + qu);
+            th = -m.m3inv[p] * (in + qu);
         }
-        theta[p] = th;
-        out[0] = th;
+        return th;
     }
+    __device__ __forceinline__ void node2(const RowCtx<T> &c, int rl, int i1, const T *in0, const T *in1, T *o0,
+                                          T *o1) const
+    {
+        const int64_t p = (c.row0 + rl) * m.n1 + i1;
+        const T t0 = node1(p, in0[0]), t1 = node1(p + 1, in1[0]);
+        store2(theta + p, t0, t1);
+        o0[0] = t0;
+        o1[0] = t1;
+    }
+    __device__ void sparse(const RowCtx<T> &, int, int) const {}
+    __device__ void emit(const RowCtx<T> &, int, int, const T *, const T *, DSum &) const {}
+    __device__ void block_done(DSum &) const {}
 };
 
 // last axis, round 2: Y_i = M^_ij X_j + i ka ghat_i Theta
@@ -113,11 +133,9 @@ struct CombState {
     static constexpr int kFin = 4, kFout = 3, kMode = 2, kPre = 3;
     static constexpr bool kStoreIn = false;
     Model<T> m;
-    cx<T> *spec;
-    int64_t fstride;
-    __device__ const cx<T> *spec_in(int f) const { return spec + (f < 3 ? 5 + f : 4) * fstride; }
-    __device__ cx<T> *spec_out(int f) const { return spec + f * fstride; }
-    __device__ cx<T> *spec_aux(int) const { return nullptr; }
+    __device__ int slot_in(int f) const { return f < 3 ? 5 + f : 4; }
+    __device__ int slot_out(int f) const { return f; }
+    __device__ int slot_aux(int) const { return 0; }
     __device__ __forceinline__ void combine(int kx, int ky, int kz, const cx<T> *in, cx<T> *out) const
     {
         T M[9], g[3];
@@ -131,9 +149,12 @@ struct CombState {
     }
 };
 
+// rows: inverse of Y, L = chi y staged, boundary fix-up
+//   L_i -= G_ij u_j - ka theta q_i   (q_i and G vanish off the boundary list)
 template <typename T>
 struct EpiState {
-    static constexpr int kFin = 3, kFout = 0;
+    static constexpr int kFin = 3, kFout = 0, kNF = 0, kNB = 1, kStage = 3;
+    static constexpr bool kSparse = true;
     Model<T> m;
     const T *u;
     const T *theta;
@@ -142,29 +163,43 @@ struct EpiState {
     int64_t fstride;
     __device__ const cx<T> *spec_in(int f) const { return spec + f * fstride; }
     __device__ cx<T> *spec_out(int) const { return nullptr; }
-    __device__ __forceinline__ void node(int64_t row, int i1, const T *in, T *) const
+    __device__ const T *nf_src(int) const { return nullptr; }
+    __device__ const uint8_t *nb_src(int) const { return m.chi; }
+    __device__ __forceinline__ void node2(const RowCtx<T> &c, int rl, int i1, const T *in0, const T *in1, T *o0,
+                                          T *o1) const
     {
-        const int64_t p = row * m.n1 + i1;
-        const int64_t N = m.N;
-        if (!m.chi[p]) {
+        const T v0 = c.b(0, rl, i1) ? T(1) : T(0), v1 = c.b(0, rl, i1 + 1) ? T(1) : T(0);
 #pragma unroll
-            for (int i = 0; i < 3; ++i) L[i * N + p] = T(0);
-            return;
+        for (int i = 0; i < 3; ++i) {
+            o0[i] = v0 * in0[i];
+            o1[i] = v1 * in1[i];
         }
-        T uu[3], Gu[3] = {T(0), T(0), T(0)};
-#pragma unroll
-        for (int j = 0; j < 3; ++j) uu[j] = u[j * N + p];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            const int a = Sym<3>::i(c), b = Sym<3>::j(c);
-            const T gc = m.G[c * N + p];
-            Gu[a] += gc * uu[b];
-            if (a != b) Gu[b] += gc * uu[a];
-        }
-        const T th = theta[p];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) L[i * N + p] = in[i] - Gu[i] + m.ka * th * m.qt[i * N + p];
     }
+    __device__ void sparse(const RowCtx<T> &c, int tid, int nthreads) const
+    {
+        const int64_t N = m.N;
+        const int k0 = m.goff[c.row0], k1 = m.goff[c.row0 + c.rows];
+        for (int k = k0 + tid; k < k1; k += nthreads) {
+            const GEntry<T> e = m.gent[k];
+            const int64_t p = e.p;
+            const int rl = (int)(p / m.n1 - c.row0), i1 = (int)(p % m.n1);
+            T uu[3], Gu[3] = {T(0), T(0), T(0)};
+#pragma unroll
+            for (int j = 0; j < 3; ++j) uu[j] = u[j * N + p];
+            sym_apply<T, 3>(e.g, uu, Gu);
+            const T th = theta[p];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) c.stage(i, rl, i1) -= Gu[i] - m.ka * th * m.qt[i * N + p];
+        }
+    }
+    __device__ __forceinline__ void emit(const RowCtx<T> &c, int rl, int i1, const T *s0, const T *s1,
+                                         DSum &) const
+    {
+        const int64_t p = (c.row0 + rl) * m.n1 + i1;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) store2(L + i * m.N + p, s0[i], s1[i]);
+    }
+    __device__ void block_done(DSum &) const {}
 };
 
 template <typename T>
@@ -173,20 +208,20 @@ pd_status force_state_pipeline(pd_plan *p, const T *u, T *L, T *theta, cudaStrea
     cx<T> *spec = reinterpret_cast<cx<T> *>(spec_buf<T>(p));
     const int64_t fs = p->N / 2;
     const Model<T> m = model_view<T>(p);
-    ProForce<T, 3, false> pro{u, nullptr, nullptr, p->chi, p->N, p->n1, spec, fs};
-    PD_TRY(launch_rows<T>(p, pro, 3, st));
-    PD_TRY((col_pass<T, 3>(p, spec, false, st)));
-    CombTheta<T> c1{m, spec, fs};
+    ProForce<T, 3, false, W_NONE> pro{u, nullptr, nullptr, p->chi, p->N, spec, fs};
+    PD_TRY(launch_rows<T>(p, pro, st));
+    PD_TRY((col_pass<T, 3>(p, 0, false, st)));
+    CombTheta<T> c1{m};
     PD_TRY(launch_cols<T>(p, c1, 2, true, 3, st));
-    PD_TRY((col_pass<T, 1>(p, spec + 3 * fs, true, st)));
+    PD_TRY((col_pass<T, 1>(p, 3, true, st)));
     RowTheta<T> rt{m, u, theta, spec, fs};
-    PD_TRY(launch_rows<T>(p, rt, 1, st));
-    PD_TRY((col_pass<T, 1>(p, spec + 4 * fs, false, st)));
-    CombState<T> c2{m, spec, fs};
+    PD_TRY(launch_rows<T>(p, rt, st));
+    PD_TRY((col_pass<T, 1>(p, 4, false, st)));
+    CombState<T> c2{m};
     PD_TRY(launch_cols<T>(p, c2, 2, true, 4, st));
-    PD_TRY((col_pass<T, 3>(p, spec, true, st)));
+    PD_TRY((col_pass<T, 3>(p, 0, true, st)));
     EpiState<T> epi{m, u, theta, L, spec, fs};
-    PD_TRY(launch_rows<T>(p, epi, 3, st));
+    PD_TRY(launch_rows<T>(p, epi, st));
     return PD_OK;
 }
 
@@ -209,16 +244,29 @@ pd_status weight_gfield(pd_plan *p, const T *s, const uint8_t *lam, T *G, cudaSt
     return PD_OK;
 }
 
+// Bond-model force with weight chi_B (s = lam = null: sparse plan G), chi_B s
+// or chi_B lam (dense G of that weight passed in G).
 template <typename T>
 pd_status force_any(pd_plan *p, const T *u, const T *s, const uint8_t *lam, const T *G, T *L, T *W,
                     cudaStream_t st)
 {
-    if (p->dim == 2) {
-        if (W) return force_bond_pipeline<T, 2, true>(p, u, s, lam, G, L, W, st);
-        return force_bond_pipeline<T, 2, false>(p, u, s, lam, G, L, nullptr, st);
+    if (s && lam) {
+        set_error("force: s and lambda together are not supported");
+        return PD_ERR_ARG;
     }
-    if (W) return force_bond_pipeline<T, 3, true>(p, u, s, lam, G, L, W, st);
-    return force_bond_pipeline<T, 3, false>(p, u, s, lam, G, L, nullptr, st);
+#define PD_FORCE_CASE(D, E)                                                                         \
+    do {                                                                                            \
+        if (s) return force_bond_pipeline<T, D, E, W_S>(p, u, s, lam, G, L, W, st);                 \
+        if (lam) return force_bond_pipeline<T, D, E, W_LAM>(p, u, s, lam, G, L, W, st);             \
+        return force_bond_pipeline<T, D, E, W_NONE>(p, u, s, lam, G, L, W, st);                     \
+    } while (0)
+    if (p->dim == 2) {
+        if (W) PD_FORCE_CASE(2, true);
+        PD_FORCE_CASE(2, false);
+    }
+    if (W) PD_FORCE_CASE(3, true);
+    PD_FORCE_CASE(3, false);
+#undef PD_FORCE_CASE
 }
 
 template <typename T>

@@ -19,8 +19,9 @@
 // object, not device memory); make that first call before any stream capture.
 // Every call recomputes everything it reads from the array (horizon table,
 // kernel spectrum, boundary field, twiddles, spectra), so nothing depends on
-// the previous call's contents; the only value that must start at zero, the
-// mask-check flag, is cleared at the start of each call. All calls share the
+// the previous call's contents; the only values that must start at zero, the
+// mask-check flag and the passes' wait-status word, are cleared at the start of
+// each call. All calls share the
 // one array: calls that overlap on the GPU (other streams, other host
 // threads) race on it and must be serialised by the caller.
 #include <cmath>
@@ -217,7 +218,7 @@ extern "C" pd_status pd_force2d_noalloc(const pd_problem *pr, const uint8_t *chi
     int *flag = (int *)(base + b_spec + b_G + b_mh + b_tw + b_off + b_c);
 
     cudaStream_t st = (cudaStream_t)stream;
-    PD_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
+    PD_CUDA_TRY(cudaMemsetAsync(flag, 0, 2 * sizeof(int), st));
     k_na_check<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(n1, n2, r1, r2, chi_B, N, flag);
     PD_LAUNCH_CHECK();
     int hbad = 0;
@@ -265,8 +266,10 @@ extern "C" pd_status pd_force2d_noalloc(const pd_problem *pr, const uint8_t *chi
     p.G32 = G;
     p.tw32 = tw;
     p.spec32 = spec;
+    p.spec32_slots = 2;
+    p.dev_status = flag + 1;
     p.hdev = hd;
-    const pd_status s = force_bond_pipeline<float, 2, false>(&p, u, nullptr, nullptr, G, L, nullptr, st);
+    const pd_status s = force_bond_pipeline<float, 2, false, W_NONE, false>(&p, u, nullptr, nullptr, G, L, nullptr, st);
     // the stack plan owns nothing: detach its views before it goes out of scope
     p.chi = nullptr;
     p.mhat32 = nullptr;

@@ -22,6 +22,39 @@ void set_error(const char *fmt, ...)
     va_end(ap);
 }
 
+pd_status encode_tmap_3d(CUtensorMap *m, void *base, bool fp64, const unsigned long long dims[3],
+                         const unsigned long long strides[2], const unsigned box[3])
+{
+    typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static EncodeFn fn = nullptr;
+    if (!fn) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000,
+                                                               cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !f) {
+            set_error("cuTensorMapEncodeTiled is not available from the driver");
+            return PD_ERR_CUDA;
+        }
+        fn = (EncodeFn)f;
+    }
+    const cuuint64_t gd[3] = {dims[0], dims[1], dims[2]};
+    const cuuint64_t gs[2] = {strides[0], strides[1]};
+    const cuuint32_t bx[3] = {box[0], box[1], box[2]};
+    const cuuint32_t es[3] = {1, 1, 1};
+    const CUresult r = fn(m, fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, gd, gs,
+                          bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d): dims %llu x %llu x %llu, box %u x %u x %u", (int)r, dims[0],
+                  dims[1], dims[2], box[0], box[1], box[2]);
+        return PD_ERR_CUDA;
+    }
+    return PD_OK;
+}
+
 pd_status set_smem_attr(const void *func, size_t smem)
 {
     if (smem > 48 * 1024) {
@@ -34,17 +67,24 @@ pd_status set_smem_attr(const void *func, size_t smem)
     return PD_OK;
 }
 
-pd_status prof_harvest(pd_plan *p)
+pd_status prof_harvest_range(pd_plan *p, int b, int e)
 {
-    if (p->ev_used == 0) return PD_OK;
-    PD_CUDA_TRY(cudaEventSynchronize(p->ev[2 * p->ev_used - 1]));
-    for (int i = 0; i < p->ev_used; ++i) {
+    if (e <= b) return PD_OK;
+    PD_CUDA_TRY(cudaEventSynchronize(p->ev[2 * e - 1]));
+    for (int i = b; i < e; ++i) {
         float ms = 0.f;
         PD_CUDA_TRY(cudaEventElapsedTime(&ms, p->ev[2 * i], p->ev[2 * i + 1]));
         p->prof_ms[p->ev_kind[i]] += ms;
         p->prof_n[p->ev_kind[i]]++;
     }
-    p->ev_used = 0;
+    return PD_OK;
+}
+
+// Harvest the event pairs of direct launches (those above the graph reservation).
+pd_status prof_harvest(pd_plan *p)
+{
+    PD_TRY(prof_harvest_range(p, p->ev_reserved, p->ev_used));
+    p->ev_used = p->ev_reserved;
     return PD_OK;
 }
 
@@ -64,13 +104,16 @@ Model<T> model_view(const pd_plan *p)
     m.fold_sz = p->fold_sz;
     m.chi = p->chi;
     m.chi_om = p->chi_om;
+    m.goff = p->goff;
     if constexpr (sizeof(T) == 8) {
+        m.gent = (const GEntry<T> *)p->gent64;
         m.mhat = (const T *)p->mhat64;
         m.ghat = (const T *)p->ghat64;
         m.G = (const T *)p->G64;
         m.qt = (const T *)p->qt64;
         m.m3inv = (const T *)p->m3inv64;
     } else {
+        m.gent = (const GEntry<T> *)p->gent32;
         m.mhat = (const T *)p->mhat32;
         m.ghat = (const T *)p->ghat32;
         m.G = (const T *)p->G32;
@@ -249,6 +292,47 @@ __global__ void k_check_masks(int n1, int n2, int n3, int r1, int r2, int r3, co
             if (chi_om[k * N + p] > c) atomicOr(bad, 2);
 }
 
+// Boundary-node list of G: per row, the nodes with chi = 1 and G != 0.
+__global__ void k_gcount(int n1, int64_t nrows, const uint8_t *chi, const double *G, int nc, int64_t N, int *cnt)
+{
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= nrows) return;
+    int k = 0;
+    for (int i = 0; i < n1; ++i) {
+        const int64_t p = row * n1 + i;
+        if (!chi[p]) continue;
+        bool nz = false;
+        for (int c = 0; c < nc; ++c) nz |= (G[c * N + p] != 0.0);
+        k += nz;
+    }
+    cnt[row] = k;
+}
+
+__global__ void k_gfill(int n1, int64_t nrows, const uint8_t *chi, const double *G, int nc, int64_t N, const int *off,
+                        GEntry<double> *e64, GEntry<float> *e32)
+{
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= nrows) return;
+    int k = off[row];
+    for (int i = 0; i < n1; ++i) {
+        const int64_t p = row * n1 + i;
+        if (!chi[p]) continue;
+        bool nz = false;
+        for (int c = 0; c < nc; ++c) nz |= (G[c * N + p] != 0.0);
+        if (!nz) continue;
+        GEntry<double> a;
+        GEntry<float> b;
+        for (int c = 0; c < 6; ++c) {
+            a.g[c] = c < nc ? G[c * N + p] : 0.0;
+            b.g[c] = (float)a.g[c];
+        }
+        a.p = b.p = p;
+        e64[k] = a;
+        e32[k] = b;
+        ++k;
+    }
+}
+
 template <typename Tout>
 __global__ void k_convert(const double *in, Tout *out, int64_t n)
 {
@@ -370,7 +454,14 @@ pd_status pd_plan_profile(pd_plan *p, int enable)
         p->prof_ms[k] = 0.0;
         p->prof_n[k] = 0;
     }
+    // cached graphs hold event nodes of the old setting: rebuild on next use
+    for (int k = 0; k < 2; ++k)
+        if (p->cg_graph[k]) {
+            cudaGraphExecDestroy(p->cg_graph[k]);
+            p->cg_graph[k] = nullptr;
+        }
     p->ev_used = 0;
+    p->ev_reserved = 0;
     return PD_OK;
 }
 
@@ -397,12 +488,19 @@ void pd_plan_destroy(pd_plan *p)
 {
     if (!p) return;
     void *ptrs[] = {p->chi, p->chi_om, p->hoff, p->mhat64, p->mhat32, p->ghat64, p->ghat32, p->G64, p->G32,
+                    p->goff, p->gent64, p->gent32,
                     p->qt64, p->m3inv64, p->qt32, p->m3inv32, p->tw64, p->tw32, p->spec32, p->spec64,
                     p->work, p->red};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (int i = 0; i < 2 * pd_plan::kEvPool; ++i)
         if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+    for (int k = 0; k < 2; ++k)
+        if (p->cg_graph[k]) cudaGraphExecDestroy(p->cg_graph[k]);
+    if (p->host_scal) cudaFreeHost(p->host_scal);
+    for (int k = 0; k < 2; ++k)
+        if (p->ev_join[k]) cudaEventDestroy(p->ev_join[k]);
+    if (p->own_stream) cudaStreamDestroy(p->own_stream);
     delete p;
 }
 
@@ -539,8 +637,10 @@ static pd_status plan_create_impl(const pd_problem *pr, const uint8_t *chi_B, co
     HorizonDev hd{d_off, d_c, d_g, d_w2, hz.cnt};
     p->hdev = hd;
 
-    // reduction scratch
+    // reduction scratch; the last 64 bytes hold the device status word
     PD_TRY(dalloc(p, &p->red, sizeof(double) * 65536));
+    p->dev_status = reinterpret_cast<int *>(p->red + 65536 - 8);  // last 64 bytes
+    PD_CUDA_TRY(cudaMemsetAsync(p->dev_status, 0, 64, st));
 
     // mask checks
     {
@@ -610,6 +710,31 @@ static pd_status plan_create_impl(const pd_problem *pr, const uint8_t *chi_B, co
     PD_LAUNCH_CHECK();
     k_convert<float><<<nblk(nc * N), 256, 0, st>>>(p->G64, p->G32, nc * N);
     PD_LAUNCH_CHECK();
+    {
+        // sparse list of the boundary nodes of G, ordered by row
+        const int64_t nr = p->nrows;
+        PD_TRY(dalloc(p, &p->goff, sizeof(int) * (size_t)(nr + 1)));
+        k_gcount<<<nblk(nr, 128), 128, 0, st>>>(n1, nr, p->chi, p->G64, nc, N, p->goff);
+        PD_LAUNCH_CHECK();
+        std::vector<int> cnt((size_t)nr + 1, 0);
+        PD_CUDA_TRY(cudaMemcpyAsync(cnt.data(), p->goff, sizeof(int) * (size_t)nr, cudaMemcpyDeviceToHost, st));
+        PD_CUDA_TRY(cudaStreamSynchronize(st));
+        int64_t acc = 0;
+        for (int64_t r = 0; r < nr; ++r) {
+            const int c = cnt[(size_t)r];
+            cnt[(size_t)r] = (int)acc;
+            acc += c;
+        }
+        cnt[(size_t)nr] = (int)acc;
+        p->ngent = acc;
+        PD_CUDA_TRY(cudaMemcpyAsync(p->goff, cnt.data(), sizeof(int) * (size_t)(nr + 1), cudaMemcpyHostToDevice, st));
+        PD_TRY(dalloc(p, &p->gent64, sizeof(GEntry<double>) * (size_t)std::max<int64_t>(acc, 1)));
+        PD_TRY(dalloc(p, &p->gent32, sizeof(GEntry<float>) * (size_t)std::max<int64_t>(acc, 1)));
+        k_gfill<<<nblk(nr, 128), 128, 0, st>>>(n1, nr, p->chi, p->G64, nc, N, p->goff, (GEntry<double> *)p->gent64,
+                                              (GEntry<float> *)p->gent32);
+        PD_LAUNCH_CHECK();
+        PD_CUDA_TRY(cudaStreamSynchronize(st));
+    }
     if (pr->model == PD_LIN_STATE) {
         PD_TRY(dalloc(p, &p->qt64, sizeof(double) * 3 * N));
         PD_TRY(dalloc(p, &p->m3inv64, sizeof(double) * N));
@@ -648,12 +773,21 @@ static pd_status plan_create_impl(const pd_problem *pr, const uint8_t *chi_B, co
         PD_CUDA_TRY(cudaStreamSynchronize(st));
     }
 
-    // timing events (created here so that later calls allocate nothing)
+    // timing events and the pinned solver scalars (created here so that later
+    // calls allocate nothing)
     for (int i = 0; i < 2 * pd_plan::kEvPool; ++i) PD_CUDA_TRY(cudaEventCreate(&p->ev[i]));
+    PD_CUDA_TRY(cudaMallocHost((void **)&p->host_scal, sizeof(double) * 64));
+    PD_CUDA_TRY(cudaStreamCreateWithFlags(&p->own_stream, cudaStreamNonBlocking));
+    PD_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_join[0], cudaEventDisableTiming));
+    PD_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_join[1], cudaEventDisableTiming));
 
     // spectra and scratch
-    if (!pr->fp64) PD_TRY(dalloc(p, &p->spec32, sizeof(float) * (size_t)kMaxSpecFields * N));
-    PD_TRY(dalloc(p, &p->spec64, sizeof(double) * (size_t)(pr->fp64 ? kMaxSpecFields : 8) * N));
+    if (!pr->fp64) {
+        p->spec32_slots = kMaxSpecFields;
+        PD_TRY(dalloc(p, &p->spec32, sizeof(float) * (size_t)p->spec32_slots * N));
+    }
+    p->spec64_slots = pr->fp64 ? kMaxSpecFields : 8;
+    PD_TRY(dalloc(p, &p->spec64, sizeof(double) * (size_t)p->spec64_slots * N));
     {
         const size_t tb = pr->fp64 ? sizeof(double) : sizeof(float);
         const size_t vec = tb * (size_t)dim * N;  // one vector field

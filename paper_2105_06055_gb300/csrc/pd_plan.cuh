@@ -13,6 +13,14 @@ namespace pd {
 // go to slots after the inputs (inputs + outputs <= kMaxSpecFields).
 constexpr int kMaxSpecFields = 20;
 
+// One boundary node of the plan's G field (G != 0 only within delta of the
+// body's boundary): the ncomp components in Sym order and the node index.
+template <typename T>
+struct GEntry {
+    T g[6];
+    int64_t p;
+};
+
 // Device-side view of the model used by the per-node and per-mode functors.
 template <typename T>
 struct Model {
@@ -28,6 +36,8 @@ struct Model {
     const uint8_t *chi;
     const uint8_t *chi_om;  // d x N
     const T *G;        // ncomp x N boundary field for v = chi
+    const GEntry<T> *gent;  // the same field as a list of boundary nodes, by row
+    const int *goff;        // nrows + 1 offsets into gent
     const T *qt;       // 3 x N, state-based q_i(x) = dV (g_i * chi)
     const T *m3inv;    // N, 3/m(x) (0 outside the body)
     T ka;              // (3 kappa - 5 mu)/m0 (state-based)
@@ -135,12 +145,18 @@ struct pd_plan {
     int64_t fold_sz = 0;
     double *G64 = nullptr;         // ncomp x N
     float *G32 = nullptr;
+    int *goff = nullptr;           // nrows + 1: boundary-node list offsets per row
+    void *gent64 = nullptr;        // GEntry<double>[ngent]
+    void *gent32 = nullptr;        // GEntry<float>[ngent]
+    int64_t ngent = 0;
     double *qt64 = nullptr, *m3inv64 = nullptr;  // state-based
     float *qt32 = nullptr, *m3inv32 = nullptr;
     pd::cx<double> *tw64 = nullptr;
     pd::cx<float> *tw32 = nullptr;
-    void *spec32 = nullptr;        // kMaxSpecFields x N floats (packed spectra)
-    void *spec64 = nullptr;        // kMaxSpecFields x N doubles
+    void *spec32 = nullptr;        // spec32_slots x N floats (packed spectra)
+    void *spec64 = nullptr;        // spec64_slots x N doubles
+    int spec32_slots = 0, spec64_slots = 0;
+    int *dev_status = nullptr;     // device status word (bounded-wait time-outs)
     void *work = nullptr;          // one allocation carved into the scratch fields below
     size_t work_bytes = 0;
     // scratch fields (plan precision T unless noted)
@@ -160,7 +176,15 @@ struct pd_plan {
     cudaEvent_t ev[2 * kEvPool] = {};
     int ev_kind[kEvPool] = {};
     int ev_used = 0;
+    int ev_reserved = 0;            // pairs [0, ev_reserved) belong to captured graphs
     int prof_on = 0;
+    // cached CUDA graph of a chunk of CG iterations (per precision)
+    cudaGraphExec_t cg_graph[2] = {nullptr, nullptr};
+    int cg_graph_prof[2] = {0, 0};
+    int cg_graph_ev[2][2] = {{0, 0}, {0, 0}};
+    double *host_scal = nullptr;    // pinned host copy of the solver scalars
+    cudaStream_t own_stream = nullptr;  // plan stream for captured work (never the legacy stream)
+    cudaEvent_t ev_join[2] = {nullptr, nullptr};
     double prof_ms[kKinds] = {};
     int64_t prof_n[kKinds] = {};
 };
@@ -184,66 +208,61 @@ inline const cx<float> *tw_buf<float>(const pd_plan *p) { return p->tw32; }
 template <>
 inline const cx<double> *tw_buf<double>(const pd_plan *p) { return p->tw64; }
 
-// Row-pass configuration for F fields in shared memory.
+// Row-pass configuration: FB packed-row slots, NF node fields of T, NB byte fields.
 template <typename T>
-inline void row_cfg(const pd_plan *p, int F, RowGeom &g, LaunchCfg &c)
+inline void row_cfg(const pd_plan *p, int FB, int NF, int NB, RowGeom &g, LaunchCfg &c)
 {
-    const int H = p->h, nt = H >> 4;
+    const int H = p->h, nt = H >> 4, n1 = 2 * H;
+    const int pad = nt < 16 ? (nt < 2 ? 2 : nt) : 0;  // keeps rows 16-byte aligned, spreads banks
+    const int pitch = H + pad;
+    auto smem_of = [&](int rows) {
+        return (size_t)n1 * sizeof(cx<T>) + (size_t)FB * rows * pitch * sizeof(cx<T>) +
+               (size_t)NF * rows * n1 * sizeof(T) + (((size_t)NB * rows * n1 + 15) & ~(size_t)15) + 16;
+    };
     int rows = 256 / nt;
     if (rows < 1) rows = 1;
-    // keep the per-block shared memory modest
-    const int pad = nt < 16 ? nt : 0;
-    while (rows > 1 && (size_t)F * rows * (H + pad) * sizeof(cx<T>) > 96 * 1024) rows >>= 1;
+    while (rows > 1 && smem_of(rows) > 100 * 1024) rows >>= 1;
     while (p->nrows % rows) rows >>= 1;
     g.lgh = ilog2(H);
     g.rows = rows;
-    g.pitch = H + pad;
+    g.pitch = pitch;
     g.nrows = p->nrows;
     g.lgl = p->lgl;
+    g.err = p->dev_status;
     c.grid = dim3((unsigned)(p->nrows / rows));
     c.block = dim3(rows * nt);
-    c.smem = (size_t)F * rows * g.pitch * sizeof(cx<T>);
+    c.smem = smem_of(rows);
 }
 
-// Column-pass configuration: axis 1 = x2, axis 2 = x3 (3D), F fields in smem.
+// Column-pass configuration: axis 1 = x2, axis 2 = x3 (3D); FB fields in the
+// tile, FI of them with a mirror column.
 template <typename T>
-inline void col_cfg(const pd_plan *p, int axis, bool last, int F, ColGeom &g, LaunchCfg &c)
+inline void col_cfg(const pd_plan *p, int axis, bool last, int FB, int FI, ColGeom &g, LaunchCfg &c,
+                    int64_t &inner)
 {
     const int H = p->h;
     const int L = axis == 1 ? p->n2 : p->n3;
     const int nt = L >> 4;
     const int mirror = (p->dim == 3 && last) ? 1 : 0;
-    int64_t inner;
-    int64_t rowstride, outer, outerstride;
-    if (axis == 1) {
-        inner = H;
-        rowstride = H;
-        outer = p->n3;
-        outerstride = (int64_t)p->n2 * H;
-    } else {
-        inner = (int64_t)p->n2 * H;
-        rowstride = inner;
-        outer = 1;
-        outerstride = 0;
-    }
-    int w = 16;
-    while (w > 2 && ((w + mirror) * nt > 512 ||
-                     (size_t)F * L * (w + 1) * sizeof(cx<T>) > 200 * 1024))
-        w >>= 1;
-    while (w > 1 && (H % w)) w >>= 1;
+    inner = axis == 1 ? (int64_t)H : (int64_t)p->n2 * H;
+    auto smem_of = [&](int w) {
+        return (size_t)L * sizeof(cx<T>) + (size_t)FB * L * w * sizeof(cx<T>) +
+               (mirror ? (size_t)FI * L * 2 * sizeof(cx<T>) : 0) + 16;
+    };
+    int w = 32;
+    while (w > 4 && ((w + mirror) * nt > 512 || smem_of(w) > 100 * 1024 || (H % w))) w >>= 1;
     g.lgl = ilog2(L);
     g.w = w;
-    g.pitch = w + 1;
     g.mirror = mirror;
-    g.inner = inner;
-    g.rowstride = rowstride;
-    g.outerstride = outerstride;
     g.lgh = ilog2(H);
     g.n2 = p->n2;
     g.lgtw = p->lgl;
-    c.grid = dim3((unsigned)(inner / w), (unsigned)outer);
+    g.lb = L < 256 ? L : 256;
+    g.outer = axis == 1 ? p->n3 : 1;
+    g.err = p->dev_status;
+    c.grid = dim3((unsigned)(inner / w), (unsigned)g.outer);
     c.block = dim3((w + mirror) * nt);
-    c.smem = (size_t)F * L * g.pitch * sizeof(cx<T>);
+    c.smem = smem_of(w);
 }
 
 pd_status set_smem_attr(const void *func, size_t smem);
@@ -251,28 +270,53 @@ pd_status set_smem_attr(const void *func, size_t smem);
 // pass kinds for the timing facility
 enum PassKind { PASS_ROWS_FWD = 0, PASS_COLS = 1, PASS_LAST = 2, PASS_ROWS_INV = 3 };
 pd_status prof_harvest(pd_plan *p);
+pd_status prof_harvest_range(pd_plan *p, int b, int e);
+
+// Layout of the plan's FP64 reduction buffer (65536 doubles).
+constexpr int kRedPart = 0;       // block partial sums (up to kMaxPart)
+constexpr int kMaxPart = 58000;
+constexpr int kRedScal = 60000;   // solver scalars
+constexpr int kRedVerlet = 62000; // Verlet counters
+// the device status word sits in the last 64 bytes
+// Events recorded while the stream is being captured must become external
+// event nodes of the graph, so that each replay records them.
+inline cudaError_t prof_record(cudaEvent_t e, cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t r = cudaStreamIsCapturing(st, &cs);
+    if (r != cudaSuccess) return r;
+    return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e, st, cudaEventRecordExternal)
+                                               : cudaEventRecord(e, st);
+}
+
 inline pd_status prof_begin(pd_plan *p, int kind, cudaStream_t st)
 {
     if (!p->prof_on) return PD_OK;
     if (p->ev_used == pd_plan::kEvPool) PD_TRY(prof_harvest(p));
+    if (p->ev_used == pd_plan::kEvPool) {
+        set_error("profiling event pool exhausted");
+        return PD_ERR_ARG;
+    }
     p->ev_kind[p->ev_used] = kind;
-    PD_CUDA_TRY(cudaEventRecord(p->ev[2 * p->ev_used], st));
+    PD_CUDA_TRY(prof_record(p->ev[2 * p->ev_used], st));
     return PD_OK;
 }
 inline pd_status prof_end(pd_plan *p, cudaStream_t st)
 {
     if (!p->prof_on) return PD_OK;
-    PD_CUDA_TRY(cudaEventRecord(p->ev[2 * p->ev_used + 1], st));
+    PD_CUDA_TRY(prof_record(p->ev[2 * p->ev_used + 1], st));
     p->ev_used++;
     return PD_OK;
 }
 
 template <typename T, class Op>
-pd_status launch_rows(pd_plan *p, const Op &op, int F, cudaStream_t st)
+pd_status launch_rows(pd_plan *p, const Op &op, cudaStream_t st)
 {
     RowGeom g;
     LaunchCfg c;
-    row_cfg<T>(p, F, g, c);
+    constexpr int KO = Op::kFout > Op::kStage ? Op::kFout : Op::kStage;
+    constexpr int FB = Op::kFin > KO ? Op::kFin : KO;
+    row_cfg<T>(p, FB, Op::kNF, Op::kNB, g, c);
     PD_TRY(set_smem_attr((const void *)k_rows<T, Op>, c.smem));
     PD_TRY(prof_begin(p, Op::kFin > 0 ? PASS_ROWS_INV : PASS_ROWS_FWD, st));
     k_rows<T, Op><<<c.grid, c.block, c.smem, st>>>(g, op, tw_buf<T>(p));
@@ -282,42 +326,55 @@ pd_status launch_rows(pd_plan *p, const Op &op, int F, cudaStream_t st)
     return PD_OK;
 }
 
+template <typename T>
+inline int spec_slots(const pd_plan *p) { return sizeof(T) == 8 ? p->spec64_slots : p->spec32_slots; }
+
 template <typename T, class Op>
 pd_status launch_cols(pd_plan *p, const Op &op, int axis, bool last, int F, cudaStream_t st)
 {
     ColGeom g;
     LaunchCfg c;
-    col_cfg<T>(p, axis, last, F, g, c);
+    int64_t inner = 0;
+    col_cfg<T>(p, axis, last, F, Op::kFin, g, c, inner);
+    const int L = 1 << g.lgl;
+    const unsigned long long dims[3] = {(unsigned long long)(2 * inner), (unsigned long long)L,
+                                        (unsigned long long)g.outer * spec_slots<T>(p)};
+    const unsigned long long strides[2] = {(unsigned long long)(2 * inner * sizeof(T)),
+                                           (unsigned long long)(2 * inner * L * sizeof(T))};
+    const unsigned box_t[3] = {(unsigned)(2 * g.w), (unsigned)g.lb, 1u};
+    const unsigned box_m[3] = {4u, (unsigned)g.lb, 1u};
+    CUtensorMap tmt, tmm;
+    PD_TRY(encode_tmap_3d(&tmt, spec_buf<T>(p), sizeof(T) == 8, dims, strides, box_t));
+    PD_TRY(encode_tmap_3d(&tmm, spec_buf<T>(p), sizeof(T) == 8, dims, strides, box_m));
     PD_TRY(set_smem_attr((const void *)k_cols<T, Op>, c.smem));
     PD_TRY(prof_begin(p, last ? PASS_LAST : PASS_COLS, st));
-    k_cols<T, Op><<<c.grid, c.block, c.smem, st>>>(g, op, tw_buf<T>(p), axis == 2 ? 1 : 0);
+    k_cols<T, Op><<<c.grid, c.block, c.smem, st>>>(g, op, tw_buf<T>(p), axis == 2 ? 1 : 0, tmt, tmm);
     PD_LAUNCH_CHECK();
     PD_TRY(prof_end(p, st));
     p->launches++;
     return PD_OK;
 }
 
-// Plain column FFT of F packed spectra along axis (forward or inverse), in place.
+// Plain column FFT of F packed spectra (slots slot0 ... slot0+F-1) along x2, in place.
 template <typename T, int F, int MODE>
 struct ColPass {
     static constexpr int kFin = F, kFout = F, kMode = MODE, kPre = 0;
     static constexpr bool kStoreIn = false;
-    cx<T> *spec;
-    int64_t fstride;  // complex elements per field
-    __device__ const cx<T> *spec_in(int f) const { return spec + f * fstride; }
-    __device__ cx<T> *spec_out(int f) const { return spec + f * fstride; }
-    __device__ cx<T> *spec_aux(int) const { return nullptr; }
+    int slot0;
+    __device__ int slot_in(int f) const { return slot0 + f; }
+    __device__ int slot_out(int f) const { return slot0 + f; }
+    __device__ int slot_aux(int) const { return 0; }
     __device__ void combine(int, int, int, const cx<T> *, cx<T> *) const {}
 };
 
 template <typename T, int F>
-pd_status col_pass(pd_plan *p, cx<T> *spec, bool inverse, cudaStream_t st)
+pd_status col_pass(pd_plan *p, int slot0, bool inverse, cudaStream_t st)
 {
     if (inverse) {
-        ColPass<T, F, 1> op{spec, p->N / 2};
+        ColPass<T, F, 1> op{slot0};
         return launch_cols<T>(p, op, 1, false, F, st);
     }
-    ColPass<T, F, 0> op{spec, p->N / 2};
+    ColPass<T, F, 0> op{slot0};
     return launch_cols<T>(p, op, 1, false, F, st);
 }
 

@@ -6,59 +6,50 @@
 // definite on Omega (the bond sum of Eq. 17-18 / 36 with the chi_B cut is a
 // weighted graph Laplacian once the constraint removes the rigid motions).
 //
-// Precision: on an FP32 plan the CG runs on FP32 FFT convolutions with FP64
-// inner products, inside an iterative refinement whose residual R(u) is
-// recomputed with the FP64 convolution path on the FP64 iterate u. The outer
-// loop stops when ||R(u)||_2 <= rtol ||chi_O b||_2 (both in FP64). On an FP64
-// plan the same code runs with FP64 everywhere.
+// Precision: on an FP32 plan the CG runs on FP32 FFT convolutions inside an
+// iterative refinement whose residual R(u) is recomputed with the FP64
+// convolution path on the FP64 iterate u; the outer loop stops when
+// ||R(u)||_2 <= rtol ||chi_O b||_2 (both in FP64). On an FP64 plan the same code
+// runs in FP64. CG inner products are accumulated per thread in compensated
+// FP32 (two-sum) and per block in FP64.
 //
-// All CG scalars (alpha, beta, residual norms) stay on the device; the host
-// reads the residual norm every kCheck iterations to decide when to stop.
+// One CG iteration is five fused passes and three small kernels:
+//   rows  : p = r + beta p (stored), FFT_x1 of chi p
+//   cols / last / cols : FFT_x2, M^ multiply with FFT_x3, inverse (3D)
+//   rows  : inverse FFT_x1, q = -chi_O L(p) (stored), block partials of p.q
+//   finish: alpha = rr / p.q
+//   update: e += alpha p, r -= alpha q, block partials of r.r
+//   finish: beta = rr_new / rr
+// All CG scalars stay on the device. Chunks of kChunk iterations are captured
+// once into a CUDA graph and replayed; the host reads the residual norm after
+// each chunk.
+#include <algorithm>
 #include <cmath>
-#include <vector>
 
-#include "pd_plan.cuh"
+#include "pd_force_impl.cuh"
 
 namespace pd {
-
-template <typename T>
-pd_status force_plain(pd_plan *p, const T *u, const T *s, T *L, T *W, cudaStream_t st);
-
 namespace {
 
-constexpr int kRedBlocks = 1024;     // partial-sum slots per reduction
-constexpr int kCheck = 16;           // CG iterations between host checks
-// layout of the plan's reduction buffer (doubles)
-constexpr int RED_PART = 0;          // kRedBlocks partials
-constexpr int RED_SCAL = 2048;       // scalars below
+constexpr int kChunk = 16;       // CG iterations per graph replay
+constexpr int kUpdBlocks = 1024;  // blocks of the vector kernels
 enum { S_RR = 0, S_PQ, S_ALPHA, S_BETA, S_RRNEW, S_NORM, S_BN, S_FLAG, S_COUNT };
 
-unsigned red_blocks(const pd_plan *p) { return (unsigned)std::min<int64_t>(kRedBlocks, 2 * (int64_t)p->nsm); }
-
-__device__ __forceinline__ double block_sum(double v)
+__device__ __forceinline__ void write_partial(double *red, double v)
 {
-    __shared__ double sh[32];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
-    if (wid == 0)
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    __syncthreads();
-    return v;
+    const double t = block_sum_d(v);
+    if (threadIdx.x == 0) red[kRedPart + blockIdx.x] = t;
 }
 
-// Final reduction of the block partials into scalar `dst`, then the CG scalar
-// update selected by `what`:
+// Final reduction of nparts block partials into scalar `dst`, then:
 //   0: store only; 1: alpha = rr / pq; 2: beta = rrnew / rr, rr = rrnew
 __global__ void k_finish(double *red, int nparts, int dst, int what)
 {
     double v = 0.0;
-    for (int i = threadIdx.x; i < nparts; i += blockDim.x) v += red[RED_PART + i];
-    v = block_sum(v);
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) v += red[kRedPart + i];
+    v = block_sum_d(v);
     if (threadIdx.x == 0) {
-        double *s = red + RED_SCAL;
+        double *s = red + kRedScal;
         s[dst] = v;
         if (!isfinite(v)) s[S_FLAG] = 1.0;
         if (what == 1) {
@@ -82,8 +73,7 @@ __global__ void k_apply_bc(double *u, const double *w, const double *b, const ui
         const double bb = m * b[i];
         acc += bb * bb;
     }
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) red[RED_PART + blockIdx.x] = acc;
+    write_partial(red, acc);
 }
 
 // r = chi_O (b + L) in place on L ; partial ||r||^2
@@ -95,64 +85,69 @@ __global__ void k_residual(double *r, const double *b, const uint8_t *co, int64_
         r[i] = v;
         acc += v * v;
     }
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) red[RED_PART + blockIdx.x] = acc;
+    write_partial(red, acc);
 }
 
-// r = (T) r64, p = r, e = 0 ; partial r.r
+// r = (T) r64, p = 0, e = 0 ; partial r.r
 template <typename T>
 __global__ void k_cg_init(const double *r64, T *r, T *pp, T *e, int64_t n, double *red)
 {
-    double acc = 0.0;
+    DSum acc;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const T v = (T)r64[i];
         r[i] = v;
-        pp[i] = v;
+        pp[i] = T(0);
         e[i] = T(0);
-        acc += (double)v * (double)v;
+        acc.add(v * v);
     }
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) red[RED_PART + blockIdx.x] = acc;
+    write_partial(red, acc.value());
 }
 
-// q = -chi_O L(p) in place ; partial p.q
-template <typename T>
-__global__ void k_cg_q(T *q, const T *pp, const uint8_t *co, int64_t n, double *red)
-{
-    double acc = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const T v = co[i] ? -q[i] : T(0);
-        q[i] = v;
-        acc += (double)pp[i] * (double)v;
-    }
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) red[RED_PART + blockIdx.x] = acc;
-}
-
-// e += alpha p ; r -= alpha q ; partial r.r
+// e += alpha p ; r -= alpha q ; partial r.r   (n a multiple of 2)
 template <typename T>
 __global__ void k_cg_update(T *e, T *r, const T *pp, const T *q, int64_t n, double *red)
 {
-    const double a = red[RED_SCAL + S_ALPHA];
-    const T at = (T)a;
-    double acc = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        e[i] += at * pp[i];
-        const T rv = r[i] - at * q[i];
-        r[i] = rv;
-        acc += (double)rv * (double)rv;
+    using V = typename vec2<T>::type;
+    const T a = (T)red[kRedScal + S_ALPHA];
+    DSum acc;
+    const int64_t n2 = n / 2;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
+        V ev = reinterpret_cast<V *>(e)[i];
+        V rv = reinterpret_cast<V *>(r)[i];
+        const V pv = reinterpret_cast<const V *>(pp)[i];
+        const V qv = reinterpret_cast<const V *>(q)[i];
+        ev.x += a * pv.x;
+        ev.y += a * pv.y;
+        rv.x -= a * qv.x;
+        rv.y -= a * qv.y;
+        reinterpret_cast<V *>(e)[i] = ev;
+        reinterpret_cast<V *>(r)[i] = rv;
+        acc.add(rv.x * rv.x);
+        acc.add(rv.y * rv.y);
     }
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) red[RED_PART + blockIdx.x] = acc;
+    write_partial(red, acc.value());
 }
 
-// p = r + beta p
+// p = r + beta p (state-based path, unfused)
 template <typename T>
 __global__ void k_cg_dir(T *pp, const T *r, int64_t n, const double *red)
 {
-    const T bt = (T)red[RED_SCAL + S_BETA];
+    const T bt = (T)red[kRedScal + S_BETA];
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         pp[i] = r[i] + bt * pp[i];
+}
+
+// q = -chi_O L(p) in place ; partial p.q (state-based path, unfused)
+template <typename T>
+__global__ void k_cg_q(T *q, const T *pp, const uint8_t *co, int64_t n, double *red)
+{
+    DSum acc;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const T v = co[i] ? -q[i] : T(0);
+        q[i] = v;
+        acc.add(pp[i] * v);
+    }
+    write_partial(red, acc.value());
 }
 
 // u += e on Omega
@@ -163,23 +158,130 @@ __global__ void k_ir_update(double *u, const T *e, const uint8_t *co, int64_t n)
         if (co[i]) u[i] += (double)e[i];
 }
 
+// rows, forward: p = r + beta p (stored), transform chi p
+template <typename T, int D>
+struct ProCG {
+    static constexpr int kFin = 0, kFout = D, kNF = 2 * D, kNB = 1, kStage = 0;
+    static constexpr bool kSparse = false;
+    const T *r;
+    T *pv;
+    const uint8_t *chi;
+    const double *scal;
+    int64_t N;
+    int n1;
+    cx<T> *spec;
+    int64_t fstride;
+    __device__ const cx<T> *spec_in(int) const { return nullptr; }
+    __device__ cx<T> *spec_out(int f) const { return spec + f * fstride; }
+    __device__ const T *nf_src(int k) const { return k < D ? r + k * N : pv + (k - D) * N; }
+    __device__ const uint8_t *nb_src(int) const { return chi; }
+    __device__ __forceinline__ void node2(const RowCtx<T> &c, int rl, int i1, const T *, const T *, T *o0,
+                                          T *o1) const
+    {
+        const T beta = (T)scal[S_BETA];
+        const T v0 = c.b(0, rl, i1) ? T(1) : T(0), v1 = c.b(0, rl, i1 + 1) ? T(1) : T(0);
+        const int64_t p = (c.row0 + rl) * n1 + i1;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            const T a = c.f(j, rl, i1) + beta * c.f(D + j, rl, i1);
+            const T b = c.f(j, rl, i1 + 1) + beta * c.f(D + j, rl, i1 + 1);
+            store2(pv + j * N + p, a, b);
+            o0[j] = v0 * a;
+            o1[j] = v1 * b;
+        }
+    }
+    __device__ void sparse(const RowCtx<T> &, int, int) const {}
+    __device__ void emit(const RowCtx<T> &, int, int, const T *, const T *, DSum &) const {}
+    __device__ void block_done(DSum &) const {}
+};
+
+// rows, inverse: L = chi y staged, boundary fix-up with G p, q = -chi_O L,
+// block partials of p.q
+template <typename T, int D>
+struct EpiCG {
+    static constexpr int kFin = D, kFout = 0, kStage = D, kNF = D, kNB = 1 + D;
+    static constexpr bool kSparse = true;
+    const T *pv;
+    const uint8_t *chi, *co;
+    const GEntry<T> *gent;
+    const int *goff;
+    T *q;
+    double *red;
+    int64_t N;
+    int n1;
+    const cx<T> *spec;
+    int64_t fstride;
+    __device__ const cx<T> *spec_in(int f) const { return spec + f * fstride; }
+    __device__ cx<T> *spec_out(int) const { return nullptr; }
+    __device__ const T *nf_src(int k) const { return pv + k * N; }
+    __device__ const uint8_t *nb_src(int k) const { return k == 0 ? chi : co + (k - 1) * N; }
+    __device__ __forceinline__ void node2(const RowCtx<T> &c, int rl, int i1, const T *in0, const T *in1, T *o0,
+                                          T *o1) const
+    {
+        const T v0 = c.b(0, rl, i1) ? T(1) : T(0), v1 = c.b(0, rl, i1 + 1) ? T(1) : T(0);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            o0[i] = v0 * in0[i];
+            o1[i] = v1 * in1[i];
+        }
+    }
+    __device__ void sparse(const RowCtx<T> &c, int tid, int nthreads) const
+    {
+        const int k0 = goff[c.row0], k1 = goff[c.row0 + c.rows];
+        for (int k = k0 + tid; k < k1; k += nthreads) {
+            const GEntry<T> e = gent[k];
+            const int64_t p = e.p;
+            const int rl = (int)(p / n1 - c.row0), i1 = (int)(p % n1);
+            T pp[D], Gp[D];
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                pp[j] = c.f(j, rl, i1);
+                Gp[j] = T(0);
+            }
+            sym_apply<T, D>(e.g, pp, Gp);
+#pragma unroll
+            for (int i = 0; i < D; ++i) c.stage(i, rl, i1) -= Gp[i];
+        }
+    }
+    __device__ __forceinline__ void emit(const RowCtx<T> &c, int rl, int i1, const T *s0, const T *s1,
+                                         DSum &acc) const
+    {
+        const int64_t p = (c.row0 + rl) * n1 + i1;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const T a = c.b(1 + i, rl, i1) ? -s0[i] : T(0);
+            const T b = c.b(1 + i, rl, i1 + 1) ? -s1[i] : T(0);
+            store2(q + i * N + p, a, b);
+            acc.add(c.f(i, rl, i1) * a);
+            acc.add(c.f(i, rl, i1 + 1) * b);
+        }
+    }
+    __device__ void block_done(DSum &acc) const { write_partial(red, acc.value()); }
+};
+
 struct Solver {
     pd_plan *p;
     cudaStream_t st;
-    double *hbuf;  // pinned host scalars
     int64_t nvec;
     unsigned nb;
 
-    pd_status finish(int dst, int what)
+    double *hs() const { return p->host_scal; }
+
+    pd_status finish(int nparts, int dst, int what)
     {
-        k_finish<<<1, 1024, 0, st>>>(p->red, nb, dst, what);
+        k_finish<<<1, 1024, 0, st>>>(p->red, nparts, dst, what);
         PD_LAUNCH_CHECK();
         p->launches++;
         return PD_OK;
     }
+    pd_status copy_scalars()
+    {
+        PD_CUDA_TRY(cudaMemcpyAsync(hs(), p->red + kRedScal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, st));
+        return PD_OK;
+    }
     pd_status read_scalars()
     {
-        PD_CUDA_TRY(cudaMemcpyAsync(hbuf, p->red + RED_SCAL, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, st));
+        PD_TRY(copy_scalars());
         PD_CUDA_TRY(cudaStreamSynchronize(st));
         return PD_OK;
     }
@@ -191,9 +293,9 @@ struct Solver {
         k_residual<<<nb, 256, 0, st>>>(p->r64, b, p->chi_om, nvec, p->red);
         PD_LAUNCH_CHECK();
         p->launches++;
-        PD_TRY(finish(S_NORM, 0));
+        PD_TRY(finish(nb, S_NORM, 0));
         PD_TRY(read_scalars());
-        *rn = std::sqrt(hbuf[S_NORM]);
+        *rn = std::sqrt(hs()[S_NORM]);
         if (!std::isfinite(*rn)) {
             set_error("pd_solve_static: non-finite residual");
             return PD_ERR_NONFINITE;
@@ -201,46 +303,125 @@ struct Solver {
         return PD_OK;
     }
 
-    // CG on A e = r64 until ||r|| <= tol_abs or max_it; returns iterations done
-    template <typename T>
-    pd_status cg(double tol_abs, int max_it, int *done, double *rr_last)
+    // one CG iteration (enqueued; no host synchronisation)
+    template <typename T, int D>
+    pd_status iteration()
     {
-        T *e = (T *)p->cg_e, *r = (T *)p->cg_r, *pp = (T *)p->cg_p, *q = (T *)p->cg_q;
-        k_cg_init<T><<<nb, 256, 0, st>>>(p->r64, r, pp, e, nvec, p->red);
+        T *e = (T *)p->cg_e, *r = (T *)p->cg_r, *pv = (T *)p->cg_p, *q = (T *)p->cg_q;
+        if (p->state_based) {
+            // state-based solid: the dilatation round trip sits between the
+            // halves of the operator, so the vector steps run as own kernels
+            k_cg_dir<T><<<nb, 256, 0, st>>>(pv, r, nvec, p->red);
+            PD_LAUNCH_CHECK();
+            PD_TRY(force_plain<T>(p, pv, nullptr, q, nullptr, st));
+            k_cg_q<T><<<nb, 256, 0, st>>>(q, pv, p->chi_om, nvec, p->red);
+            PD_LAUNCH_CHECK();
+            PD_TRY(finish(nb, S_PQ, 1));
+            k_cg_update<T><<<kUpdBlocks, 256, 0, st>>>(e, r, pv, q, nvec, p->red);
+            PD_LAUNCH_CHECK();
+            p->launches += 3;
+            return finish(kUpdBlocks, S_RRNEW, 2);
+        }
+        cx<T> *spec = reinterpret_cast<cx<T> *>(spec_buf<T>(p));
+        const int64_t fs = p->N / 2;
+        const Model<T> m = model_view<T>(p);
+        ProCG<T, D> pro{r, pv, p->chi, p->red + kRedScal, p->N, p->n1, spec, fs};
+        PD_TRY(launch_rows<T>(p, pro, st));
+        if (D == 3) PD_TRY((col_pass<T, D>(p, 0, false, st)));
+        const int ob = D == 3 ? D : 0;
+        CombForce<T, D, false> cmb{m, ob};
+        PD_TRY(launch_cols<T>(p, cmb, D == 3 ? 2 : 1, true, D, st));
+        if (D == 3) PD_TRY((col_pass<T, D>(p, ob, true, st)));
+        EpiCG<T, D> epi{pv, p->chi, p->chi_om, m.gent, m.goff, q, p->red, p->N, p->n1, spec + ob * fs, fs};
+        RowGeom g;
+        LaunchCfg c;
+        row_cfg<T>(p, D, EpiCG<T, D>::kNF, EpiCG<T, D>::kNB, g, c);
+        if ((int64_t)c.grid.x > kMaxPart) {
+            set_error("pd_solve_static: %u row blocks exceed the reduction buffer", c.grid.x);
+            return PD_ERR_SIZE;
+        }
+        PD_TRY(launch_rows<T>(p, epi, st));
+        PD_TRY(finish((int)c.grid.x, S_PQ, 1));
+        k_cg_update<T><<<kUpdBlocks, 256, 0, st>>>(e, r, pv, q, nvec, p->red);
         PD_LAUNCH_CHECK();
         p->launches++;
-        PD_TRY(finish(S_RR, 0));
+        PD_TRY(finish(kUpdBlocks, S_RRNEW, 2));
+        return PD_OK;
+    }
+
+    // a chunk of kChunk iterations followed by a copy of the scalars to the
+    // pinned host buffer, captured once into a CUDA graph per precision
+    template <typename T, int D>
+    pd_status chunk()
+    {
+        const int gi = sizeof(T) == 8 ? 1 : 0;
+        if (p->cg_graph[gi] && p->cg_graph_prof[gi] != p->prof_on) {
+            cudaGraphExecDestroy(p->cg_graph[gi]);
+            p->cg_graph[gi] = nullptr;
+        }
+        if (!p->cg_graph[gi]) {
+            if (p->prof_on) PD_TRY(prof_harvest(p));
+            const int ev0 = p->ev_used;
+            cudaGraph_t graph = nullptr;
+            PD_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            pd_status s = PD_OK;
+            for (int k = 0; k < kChunk && s == PD_OK; ++k) s = iteration<T, D>();
+            if (s == PD_OK) s = copy_scalars();
+            const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+            if (s != PD_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return s;
+            }
+            if (ce != cudaSuccess) {
+                set_error("graph capture failed: %s", cudaGetErrorString(ce));
+                return PD_ERR_CUDA;
+            }
+            const cudaError_t ie = cudaGraphInstantiate(&p->cg_graph[gi], graph, 0);
+            cudaGraphDestroy(graph);
+            if (ie != cudaSuccess) {
+                p->cg_graph[gi] = nullptr;
+                set_error("graph instantiation failed: %s", cudaGetErrorString(ie));
+                return PD_ERR_CUDA;
+            }
+            p->cg_graph_prof[gi] = p->prof_on;
+            p->cg_graph_ev[gi][0] = ev0;
+            p->cg_graph_ev[gi][1] = p->ev_used;
+            p->ev_reserved = p->ev_used;  // keep the graph's event pairs
+        }
+        PD_CUDA_TRY(cudaGraphLaunch(p->cg_graph[gi], st));
+        p->launches += (int64_t)kChunk * (p->state_based ? 13 : (D == 3 ? 8 : 6));
+        PD_CUDA_TRY(cudaStreamSynchronize(st));
+        if (p->prof_on) PD_TRY(prof_harvest_range(p, p->cg_graph_ev[gi][0], p->cg_graph_ev[gi][1]));
+        return PD_OK;
+    }
+
+    // CG on A e = r64 until ||r|| <= tol_abs or max_it; returns iterations done
+    template <typename T, int D>
+    pd_status cg(double tol_abs, int max_it, int *done)
+    {
+        T *e = (T *)p->cg_e, *r = (T *)p->cg_r, *pv = (T *)p->cg_p;
+        k_cg_init<T><<<nb, 256, 0, st>>>(p->r64, r, pv, e, nvec, p->red);
+        PD_LAUNCH_CHECK();
+        p->launches++;
+        PD_TRY(finish(nb, S_RR, 0));
+        PD_CUDA_TRY(cudaMemsetAsync(p->red + kRedScal + S_BETA, 0, sizeof(double), st));
         int it = 0;
         double best = HUGE_VAL;
         int since_best = 0;
         while (it < max_it) {
-            const int chunk = std::min(kCheck, max_it - it);
-            for (int k = 0; k < chunk; ++k) {
-                PD_TRY(force_plain<T>(p, pp, nullptr, q, nullptr, st));
-                k_cg_q<T><<<nb, 256, 0, st>>>(q, pp, p->chi_om, nvec, p->red);
-                PD_LAUNCH_CHECK();
-                PD_TRY(finish(S_PQ, 1));
-                k_cg_update<T><<<nb, 256, 0, st>>>(e, r, pp, q, nvec, p->red);
-                PD_LAUNCH_CHECK();
-                PD_TRY(finish(S_RRNEW, 2));
-                k_cg_dir<T><<<nb, 256, 0, st>>>(pp, r, nvec, p->red);
-                PD_LAUNCH_CHECK();
-                p->launches += 3;
-            }
-            it += chunk;
-            PD_TRY(read_scalars());
-            const double rn = std::sqrt(hbuf[S_RR]);
-            *rr_last = rn;
-            if (hbuf[S_FLAG] == 1.0) {
+            PD_TRY((chunk<T, D>()));
+            it += kChunk;
+            const double rn = std::sqrt(hs()[S_RR]);
+            if (hs()[S_FLAG] == 1.0) {
                 set_error("pd_solve_static: non-finite CG scalar");
                 return PD_ERR_NONFINITE;
             }
-            if (hbuf[S_FLAG] == 2.0 || rn <= tol_abs) break;
+            if (hs()[S_FLAG] == 2.0 || rn <= tol_abs) break;
             // stagnation of the recursive residual (FP32 attainable accuracy)
             if (rn < 0.999 * best) {
                 best = rn;
                 since_best = 0;
-            } else if ((since_best += chunk) >= 8 * kCheck) {
+            } else if ((since_best += kChunk) >= 8 * kChunk) {
                 break;
             }
         }
@@ -265,23 +446,24 @@ extern "C" pd_status pd_solve_static(pd_plan *p, double *u, const double *b, con
         set_error("pd_solve_static: rtol must be > 0 and max_iter >= 1");
         return PD_ERR_ARG;
     }
+    // The solve runs on the plan's own stream (CUDA graphs cannot be captured
+    // on the legacy default stream), ordered after the caller's stream.
+    cudaStream_t caller = (cudaStream_t)stream;
+    PD_CUDA_TRY(cudaEventRecord(p->ev_join[0], caller));
+    PD_CUDA_TRY(cudaStreamWaitEvent(p->own_stream, p->ev_join[0], 0));
     Solver S;
     S.p = p;
-    S.st = (cudaStream_t)stream;
+    S.st = p->own_stream;
     S.nvec = (int64_t)p->dim * p->N;
-    S.nb = red_blocks(p);
-    PD_CUDA_TRY(cudaMallocHost((void **)&S.hbuf, sizeof(double) * S_COUNT));
-    struct HostFree {
-        double *h;
-        ~HostFree() { cudaFreeHost(h); }
-    } hf{S.hbuf};
-    PD_CUDA_TRY(cudaMemsetAsync(p->red + RED_SCAL, 0, sizeof(double) * S_COUNT, S.st));
+    S.nb = (unsigned)std::min<int64_t>(kUpdBlocks, (S.nvec + 255) / 256);
+    PD_CUDA_TRY(cudaMemsetAsync(p->red + kRedScal, 0, sizeof(double) * S_COUNT, S.st));
+    PD_CUDA_TRY(cudaMemsetAsync(p->dev_status, 0, sizeof(int), S.st));
     k_apply_bc<<<S.nb, 256, 0, S.st>>>(u, w, b, p->chi_om, S.nvec, p->red);
     PD_LAUNCH_CHECK();
     p->launches++;
-    PD_TRY(S.finish(S_BN, 0));
+    PD_TRY(S.finish(S.nb, S_BN, 0));
     PD_TRY(S.read_scalars());
-    const double bn = std::sqrt(S.hbuf[S_BN]);
+    const double bn = std::sqrt(S.hs()[S_BN]);
     int total = 0;
     double rel = 0.0;
     pd_status result = PD_ERR_NOT_CONVERGED;
@@ -296,24 +478,36 @@ extern "C" pd_status pd_solve_static(pd_plan *p, double *u, const double *b, con
         }
         if (total >= max_iter) break;
         int done = 0;
-        double rlast = 0.0;
         if (p->prob.fp64) {
-            PD_TRY(S.cg<double>(0.5 * target, max_iter - total, &done, &rlast));
-            total += done;
+            if (p->dim == 3)
+                PD_TRY((S.cg<double, 3>(0.5 * target, max_iter - total, &done)));
+            else
+                PD_TRY((S.cg<double, 2>(0.5 * target, max_iter - total, &done)));
             k_ir_update<double><<<S.nb, 256, 0, S.st>>>(u, (const double *)p->cg_e, p->chi_om, S.nvec);
         } else {
             // inner FP32 solve: reduce the residual by 1e-3 (the FP32 operator
             // resolves A e to about that accuracy), never below the target
             const double tol = std::max(1e-3 * rn, 0.5 * target);
-            PD_TRY(S.cg<float>(tol, max_iter - total, &done, &rlast));
-            total += done;
+            if (p->dim == 3)
+                PD_TRY((S.cg<float, 3>(tol, max_iter - total, &done)));
+            else
+                PD_TRY((S.cg<float, 2>(tol, max_iter - total, &done)));
             k_ir_update<float><<<S.nb, 256, 0, S.st>>>(u, (const float *)p->cg_e, p->chi_om, S.nvec);
         }
         PD_LAUNCH_CHECK();
         p->launches++;
+        total += done;
         if (done == 0) break;
     }
     PD_CUDA_TRY(cudaStreamSynchronize(S.st));
+    PD_CUDA_TRY(cudaEventRecord(p->ev_join[1], S.st));
+    PD_CUDA_TRY(cudaStreamWaitEvent(caller, p->ev_join[1], 0));
+    int hstat = 0;
+    PD_CUDA_TRY(cudaMemcpy(&hstat, p->dev_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (hstat) {
+        set_error("pd_solve_static: a bounded device wait timed out (status %d)", hstat);
+        return PD_ERR_TIMEOUT;
+    }
     if (iters_out) *iters_out = total;
     if (relres_out) *relres_out = rel;
     if (result != PD_OK) set_error("pd_solve_static: relative residual %.3e above rtol %.3e after %d iterations",

@@ -99,7 +99,7 @@ pd_status verlet_impl(pd_plan *p, T *u, T *v, uint8_t *lam, const T *b, const T 
     T *W = (T *)p->theta;
     T *G = lam ? (T *)p->Gw : (sizeof(T) == 8 ? (T *)p->G64 : (T *)p->G32);
     const int breaking = (lam && p->prob.Wc > 0) ? 1 : 0;
-    VerletCounters *cnt = reinterpret_cast<VerletCounters *>(p->red + 4096);
+    VerletCounters *cnt = reinterpret_cast<VerletCounters *>(p->red + kRedVerlet);
     PD_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(VerletCounters), st));
     const unsigned nbl = (unsigned)((N + 127) / 128);
     if (lam) {
