@@ -229,19 +229,25 @@ double pd_stable_dt(const pd_plan *plan);
  * created (for launch accounting). */
 int64_t pd_plan_launch_count(const pd_plan *plan);
 
+/* Number of body nodes within delta of the body's boundary, where the
+ * boundary field G of pd_plan_create is nonzero (kept as a sparse list). */
+int64_t pd_plan_boundary_nodes(const pd_plan *plan);
+
 /*
- * Per-pass timing (diagnostics). With profiling enabled, every FFT-pass launch
- * of the plan is bracketed by two CUDA events recorded on the launching stream
- * (the events are created in pd_plan_create); pd_plan_profile_read returns the
- * summed event time and the launch count of one pass kind since the last
- * pd_plan_profile call:
+ * Per-pass timing (diagnostics). pd_plan_profile(plan, mask) selects the pass
+ * kinds to time (bit k for kind k, 0 switches timing off): every FFT-pass
+ * launch of a selected kind is then bracketed by two CUDA events recorded on
+ * the launching stream (the events are created in pd_plan_create; inside the
+ * solver's CUDA graphs they are graph event nodes). pd_plan_profile_read
+ * returns the summed event time and the launch count of one pass kind since
+ * the last pd_plan_profile call:
  *   0 row pass, forward (prologue + x1 transform)
  *   1 column pass along x2 (3D), forward or inverse
  *   2 last-axis pass (forward transform, spectral combine, inverse transform)
  *   3 row pass, inverse (x1 transform + epilogue)
  * Reading synchronises on the recorded events. Enabling resets the counters.
  */
-pd_status pd_plan_profile(pd_plan *plan, int enable);
+pd_status pd_plan_profile(pd_plan *plan, int mask);
 pd_status pd_plan_profile_read(pd_plan *plan, int kind, double *ms_total, int64_t *launches);
 
 const char *pd_status_string(pd_status status);

@@ -68,17 +68,18 @@ struct ProAdj {
 template <typename T, int D>
 struct CombAdj {
     static constexpr int NC = Sym<D>::n;
-    static constexpr int kFin = 2 * D + NC, kFout = 2 * D + 1, kMode = 2, kPre = 0;
+    static constexpr int kFin = 2 * D + NC, kFout = 2 * D + 1, kMode = 2, kPre = 0, kTab = NC;
     static constexpr bool kStoreIn = false;
     Model<T> m;
     int obase;  // first output slot (out of place in 3D)
     __device__ int slot_in(int f) const { return f; }
     __device__ int slot_out(int f) const { return obase + f; }
     __device__ int slot_aux(int) const { return 0; }
-    __device__ __forceinline__ void combine(int kx, int ky, int kz, const cx<T> *in, cx<T> *out) const
+    __device__ const T *table(int c) const { return m.mhat + c * m.fold_sz; }
+    __device__ __forceinline__ void combine(const T *t, int cs, bool fy, bool fz, const cx<T> *in, cx<T> *out) const
     {
         T M[9];
-        load_mhat(m, spec_index(m, kx, ky, kz), M);
+        load_mhat_s(D, t, cs, fy, fz, M);
         mat_vec<T, D>(M, in, out);
         mat_vec<T, D>(M, in + D, out + D);
         cx<T> acc = mk(T(0), T(0));

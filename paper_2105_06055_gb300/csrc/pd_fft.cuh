@@ -296,13 +296,13 @@ __global__ void __launch_bounds__(256) k_rows(RowGeom g, Op op, const cx<T> *__r
             }
         }
         __syncthreads();
-#pragma unroll
+#pragma unroll 1
         for (int f = 0; f < FI; ++f) fft_smem<T>(spec + (f * rows + rf) * pitch, 1, g.lgh, jt, tws, lg1);
     }
 
     // per-node work, lanes over consecutive packed slots (2 nodes each)
     for (int idx = threadIdx.x; idx < rows * H; idx += blockDim.x) {
-        const int rl = idx / H, n = idx - rl * H;
+        const int rl = idx >> g.lgh, n = idx & (H - 1);
         T in0[FI > 0 ? FI : 1], in1[FI > 0 ? FI : 1];
         T o0[KO > 0 ? KO : 1], o1[KO > 0 ? KO : 1];
 #pragma unroll
@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(256) k_rows(RowGeom g, Op op, const cx<T> *__r
     DSum acc;
     if constexpr (ST > 0) {
         for (int idx = threadIdx.x; idx < rows * H; idx += blockDim.x) {
-            const int rl = idx / H, n = idx - rl * H;
+            const int rl = idx >> g.lgh, n = idx & (H - 1);
             T s0[ST], s1[ST];
 #pragma unroll
             for (int f = 0; f < ST; ++f) {
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(256) k_rows(RowGeom g, Op op, const cx<T> *__r
     op.block_done(acc);
 
     if constexpr (FO > 0) {
-#pragma unroll
+#pragma unroll 1
         for (int f = 0; f < FO; ++f) fft_smem<T>(spec + (f * rows + rf) * pitch, 1, g.lgh, jt, tws, lg1);
         const T half = T(0.5);
 #pragma unroll
@@ -370,6 +370,7 @@ __global__ void __launch_bounds__(256) k_rows(RowGeom g, Op op, const cx<T> *__r
 struct ColGeom {
     int lgl;     // log2 of the transform length L (axis length)
     int w;       // tile width (columns, power of two, divides the inner extent)
+    int lgw;     // log2(w)
     int mirror;  // 1: 3D last-axis pass, also loads the mirror of column kx = 0
     int lgh;     // log2(n1/2) (packed row length), for mode coordinates
     int n2;      // n2 (3D mirror of k2)
@@ -386,9 +387,14 @@ struct ColGeom {
 //   kPre: (kMode 2) leading inputs already transformed along this axis
 //   kStoreIn: (kMode 2) store the transformed inputs to slot_aux(f) first
 //   int slot_in(int f), slot_out(int f), slot_aux(int f): packed-spectrum slots
-//   void combine(int kx, int ky, int kz, const cx<T>* in, cx<T>* out) const;
+//   static constexpr int kTab; const T* table(int c): kTab folded kernel-spectrum
+//        components (layout [k3f][k2f][k1], k1 in [0, n1/2]); the tile's slice is
+//        prefetched into shared memory while the TMA loads are in flight
+//   void combine(const T* t, int cs, bool fy, bool fz, const cx<T>* in, cx<T>* out);
 //        (kMode 2; called for true modes with kx in [0, n1/2], so both the
-//         kx = 0 and kx = n1/2 halves of the packed column are visited)
+//         kx = 0 and kx = n1/2 halves of the packed column are visited; t points
+//         at component 0 of the mode in the slice, cs is the component stride,
+//         fy / fz say that k2 / k3 were folded to n - k)
 // Tensor maps: tmt covers all slots of the spectrum buffer as
 // [outer * slots][L][2 * inner] scalars with box (2w, lb, 1); tmm the same with
 // box (4, lb, 1) for the mirror column.
@@ -413,7 +419,10 @@ __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__r
     cx<T> *tws = reinterpret_cast<cx<T> *>(smem_raw);  // W_L^i, i < L
     cx<T> *tile = tws + L;
     cx<T> *mir = tile + FB * fsz;
-    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(mir + (g.mirror ? FI * L * 2 : 0));
+    constexpr int NTAB = (MODE == 2) ? Op::kTab : 0;
+    const int trows = L / 2 + 1, tcols = w + 1, tcs = trows * tcols;  // table slice [comp][fold row][kx]
+    T *tab = reinterpret_cast<T *>(mir + (g.mirror ? FI * L * 2 : 0));
+    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(tab + ((NTAB * tcs + 1) & ~1));
 
     // mirror column (3D last axis): kx = 0 of k2' = (n2 - k2) mod n2
     int mcol = -1;
@@ -434,7 +443,23 @@ __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__r
             }
         }
     }
+    // kernel-table slice of this tile (overlaps the TMA loads)
+    const int kx0 = axis_is_z ? (c0 & (H - 1)) : c0;
+    const int kyt = c0 >> g.lgh;  // 3D: the tile's k2
+    const bool fyt = axis_is_z && kyt > (g.n2 >> 1);
+    if constexpr (NTAB > 0) {
+        const int kyf = fyt ? g.n2 - kyt : kyt;
+        for (int i = threadIdx.x; i < NTAB * tcs; i += nthreads) {
+            const int comp = i / tcs, rem = i - comp * tcs;
+            const int rr = rem / tcols, cc = rem - rr * tcols;
+            const int kx = (cc == w) ? H : kx0 + cc;
+            const int64_t gi = axis_is_z ? ((int64_t)rr * ((g.n2 >> 1) + 1) + kyf) * (H + 1) + kx
+                                         : (int64_t)rr * (H + 1) + kx;
+            tab[i] = op.table(comp)[gi];
+        }
+    }
     if (!mbar_wait(mbar, 0, g.err)) return;
+    if constexpr (NTAB > 0) __syncthreads();
 
     // per-thread transform: a tile column, or the mirror column
     const bool is_m = col >= w;
@@ -442,7 +467,7 @@ __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__r
     auto colbase = [&](int f) -> cx<T> * { return is_m ? (mir + f * L * 2) : (tile + f * fsz + col); };
 
     constexpr int FPRE = (MODE == 2) ? Op::kPre : 0;
-#pragma unroll
+#pragma unroll 1
     for (int f = FPRE; f < FI; ++f)
         fft_smem<T>(colbase(f), cstride, g.lgl, jt, tws, g.lgl, MODE == 1, MODE == 1);
 
@@ -463,24 +488,19 @@ __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__r
     if constexpr (MODE == 2) {
         // ---- spectral combine; writes conj(output) for the inverse
         const bool self_m = (mcol == c0);  // k2 is its own mirror: results parked in mir
+        const int half = L >> 1;
+        // table position of mode (row r, column c) and of the kx = n1/2 half
+        auto tpos = [&](int r, int kxl) { return (r <= half ? r : L - r) * tcols + kxl; };
         for (int idx = threadIdx.x; idx < L * w; idx += nthreads) {
-            const int r = idx / w, c = idx % w;
-            const int ic = c0 + c;
-            int kx, ky, kz;
-            if (axis_is_z) {
-                kz = r;
-                ky = ic >> g.lgh;
-                kx = ic & (H - 1);
-            } else {
-                kz = 0;
-                ky = r;
-                kx = ic;
-            }
+            const int r = idx >> g.lgw, c = idx & (w - 1);
+            const int kx = kx0 + c;
+            const bool fr = r > half;  // the row's wave number was folded
+            const bool fy = axis_is_z ? fyt : fr, fz = axis_is_z && fr;
             cx<T> in[FB], out[FB];
             if (kx != 0) {
 #pragma unroll
                 for (int f = 0; f < FI; ++f) in[f] = tile[f * fsz + r * w + c];
-                op.combine(kx, ky, kz, in, out);
+                op.combine(tab + tpos(r, c), tcs, fy, fz, in, out);
 #pragma unroll
                 for (int f = 0; f < FO; ++f) tile[f * fsz + r * w + c] = conjg(out[f]);
             } else if (axis_is_z) {
@@ -496,8 +516,8 @@ __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__r
                     const cx<T> d = scale(z - zm, T(0.5));
                     b[f] = mk(d.y, -d.x);  // d / i
                 }
-                op.combine(0, ky, kz, a, ya);
-                op.combine(H, ky, kz, b, yb);
+                op.combine(tab + tpos(r, c), tcs, fy, fz, a, ya);
+                op.combine(tab + tpos(r, w), tcs, fy, fz, b, yb);
 #pragma unroll
                 for (int f = 0; f < FO; ++f) {
                     const cx<T> y = conjg(ya[f] + mul_i(yb[f]));
@@ -523,8 +543,8 @@ __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__r
                     const cx<T> d = scale(z[f] - conjg(zm[f]), T(0.5));
                     b[f] = mk(d.y, -d.x);
                 }
-                op.combine(0, ky, kz, a, ya);
-                op.combine(H, ky, kz, b, yb);
+                op.combine(tab + tpos(r, c), tcs, fy, fz, a, ya);
+                op.combine(tab + tpos(r, w), tcs, fy, fz, b, yb);
 #pragma unroll
                 for (int f = 0; f < FO; ++f) out[f] = ya[f] + mul_i(yb[f]);
                 if (rm != r) {
@@ -535,8 +555,9 @@ __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__r
                         const cx<T> d = scale(zm[f] - conjg(z[f]), T(0.5));
                         b[f] = mk(d.y, -d.x);
                     }
-                    op.combine(0, rm, kz, a, ya);
-                    op.combine(H, rm, kz, b, yb);
+                    const bool frm = rm > half;
+                    op.combine(tab + tpos(rm, c), tcs, frm, false, a, ya);
+                    op.combine(tab + tpos(rm, w), tcs, frm, false, b, yb);
 #pragma unroll
                     for (int f = 0; f < FO; ++f) out2[f] = ya[f] + mul_i(yb[f]);
 #pragma unroll
@@ -554,7 +575,7 @@ __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__r
             }
             __syncthreads();
         }
-#pragma unroll
+#pragma unroll 1
         for (int f = 0; f < FO; ++f) fft_smem<T>(colbase(f), cstride, g.lgl, jt, tws, g.lgl, false, true);
     }
 

@@ -71,16 +71,17 @@ __device__ __forceinline__ void load_ghat(const Model<T> &m, const SpecIdx<T> &s
 // last axis, round 1: transform chi u_j (kept in slots 5-7), S = Σ -i ghat_i X_i
 template <typename T>
 struct CombTheta {
-    static constexpr int kFin = 3, kFout = 1, kMode = 2, kPre = 0;
+    static constexpr int kFin = 3, kFout = 1, kMode = 2, kPre = 0, kTab = 3;
     static constexpr bool kStoreIn = true;
     Model<T> m;
     __device__ int slot_in(int f) const { return f; }
     __device__ int slot_aux(int f) const { return 5 + f; }
     __device__ int slot_out(int) const { return 3; }
-    __device__ __forceinline__ void combine(int kx, int ky, int kz, const cx<T> *in, cx<T> *out) const
+    __device__ const T *table(int c) const { return m.ghat + c * m.fold_sz; }
+    __device__ __forceinline__ void combine(const T *t, int cs, bool fy, bool fz, const cx<T> *in, cx<T> *out) const
     {
         T g[3];
-        load_ghat(m, spec_index(m, kx, ky, kz), g);
+        load_ghat_s(t, cs, fy, fz, g);
         cx<T> acc = mk(T(0), T(0));
 #pragma unroll
         for (int i = 0; i < 3; ++i) acc = acc + scale(in[i], g[i]);
@@ -130,18 +131,18 @@ struct RowTheta {
 // last axis, round 2: Y_i = M^_ij X_j + i ka ghat_i Theta
 template <typename T>
 struct CombState {
-    static constexpr int kFin = 4, kFout = 3, kMode = 2, kPre = 3;
+    static constexpr int kFin = 4, kFout = 3, kMode = 2, kPre = 3, kTab = 9;
     static constexpr bool kStoreIn = false;
     Model<T> m;
     __device__ int slot_in(int f) const { return f < 3 ? 5 + f : 4; }
     __device__ int slot_out(int f) const { return f; }
     __device__ int slot_aux(int) const { return 0; }
-    __device__ __forceinline__ void combine(int kx, int ky, int kz, const cx<T> *in, cx<T> *out) const
+    __device__ const T *table(int c) const { return c < 6 ? m.mhat + c * m.fold_sz : m.ghat + (c - 6) * m.fold_sz; }
+    __device__ __forceinline__ void combine(const T *t, int cs, bool fy, bool fz, const cx<T> *in, cx<T> *out) const
     {
         T M[9], g[3];
-        const SpecIdx<T> si = spec_index(m, kx, ky, kz);
-        load_mhat(m, si, M);
-        load_ghat(m, si, g);
+        load_mhat_s(3, t, cs, fy, fz, M);
+        load_ghat_s(t + 6 * cs, cs, fy, fz, g);
         mat_vec<T, 3>(M, in, out);
         const cx<T> it = mul_i(in[3]);
 #pragma unroll

@@ -131,18 +131,18 @@ template <typename T, int D, bool ENERGY>
 struct CombForce {
     static constexpr int kFin = D + (ENERGY ? Sym<D>::n : 0);
     static constexpr int kFout = D + (ENERGY ? 1 : 0);
-    static constexpr int kMode = 2, kPre = 0;
+    static constexpr int kMode = 2, kPre = 0, kTab = Sym<D>::n;
     static constexpr bool kStoreIn = false;
     Model<T> m;
     int obase;  // first output slot (kFin in 3D: the pass is out of place)
     __device__ int slot_in(int f) const { return f; }
     __device__ int slot_out(int f) const { return obase + f; }
     __device__ int slot_aux(int) const { return 0; }
-    __device__ __forceinline__ void combine(int kx, int ky, int kz, const cx<T> *in, cx<T> *out) const
+    __device__ const T *table(int c) const { return m.mhat + c * m.fold_sz; }
+    __device__ __forceinline__ void combine(const T *t, int cs, bool fy, bool fz, const cx<T> *in, cx<T> *out) const
     {
         T M[9];
-        const SpecIdx<T> si = spec_index(m, kx, ky, kz);
-        load_mhat(m, si, M);
+        load_mhat_s(D, t, cs, fy, fz, M);
         mat_vec<T, D>(M, in, out);
         if constexpr (ENERGY) {
             cx<T> acc = mk(T(0), T(0));

@@ -442,14 +442,14 @@ const char *pd_status_string(pd_status s)
 
 int64_t pd_plan_workspace_bytes(const pd_plan *p) { return p ? p->bytes : 0; }
 
-pd_status pd_plan_profile(pd_plan *p, int enable)
+pd_status pd_plan_profile(pd_plan *p, int mask)
 {
     if (!p) {
         set_error("pd_plan_profile: null plan");
         return PD_ERR_ARG;
     }
-    if (p->prof_on && !enable) PD_TRY(prof_harvest(p));
-    p->prof_on = enable ? 1 : 0;
+    if (p->prof_on && !mask) PD_TRY(prof_harvest(p));
+    p->prof_on = mask & ((1 << pd_plan::kKinds) - 1);
     for (int k = 0; k < pd_plan::kKinds; ++k) {
         p->prof_ms[k] = 0.0;
         p->prof_n[k] = 0;
@@ -477,6 +477,7 @@ pd_status pd_plan_profile_read(pd_plan *p, int kind, double *ms_total, int64_t *
     return PD_OK;
 }
 int64_t pd_plan_launch_count(const pd_plan *p) { return p ? p->launches : 0; }
+int64_t pd_plan_boundary_nodes(const pd_plan *p) { return p ? p->ngent : 0; }
 
 double pd_stable_dt(const pd_plan *p)
 {

@@ -118,6 +118,33 @@ __global__ void k_gfield(int n1, int n2, int n3, HorizonDev hz, int ncomp, const
     for (int k = 0; k < ncomp; ++k) G[k * N + p] = (T)acc[k];
 }
 
+// Kernel-spectrum lookup from a tile's shared-memory slice (component stride cs)
+template <typename T>
+__device__ __forceinline__ void load_mhat_s(int dim, const T *t, int cs, bool fy, bool fz, T *M /*3x3*/)
+{
+    if (dim == 2) {
+        const T m11 = t[0], m22 = t[cs], m12 = fy ? -t[2 * cs] : t[2 * cs];
+        M[0] = m11; M[1] = m12; M[3] = m12; M[4] = m22;
+    } else {
+        const T m11 = t[0], m22 = t[cs], m33 = t[2 * cs];
+        const T m12 = fy ? -t[3 * cs] : t[3 * cs];
+        const T m13 = fz ? -t[4 * cs] : t[4 * cs];
+        const T m23 = (fy != fz) ? -t[5 * cs] : t[5 * cs];
+        M[0] = m11; M[1] = m12; M[2] = m13;
+        M[3] = m12; M[4] = m22; M[5] = m23;
+        M[6] = m13; M[7] = m23; M[8] = m33;
+    }
+}
+
+// gamma_i (odd in k_i) from a slice whose components start at t
+template <typename T>
+__device__ __forceinline__ void load_ghat_s(const T *t, int cs, bool fy, bool fz, T *g)
+{
+    g[0] = t[0];
+    g[1] = fy ? -t[cs] : t[cs];
+    g[2] = fz ? -t[2 * cs] : t[2 * cs];
+}
+
 struct LaunchCfg {
     dim3 grid, block;
     size_t smem;
@@ -177,7 +204,8 @@ struct pd_plan {
     int ev_kind[kEvPool] = {};
     int ev_used = 0;
     int ev_reserved = 0;            // pairs [0, ev_reserved) belong to captured graphs
-    int prof_on = 0;
+    int prof_on = 0;                // bit k: time pass kind k
+    int prof_cur = 0;               // the launch being bracketed is timed
     // cached CUDA graph of a chunk of CG iterations (per precision)
     cudaGraphExec_t cg_graph[2] = {nullptr, nullptr};
     int cg_graph_prof[2] = {0, 0};
@@ -237,7 +265,7 @@ inline void row_cfg(const pd_plan *p, int FB, int NF, int NB, RowGeom &g, Launch
 // Column-pass configuration: axis 1 = x2, axis 2 = x3 (3D); FB fields in the
 // tile, FI of them with a mirror column.
 template <typename T>
-inline void col_cfg(const pd_plan *p, int axis, bool last, int FB, int FI, ColGeom &g, LaunchCfg &c,
+inline void col_cfg(const pd_plan *p, int axis, bool last, int FB, int FI, int NTAB, ColGeom &g, LaunchCfg &c,
                     int64_t &inner)
 {
     const int H = p->h;
@@ -246,13 +274,15 @@ inline void col_cfg(const pd_plan *p, int axis, bool last, int FB, int FI, ColGe
     const int mirror = (p->dim == 3 && last) ? 1 : 0;
     inner = axis == 1 ? (int64_t)H : (int64_t)p->n2 * H;
     auto smem_of = [&](int w) {
+        const size_t tab = (((size_t)NTAB * (L / 2 + 1) * (w + 1) + 1) & ~(size_t)1) * sizeof(T);
         return (size_t)L * sizeof(cx<T>) + (size_t)FB * L * w * sizeof(cx<T>) +
-               (mirror ? (size_t)FI * L * 2 * sizeof(cx<T>) : 0) + 16;
+               (mirror ? (size_t)FI * L * 2 * sizeof(cx<T>) : 0) + tab + 16;
     };
     int w = 32;
     while (w > 4 && ((w + mirror) * nt > 512 || smem_of(w) > 100 * 1024 || (H % w))) w >>= 1;
     g.lgl = ilog2(L);
     g.w = w;
+    g.lgw = ilog2(w);
     g.mirror = mirror;
     g.lgh = ilog2(H);
     g.n2 = p->n2;
@@ -291,7 +321,8 @@ inline cudaError_t prof_record(cudaEvent_t e, cudaStream_t st)
 
 inline pd_status prof_begin(pd_plan *p, int kind, cudaStream_t st)
 {
-    if (!p->prof_on) return PD_OK;
+    p->prof_cur = ((p->prof_on >> kind) & 1) != 0;
+    if (!p->prof_cur) return PD_OK;
     if (p->ev_used == pd_plan::kEvPool) PD_TRY(prof_harvest(p));
     if (p->ev_used == pd_plan::kEvPool) {
         set_error("profiling event pool exhausted");
@@ -303,7 +334,7 @@ inline pd_status prof_begin(pd_plan *p, int kind, cudaStream_t st)
 }
 inline pd_status prof_end(pd_plan *p, cudaStream_t st)
 {
-    if (!p->prof_on) return PD_OK;
+    if (!p->prof_cur) return PD_OK;
     PD_CUDA_TRY(prof_record(p->ev[2 * p->ev_used + 1], st));
     p->ev_used++;
     return PD_OK;
@@ -329,13 +360,22 @@ pd_status launch_rows(pd_plan *p, const Op &op, cudaStream_t st)
 template <typename T>
 inline int spec_slots(const pd_plan *p) { return sizeof(T) == 8 ? p->spec64_slots : p->spec32_slots; }
 
+template <class Op>
+constexpr int op_tab()
+{
+    if constexpr (Op::kMode == 2)
+        return Op::kTab;
+    else
+        return 0;
+}
+
 template <typename T, class Op>
 pd_status launch_cols(pd_plan *p, const Op &op, int axis, bool last, int F, cudaStream_t st)
 {
     ColGeom g;
     LaunchCfg c;
     int64_t inner = 0;
-    col_cfg<T>(p, axis, last, F, Op::kFin, g, c, inner);
+    col_cfg<T>(p, axis, last, F, Op::kFin, Op::kMode == 2 ? op_tab<Op>() : 0, g, c, inner);
     const int L = 1 << g.lgl;
     const unsigned long long dims[3] = {(unsigned long long)(2 * inner), (unsigned long long)L,
                                         (unsigned long long)g.outer * spec_slots<T>(p)};
@@ -358,13 +398,14 @@ pd_status launch_cols(pd_plan *p, const Op &op, int axis, bool last, int F, cuda
 // Plain column FFT of F packed spectra (slots slot0 ... slot0+F-1) along x2, in place.
 template <typename T, int F, int MODE>
 struct ColPass {
-    static constexpr int kFin = F, kFout = F, kMode = MODE, kPre = 0;
+    static constexpr int kFin = F, kFout = F, kMode = MODE, kPre = 0, kTab = 0;
     static constexpr bool kStoreIn = false;
     int slot0;
     __device__ int slot_in(int f) const { return slot0 + f; }
     __device__ int slot_out(int f) const { return slot0 + f; }
     __device__ int slot_aux(int) const { return 0; }
-    __device__ void combine(int, int, int, const cx<T> *, cx<T> *) const {}
+    __device__ const T *table(int) const { return nullptr; }
+    __device__ void combine(const T *, int, bool, bool, const cx<T> *, cx<T> *) const {}
 };
 
 template <typename T, int F>

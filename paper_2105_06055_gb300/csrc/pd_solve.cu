@@ -228,19 +228,27 @@ struct EpiCG {
     __device__ void sparse(const RowCtx<T> &c, int tid, int nthreads) const
     {
         const int k0 = goff[c.row0], k1 = goff[c.row0 + c.rows];
-        for (int k = k0 + tid; k < k1; k += nthreads) {
-            const GEntry<T> e = gent[k];
-            const int64_t p = e.p;
-            const int rl = (int)(p / n1 - c.row0), i1 = (int)(p % n1);
-            T pp[D], Gp[D];
+        constexpr int U = 4;  // entries in flight per thread
+        for (int kb = k0 + tid; kb < k1; kb += U * nthreads) {
+            GEntry<T> e[U];
 #pragma unroll
-            for (int j = 0; j < D; ++j) {
-                pp[j] = c.f(j, rl, i1);
-                Gp[j] = T(0);
+            for (int j = 0; j < U; ++j)
+                if (kb + j * nthreads < k1) e[j] = gent[kb + j * nthreads];
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                if (kb + j * nthreads >= k1) break;
+                const int64_t p = e[j].p;
+                const int rl = (int)(p / n1 - c.row0), i1 = (int)(p % n1);
+                T pp[D], Gp[D];
+#pragma unroll
+                for (int q = 0; q < D; ++q) {
+                    pp[q] = c.f(q, rl, i1);
+                    Gp[q] = T(0);
+                }
+                sym_apply<T, D>(e[j].g, pp, Gp);
+#pragma unroll
+                for (int i = 0; i < D; ++i) c.stage(i, rl, i1) -= Gp[i];
             }
-            sym_apply<T, D>(e.g, pp, Gp);
-#pragma unroll
-            for (int i = 0; i < D; ++i) c.stage(i, rl, i1) -= Gp[i];
         }
     }
     __device__ __forceinline__ void emit(const RowCtx<T> &c, int rl, int i1, const T *s0, const T *s1,

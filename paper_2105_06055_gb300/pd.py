@@ -27,7 +27,7 @@ STATUS = {0: "PD_OK", -1: "PD_ERR_ARG", -2: "PD_ERR_SIZE", -3: "PD_ERR_NOMEM", -
 EXPORTS = ["pd_plan_create", "pd_plan_destroy", "pd_kernel_spectrum", "pd_force", "pd_step_verlet",
            "pd_solve_static", "pd_force_adjoint", "pd_damage", "pd_plan_workspace_bytes",
            "pd_stable_dt", "pd_plan_launch_count", "pd_status_string", "pd_last_error_detail",
-           "pd_plan_profile", "pd_plan_profile_read", "pd_force2d_noalloc"]
+           "pd_plan_profile", "pd_plan_profile_read", "pd_force2d_noalloc", "pd_plan_boundary_nodes"]
 
 PASS_KINDS = {0: "rows_fwd", 1: "cols_x2", 2: "last_axis", 3: "rows_inv"}
 
@@ -77,6 +77,8 @@ def load():
     lib.pd_plan_workspace_bytes.restype = I64
     lib.pd_plan_launch_count.argtypes = [P]
     lib.pd_plan_launch_count.restype = I64
+    lib.pd_plan_boundary_nodes.argtypes = [P]
+    lib.pd_plan_boundary_nodes.restype = I64
     lib.pd_stable_dt.argtypes = [P]
     lib.pd_stable_dt.restype = D
     lib.pd_plan_profile.argtypes = [P, I]
@@ -256,8 +258,15 @@ class Plan:
         _check(load().pd_damage(self._h, _ptr(lam), _ptr(nb), _ptr(d), _stream(stream)), "pd_damage")
         return nb, d
 
-    def profile(self, enable: bool = True):
-        _check(load().pd_plan_profile(self._h, 1 if enable else 0), "pd_plan_profile")
+    def profile(self, enable: bool = True, kinds=None):
+        """Time the selected pass kinds (names of PASS_KINDS; all by default)."""
+        mask = 0
+        if enable:
+            names = list(PASS_KINDS.values()) if kinds is None else list(kinds)
+            for k, nm in PASS_KINDS.items():
+                if nm in names:
+                    mask |= 1 << k
+        _check(load().pd_plan_profile(self._h, mask), "pd_plan_profile")
 
     def profile_read(self):
         """{pass kind: (total ms, launches)} since the last profile() call."""
@@ -277,6 +286,10 @@ class Plan:
     @property
     def launch_count(self):
         return int(load().pd_plan_launch_count(self._h))
+
+    @property
+    def boundary_nodes(self):
+        return int(load().pd_plan_boundary_nodes(self._h))
 
     @property
     def stable_dt(self):
