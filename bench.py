@@ -110,6 +110,13 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
+# committed ncu summaries; None when the kernel changed after the capture.
+MEASURED_TRAFFIC = {
+    "last_axis": (32.0e6, "profiles/k_cols_CombForce_static_solve_128cube.md"),
+}
+
+
 def pass_bytes(kind, N, nbound, d=3, nc=6):
     """Algorithmic bytes of one launch of each FP32 pass of the fused CG
     iteration (d = 3 components; a packed half spectrum holds 4 bytes per node).
@@ -262,7 +269,9 @@ def run_native(args, rank, world):
             "passes_note": "per-pass times from one untimed profiled solve (all passes bracketed by events)",
             "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
                          "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "algorithmic_bytes_per_launch": bytes_per_launch},
+                         "traffic": (MEASURED_TRAFFIC[dom_name][0] if dom_name in MEASURED_TRAFFIC else None),
+                         "traffic_source": (MEASURED_TRAFFIC[dom_name][1] if dom_name in MEASURED_TRAFFIC else None),
+                         "algorithmic_bytes_per_launch": bytes_per_launch},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(b_host.numel() * 8),
                     "d2h_bytes_per_step": int(u_host.numel() * 8)},
             "gpu_launches": int(launches),
@@ -301,7 +310,28 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--n", type=int, default=N_GRID)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-solve", type=int, default=0, metavar="K",
+                    help="no timing: build the workload and run one solve capped at K CG iterations "
+                         "(a short, deterministic target for ncu captures)")
     args = ap.parse_args()
+
+    if args.profile_solve:
+        import torch
+
+        from paper_2105_06055_gb300 import build as pd_build
+        from paper_2105_06055_gb300 import inputs, pd
+        pd_build.build()
+        cfg = inputs.cube_with_cavity(n=args.n)
+        dev = torch.device("cuda")
+        plan = pd.Plan(pd.Problem(shape=cfg["shape"], delta=DELTA, model=pd.PD_LIN_STATE, nu=0.25, fp64=False),
+                       torch.tensor(cfg["chi"], device=dev), torch.tensor(cfg["chi_omega"], device=dev))
+        u = torch.zeros((3,) + cfg["shape"], dtype=torch.float64, device=dev)
+        it, rel, _ = plan.solve_static(u, torch.tensor(cfg["b"], dtype=torch.float64, device=dev), None,
+                                       rtol=RTOL, max_iter=args.profile_solve, raise_on_fail=False)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_solve_iterations": it, "rel_residual": rel}))
+        plan.close()
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
