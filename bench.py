@@ -112,9 +112,7 @@ class ClockSampler:
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
 # committed ncu summaries; None when the kernel changed after the capture.
-MEASURED_TRAFFIC = {
-    "last_axis": (32.0e6, "profiles/k_cols_CombForce_static_solve_128cube.md"),
-}
+MEASURED_TRAFFIC = {}
 
 
 def pass_bytes(kind, N, nbound, d=3, nc=6):

@@ -20,10 +20,10 @@
 // X^(0,k') + i X^(n1/2,k') for every (k2,k3); the spectral combine unpacks it
 // with the mirror mode (-k2,-k3).
 //
-// The in-register DFTs are radix 2/4/8/16 (radix-2 butterflies with the
-// eighth roots of unity as constants); inter-stage data moves through shared
-// memory in Stockham autosort order (no bit reversal pass). Each thread owns
-// 16 complex values per stage; a transform of length L uses L/16 threads.
+// The in-register DFTs are radix 2/4/8 (radix-2 butterflies with the eighth
+// roots of unity as constants); inter-stage data moves through shared memory
+// in Stockham autosort order (no bit reversal pass). Each thread owns kV = 8
+// complex values per stage; a transform of length L uses L/8 threads.
 // Inverse transforms reuse the forward code: IDFT(x) = conj(DFT(conj(x))).
 #pragma once
 
@@ -31,6 +31,9 @@
 #include "pd_tma.cuh"
 
 namespace pd {
+
+constexpr int kV = 8;    // complex values per thread and FFT stage
+constexpr int kLgV = 3;  // log2(kV)
 
 __host__ __device__ constexpr int bit_reverse(int i, int bits)
 {
@@ -87,14 +90,15 @@ __device__ __forceinline__ void dft_reg(cx<T> *v)
 }
 
 // One radix-R Stockham stage of a length-n transform stored at s[e * stride].
-// Thread jt (of nt = n/16) handles butterflies j = jt + b nt, b < 16/R.
+// Thread jt (of nt = n/kV) handles butterflies j = jt + b nt, b < kV/R.
 // tw[i] = e^{-2 pi i i / 2^lgl}. Ends with a block-wide barrier.
 template <typename T, int R>
 __device__ __forceinline__ void fft_stage(cx<T> *s, int stride, int n, int ns, int lgnsr, int jt,
                                           int nt, const cx<T> *__restrict__ tw, int lgl, bool cin, bool cout)
 {
-    constexpr int B = 16 / R;
-    cx<T> v[16];
+    static_assert(R <= kV, "radix larger than the values per thread");
+    constexpr int B = kV / R;
+    cx<T> v[kV];
     const int q = n / R;
 #pragma unroll
     for (int b = 0; b < B; ++b) {
@@ -122,7 +126,8 @@ __device__ __forceinline__ void fft_stage(cx<T> *s, int stride, int n, int ns, i
     __syncthreads();
 }
 
-// Forward DFT of length 2^lgn (>= 16) in shared memory, in place. With cin the
+// Forward DFT of length 2^lgn (>= 16) in shared memory, in place (stages of
+// radix 8, then one of radix 4 or 2 for the remainder). With cin the
 // input is conjugated as it is read, with cout the output as it is written
 // (IDFT(x) = conj(DFT(conj(x))) costs no extra pass).
 template <typename T>
@@ -130,14 +135,13 @@ __device__ __forceinline__ void fft_smem(cx<T> *s, int stride, int lgn, int jt,
                                          const cx<T> *__restrict__ tw, int lgl, bool cin = false,
                                          bool cout = false)
 {
-    const int n = 1 << lgn, nt = n >> 4;
+    const int n = 1 << lgn, nt = n >> kLgV;
     int ns = 1, lgns = 0, rem = lgn;
     while (rem > 0) {
-        const int lr = rem >= 4 ? 4 : rem;
+        const int lr = rem >= kLgV ? kLgV : rem;
         const bool first = (lgns == 0), last = (rem == lr);
         const bool ci = cin && first, co = cout && last;
         switch (lr) {
-            case 4: fft_stage<T, 16>(s, stride, n, ns, lgns + 4, jt, nt, tw, lgl, ci, co); break;
             case 3: fft_stage<T, 8>(s, stride, n, ns, lgns + 3, jt, nt, tw, lgl, ci, co); break;
             case 2: fft_stage<T, 4>(s, stride, n, ns, lgns + 2, jt, nt, tw, lgl, ci, co); break;
             default: fft_stage<T, 2>(s, stride, n, ns, lgns + 1, jt, nt, tw, lgl, ci, co); break;
@@ -240,7 +244,7 @@ __global__ void __launch_bounds__(256) k_rows(RowGeom g, Op op, const cx<T> *__r
     constexpr int KO = FO > ST ? FO : ST;
     constexpr int FB = FI > KO ? FI : KO;
     static_assert(!(FO > 0 && ST > 0), "an op either stages outputs or transforms forward");
-    const int H = 1 << g.lgh, n1 = 2 * H, nt = H >> 4, lg1 = g.lgh + 1;
+    const int H = 1 << g.lgh, n1 = 2 * H, nt = H >> kLgV, lg1 = g.lgh + 1;
     const int rows = g.rows, pitch = g.pitch;
     const int64_t row0 = (int64_t)blockIdx.x * rows;
     cx<T> *tws = reinterpret_cast<cx<T> *>(smem_raw);
@@ -409,7 +413,7 @@ __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__r
     constexpr int FB = FI > FO ? FI : FO;
     static_assert(MODE != 2 || FO <= FI, "combine writes its outputs over its inputs");
     const int L = 1 << g.lgl;
-    const int w = g.w, ncol = w + g.mirror;
+    const int w = g.w, ncol = w + g.mirror;  // threads: ncol x (L / kV)
     const int col = threadIdx.x % ncol, jt = threadIdx.x / ncol;
     const int c0 = blockIdx.x * w;
     const int o = blockIdx.y;

@@ -68,6 +68,12 @@ struct vec2<double> {
     using type = double2;
 };
 template <typename T>
+__device__ __forceinline__ typename vec2<T>::type load2(const T *p)
+{
+    return *reinterpret_cast<const typename vec2<T>::type *>(p);
+}
+
+template <typename T>
 __device__ __forceinline__ void store2(T *p, T a, T b)
 {
     typename vec2<T>::type v;

@@ -240,7 +240,7 @@ inline const cx<double> *tw_buf<double>(const pd_plan *p) { return p->tw64; }
 template <typename T>
 inline void row_cfg(const pd_plan *p, int FB, int NF, int NB, RowGeom &g, LaunchCfg &c)
 {
-    const int H = p->h, nt = H >> 4, n1 = 2 * H;
+    const int H = p->h, nt = H >> kLgV, n1 = 2 * H;
     const int pad = nt < 16 ? (nt < 2 ? 2 : nt) : 0;  // keeps rows 16-byte aligned, spreads banks
     const int pitch = H + pad;
     auto smem_of = [&](int rows) {
@@ -270,7 +270,7 @@ inline void col_cfg(const pd_plan *p, int axis, bool last, int FB, int FI, int N
 {
     const int H = p->h;
     const int L = axis == 1 ? p->n2 : p->n3;
-    const int nt = L >> 4;
+    const int nt = L >> kLgV;
     const int mirror = (p->dim == 3 && last) ? 1 : 0;
     inner = axis == 1 ? (int64_t)H : (int64_t)p->n2 * H;
     auto smem_of = [&](int w) {
@@ -279,7 +279,7 @@ inline void col_cfg(const pd_plan *p, int axis, bool last, int FB, int FI, int N
                (mirror ? (size_t)FI * L * 2 * sizeof(cx<T>) : 0) + tab + 16;
     };
     int w = 32;
-    while (w > 4 && ((w + mirror) * nt > 512 || smem_of(w) > 100 * 1024 || (H % w))) w >>= 1;
+    while (w > 2 && ((w + mirror) * nt > 512 || smem_of(w) > 100 * 1024 || (H % w))) w >>= 1;
     g.lgl = ilog2(L);
     g.w = w;
     g.lgw = ilog2(w);

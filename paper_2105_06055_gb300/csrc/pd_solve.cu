@@ -158,10 +158,11 @@ __global__ void k_ir_update(double *u, const T *e, const uint8_t *co, int64_t n)
         if (co[i]) u[i] += (double)e[i];
 }
 
-// rows, forward: p = r + beta p (stored), transform chi p
+// rows, forward: p = r + beta p (stored), transform chi p. Node fields come
+// straight from global memory (coalesced pairs); only chi is staged.
 template <typename T, int D>
 struct ProCG {
-    static constexpr int kFin = 0, kFout = D, kNF = 2 * D, kNB = 1, kStage = 0;
+    static constexpr int kFin = 0, kFout = D, kNF = 0, kNB = 1, kStage = 0;
     static constexpr bool kSparse = false;
     const T *r;
     T *pv;
@@ -173,7 +174,7 @@ struct ProCG {
     int64_t fstride;
     __device__ const cx<T> *spec_in(int) const { return nullptr; }
     __device__ cx<T> *spec_out(int f) const { return spec + f * fstride; }
-    __device__ const T *nf_src(int k) const { return k < D ? r + k * N : pv + (k - D) * N; }
+    __device__ const T *nf_src(int) const { return nullptr; }
     __device__ const uint8_t *nb_src(int) const { return chi; }
     __device__ __forceinline__ void node2(const RowCtx<T> &c, int rl, int i1, const T *, const T *, T *o0,
                                           T *o1) const
@@ -181,10 +182,16 @@ struct ProCG {
         const T beta = (T)scal[S_BETA];
         const T v0 = c.b(0, rl, i1) ? T(1) : T(0), v1 = c.b(0, rl, i1 + 1) ? T(1) : T(0);
         const int64_t p = (c.row0 + rl) * n1 + i1;
+        typename vec2<T>::type rr[D], pp[D];
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            const T a = c.f(j, rl, i1) + beta * c.f(D + j, rl, i1);
-            const T b = c.f(j, rl, i1 + 1) + beta * c.f(D + j, rl, i1 + 1);
+            rr[j] = load2(r + j * N + p);
+            pp[j] = load2(pv + j * N + p);
+        }
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            const T a = rr[j].x + beta * pp[j].x;
+            const T b = rr[j].y + beta * pp[j].y;
             store2(pv + j * N + p, a, b);
             o0[j] = v0 * a;
             o1[j] = v1 * b;
@@ -199,7 +206,7 @@ struct ProCG {
 // block partials of p.q
 template <typename T, int D>
 struct EpiCG {
-    static constexpr int kFin = D, kFout = 0, kStage = D, kNF = D, kNB = 1 + D;
+    static constexpr int kFin = D, kFout = 0, kStage = D, kNF = 0, kNB = 1 + D;
     static constexpr bool kSparse = true;
     const T *pv;
     const uint8_t *chi, *co;
@@ -213,7 +220,7 @@ struct EpiCG {
     int64_t fstride;
     __device__ const cx<T> *spec_in(int f) const { return spec + f * fstride; }
     __device__ cx<T> *spec_out(int) const { return nullptr; }
-    __device__ const T *nf_src(int k) const { return pv + k * N; }
+    __device__ const T *nf_src(int) const { return nullptr; }
     __device__ const uint8_t *nb_src(int k) const { return k == 0 ? chi : co + (k - 1) * N; }
     __device__ __forceinline__ void node2(const RowCtx<T> &c, int rl, int i1, const T *in0, const T *in1, T *o0,
                                           T *o1) const
@@ -231,21 +238,25 @@ struct EpiCG {
         constexpr int U = 4;  // entries in flight per thread
         for (int kb = k0 + tid; kb < k1; kb += U * nthreads) {
             GEntry<T> e[U];
+            T pp[U][D];
 #pragma unroll
             for (int j = 0; j < U; ++j)
                 if (kb + j * nthreads < k1) e[j] = gent[kb + j * nthreads];
+#pragma unroll
+            for (int j = 0; j < U; ++j)
+                if (kb + j * nthreads < k1) {
+#pragma unroll
+                    for (int q = 0; q < D; ++q) pp[j][q] = pv[q * N + e[j].p];
+                }
 #pragma unroll
             for (int j = 0; j < U; ++j) {
                 if (kb + j * nthreads >= k1) break;
                 const int64_t p = e[j].p;
                 const int rl = (int)(p / n1 - c.row0), i1 = (int)(p % n1);
-                T pp[D], Gp[D];
+                T Gp[D];
 #pragma unroll
-                for (int q = 0; q < D; ++q) {
-                    pp[q] = c.f(q, rl, i1);
-                    Gp[q] = T(0);
-                }
-                sym_apply<T, D>(e[j].g, pp, Gp);
+                for (int q = 0; q < D; ++q) Gp[q] = T(0);
+                sym_apply<T, D>(e[j].g, pp[j], Gp);
 #pragma unroll
                 for (int i = 0; i < D; ++i) c.stage(i, rl, i1) -= Gp[i];
             }
@@ -255,13 +266,16 @@ struct EpiCG {
                                          DSum &acc) const
     {
         const int64_t p = (c.row0 + rl) * n1 + i1;
+        typename vec2<T>::type pp[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) pp[i] = load2(pv + i * N + p);
 #pragma unroll
         for (int i = 0; i < D; ++i) {
             const T a = c.b(1 + i, rl, i1) ? -s0[i] : T(0);
             const T b = c.b(1 + i, rl, i1 + 1) ? -s1[i] : T(0);
             store2(q + i * N + p, a, b);
-            acc.add(c.f(i, rl, i1) * a);
-            acc.add(c.f(i, rl, i1 + 1) * b);
+            acc.add(pp[i].x * a);
+            acc.add(pp[i].y * b);
         }
     }
     __device__ void block_done(DSum &acc) const { write_partial(red, acc.value()); }
