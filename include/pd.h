@@ -170,6 +170,75 @@ pd_status pd_solve_static(pd_plan *plan, double *u, const double *b, const doubl
                           void *stream);
 
 /*
+ * pd_solve_dr -- the static problem of pd_solve_static (same arguments,
+ * same FP64 iterative refinement and stopping rule) with dynamic relaxation
+ * as the inner solver instead of CG. Dynamic relaxation is not in the paper;
+ * the method is the adaptive dynamic relaxation of Kilic and Madenci (Theor.
+ * Appl. Fract. Mech. 53 (2010) 194-204): damped central-difference pseudo
+ * dynamics with a fictitious density of 1.05/4 of the largest eigenvalue of
+ * the periodic symbol (pd_stable_dt), unit pseudo time step and the damping
+ * 2 sqrt(e.K e / e.e) from the local stiffness estimate of that paper.
+ * The whole solve, including its stopping decisions, runs as one CUDA graph
+ * launch with device-side conditional nodes.
+ * max_iter: cap on the total number of relaxation steps (rounded up to a
+ *     multiple of 16; at most 16777216).
+ * iters_out: relaxation steps done. The call synchronises the stream.
+ */
+pd_status pd_solve_dr(pd_plan *plan, double *u, const double *b, const double *w,
+                      double rtol, int max_iter, int *iters_out, double *relres_out, void *stream);
+
+/*
+ * Batched specimens: nspec independent problems (each its own grid, horizon,
+ * masks and material) solved together. pd_plan_create_batched creates one plan
+ * per specimen (same rules and arguments as pd_plan_create, element i of each
+ * array for specimen i; chi_Omega may be NULL for chi_Omega = chi_B for all,
+ * or contain NULL entries) and the batch's streams and events.
+ */
+typedef struct pd_batch pd_batch;  /* opaque; owns its plans */
+pd_status pd_plan_create_batched(int nspec, const pd_problem *problems, const uint8_t *const *chi_B,
+                                 const uint8_t *const *chi_Omega, void *stream, pd_batch **out);
+int pd_batch_size(const pd_batch *batch);
+/* Plan of specimen i (owned by the batch; NULL if i is out of range). */
+pd_plan *pd_batch_plan(pd_batch *batch, int i);
+/*
+ * pd_solve_dr_batched -- pd_solve_dr for every specimen, all in ONE CUDA-graph
+ * launch: each specimen is an independent branch of the graph whose loop of
+ * relaxation steps and refinement cycles is controlled on the device
+ * (conditional WHILE / IF nodes set by the solver's check kernels), so
+ * specimens of different sizes converge without host round trips and run
+ * concurrently. The executable graph is cached and rebuilt only when the
+ * buffers, rtol or max_iter change.
+ * u, b, w: host arrays of nspec device pointers (d_i x N_i FP64 each; w may be
+ *     NULL, or hold NULL entries, for w = 0).
+ * iters_out, relres_out, status_out: host arrays of nspec (each may be NULL):
+ *     steps, final FP64 relative residual and pd_status of each specimen.
+ * Returns PD_OK if every specimen converged, else the first failure's status.
+ * Synchronises the stream.
+ */
+pd_status pd_solve_dr_batched(pd_batch *batch, double *const *u, const double *const *b,
+                              const double *const *w, double rtol, int max_iter, int *iters_out,
+                              double *relres_out, int *status_out, void *stream);
+/* Release the batch and all of its plans. NULL is a no-op. */
+void pd_batch_destroy(pd_batch *batch);
+
+/*
+ * Autotuning of the FFT passes. pd_plan_autotune times the plan's force
+ * evaluation (on its own workspace; no caller buffer is touched) over the
+ * candidate rows per row-pass block, column-tile widths of the x2 and
+ * last-axis passes and FFT stage schedules (radix-4/2 remainder stage first
+ * or last), coordinate-wise from the built-in heuristic, and keeps the
+ * fastest. Results do not change (the same transforms are computed); later
+ * calls use the chosen configuration. Synchronises the stream.
+ * pd_batch_autotune tunes one plan per distinct grid/precision/operator of a
+ * batch and gives the others the same configuration.
+ * pd_plan_tuning writes {rows, x2 width, last-axis width, schedule} (0 =
+ * heuristic) to out4.
+ */
+pd_status pd_plan_autotune(pd_plan *plan, void *stream);
+pd_status pd_batch_autotune(pd_batch *batch, void *stream);
+pd_status pd_plan_tuning(const pd_plan *plan, int *out4);
+
+/*
  * pd_force_adjoint -- reverse-mode derivative of pd_force (bond model). The
  * paper has no adjoint; this differentiates the quadrature of Eq. 17-18, 75
  * with bond factor s s'. Given gL = dJ/dL for some scalar J:

@@ -27,6 +27,8 @@
 // Inverse transforms reuse the forward code: IDFT(x) = conj(DFT(conj(x))).
 #pragma once
 
+#include <type_traits>
+
 #include "pd_common.cuh"
 #include "pd_tma.cuh"
 
@@ -126,19 +128,21 @@ __device__ __forceinline__ void fft_stage(cx<T> *s, int stride, int n, int ns, i
     __syncthreads();
 }
 
-// Forward DFT of length 2^lgn (>= 16) in shared memory, in place (stages of
-// radix 8, then one of radix 4 or 2 for the remainder). With cin the
-// input is conjugated as it is read, with cout the output as it is written
-// (IDFT(x) = conj(DFT(conj(x))) costs no extra pass).
+// Forward DFT of length 2^lgn (>= 16) in shared memory, in place: stages of
+// radix 8 and one stage of radix 4 or 2 for the remainder, which comes last
+// (schedule 0) or first (schedule 1). With cin the input is conjugated as it
+// is read, with cout the output as it is written (IDFT(x) =
+// conj(DFT(conj(x))) costs no extra pass).
 template <typename T>
 __device__ __forceinline__ void fft_smem(cx<T> *s, int stride, int lgn, int jt,
                                          const cx<T> *__restrict__ tw, int lgl, bool cin = false,
-                                         bool cout = false)
+                                         bool cout = false, int sched = 0)
 {
     const int n = 1 << lgn, nt = n >> kLgV;
     int ns = 1, lgns = 0, rem = lgn;
+    const int rm = lgn % kLgV;
     while (rem > 0) {
-        const int lr = rem >= kLgV ? kLgV : rem;
+        const int lr = (sched && lgns == 0 && rm) ? rm : (rem >= kLgV ? kLgV : rem);
         const bool first = (lgns == 0), last = (rem == lr);
         const bool ci = cin && first, co = cout && last;
         switch (lr) {
@@ -197,6 +201,7 @@ struct RowGeom {
     int pitch;      // shared-memory pitch of a packed row (complex elements, even)
     int64_t nrows;  // n2 * n3 (multiple of rows)
     int lgl;        // log2 of the global twiddle table length
+    int sched;      // FFT stage schedule (fft_smem)
     int *err;       // device status word (bounded-wait time-outs)
 };
 
@@ -221,6 +226,16 @@ struct RowCtx {
     }
 };
 
+// Block accumulator of a row op: Op::Acc when the op declares one, else DSum.
+template <class Op, class = void>
+struct op_acc {
+    using type = DSum;
+};
+template <class Op>
+struct op_acc<Op, std::void_t<typename Op::Acc>> {
+    using type = typename Op::Acc;
+};
+
 // Op interface (all device unless noted):
 //   static constexpr int kFin, kFout;  packed spectra read (inverse) / written (forward)
 //   static constexpr int kNF, kNB;     node fields (T / uint8) bulk-loaded for the tile's rows
@@ -232,7 +247,8 @@ struct RowCtx {
 //        in: kFin inverse-transformed values (unnormalised IDFT);
 //        o:  max(kFout, kStage) outputs (forward inputs or staged values)
 //   void sparse(ctx, tid, nthreads); void emit(ctx, rl, i1, s0, s1, acc)
-//   void block_done(acc): called by every thread at the end (block reductions)
+//   void block_done(acc): called by every thread at the end (block reductions);
+//        acc is an Op::Acc if the op declares that type, else a DSum
 // Data movement: one thread issues bulk async copies (cp.async.bulk) of the
 // tile's spectrum rows and node fields, completing on an mbarrier; twiddles
 // are copied to shared memory; outputs leave through coalesced stores.
@@ -301,7 +317,7 @@ __global__ void __launch_bounds__(256) k_rows(RowGeom g, Op op, const cx<T> *__r
         }
         __syncthreads();
 #pragma unroll 1
-        for (int f = 0; f < FI; ++f) fft_smem<T>(spec + (f * rows + rf) * pitch, 1, g.lgh, jt, tws, lg1);
+        for (int f = 0; f < FI; ++f) fft_smem<T>(spec + (f * rows + rf) * pitch, 1, g.lgh, jt, tws, lg1, false, false, g.sched);
     }
 
     // per-node work, lanes over consecutive packed slots (2 nodes each)
@@ -325,7 +341,7 @@ __global__ void __launch_bounds__(256) k_rows(RowGeom g, Op op, const cx<T> *__r
         op.sparse(ctx, threadIdx.x, blockDim.x);
         __syncthreads();
     }
-    DSum acc;
+    typename op_acc<Op>::type acc;
     if constexpr (ST > 0) {
         for (int idx = threadIdx.x; idx < rows * H; idx += blockDim.x) {
             const int rl = idx >> g.lgh, n = idx & (H - 1);
@@ -343,7 +359,7 @@ __global__ void __launch_bounds__(256) k_rows(RowGeom g, Op op, const cx<T> *__r
 
     if constexpr (FO > 0) {
 #pragma unroll 1
-        for (int f = 0; f < FO; ++f) fft_smem<T>(spec + (f * rows + rf) * pitch, 1, g.lgh, jt, tws, lg1);
+        for (int f = 0; f < FO; ++f) fft_smem<T>(spec + (f * rows + rf) * pitch, 1, g.lgh, jt, tws, lg1, false, false, g.sched);
         const T half = T(0.5);
 #pragma unroll
         for (int f = 0; f < FO; ++f) {
@@ -381,6 +397,7 @@ struct ColGeom {
     int lgtw;    // log2 of the twiddle table length
     int lb;      // rows per TMA box (<= 256, divides L)
     int outer;   // outer extent: n3 for the x2 pass, 1 for the last axis
+    int sched;   // FFT stage schedule (fft_smem)
     int *err;    // device status word (bounded-wait time-outs)
 };
 
@@ -473,7 +490,7 @@ __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__r
     constexpr int FPRE = (MODE == 2) ? Op::kPre : 0;
 #pragma unroll 1
     for (int f = FPRE; f < FI; ++f)
-        fft_smem<T>(colbase(f), cstride, g.lgl, jt, tws, g.lgl, MODE == 1, MODE == 1);
+        fft_smem<T>(colbase(f), cstride, g.lgl, jt, tws, g.lgl, MODE == 1, MODE == 1, g.sched);
 
     if constexpr (MODE == 2 && Op::kStoreIn) {
         fence_proxy_async();
@@ -580,7 +597,7 @@ __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__r
             __syncthreads();
         }
 #pragma unroll 1
-        for (int f = 0; f < FO; ++f) fft_smem<T>(colbase(f), cstride, g.lgl, jt, tws, g.lgl, false, true);
+        for (int f = 0; f < FO; ++f) fft_smem<T>(colbase(f), cstride, g.lgl, jt, tws, g.lgl, false, true, g.sched);
     }
 
     // ---- store

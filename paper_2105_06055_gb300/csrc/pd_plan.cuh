@@ -214,6 +214,10 @@ struct pd_plan {
     cudaStream_t own_stream = nullptr;  // plan stream for captured work (never the legacy stream)
     cudaEvent_t ev_join[2] = {nullptr, nullptr};
     double prof_ms[kKinds] = {};
+    // pass configuration picked by pd_plan_autotune (0: built-in heuristic)
+    int tune_rows = 0;     // rows per row-pass block
+    int tune_w[2] = {0, 0};  // column-tile width of the x2 / last-axis passes
+    int tune_sched = 0;    // FFT stage schedule
     int64_t prof_n[kKinds] = {};
 };
 
@@ -247,8 +251,9 @@ inline void row_cfg(const pd_plan *p, int FB, int NF, int NB, RowGeom &g, Launch
         return (size_t)n1 * sizeof(cx<T>) + (size_t)FB * rows * pitch * sizeof(cx<T>) +
                (size_t)NF * rows * n1 * sizeof(T) + (((size_t)NB * rows * n1 + 15) & ~(size_t)15) + 16;
     };
-    int rows = 256 / nt;
+    int rows = p->tune_rows > 0 ? p->tune_rows : 256 / nt;
     if (rows < 1) rows = 1;
+    while (rows > 1 && rows * nt > 256) rows >>= 1;  // k_rows launch bound
     while (rows > 1 && smem_of(rows) > 100 * 1024) rows >>= 1;
     while (p->nrows % rows) rows >>= 1;
     g.lgh = ilog2(H);
@@ -256,6 +261,7 @@ inline void row_cfg(const pd_plan *p, int FB, int NF, int NB, RowGeom &g, Launch
     g.pitch = pitch;
     g.nrows = p->nrows;
     g.lgl = p->lgl;
+    g.sched = p->tune_sched;
     g.err = p->dev_status;
     c.grid = dim3((unsigned)(p->nrows / rows));
     c.block = dim3(rows * nt);
@@ -278,7 +284,7 @@ inline void col_cfg(const pd_plan *p, int axis, bool last, int FB, int FI, int N
         return (size_t)L * sizeof(cx<T>) + (size_t)FB * L * w * sizeof(cx<T>) +
                (mirror ? (size_t)FI * L * 2 * sizeof(cx<T>) : 0) + tab + 16;
     };
-    int w = 32;
+    int w = p->tune_w[last ? 1 : 0] > 0 ? p->tune_w[last ? 1 : 0] : 32;
     while (w > 2 && ((w + mirror) * nt > 512 || smem_of(w) > 100 * 1024 || (H % w))) w >>= 1;
     g.lgl = ilog2(L);
     g.w = w;
@@ -289,6 +295,7 @@ inline void col_cfg(const pd_plan *p, int axis, bool last, int FB, int FI, int N
     g.lgtw = p->lgl;
     g.lb = L < 256 ? L : 256;
     g.outer = axis == 1 ? p->n3 : 1;
+    g.sched = p->tune_sched;
     g.err = p->dev_status;
     c.grid = dim3((unsigned)(inner / w), (unsigned)g.outer);
     c.block = dim3((w + mirror) * nt);

@@ -1,0 +1,164 @@
+// Autotuner for the FFT passes: picks, per plan, the rows per block of the
+// row passes, the tile width of the column passes (x2 and last axis) and the
+// FFT stage schedule (radix-4/2 remainder stage first or last) by timing the
+// plan's own force evaluation on its workspace with CUDA events.
+//
+// The search is coordinate-wise from the built-in heuristic: schedule, rows,
+// last-axis width, x2 width; each candidate is timed as the median of five
+// force evaluations after two untimed ones. Candidates are limited to the
+// shapes the passes accept (powers of two; at least one warp per row block;
+// shared memory within the pass's own limit, which the configuration
+// functions enforce by shrinking the candidate). The transforms compute the
+// same values for every candidate (only the order of block partial sums in
+// the solvers' inner products changes).
+#include <algorithm>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "pd_force_impl.cuh"
+
+using namespace pd;
+
+struct pd_batch;
+void pd_batch_invalidate(pd_batch *B);
+extern "C" pd_plan *pd_batch_plan(pd_batch *B, int i);
+extern "C" int pd_batch_size(const pd_batch *B);
+
+namespace {
+
+void drop_graphs(pd_plan *p)
+{
+    for (int k = 0; k < 2; ++k)
+        if (p->cg_graph[k]) {
+            cudaGraphExecDestroy(p->cg_graph[k]);
+            p->cg_graph[k] = nullptr;
+        }
+}
+
+template <typename T>
+pd_status time_force(pd_plan *p, cudaEvent_t e0, cudaEvent_t e1, float *ms_out)
+{
+    cudaStream_t st = p->own_stream;
+    const T *u = (const T *)p->cg_e;
+    T *L = (T *)p->cg_q;
+    for (int k = 0; k < 2; ++k) PD_TRY(force_plain<T>(p, u, nullptr, L, nullptr, st));
+    std::vector<float> t;
+    for (int k = 0; k < 5; ++k) {
+        PD_CUDA_TRY(cudaEventRecord(e0, st));
+        PD_TRY(force_plain<T>(p, u, nullptr, L, nullptr, st));
+        PD_CUDA_TRY(cudaEventRecord(e1, st));
+        PD_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        PD_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        t.push_back(ms);
+    }
+    std::sort(t.begin(), t.end());
+    *ms_out = t[2];
+    return PD_OK;
+}
+
+pd_status time_cfg(pd_plan *p, cudaEvent_t e0, cudaEvent_t e1, float *ms)
+{
+    return p->prob.fp64 ? time_force<double>(p, e0, e1, ms) : time_force<float>(p, e0, e1, ms);
+}
+
+pd_status tune_plan(pd_plan *p, cudaStream_t caller)
+{
+    PD_CUDA_TRY(cudaEventRecord(p->ev_join[0], caller));
+    PD_CUDA_TRY(cudaStreamWaitEvent(p->own_stream, p->ev_join[0], 0));
+    const size_t bytes = (size_t)p->dim * p->N * (p->prob.fp64 ? 8 : 4);
+    PD_CUDA_TRY(cudaMemsetAsync(p->cg_e, 0, bytes, p->own_stream));
+    const int prof = p->prof_on;
+    p->prof_on = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PD_CUDA_TRY(cudaEventCreate(&e0));
+    PD_CUDA_TRY(cudaEventCreate(&e1));
+    pd_status s = PD_OK;
+    auto best_of = [&](int *knob, const std::vector<int> &cands) {
+        if (s != PD_OK || cands.size() < 2) return;
+        int best = *knob;
+        float tbest = 1e30f;
+        for (int c : cands) {
+            *knob = c;
+            float ms = 0.f;
+            s = time_cfg(p, e0, e1, &ms);
+            if (s != PD_OK) return;
+            if (ms < tbest) {
+                tbest = ms;
+                best = c;
+            }
+        }
+        *knob = best;
+    };
+    // schedule: only lengths that are not powers of 8 have a remainder stage
+    const int H = p->h;
+    const bool rem = (ilog2(H) % kLgV) || (ilog2(p->n2) % kLgV) || (p->dim == 3 && (ilog2(p->n3) % kLgV));
+    if (rem) best_of(&p->tune_sched, {0, 1});
+    const int nt = H >> kLgV;
+    std::vector<int> rows;
+    for (int r = std::max(1, 32 / nt); r * nt <= 256; r *= 2)
+        if (p->nrows % r == 0) rows.push_back(r);
+    best_of(&p->tune_rows, rows);
+    best_of(&p->tune_w[1], {32, 16, 8, 4});
+    if (p->dim == 3) best_of(&p->tune_w[0], {32, 16, 8, 4});
+    p->prof_on = prof;
+    drop_graphs(p);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != PD_OK) return s;
+    PD_CUDA_TRY(cudaEventRecord(p->ev_join[1], p->own_stream));
+    PD_CUDA_TRY(cudaStreamWaitEvent(caller, p->ev_join[1], 0));
+    return PD_OK;
+}
+
+}  // namespace
+
+extern "C" pd_status pd_plan_autotune(pd_plan *p, void *stream)
+{
+    if (!p) {
+        set_error("pd_plan_autotune: null plan");
+        return PD_ERR_ARG;
+    }
+    return tune_plan(p, (cudaStream_t)stream);
+}
+
+extern "C" pd_status pd_plan_tuning(const pd_plan *p, int *out4)
+{
+    if (!p || !out4) {
+        set_error("pd_plan_tuning: null argument");
+        return PD_ERR_ARG;
+    }
+    out4[0] = p->tune_rows;
+    out4[1] = p->tune_w[0];
+    out4[2] = p->tune_w[1];
+    out4[3] = p->tune_sched;
+    return PD_OK;
+}
+
+extern "C" pd_status pd_batch_autotune(pd_batch *B, void *stream)
+{
+    if (!B) {
+        set_error("pd_batch_autotune: null batch");
+        return PD_ERR_ARG;
+    }
+    // one search per distinct grid / precision / operator; the others copy it
+    std::map<std::tuple<int, int, int, int, int, int>, pd_plan *> done;
+    for (int i = 0; i < pd_batch_size(B); ++i) {
+        pd_plan *p = pd_batch_plan(B, i);
+        const auto key = std::make_tuple(p->dim, p->n1, p->n2, p->n3, p->prob.fp64, p->state_based);
+        auto it = done.find(key);
+        if (it == done.end()) {
+            PD_TRY(tune_plan(p, (cudaStream_t)stream));
+            done[key] = p;
+        } else {
+            p->tune_rows = it->second->tune_rows;
+            p->tune_w[0] = it->second->tune_w[0];
+            p->tune_w[1] = it->second->tune_w[1];
+            p->tune_sched = it->second->tune_sched;
+            drop_graphs(p);
+        }
+    }
+    pd_batch_invalidate(B);
+    return PD_OK;
+}

@@ -27,7 +27,9 @@ STATUS = {0: "PD_OK", -1: "PD_ERR_ARG", -2: "PD_ERR_SIZE", -3: "PD_ERR_NOMEM", -
 EXPORTS = ["pd_plan_create", "pd_plan_destroy", "pd_kernel_spectrum", "pd_force", "pd_step_verlet",
            "pd_solve_static", "pd_force_adjoint", "pd_damage", "pd_plan_workspace_bytes",
            "pd_stable_dt", "pd_plan_launch_count", "pd_status_string", "pd_last_error_detail",
-           "pd_plan_profile", "pd_plan_profile_read", "pd_force2d_noalloc", "pd_plan_boundary_nodes"]
+           "pd_plan_profile", "pd_plan_profile_read", "pd_force2d_noalloc", "pd_plan_boundary_nodes",
+           "pd_solve_dr", "pd_plan_create_batched", "pd_batch_size", "pd_batch_plan", "pd_solve_dr_batched",
+           "pd_batch_destroy", "pd_plan_autotune", "pd_batch_autotune", "pd_plan_tuning"]
 
 PASS_KINDS = {0: "rows_fwd", 1: "cols_x2", 2: "last_axis", 3: "rows_inv"}
 
@@ -87,6 +89,26 @@ def load():
     lib.pd_plan_profile_read.restype = I
     lib.pd_force2d_noalloc.argtypes = [ctypes.POINTER(_Problem), P, P, P, P]
     lib.pd_force2d_noalloc.restype = I
+    lib.pd_solve_dr.argtypes = [P, P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D), P]
+    lib.pd_solve_dr.restype = I
+    lib.pd_plan_create_batched.argtypes = [I, ctypes.POINTER(_Problem), ctypes.POINTER(P), ctypes.POINTER(P), P,
+                                           ctypes.POINTER(P)]
+    lib.pd_plan_create_batched.restype = I
+    lib.pd_batch_size.argtypes = [P]
+    lib.pd_batch_size.restype = I
+    lib.pd_batch_plan.argtypes = [P, I]
+    lib.pd_batch_plan.restype = P
+    lib.pd_solve_dr_batched.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), D, I,
+                                        ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(I), P]
+    lib.pd_solve_dr_batched.restype = I
+    lib.pd_batch_destroy.argtypes = [P]
+    lib.pd_batch_destroy.restype = None
+    lib.pd_plan_autotune.argtypes = [P, P]
+    lib.pd_plan_autotune.restype = I
+    lib.pd_batch_autotune.argtypes = [P, P]
+    lib.pd_batch_autotune.restype = I
+    lib.pd_plan_tuning.argtypes = [P, ctypes.POINTER(I)]
+    lib.pd_plan_tuning.restype = I
     lib.pd_status_string.argtypes = [I]
     lib.pd_status_string.restype = ctypes.c_char_p
     lib.pd_last_error_detail.argtypes = []
@@ -165,7 +187,22 @@ class Plan:
         _check(lib.pd_plan_create(ctypes.byref(self._c), _ptr(chi), _ptr(chi_omega), _stream(stream),
                                   ctypes.byref(h)), "pd_plan_create")
         self._h = h
+        self._owned = True
         self.device = chi.device
+
+    @classmethod
+    def _borrowed(cls, handle, problem: Problem, device):
+        """A view of a plan owned by a Batch (closing it does nothing)."""
+        self = cls.__new__(cls)
+        self.problem = problem
+        self.shape = tuple(int(s) for s in problem.shape)
+        self.dim = len(self.shape)
+        self.dtype = problem.dtype
+        self._c = problem.to_c()
+        self._h = ctypes.c_void_p(handle)
+        self._owned = False
+        self.device = device
+        return self
 
     @staticmethod
     def _mask(t, shape, name):
@@ -187,7 +224,8 @@ class Plan:
 
     def close(self):
         if getattr(self, "_h", None):
-            load().pd_plan_destroy(self._h)
+            if getattr(self, "_owned", True):
+                load().pd_plan_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -240,6 +278,30 @@ class Plan:
         if st != 0 and (raise_on_fail or st != -5):
             raise PDError(st, "pd_solve_static")
         return int(it.value), float(rr.value), st
+
+    def solve_dr(self, u, b, w=None, rtol=1e-8, max_iter=200000, stream=None, raise_on_fail=True):
+        """Adaptive dynamic relaxation with FP64 refinement (pd_solve_dr)."""
+        u = self._field(u, self.dim, "u", dtype=torch.float64)
+        b = self._field(b, self.dim, "b", dtype=torch.float64)
+        w = self._field(w, self.dim, "w", dtype=torch.float64, allow_none=True)
+        it = ctypes.c_int(0)
+        rr = ctypes.c_double(0.0)
+        st = load().pd_solve_dr(self._h, _ptr(u), _ptr(b), _ptr(w), float(rtol), int(max_iter),
+                                ctypes.byref(it), ctypes.byref(rr), _stream(stream))
+        if st != 0 and (raise_on_fail or st != -5):
+            raise PDError(st, "pd_solve_dr")
+        return int(it.value), float(rr.value), st
+
+    def autotune(self, stream=None):
+        _check(load().pd_plan_autotune(self._h, _stream(stream)), "pd_plan_autotune")
+        return self.tuning
+
+    @property
+    def tuning(self):
+        """{rows, w_x2, w_last, sched} picked by autotune (0 = built-in heuristic)."""
+        out = (ctypes.c_int * 4)()
+        _check(load().pd_plan_tuning(self._h, out), "pd_plan_tuning")
+        return {"rows": out[0], "w_x2": out[1], "w_last": out[2], "sched": out[3]}
 
     def force_adjoint(self, u, gL, s=None, want_gu=True, want_gs=True, stream=None):
         u = self._field(u, self.dim, "u")
@@ -312,3 +374,68 @@ def force2d_noalloc(problem: Problem, chi: torch.Tensor, u: torch.Tensor, L: Opt
     _check(load().pd_force2d_noalloc(ctypes.byref(c), _ptr(chi.contiguous()), _ptr(u), _ptr(L), _stream(stream)),
            "pd_force2d_noalloc")
     return L
+
+
+class Batch:
+    """Owns a ``pd_batch``: independent specimens solved in one graph launch."""
+
+    def __init__(self, problems: Sequence[Problem], chis: Sequence[torch.Tensor],
+                 chi_omegas: Optional[Sequence[Optional[torch.Tensor]]] = None, stream=None):
+        lib = load()
+        n = len(problems)
+        if len(chis) != n or (chi_omegas is not None and len(chi_omegas) != n):
+            raise ValueError("one problem and one mask per specimen")
+        self.problems = list(problems)
+        self._chis = [Plan._mask(c, tuple(p.shape), "chi") for p, c in zip(problems, chis)]
+        com = [None] * n
+        if chi_omegas is not None:
+            com = [None if c is None else Plan._mask(c, (len(p.shape),) + tuple(p.shape), "chi_omega")
+                   for p, c in zip(problems, chi_omegas)]
+        cp = (_Problem * n)(*[p.to_c() for p in problems])
+        chp = (ctypes.c_void_p * n)(*[c.data_ptr() for c in self._chis])
+        cop = (ctypes.c_void_p * n)(*[None if c is None else c.data_ptr() for c in com])
+        h = ctypes.c_void_p()
+        _check(lib.pd_plan_create_batched(n, cp, chp, cop, _stream(stream), ctypes.byref(h)),
+               "pd_plan_create_batched")
+        self._h = h
+        self.device = self._chis[0].device
+        self.plans = [Plan._borrowed(lib.pd_batch_plan(h, i), problems[i], self.device) for i in range(n)]
+
+    def __len__(self):
+        return len(self.problems)
+
+    def autotune(self, stream=None):
+        _check(load().pd_batch_autotune(self._h, _stream(stream)), "pd_batch_autotune")
+        return [p.tuning for p in self.plans]
+
+    def solve_dr(self, us, bs, ws=None, rtol=1e-8, max_iter=200000, stream=None, raise_on_fail=True):
+        """Solve every specimen in one graph launch; returns (steps, relres, status) lists."""
+        n = len(self.plans)
+        us = [pl._field(u, pl.dim, "u", dtype=torch.float64) for pl, u in zip(self.plans, us)]
+        bs = [pl._field(b, pl.dim, "b", dtype=torch.float64) for pl, b in zip(self.plans, bs)]
+        if ws is not None:
+            ws = [pl._field(w, pl.dim, "w", dtype=torch.float64, allow_none=True) for pl, w in zip(self.plans, ws)]
+        up = (ctypes.c_void_p * n)(*[u.data_ptr() for u in us])
+        bp = (ctypes.c_void_p * n)(*[b.data_ptr() for b in bs])
+        wp = None if ws is None else (ctypes.c_void_p * n)(*[None if w is None else w.data_ptr() for w in ws])
+        it = (ctypes.c_int * n)()
+        rr = (ctypes.c_double * n)()
+        stt = (ctypes.c_int * n)()
+        st = load().pd_solve_dr_batched(self._h, up, bp, wp, float(rtol), int(max_iter), it, rr, stt,
+                                        _stream(stream))
+        if st != 0 and (raise_on_fail or st != -5):
+            raise PDError(st, "pd_solve_dr_batched")
+        return list(it), list(rr), list(stt)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for p in self.plans:
+                p._h = None
+            load().pd_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

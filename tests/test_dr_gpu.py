@@ -1,0 +1,151 @@
+"""Dynamic relaxation (single plan and batched specimens in one graph launch)
+and the pass autotuner, against the FP64 oracle and the FP64 GPU CG path."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2105_06055_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda")
+
+
+@pytest.fixture(scope="module")
+def pdm():
+    from paper_2105_06055_gb300 import build, pd
+    build.build()
+    pd.load()
+    return pd
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _t(a, dt=torch.float64):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dt, device=DEV)
+
+
+def _bond_problem(pdm, cfg, fp64):
+    return pdm.Problem(shape=cfg["shape"], delta=cfg["delta"], nu=1.0 / 3.0, fp64=fp64)
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_dr_2d_matches_oracle(pdm, oracle, fp64):
+    cfg = inputs.batched_specimens(count=1, seed=3, sizes=[100])[0]
+    plan = pdm.Plan(_bond_problem(pdm, cfg, fp64), _t(cfg["chi"], torch.uint8), _t(cfg["chi_omega"], torch.uint8))
+    u = torch.zeros((2,) + cfg["shape"], dtype=torch.float64, device=DEV)
+    it, rel, st = plan.solve_dr(u, _t(cfg["b"]), None, rtol=1e-8, max_iter=300000)
+    assert st == 0 and rel <= 1e-8 and it > 0
+    ug = u.cpu().numpy()
+    alpha = oracle.alpha_bond(2, 1.0, cfg["delta"])
+    op = ("bond", alpha)
+    res = oracle.static_residual(ug, cfg["chi"], cfg["chi_omega"], cfg["b"], 1.0, cfg["delta"], op)
+    bn = np.linalg.norm(cfg["chi_omega"] * cfg["b"])
+    assert np.linalg.norm(res) / bn <= 1.5e-8
+    uo, _, relo = oracle.cg_static(cfg["chi"], cfg["chi_omega"], cfg["b"], cfg["w"], 1.0, cfg["delta"], op,
+                                   rtol=1e-12)
+    assert relo < 1e-11
+    assert _rel(ug, uo) < 2e-6
+    assert np.all(ug[:, cfg["chi_omega"][0] == 0] == 0)
+    plan.close()
+
+
+def test_dr_3d_state_based_matches_oracle(pdm, oracle):
+    """The unfused step (state-based operator with its dilatation round)."""
+    cfg = inputs.cube_with_cavity(n=32, radius_frac=0.2)
+    shape = cfg["shape"]
+    prob = pdm.Problem(shape=shape, delta=3.0, model=pdm.PD_LIN_STATE, nu=0.4, fp64=False)
+    plan = pdm.Plan(prob, _t(cfg["chi"], torch.uint8), _t(cfg["chi_omega"], torch.uint8))
+    u = torch.zeros((3,) + shape, dtype=torch.float64, device=DEV)
+    it, rel, st = plan.solve_dr(u, _t(cfg["b"]), None, rtol=1e-8, max_iter=300000)
+    assert st == 0 and rel <= 1e-8
+    ka, cb, _ = oracle.lps_constants(1.0, 0.4, 1.0, 3.0)
+    op = ("lps", ka, cb)
+    uo, _, _ = oracle.cg_static(cfg["chi"], cfg["chi_omega"], cfg["b"], cfg["w"], 1.0, 3.0, op, rtol=1e-12)
+    assert _rel(u.cpu().numpy(), uo) < 2e-6
+    plan.close()
+
+
+def test_dr_3d_bond_fused_matches_cg(pdm):
+    """The fused 3D step against the FP64 GPU CG path at the same tolerance."""
+    cfg = inputs.cube_with_cavity(n=64, radius_frac=0.2)
+    shape = cfg["shape"]
+    sols = []
+    for fp64, method in ((False, "dr"), (True, "cg")):
+        prob = pdm.Problem(shape=shape, delta=3.0, model=pdm.PD_LIN_BOND, fp64=fp64)
+        plan = pdm.Plan(prob, _t(cfg["chi"], torch.uint8), _t(cfg["chi_omega"], torch.uint8))
+        u = torch.zeros((3,) + shape, dtype=torch.float64, device=DEV)
+        solve = plan.solve_dr if method == "dr" else plan.solve_static
+        it, rel, st = solve(u, _t(cfg["b"]), None, rtol=1e-8, max_iter=300000)
+        assert st == 0 and rel <= 1e-8
+        sols.append(u.cpu().numpy())
+        plan.close()
+    assert _rel(sols[0], sols[1]) < 2e-6
+
+
+def test_dr_budget_exhausted_terminates(pdm):
+    """A step budget far too small ends the device-side loop with NOT_CONVERGED."""
+    cfg = inputs.batched_specimens(count=1, seed=5, sizes=[120])[0]
+    plan = pdm.Plan(_bond_problem(pdm, cfg, False), _t(cfg["chi"], torch.uint8), _t(cfg["chi_omega"], torch.uint8))
+    u = torch.zeros((2,) + cfg["shape"], dtype=torch.float64, device=DEV)
+    it, rel, st = plan.solve_dr(u, _t(cfg["b"]), None, rtol=1e-8, max_iter=64, raise_on_fail=False)
+    assert st == -5 and 64 <= it <= 80 and 0 < rel < 10.0
+    plan.close()
+
+
+def _solve_batch(pdm, cfgs, rtol, tune=False):
+    probs = [_bond_problem(pdm, c, False) for c in cfgs]
+    batch = pdm.Batch(probs, [_t(c["chi"], torch.uint8) for c in cfgs],
+                      [_t(c["chi_omega"], torch.uint8) for c in cfgs])
+    if tune:
+        batch.autotune()
+    us = [torch.zeros((2,) + c["shape"], dtype=torch.float64, device=DEV) for c in cfgs]
+    bs = [_t(c["b"]) for c in cfgs]
+    its, rels, sts = batch.solve_dr(us, bs, rtol=rtol, max_iter=300000)
+    return batch, us, bs, its, rels, sts
+
+
+def test_dr_batched_uneven_matches_fp64_cg(pdm, oracle):
+    cfgs = inputs.batched_specimens(count=8, seed=11, nmin=40, nmax=250)
+    batch, us, bs, its, rels, sts = _solve_batch(pdm, cfgs, 1e-8)
+    assert all(s == 0 for s in sts) and all(r <= 1e-8 for r in rels)
+    assert len({c["shape"] for c in cfgs}) > 1 and len({c["delta"] for c in cfgs}) > 1
+    for c, u in zip(cfgs, us):
+        plan = pdm.Plan(_bond_problem(pdm, c, True), _t(c["chi"], torch.uint8), _t(c["chi_omega"], torch.uint8))
+        uc = torch.zeros_like(u)
+        _, relc, stc = plan.solve_static(uc, _t(c["b"]), None, rtol=1e-8, max_iter=100000)
+        assert stc == 0
+        assert _rel(u.cpu().numpy(), uc.cpu().numpy()) < 2e-6
+        plan.close()
+    # the smallest specimen also against the oracle's FP64 operator
+    k = int(np.argmin([c["shape"][0] for c in cfgs]))
+    c = cfgs[k]
+    res = oracle.static_residual(us[k].cpu().numpy(), c["chi"], c["chi_omega"], c["b"], 1.0, c["delta"],
+                                 ("bond", oracle.alpha_bond(2, 1.0, c["delta"])))
+    assert np.linalg.norm(res) / np.linalg.norm(c["chi_omega"] * c["b"]) <= 1.5e-8
+    # second call: cached graph, new right-hand sides in the same buffers
+    for b in bs:
+        b.mul_(-2.0)
+    us2 = [torch.zeros_like(u) for u in us]
+    its2, rels2, sts2 = batch.solve_dr(us2, bs, rtol=1e-8, max_iter=300000)
+    assert all(s == 0 for s in sts2)
+    for u, u2 in zip(us, us2):
+        assert _rel(u2.cpu().numpy(), -2.0 * u.cpu().numpy()) < 2e-6
+    batch.close()
+
+
+def test_autotune_keeps_results(pdm):
+    cfg = inputs.cube_with_cavity(n=64)
+    shape = cfg["shape"]
+    prob = pdm.Problem(shape=shape, delta=3.0, fp64=False)
+    plan = pdm.Plan(prob, _t(cfg["chi"], torch.uint8))
+    g = inputs.rng(2)
+    u = torch.tensor(g.normal(size=(3,) + shape) * cfg["chi"], dtype=torch.float32, device=DEV)
+    L0 = plan.force(u).double()
+    tun = plan.autotune()
+    assert tun["rows"] > 0 and tun["w_x2"] in (4, 8, 16, 32) and tun["w_last"] in (4, 8, 16, 32)
+    assert tun["sched"] in (0, 1)
+    L1 = plan.force(u).double()
+    assert float(torch.linalg.norm(L1 - L0) / torch.linalg.norm(L0)) < 2e-6
+    plan.close()
