@@ -173,11 +173,13 @@ pd_status pd_solve_static(pd_plan *plan, double *u, const double *b, const doubl
  * pd_solve_dr -- the static problem of pd_solve_static (same arguments,
  * same FP64 iterative refinement and stopping rule) with dynamic relaxation
  * as the inner solver instead of CG. Dynamic relaxation is not in the paper;
- * the method is the adaptive dynamic relaxation of Kilic and Madenci (Theor.
- * Appl. Fract. Mech. 53 (2010) 194-204): damped central-difference pseudo
- * dynamics with a fictitious density of 1.05/4 of the largest eigenvalue of
- * the periodic symbol (pd_stable_dt), unit pseudo time step and the damping
- * 2 sqrt(e.K e / e.e) from the local stiffness estimate of that paper.
+ * the method is adaptive dynamic relaxation (Underwood 1983; the peridynamic
+ * form of Kilic and Madenci, Theor. Appl. Fract. Mech. 53 (2010) 194-204):
+ * damped central-difference pseudo dynamics with a fictitious density of
+ * 1.05/4 of the largest eigenvalue of the periodic symbol (pd_stable_dt),
+ * unit pseudo time step and the damping 2 sqrt(e.Ae / (rho e.e)), with A e
+ * taken exactly (it is the right-hand side minus the pseudo force) instead
+ * of the published diagonal local-stiffness estimate.
  * The whole solve, including its stopping decisions, runs as one CUDA graph
  * launch with device-side conditional nodes.
  * max_iter: cap on the total number of relaxation steps (rounded up to a

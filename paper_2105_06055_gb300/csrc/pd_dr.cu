@@ -3,22 +3,27 @@
 // convergence by device-side control flow inside one CUDA graph launch.
 //
 // The paper solves its static problems by CG (§4.3); dynamic relaxation is
-// not in it. The method here is the adaptive dynamic relaxation (ADR) of
-// Kilic and Madenci (Theor. Appl. Fract. Mech. 53 (2010) 194-204): the
-// correction equation A e = r (A e = -chi_O L(chi_O e), see pd_solve.cu) is
-// read as the damped motion  rho_f e'' + c rho_f e' = F(e) = r - A e  with a
-// fictitious uniform density rho_f and unit pseudo time step, integrated by
-// the damped central difference
+// not in it. The method here is adaptive dynamic relaxation (ADR; Underwood
+// 1983, in the peridynamic form of Kilic and Madenci, Theor. Appl. Fract.
+// Mech. 53 (2010) 194-204): the correction equation A e = r
+// (A e = -chi_O L(chi_O e), see pd_solve.cu) is read as the damped motion
+//   rho_f e'' + c rho_f e' = F(e) = r - A e
+// with a fictitious uniform density rho_f and unit pseudo time step,
+// integrated by the damped central difference
 //   v^{n+1/2} = ((2 - c^n) v^{n-1/2} + 2 F^n / rho_f) / (2 + c^n)
 //   e^{n+1}  = e^n + v^{n+1/2}
 // from e^0 = 0, v^{1/2} = F^0 / (2 rho_f) (the general step with v = 0 and
-// c = 2 is exactly that start-up step). The damping follows the lowest mode:
-//   c^n = 2 sqrt( sum_i (e^n_i)^2 K^n_i / sum_i (e^n_i)^2 ),
-//   K^n_i = -(F^n_i - F^{n-1}_i) / (rho_f v^{n-1/2}_i)   (0 where v_i = 0),
-// and c^n = 0 when the quotient is not positive. Stability of the central
-// difference needs lambda_max(A) <= 4 rho_f; the chi cut and the restriction
-// to Omega only remove bonds, so lambda_max(A) is at most the largest
-// eigenvalue of the periodic symbol K^(0) - K^(k), and rho_f is 1.05/4 of it.
+// c = 2 is exactly that start-up step). The damping tracks the lowest mode,
+// c^n = 2 sqrt(omega^2), through the Rayleigh quotient of the current iterate
+//   omega^2 = e^n.(A e^n) / (rho_f e^n.e^n),   A e^n = r - F^n,
+// and c^n = 0 when the quotient is not positive. ADR as published estimates
+// A e^n from a diagonal local stiffness, -(F^n_i - F^{n-1}_i) / v^{n-1/2}_i;
+// here A e^n is known exactly (it is r - F^n, no extra work), and the
+// diagonal estimate was seen to turn negative for whole stretches of steps
+// and leave the iteration undamped. Stability of the central difference
+// needs lambda_max(A) <= 4 rho_f; the chi cut and the restriction to Omega
+// only remove bonds, so lambda_max(A) is at most the largest eigenvalue of
+// the periodic symbol K^(0) - K^(k), and rho_f is 1.05/4 of it.
 //
 // Precision and stopping follow pd_solve_static: the relaxation runs on the
 // plan's FFT convolutions (FP32 on an FP32 plan) inside an iterative
@@ -39,8 +44,8 @@
 // fused into its first and last passes:
 //   rows  : v, e update (needs c^{n-1}); x1 transform of chi e
 //   cols / last / cols : x2 transform, M^ multiply with x3, inverse (3D)
-//   rows  : inverse x1, F^n = r + chi_O L(e), block partials of the damping
-//           quotient and of ||F||^2
+//   rows  : inverse x1, F^n = r + chi_O L(e), block partials of e.Ae, e.e
+//           and ||F||^2
 //   finish: c^n, ||F^n||^2
 // The state-based operator (dilatation round between the halves) runs the
 // update as separate vector kernels around the plain force.
@@ -63,10 +68,11 @@ constexpr double kDrMaxSteps = 16777216.0;
 // DR scalars in the plan's reduction buffer, after the CG scalars
 enum {
     R_BN2 = 16, R_BN, R_TARGET, R_RN, R_ITOL2, R_C, R_FF, R_RHOINV, R_STEPS, R_MAXSTEPS, R_CYCLES,
-    R_STATUS, R_GO, R_REL, R_COUNT
+    R_STATUS, R_GO, R_REL, R_BEST, R_SINCE, R_CSTEPS, R_RNPREV, R_SLOW, R_COUNT
 };
 // R_STATUS values
-enum { DR_RUN = 0, DR_CONVERGED = 1, DR_MAXSTEPS = 2, DR_NONFINITE = 3, DR_TIMEOUT = 4, DR_CYCLES = 5 };
+enum { DR_RUN = 0, DR_CONVERGED = 1, DR_MAXSTEPS = 2, DR_NONFINITE = 3, DR_TIMEOUT = 4, DR_CYCLES = 5,
+       DR_STALLED = 6 };
 
 __global__ void k_dr_start(double *red, double rho_inv, double max_steps)
 {
@@ -76,8 +82,9 @@ __global__ void k_dr_start(double *red, double rho_inv, double max_steps)
     s[R_MAXSTEPS] = max_steps;
 }
 
-// Refinement check after an FP64 residual: converged / out of budget / go on.
-// Sets the WHILE handle; on "go on" arms the restart of the relaxation.
+// Refinement check after an FP64 residual: converged / out of budget /
+// stalled / go on. Sets the WHILE handle; on "go on" arms the restart of the
+// relaxation.
 __global__ void k_dr_ir_check(double *red, const int *dev_status, cudaGraphConditionalHandle hw, int first,
                               double rtol)
 {
@@ -85,9 +92,13 @@ __global__ void k_dr_ir_check(double *red, const int *dev_status, cudaGraphCondi
     if (first) {
         s[R_BN] = sqrt(s[R_BN2]);
         s[R_TARGET] = rtol * (s[R_BN] > 0.0 ? s[R_BN] : 1.0);
+        s[R_RNPREV] = HUGE_VAL;
     }
     const double rn = sqrt(s[R_RN]);
     if (isfinite(rn)) s[R_REL] = s[R_BN] > 0.0 ? rn / s[R_BN] : rn;
+    // a cycle that did not halve the residual counts as slow; two in a row stall
+    s[R_SLOW] = (rn > 0.5 * s[R_RNPREV]) ? s[R_SLOW] + 1.0 : 0.0;
+    s[R_RNPREV] = rn;
     int st = (int)s[R_STATUS];
     if (st == DR_RUN) {
         if (*dev_status)
@@ -100,6 +111,8 @@ __global__ void k_dr_ir_check(double *red, const int *dev_status, cudaGraphCondi
             st = DR_MAXSTEPS;
         else if (s[R_CYCLES] >= kDrMaxCycles)
             st = DR_CYCLES;
+        else if (s[R_SLOW] >= 2.0)
+            st = DR_STALLED;
     }
     s[R_STATUS] = st;
     const int go = st == DR_RUN;
@@ -109,21 +122,37 @@ __global__ void k_dr_ir_check(double *red, const int *dev_status, cudaGraphCondi
         const double itol = fmax(1e-3 * rn, 0.5 * s[R_TARGET]);
         s[R_ITOL2] = itol * itol;
         s[R_C] = 2.0;  // with v = 0: the start-up step v = F / (2 rho_f)
+        s[R_BEST] = HUGE_VAL;
+        s[R_SINCE] = 0.0;
+        s[R_CSTEPS] = 0.0;
     }
     cudaGraphSetConditional(hw, go ? 1u : 0u);
 }
 
-// After K steps: is the relaxation cycle over (inner tolerance, step budget,
-// failure)? Sets the IF handle of the refinement block. Backstop: should the
-// step counter ever pass the budget by two passes without the refinement
-// block having ended the loop, this kernel ends it itself.
+// After K steps: is the relaxation cycle over? It is when ||F|| reaches the
+// cycle's tolerance, when the step budget is spent, on a failure, or when
+// ||F|| has stopped improving: no new minimum (by 2%) over the last half of
+// the cycle and at least 1024 steps (the FP32 operator resolves F = r - A e
+// only to about eps32 kappa(A) relative to r, below which the relaxation
+// stalls; the refinement then starts the next cycle from the FP64 residual).
+// Sets the IF handle of the refinement block. Backstop: should the step
+// counter ever pass the budget by two passes without the refinement block
+// having ended the loop, this kernel ends it itself.
 __global__ void k_dr_check(double *red, const int *dev_status, cudaGraphConditionalHandle hif,
                            cudaGraphConditionalHandle hw, int K)
 {
     double *s = red + kRedScal;
     s[R_STEPS] += K;
+    s[R_CSTEPS] += K;
     const double ff = s[R_FF], c = s[R_C];
-    int done = ff <= s[R_ITOL2] || s[R_STEPS] >= s[R_MAXSTEPS];
+    if (ff < 0.9604 * s[R_BEST]) {  // 0.98^2: ||F|| down by 2%
+        s[R_BEST] = ff;
+        s[R_SINCE] = 0.0;
+    } else {
+        s[R_SINCE] += K;
+    }
+    const bool stalled = s[R_SINCE] >= 1024.0 && s[R_SINCE] >= 0.5 * s[R_CSTEPS];
+    int done = ff <= s[R_ITOL2] || s[R_STEPS] >= s[R_MAXSTEPS] || stalled;
     if (!isfinite(ff) || !isfinite(c)) {
         if (s[R_STATUS] == DR_RUN) s[R_STATUS] = DR_NONFINITE;
         done = 1;
@@ -164,7 +193,7 @@ __global__ void k_dr_ir_update(double *u, const T *e, const uint8_t *co, int64_t
         if (co[i]) u[i] += (double)e[i];
 }
 
-// Block partial triples (damping numerator, denominator, ||F||^2) -> c^n, ||F^n||^2
+// Block partial triples (e.Ae, e.e, ||F||^2) -> c^n, ||F^n||^2
 __global__ void k_dr_finish(double *red, int nparts)
 {
     double a = 0.0, b = 0.0, f = 0.0;
@@ -178,7 +207,7 @@ __global__ void k_dr_finish(double *red, int nparts)
     f = block_sum_d(f);
     if (threadIdx.x == 0) {
         double *s = red + kRedScal;
-        const double q = b > 0.0 ? a / b : 0.0;
+        const double q = b > 0.0 ? a / b * s[R_RHOINV] : 0.0;
         s[R_C] = q > 0.0 ? 2.0 * sqrt(q) : 0.0;
         s[R_FF] = f;
     }
@@ -200,14 +229,13 @@ __device__ __forceinline__ void write_partial3(double *red, const DrAcc &acc)
     }
 }
 
-// one node's contribution to the damping quotient and ||F||^2
+// one node's contribution to e.Ae (A e = r - F), e.e and ||F||^2
 template <typename T>
-__device__ __forceinline__ void dr_accumulate(DrAcc &acc, T Fn, T Fo, T vv, T ee, T rinv)
+__device__ __forceinline__ void dr_accumulate(DrAcc &acc, T Fn, T r, T ee)
 {
     acc.ff.add(Fn * Fn);
-    const T e2 = ee * ee;
-    acc.den.add(e2);
-    if (vv != T(0)) acc.num.add(e2 * (-(Fn - Fo) * rinv / vv));
+    acc.den.add(ee * ee);
+    acc.num.add(ee * (r - Fn));
 }
 
 // rows, forward: v^{n+1/2}, e^{n+1} from c^n, F^n; transform chi e
@@ -262,7 +290,7 @@ struct EpiDR {
     static constexpr int kFin = D, kFout = 0, kStage = D, kNF = 0, kNB = 1 + D;
     static constexpr bool kSparse = true;
     using Acc = DrAcc;
-    const T *e, *v, *rhs;
+    const T *e, *rhs;
     T *F;
     const uint8_t *chi, *co;
     const GEntry<T> *gent;
@@ -306,23 +334,20 @@ struct EpiDR {
     __device__ __forceinline__ void emit(const RowCtx<T> &c, int rl, int i1, const T *s0, const T *s1,
                                          DrAcc &acc) const
     {
-        const T rinv = (T)red[kRedScal + R_RHOINV];
         const int64_t p = (c.row0 + rl) * n1 + i1;
-        typename vec2<T>::type ev[D], vv[D], rv[D], fo[D];
+        typename vec2<T>::type ev[D], rv[D];
 #pragma unroll
         for (int i = 0; i < D; ++i) {
             ev[i] = load2(e + i * N + p);
-            vv[i] = load2(v + i * N + p);
             rv[i] = load2(rhs + i * N + p);
-            fo[i] = load2(F + i * N + p);
         }
 #pragma unroll
         for (int i = 0; i < D; ++i) {
             const T fa = c.b(1 + i, rl, i1) ? rv[i].x + s0[i] : T(0);
             const T fb = c.b(1 + i, rl, i1 + 1) ? rv[i].y + s1[i] : T(0);
             store2(F + i * N + p, fa, fb);
-            dr_accumulate<T>(acc, fa, fo[i].x, vv[i].x, ev[i].x, rinv);
-            dr_accumulate<T>(acc, fb, fo[i].y, vv[i].y, ev[i].y, rinv);
+            dr_accumulate<T>(acc, fa, rv[i].x, ev[i].x);
+            dr_accumulate<T>(acc, fb, rv[i].y, ev[i].y);
         }
     }
     __device__ void block_done(DrAcc &acc) const { write_partial3(red, acc); }
@@ -344,16 +369,13 @@ __global__ void k_dr_pre(T *e, T *v, const T *F, int64_t n, const double *red)
 
 // ... and F^n = r + chi_O L(e) with the partials
 template <typename T>
-__global__ void k_dr_post(const T *L, const T *e, const T *v, const T *rhs, T *F, const uint8_t *co, int64_t n,
-                          double *red)
+__global__ void k_dr_post(const T *L, const T *e, const T *rhs, T *F, const uint8_t *co, int64_t n, double *red)
 {
-    const T rinv = (T)red[kRedScal + R_RHOINV];
     DrAcc acc;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const T fn = co[i] ? rhs[i] + L[i] : T(0);
-        const T fo = F[i];
         F[i] = fn;
-        dr_accumulate<T>(acc, fn, fo, v[i], e[i], rinv);
+        dr_accumulate<T>(acc, fn, rhs[i], e[i]);
     }
     write_partial3(red, acc);
 }
@@ -403,7 +425,7 @@ struct DrSpec {
             PD_LAUNCH_CHECK();
             T *L = reinterpret_cast<T *>(p->r64);  // scratch between refinement residuals
             PD_TRY(force_plain<T>(p, e, nullptr, L, nullptr, st));
-            k_dr_post<T><<<nb, 256, 0, st>>>(L, e, v, rhs, F, p->chi_om, nvec, p->red);
+            k_dr_post<T><<<nb, 256, 0, st>>>(L, e, rhs, F, p->chi_om, nvec, p->red);
             PD_LAUNCH_CHECK();
             k_dr_finish<<<1, 1024, 0, st>>>(p->red, (int)nb);
             PD_LAUNCH_CHECK();
@@ -420,7 +442,7 @@ struct DrSpec {
         CombForce<T, D, false> cmb{m, ob};
         PD_TRY(launch_cols<T>(p, cmb, D == 3 ? 2 : 1, true, D, st));
         if (D == 3) PD_TRY((col_pass<T, D>(p, ob, true, st)));
-        EpiDR<T, D> epi{e, v, rhs, F, p->chi, p->chi_om, m.gent, m.goff, p->red, p->N, p->n1, spec + ob * fs, fs};
+        EpiDR<T, D> epi{e, rhs, F, p->chi, p->chi_om, m.gent, m.goff, p->red, p->N, p->n1, spec + ob * fs, fs};
         RowGeom g;
         LaunchCfg c;
         row_cfg<T>(p, D, EpiDR<T, D>::kNF, EpiDR<T, D>::kNB, g, c);

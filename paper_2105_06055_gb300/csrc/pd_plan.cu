@@ -8,6 +8,9 @@
 #include <cstring>
 #include <vector>
 
+#include <map>
+#include <mutex>
+
 #include "pd_plan.cuh"
 
 namespace pd {
@@ -55,15 +58,23 @@ pd_status encode_tmap_3d(CUtensorMap *m, void *base, bool fp64, const unsigned l
     return PD_OK;
 }
 
+// The dynamic shared-memory limit is a property of the kernel function, shared
+// by every plan and by every kernel node of a captured graph: it only ever
+// grows, so plans of different sizes never lower it under each other.
 pd_status set_smem_attr(const void *func, size_t smem)
 {
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) {
-            set_error("cudaFuncSetAttribute(%zu bytes): %s", smem, cudaGetErrorString(e));
-            return PD_ERR_CUDA;
-        }
+    static std::mutex mu;
+    static std::map<const void *, size_t> set;
+    if (smem <= 48 * 1024) return PD_OK;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t &cur = set[func];
+    if (smem <= cur) return PD_OK;
+    cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) {
+        set_error("cudaFuncSetAttribute(%zu bytes): %s", smem, cudaGetErrorString(e));
+        return PD_ERR_CUDA;
     }
+    cur = smem;
     return PD_OK;
 }
 
