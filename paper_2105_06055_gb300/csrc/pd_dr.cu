@@ -25,6 +25,13 @@
 // only remove bonds, so lambda_max(A) is at most the largest eigenvalue of
 // the periodic symbol K^(0) - K^(k), and rho_f is 1.05/4 of it.
 //
+// The pseudo force is carried recursively, F^{n+1} = F^n - A v^{n+1/2}
+// (e^{n+1} - e^n = v^{n+1/2}), so each step applies the operator to the
+// velocity, which shrinks with F, and not to e: an FP32 evaluation of A e
+// has an error of about eps32 lambda_max ||e||, which stalls the relaxation
+// at eps32 kappa(A) relative to r, while the error of A v stays relative to
+// F. The drift of the recursion is removed by the FP64 refinement.
+//
 // Precision and stopping follow pd_solve_static: the relaxation runs on the
 // plan's FFT convolutions (FP32 on an FP32 plan) inside an iterative
 // refinement whose residual R(u) = chi_O (b + L(u)) is recomputed with the
@@ -42,9 +49,9 @@
 //
 // One relaxation step (bond model) is the force pipeline with the update
 // fused into its first and last passes:
-//   rows  : v, e update (needs c^{n-1}); x1 transform of chi e
+//   rows  : v, e update (needs c^{n-1}); x1 transform of chi v
 //   cols / last / cols : x2 transform, M^ multiply with x3, inverse (3D)
-//   rows  : inverse x1, F^n = r + chi_O L(e), block partials of e.Ae, e.e
+//   rows  : inverse x1, F += chi_O L(v), block partials of e.Ae, e.e
 //           and ||F||^2
 //   finish: c^n, ||F^n||^2
 // The state-based operator (dilatation round between the halves) runs the
@@ -238,7 +245,7 @@ __device__ __forceinline__ void dr_accumulate(DrAcc &acc, T Fn, T r, T ee)
     acc.num.add(ee * (r - Fn));
 }
 
-// rows, forward: v^{n+1/2}, e^{n+1} from c^n, F^n; transform chi e
+// rows, forward: v^{n+1/2}, e^{n+1} from c^n, F^n; transform chi v
 template <typename T, int D>
 struct ProDR {
     static constexpr int kFin = 0, kFout = D, kNF = 0, kNB = 1, kStage = 0;
@@ -275,8 +282,8 @@ struct ProDR {
             const T ea = ev[j].x + va, eb = ev[j].y + vb;
             store2(v + j * N + p, va, vb);
             store2(e + j * N + p, ea, eb);
-            o0[j] = m0 * ea;
-            o1[j] = m1 * eb;
+            o0[j] = m0 * va;
+            o1[j] = m1 * vb;
         }
     }
     __device__ void sparse(const RowCtx<T> &, int, int) const {}
@@ -284,13 +291,13 @@ struct ProDR {
     __device__ void block_done(DSum &) const {}
 };
 
-// rows, inverse: L(e) = chi y - G e staged, F^n = r + chi_O L(e), partials
+// rows, inverse: L(v) = chi y - G v staged, F^{n+1} = F^n + chi_O L(v), partials
 template <typename T, int D>
 struct EpiDR {
     static constexpr int kFin = D, kFout = 0, kStage = D, kNF = 0, kNB = 1 + D;
     static constexpr bool kSparse = true;
     using Acc = DrAcc;
-    const T *e, *rhs;
+    const T *e, *v, *rhs;
     T *F;
     const uint8_t *chi, *co;
     const GEntry<T> *gent;
@@ -319,32 +326,33 @@ struct EpiDR {
         const int k0 = goff[c.row0], k1 = goff[c.row0 + c.rows];
         for (int k = k0 + tid; k < k1; k += nthreads) {
             const GEntry<T> g = gent[k];
-            T ee[D], Ge[D];
+            T vv[D], Gv[D];
 #pragma unroll
             for (int q = 0; q < D; ++q) {
-                ee[q] = e[q * N + g.p];
-                Ge[q] = T(0);
+                vv[q] = v[q * N + g.p];
+                Gv[q] = T(0);
             }
-            sym_apply<T, D>(g.g, ee, Ge);
+            sym_apply<T, D>(g.g, vv, Gv);
             const int rl = (int)(g.p / n1 - c.row0), i1 = (int)(g.p % n1);
 #pragma unroll
-            for (int i = 0; i < D; ++i) c.stage(i, rl, i1) -= Ge[i];
+            for (int i = 0; i < D; ++i) c.stage(i, rl, i1) -= Gv[i];
         }
     }
     __device__ __forceinline__ void emit(const RowCtx<T> &c, int rl, int i1, const T *s0, const T *s1,
                                          DrAcc &acc) const
     {
         const int64_t p = (c.row0 + rl) * n1 + i1;
-        typename vec2<T>::type ev[D], rv[D];
+        typename vec2<T>::type ev[D], rv[D], fv[D];
 #pragma unroll
         for (int i = 0; i < D; ++i) {
             ev[i] = load2(e + i * N + p);
             rv[i] = load2(rhs + i * N + p);
+            fv[i] = load2(F + i * N + p);
         }
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-            const T fa = c.b(1 + i, rl, i1) ? rv[i].x + s0[i] : T(0);
-            const T fb = c.b(1 + i, rl, i1 + 1) ? rv[i].y + s1[i] : T(0);
+            const T fa = c.b(1 + i, rl, i1) ? fv[i].x + s0[i] : T(0);
+            const T fb = c.b(1 + i, rl, i1 + 1) ? fv[i].y + s1[i] : T(0);
             store2(F + i * N + p, fa, fb);
             dr_accumulate<T>(acc, fa, rv[i].x, ev[i].x);
             dr_accumulate<T>(acc, fb, rv[i].y, ev[i].y);
@@ -367,13 +375,13 @@ __global__ void k_dr_pre(T *e, T *v, const T *F, int64_t n, const double *red)
     }
 }
 
-// ... and F^n = r + chi_O L(e) with the partials
+// ... and F^{n+1} = F^n + chi_O L(v) with the partials
 template <typename T>
 __global__ void k_dr_post(const T *L, const T *e, const T *rhs, T *F, const uint8_t *co, int64_t n, double *red)
 {
     DrAcc acc;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const T fn = co[i] ? rhs[i] + L[i] : T(0);
+        const T fn = co[i] ? F[i] + L[i] : T(0);
         F[i] = fn;
         dr_accumulate<T>(acc, fn, rhs[i], e[i]);
     }
@@ -424,7 +432,7 @@ struct DrSpec {
             k_dr_pre<T><<<nb, 256, 0, st>>>(e, v, F, nvec, p->red);
             PD_LAUNCH_CHECK();
             T *L = reinterpret_cast<T *>(p->r64);  // scratch between refinement residuals
-            PD_TRY(force_plain<T>(p, e, nullptr, L, nullptr, st));
+            PD_TRY(force_plain<T>(p, v, nullptr, L, nullptr, st));
             k_dr_post<T><<<nb, 256, 0, st>>>(L, e, rhs, F, p->chi_om, nvec, p->red);
             PD_LAUNCH_CHECK();
             k_dr_finish<<<1, 1024, 0, st>>>(p->red, (int)nb);
@@ -442,7 +450,7 @@ struct DrSpec {
         CombForce<T, D, false> cmb{m, ob};
         PD_TRY(launch_cols<T>(p, cmb, D == 3 ? 2 : 1, true, D, st));
         if (D == 3) PD_TRY((col_pass<T, D>(p, ob, true, st)));
-        EpiDR<T, D> epi{e, rhs, F, p->chi, p->chi_om, m.gent, m.goff, p->red, p->N, p->n1, spec + ob * fs, fs};
+        EpiDR<T, D> epi{e, v, rhs, F, p->chi, p->chi_om, m.gent, m.goff, p->red, p->N, p->n1, spec + ob * fs, fs};
         RowGeom g;
         LaunchCfg c;
         row_cfg<T>(p, D, EpiDR<T, D>::kNF, EpiDR<T, D>::kNB, g, c);

@@ -377,11 +377,14 @@ struct Solver {
                 return PD_ERR_NONFINITE;
             }
             if (hs()[S_FLAG] == 2.0 || rn <= tol_abs) break;
-            // stagnation of the recursive residual (FP32 attainable accuracy)
+            // stagnation of the recursive residual (FP32 attainable accuracy):
+            // no new minimum (by 0.1%) over the last half of the iterations and
+            // at least 8 chunks (the CG residual norm is not monotone and can
+            // plateau for long stretches on ill-conditioned problems)
             if (rn < 0.999 * best) {
                 best = rn;
                 since_best = 0;
-            } else if ((since_best += kChunk) >= 8 * kChunk) {
+            } else if ((since_best += kChunk) >= 8 * kChunk && 2 * since_best >= it) {
                 break;
             }
         }
