@@ -149,3 +149,28 @@ def test_autotune_keeps_results(pdm):
     L1 = plan.force(u).double()
     assert float(torch.linalg.norm(L1 - L0) / torch.linalg.norm(L0)) < 2e-6
     plan.close()
+
+
+def test_dr_batched_config4_full_size(pdm, oracle):
+    """64 uneven specimens (sides 256..1024, delta 3..5) in one graph launch,
+    each to 1e-8; two against the FP64 GPU CG path, one against the oracle's
+    FP64 operator."""
+    cfgs = inputs.batched_specimens(count=64, seed=0)
+    batch, us, bs, its, rels, sts = _solve_batch(pdm, cfgs, 1e-8, tune=True)
+    assert all(s == 0 for s in sts), sts
+    assert max(rels) <= 1e-8
+    assert {c["shape"][0] for c in cfgs} >= {512, 1024} and {c["delta"] for c in cfgs} == {3.0, 4.0, 5.0}
+    for k in (0, 2):
+        c = cfgs[k]
+        plan = pdm.Plan(_bond_problem(pdm, c, True), _t(c["chi"], torch.uint8), _t(c["chi_omega"], torch.uint8))
+        uc = torch.zeros_like(us[k])
+        _, _, stc = plan.solve_static(uc, bs[k], None, rtol=1e-8, max_iter=100000)
+        assert stc == 0
+        assert float(torch.linalg.norm(uc - us[k]) / torch.linalg.norm(uc)) < 1e-6
+        plan.close()
+    k = next(i for i, c in enumerate(cfgs) if c["shape"][0] == 512)
+    c = cfgs[k]
+    res = oracle.static_residual(us[k].cpu().numpy(), c["chi"], c["chi_omega"], c["b"], 1.0, c["delta"],
+                                 ("bond", oracle.alpha_bond(2, 1.0, c["delta"])))
+    assert np.linalg.norm(res) / np.linalg.norm(c["chi_omega"] * c["b"]) <= 1.5e-8
+    batch.close()
