@@ -3,10 +3,11 @@ delta = 4, critical energy from s0 = 1e-3 (reading R10 of the design notes),
 4000 FP32 velocity-Verlet steps with bond breaking (Eq. 63, 83-84, 101-102).
 
 Full-size parity: the FP64 GPU path follows the FP64 oracle bit for bit in
-the integrity index through the first 600 steps (crack initiation); after the
-FP32 run's 4000 steps, one more step from its state takes the oracle's
-decisions on every node whose W is not within 1e-4 Wc of the threshold; the
-damage counts of the final state are exact integers."""
+the integrity index through the first 250 steps (bonds start to break at
+about step 120); after the FP32 run's 4000 steps, one more step from its
+state takes the oracle's decisions on every node whose W is not within
+1e-4 Wc of the threshold; the damage counts of the final state are exact
+integers."""
 import math
 
 import numpy as np
@@ -44,7 +45,7 @@ def test_fracture_config3_full_size(pdm, oracle):
     dt = 0.8 * plans[True].stable_dt
 
     # (1) FP64 GPU path against the oracle through crack initiation
-    n0 = 600
+    n0 = 250
     uo, vo, lo, flo = oracle.verlet_damage(np.zeros((2,) + shape), np.zeros((2,) + shape), cfg["lam"], cfg["chi"],
                                            cfg["chi_omega"], b, cfg["w"], 1.0, delta, alpha, 1.0, dt, wc, n0)
     assert flo > 0
