@@ -161,6 +161,7 @@ def run_native(args, rank, world):
     chi = torch.tensor(cfg["chi"], device=dev)
     chi_om = torch.tensor(cfg["chi_omega"], device=dev)
     plan = pd.Plan(prob, chi, chi_om)
+    tuning = plan.autotune() if args.autotune else None
     b = torch.tensor(cfg["b"], dtype=torch.float64, device=dev)
     u = torch.zeros((3,) + shape, dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
@@ -281,6 +282,7 @@ def run_native(args, rank, world):
                     "d2h_bytes_per_step": int(u_host.numel() * 8)},
             "gpu_launches": int(launches),
             "clocks": clocks,
+            "tuning": tuning,
         }
     plan.close()
     return result, cfg
@@ -398,6 +400,7 @@ def main():
     ap.add_argument("--n", type=int, default=N_GRID)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="static", choices=["static", "batched"])
+    ap.add_argument("--autotune", action="store_true", help="run the pass autotuner on the plan first")
     ap.add_argument("--specimens", type=int, default=64)
     ap.add_argument("--profile-solve", type=int, default=0, metavar="K",
                     help="no timing: build the workload and run one solve capped at K CG iterations "

@@ -236,6 +236,15 @@ struct op_acc<Op, std::void_t<typename Op::Acc>> {
     using type = typename Op::Acc;
 };
 
+// Row ops whose node2 also accumulates into the block accumulator declare
+// kNodeAcc = true and take the accumulator as a last argument.
+template <class Op, class = void>
+struct op_node_acc : std::false_type {
+};
+template <class Op>
+struct op_node_acc<Op, std::void_t<decltype(Op::kNodeAcc)>> : std::bool_constant<Op::kNodeAcc> {
+};
+
 // Op interface (all device unless noted):
 //   static constexpr int kFin, kFout;  packed spectra read (inverse) / written (forward)
 //   static constexpr int kNF, kNB;     node fields (T / uint8) bulk-loaded for the tile's rows
@@ -320,6 +329,7 @@ __global__ void __launch_bounds__(256) k_rows(RowGeom g, Op op, const cx<T> *__r
         for (int f = 0; f < FI; ++f) fft_smem<T>(spec + (f * rows + rf) * pitch, 1, g.lgh, jt, tws, lg1, false, false, g.sched);
     }
 
+    typename op_acc<Op>::type acc;
     // per-node work, lanes over consecutive packed slots (2 nodes each)
     for (int idx = threadIdx.x; idx < rows * H; idx += blockDim.x) {
         const int rl = idx >> g.lgh, n = idx & (H - 1);
@@ -331,7 +341,10 @@ __global__ void __launch_bounds__(256) k_rows(RowGeom g, Op op, const cx<T> *__r
             in0[f] = w.x;
             in1[f] = -w.y;
         }
-        op.node2(ctx, rl, 2 * n, in0, in1, o0, o1);
+        if constexpr (op_node_acc<Op>::value)
+            op.node2(ctx, rl, 2 * n, in0, in1, o0, o1, acc);
+        else
+            op.node2(ctx, rl, 2 * n, in0, in1, o0, o1);
 #pragma unroll
         for (int f = 0; f < KO; ++f) spec[(f * rows + rl) * pitch + n] = mk(o0[f], o1[f]);
     }
@@ -341,7 +354,6 @@ __global__ void __launch_bounds__(256) k_rows(RowGeom g, Op op, const cx<T> *__r
         op.sparse(ctx, threadIdx.x, blockDim.x);
         __syncthreads();
     }
-    typename op_acc<Op>::type acc;
     if constexpr (ST > 0) {
         for (int idx = threadIdx.x; idx < rows * H; idx += blockDim.x) {
             const int rl = idx >> g.lgh, n = idx & (H - 1);

@@ -285,6 +285,17 @@ __global__ void k_lam_max(int dim, const double *mhat, const double *ghat, doubl
     if (threadIdx.x == 0) out[blockIdx.x] = sm[0];
 }
 
+// Packed masks: bit 0 chi_B, bit 1+c chi_Omega of component c.
+__global__ void k_mask_bits(const uint8_t *chi, const uint8_t *chi_om, int d, int64_t N, uint8_t *bits)
+{
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+        unsigned b = chi[p] ? 1u : 0u;
+        for (int k = 0; k < d; ++k)
+            if (chi_om[k * N + p]) b |= 2u << k;
+        bits[p] = (uint8_t)b;
+    }
+}
+
 // Body must keep delta away from the box faces (§4.2.2) and chi_Omega <= chi_B.
 __global__ void k_check_masks(int n1, int n2, int n3, int r1, int r2, int r3, const uint8_t *chi,
                               const uint8_t *chi_om, int d, int64_t N, int *bad)
@@ -499,7 +510,7 @@ double pd_stable_dt(const pd_plan *p)
 void pd_plan_destroy(pd_plan *p)
 {
     if (!p) return;
-    void *ptrs[] = {p->chi, p->chi_om, p->hoff, p->mhat64, p->mhat32, p->ghat64, p->ghat32, p->G64, p->G32,
+    void *ptrs[] = {p->chi, p->chi_om, p->mbits, p->hoff, p->mhat64, p->mhat32, p->ghat64, p->ghat32, p->G64, p->G32,
                     p->goff, p->gent64, p->gent32,
                     p->qt64, p->m3inv64, p->qt32, p->m3inv32, p->tw64, p->tw32, p->spec32, p->spec64,
                     p->work, p->red};
@@ -630,6 +641,9 @@ static pd_status plan_create_impl(const pd_problem *pr, const uint8_t *chi_B, co
     for (int k = 0; k < dim; ++k)
         PD_CUDA_TRY(cudaMemcpyAsync(p->chi_om + k * N, chi_Omega ? chi_Omega + k * N : chi_B, (size_t)N,
                                     cudaMemcpyDeviceToDevice, st));
+    PD_TRY(dalloc(p, &p->mbits, (size_t)N));
+    k_mask_bits<<<1024, 256, 0, st>>>(p->chi, p->chi_om, dim, N, p->mbits);
+    PD_LAUNCH_CHECK();
     // horizon tables on device (one buffer: ints, then doubles)
     int *d_off = nullptr;
     double *d_c = nullptr, *d_g = nullptr, *d_w2 = nullptr;

@@ -164,6 +164,7 @@ struct pd_plan {
     int hcount;
     // device memory
     uint8_t *chi = nullptr, *chi_om = nullptr;
+    uint8_t *mbits = nullptr;      // N: bit 0 chi_B, bit 1+c chi_Omega of component c
     int *hoff = nullptr;           // 3 x hcount integer offsets
     double *mhat64 = nullptr;      // ncomp x fold_sz
     float *mhat32 = nullptr;

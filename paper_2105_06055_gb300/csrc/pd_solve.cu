@@ -13,13 +13,17 @@
 // runs in FP64. CG inner products are accumulated per thread in compensated
 // FP32 (two-sum) and per block in FP64.
 //
-// One CG iteration is five fused passes and three small kernels:
-//   rows  : p = r + beta p (stored), FFT_x1 of chi p
+// One CG iteration is five fused passes and one small kernel; the vector
+// updates of iteration i are applied in the first pass of iteration i+1, so
+// all reductions of an iteration happen in one place (r.q and q.q give the
+// next r.r before r is updated: (r - alpha q).(r - alpha q) = rr - 2 alpha rq
+// + alpha^2 qq; the true r.r is summed again by the next first pass):
+//   rows  : e += alpha p, r -= alpha q, p = r + beta p (stored), partials of
+//           r.r, FFT_x1 of chi p
 //   cols / last / cols : FFT_x2, M^ multiply with FFT_x3, inverse (3D)
-//   rows  : inverse FFT_x1, q = -chi_O L(p) (stored), block partials of p.q
-//   finish: alpha = rr / p.q
-//   update: e += alpha p, r -= alpha q, block partials of r.r
-//   finish: beta = rr_new / rr
+//   rows  : inverse FFT_x1, q = -chi_O L(p) (stored), partials of p.q, r.q, q.q
+//   finish: rr, alpha = rr / p.q, beta = (rr - 2 alpha rq + alpha^2 qq) / rr
+// After the last iteration one update kernel applies the pending e, r update.
 // All CG scalars stay on the device. Chunks of kChunk iterations are captured
 // once into a CUDA graph and replayed; the host reads the residual norm after
 // each chunk.
@@ -33,10 +37,39 @@ namespace pd {
 namespace {
 
 constexpr int kChunk = 16;       // CG iterations per graph replay
+constexpr int kPartB = 14400;    // fused iteration: r.r partials below, (p.q, r.q, q.q) triples above
 
-// r = (T) r64, p = 0, e = 0 ; partial r.r
+// rr = sum of the first pass's partials; alpha, beta from the second pass's triples
+__global__ void k_cg_finish_fused(double *red, int na, int nb)
+{
+    double rr = 0.0, pq = 0.0, rq = 0.0, qq = 0.0;
+    for (int i = threadIdx.x; i < na; i += blockDim.x) rr += red[kRedPart + i];
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        pq += red[kRedPart + kPartB + 3 * i];
+        rq += red[kRedPart + kPartB + 3 * i + 1];
+        qq += red[kRedPart + kPartB + 3 * i + 2];
+    }
+    rr = block_sum_d(rr);
+    pq = block_sum_d(pq);
+    rq = block_sum_d(rq);
+    qq = block_sum_d(qq);
+    if (threadIdx.x == 0) {
+        double *s = red + kRedScal;
+        if (!isfinite(rr) || !isfinite(pq) || !isfinite(rq) || !isfinite(qq)) s[S_FLAG] = 1.0;
+        const double a = pq > 0.0 ? rr / pq : 0.0;
+        if (!(pq > 0.0) && rr > 0.0) s[S_FLAG] = 2.0;  // breakdown: p.Ap <= 0
+        const double rn = fmax(rr - 2.0 * a * rq + a * a * qq, 0.0);
+        s[S_ALPHA] = a;
+        s[S_BETA] = rr > 0.0 ? rn / rr : 0.0;
+        s[S_PQ] = pq;
+        s[S_RR] = rn;  // r.r after this iteration's (pending) update
+    }
+}
+
+
+// r = (T) r64, p = 0, e = 0, q = 0 ; partial r.r
 template <typename T>
-__global__ void k_cg_init(const double *r64, T *r, T *pp, T *e, int64_t n, double *red)
+__global__ void k_cg_init(const double *r64, T *r, T *pp, T *e, T *q, int64_t n, double *red)
 {
     DSum acc;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -44,6 +77,7 @@ __global__ void k_cg_init(const double *r64, T *r, T *pp, T *e, int64_t n, doubl
         r[i] = v;
         pp[i] = T(0);
         e[i] = T(0);
+        q[i] = T(0);
         acc.add(v * v);
     }
     write_partial(red, acc.value());
@@ -96,16 +130,17 @@ __global__ void k_cg_q(T *q, const T *pp, const uint8_t *co, int64_t n, double *
     write_partial(red, acc.value());
 }
 
-// rows, forward: p = r + beta p (stored), transform chi p. Node fields come
-// straight from global memory (coalesced pairs); only chi is staged.
+// rows, forward: pending update e += alpha p, r -= alpha q, then
+// p = r + beta p (stored), partials of r.r, transform chi p. Node fields come
+// straight from global memory (coalesced pairs); only the mask bits are staged.
 template <typename T, int D>
 struct ProCG {
     static constexpr int kFin = 0, kFout = D, kNF = 0, kNB = 1, kStage = 0;
-    static constexpr bool kSparse = false;
-    const T *r;
-    T *pv;
-    const uint8_t *chi;
-    const double *scal;
+    static constexpr bool kSparse = false, kNodeAcc = true;
+    T *e, *r, *pv;
+    const T *q;
+    const uint8_t *bits;
+    double *red;
     int64_t N;
     int n1;
     cx<T> *spec;
@@ -113,23 +148,31 @@ struct ProCG {
     __device__ const cx<T> *spec_in(int) const { return nullptr; }
     __device__ cx<T> *spec_out(int f) const { return spec + f * fstride; }
     __device__ const T *nf_src(int) const { return nullptr; }
-    __device__ const uint8_t *nb_src(int) const { return chi; }
+    __device__ const uint8_t *nb_src(int) const { return bits; }
     __device__ __forceinline__ void node2(const RowCtx<T> &c, int rl, int i1, const T *, const T *, T *o0,
-                                          T *o1) const
+                                          T *o1, DSum &acc) const
     {
-        const T beta = (T)scal[S_BETA];
-        const T v0 = c.b(0, rl, i1) ? T(1) : T(0), v1 = c.b(0, rl, i1 + 1) ? T(1) : T(0);
+        const double *s = red + kRedScal;
+        const T alpha = (T)s[S_ALPHA], beta = (T)s[S_BETA];
+        const T v0 = (c.b(0, rl, i1) & 1) ? T(1) : T(0), v1 = (c.b(0, rl, i1 + 1) & 1) ? T(1) : T(0);
         const int64_t p = (c.row0 + rl) * n1 + i1;
-        typename vec2<T>::type rr[D], pp[D];
+        typename vec2<T>::type ee[D], rr[D], pp[D], qq[D];
 #pragma unroll
         for (int j = 0; j < D; ++j) {
+            ee[j] = load2(e + j * N + p);
             rr[j] = load2(r + j * N + p);
             pp[j] = load2(pv + j * N + p);
+            qq[j] = load2(q + j * N + p);
         }
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            const T a = rr[j].x + beta * pp[j].x;
-            const T b = rr[j].y + beta * pp[j].y;
+            store2(e + j * N + p, ee[j].x + alpha * pp[j].x, ee[j].y + alpha * pp[j].y);
+            const T ra = rr[j].x - alpha * qq[j].x, rb = rr[j].y - alpha * qq[j].y;
+            store2(r + j * N + p, ra, rb);
+            acc.add(ra * ra);
+            acc.add(rb * rb);
+            const T a = ra + beta * pp[j].x;
+            const T b = rb + beta * pp[j].y;
             store2(pv + j * N + p, a, b);
             o0[j] = v0 * a;
             o1[j] = v1 * b;
@@ -137,17 +180,22 @@ struct ProCG {
     }
     __device__ void sparse(const RowCtx<T> &, int, int) const {}
     __device__ void emit(const RowCtx<T> &, int, int, const T *, const T *, DSum &) const {}
-    __device__ void block_done(DSum &) const {}
+    __device__ void block_done(DSum &acc) const { write_partial(red, acc.value()); }
+};
+
+struct CgAcc {
+    DSum pq, rq, qq;
 };
 
 // rows, inverse: L = chi y staged, boundary fix-up with G p, q = -chi_O L,
-// block partials of p.q
+// block partials of p.q, r.q, q.q
 template <typename T, int D>
 struct EpiCG {
-    static constexpr int kFin = D, kFout = 0, kStage = D, kNF = 0, kNB = 1 + D;
+    static constexpr int kFin = D, kFout = 0, kStage = D, kNF = 0, kNB = 1;
     static constexpr bool kSparse = true;
-    const T *pv;
-    const uint8_t *chi, *co;
+    using Acc = CgAcc;
+    const T *pv, *r;
+    const uint8_t *bits;
     const GEntry<T> *gent;
     const int *goff;
     T *q;
@@ -159,11 +207,11 @@ struct EpiCG {
     __device__ const cx<T> *spec_in(int f) const { return spec + f * fstride; }
     __device__ cx<T> *spec_out(int) const { return nullptr; }
     __device__ const T *nf_src(int) const { return nullptr; }
-    __device__ const uint8_t *nb_src(int k) const { return k == 0 ? chi : co + (k - 1) * N; }
+    __device__ const uint8_t *nb_src(int) const { return bits; }
     __device__ __forceinline__ void node2(const RowCtx<T> &c, int rl, int i1, const T *in0, const T *in1, T *o0,
                                           T *o1) const
     {
-        const T v0 = c.b(0, rl, i1) ? T(1) : T(0), v1 = c.b(0, rl, i1 + 1) ? T(1) : T(0);
+        const T v0 = (c.b(0, rl, i1) & 1) ? T(1) : T(0), v1 = (c.b(0, rl, i1 + 1) & 1) ? T(1) : T(0);
 #pragma unroll
         for (int i = 0; i < D; ++i) {
             o0[i] = v0 * in0[i];
@@ -184,7 +232,7 @@ struct EpiCG {
             for (int j = 0; j < U; ++j)
                 if (kb + j * nthreads < k1) {
 #pragma unroll
-                    for (int q = 0; q < D; ++q) pp[j][q] = pv[q * N + e[j].p];
+                    for (int qd = 0; qd < D; ++qd) pp[j][qd] = pv[qd * N + e[j].p];
                 }
 #pragma unroll
             for (int j = 0; j < U; ++j) {
@@ -193,7 +241,7 @@ struct EpiCG {
                 const int rl = (int)(p / n1 - c.row0), i1 = (int)(p % n1);
                 T Gp[D];
 #pragma unroll
-                for (int q = 0; q < D; ++q) Gp[q] = T(0);
+                for (int qd = 0; qd < D; ++qd) Gp[qd] = T(0);
                 sym_apply<T, D>(e[j].g, pp[j], Gp);
 #pragma unroll
                 for (int i = 0; i < D; ++i) c.stage(i, rl, i1) -= Gp[i];
@@ -201,22 +249,41 @@ struct EpiCG {
         }
     }
     __device__ __forceinline__ void emit(const RowCtx<T> &c, int rl, int i1, const T *s0, const T *s1,
-                                         DSum &acc) const
+                                         CgAcc &acc) const
     {
         const int64_t p = (c.row0 + rl) * n1 + i1;
-        typename vec2<T>::type pp[D];
-#pragma unroll
-        for (int i = 0; i < D; ++i) pp[i] = load2(pv + i * N + p);
+        const unsigned b0 = c.b(0, rl, i1), b1 = c.b(0, rl, i1 + 1);
+        typename vec2<T>::type pp[D], rr[D];
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-            const T a = c.b(1 + i, rl, i1) ? -s0[i] : T(0);
-            const T b = c.b(1 + i, rl, i1 + 1) ? -s1[i] : T(0);
+            pp[i] = load2(pv + i * N + p);
+            rr[i] = load2(r + i * N + p);
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const T a = ((b0 >> (1 + i)) & 1) ? -s0[i] : T(0);
+            const T b = ((b1 >> (1 + i)) & 1) ? -s1[i] : T(0);
             store2(q + i * N + p, a, b);
-            acc.add(pp[i].x * a);
-            acc.add(pp[i].y * b);
+            acc.pq.add(pp[i].x * a);
+            acc.pq.add(pp[i].y * b);
+            acc.rq.add(rr[i].x * a);
+            acc.rq.add(rr[i].y * b);
+            acc.qq.add(a * a);
+            acc.qq.add(b * b);
         }
     }
-    __device__ void block_done(DSum &acc) const { write_partial(red, acc.value()); }
+    __device__ void block_done(CgAcc &acc) const
+    {
+        const double x = block_sum_d(acc.pq.value());
+        const double y = block_sum_d(acc.rq.value());
+        const double z = block_sum_d(acc.qq.value());
+        if (threadIdx.x == 0) {
+            double *o = red + kRedPart + kPartB + 3 * blockIdx.x;
+            o[0] = x;
+            o[1] = y;
+            o[2] = z;
+        }
+    }
 };
 
 struct Solver {
@@ -285,27 +352,25 @@ struct Solver {
         cx<T> *spec = reinterpret_cast<cx<T> *>(spec_buf<T>(p));
         const int64_t fs = p->N / 2;
         const Model<T> m = model_view<T>(p);
-        ProCG<T, D> pro{r, pv, p->chi, p->red + kRedScal, p->N, p->n1, spec, fs};
+        RowGeom g;
+        LaunchCfg c;
+        row_cfg<T>(p, D, 0, 1, g, c);
+        if ((int64_t)c.grid.x > kPartB) {
+            set_error("pd_solve_static: %u row blocks exceed the reduction buffer", c.grid.x);
+            return PD_ERR_SIZE;
+        }
+        ProCG<T, D> pro{e, r, pv, q, p->mbits, p->red, p->N, p->n1, spec, fs};
         PD_TRY(launch_rows<T>(p, pro, st));
         if (D == 3) PD_TRY((col_pass<T, D>(p, 0, false, st)));
         const int ob = D == 3 ? D : 0;
         CombForce<T, D, false> cmb{m, ob};
         PD_TRY(launch_cols<T>(p, cmb, D == 3 ? 2 : 1, true, D, st));
         if (D == 3) PD_TRY((col_pass<T, D>(p, ob, true, st)));
-        EpiCG<T, D> epi{pv, p->chi, p->chi_om, m.gent, m.goff, q, p->red, p->N, p->n1, spec + ob * fs, fs};
-        RowGeom g;
-        LaunchCfg c;
-        row_cfg<T>(p, D, EpiCG<T, D>::kNF, EpiCG<T, D>::kNB, g, c);
-        if ((int64_t)c.grid.x > kMaxPart) {
-            set_error("pd_solve_static: %u row blocks exceed the reduction buffer", c.grid.x);
-            return PD_ERR_SIZE;
-        }
+        EpiCG<T, D> epi{pv, r, p->mbits, m.gent, m.goff, q, p->red, p->N, p->n1, spec + ob * fs, fs};
         PD_TRY(launch_rows<T>(p, epi, st));
-        PD_TRY(finish((int)c.grid.x, S_PQ, 1));
-        k_cg_update<T><<<kUpdBlocks, 256, 0, st>>>(e, r, pv, q, nvec, p->red);
+        k_cg_finish_fused<<<1, 1024, 0, st>>>(p->red, (int)c.grid.x, (int)c.grid.x);
         PD_LAUNCH_CHECK();
         p->launches++;
-        PD_TRY(finish(kUpdBlocks, S_RRNEW, 2));
         return PD_OK;
     }
 
@@ -349,7 +414,7 @@ struct Solver {
             p->ev_reserved = p->ev_used;  // keep the graph's event pairs
         }
         PD_CUDA_TRY(cudaGraphLaunch(p->cg_graph[gi], st));
-        p->launches += (int64_t)kChunk * (p->state_based ? 13 : (D == 3 ? 8 : 6));
+        p->launches += (int64_t)kChunk * (p->state_based ? 13 : (D == 3 ? 6 : 4));
         PD_CUDA_TRY(cudaStreamSynchronize(st));
         if (p->prof_on) PD_TRY(prof_harvest_range(p, p->cg_graph_ev[gi][0], p->cg_graph_ev[gi][1]));
         return PD_OK;
@@ -359,12 +424,12 @@ struct Solver {
     template <typename T, int D>
     pd_status cg(double tol_abs, int max_it, int *done)
     {
-        T *e = (T *)p->cg_e, *r = (T *)p->cg_r, *pv = (T *)p->cg_p;
-        k_cg_init<T><<<nb, 256, 0, st>>>(p->r64, r, pv, e, nvec, p->red);
+        T *e = (T *)p->cg_e, *r = (T *)p->cg_r, *pv = (T *)p->cg_p, *q = (T *)p->cg_q;
+        k_cg_init<T><<<nb, 256, 0, st>>>(p->r64, r, pv, e, q, nvec, p->red);
         PD_LAUNCH_CHECK();
         p->launches++;
         PD_TRY(finish(nb, S_RR, 0));
-        PD_CUDA_TRY(cudaMemsetAsync(p->red + kRedScal + S_BETA, 0, sizeof(double), st));
+        PD_CUDA_TRY(cudaMemsetAsync(p->red + kRedScal + S_ALPHA, 0, 2 * sizeof(double), st));  // alpha, beta
         int it = 0;
         double best = HUGE_VAL;
         int since_best = 0;
@@ -387,6 +452,12 @@ struct Solver {
             } else if ((since_best += kChunk) >= 8 * kChunk && 2 * since_best >= it) {
                 break;
             }
+        }
+        if (!p->state_based) {
+            // the fused iteration leaves the last e, r update pending
+            k_cg_update<T><<<kUpdBlocks, 256, 0, st>>>(e, r, pv, (const T *)p->cg_q, nvec, p->red);
+            PD_LAUNCH_CHECK();
+            p->launches++;
         }
         *done = it;
         return PD_OK;

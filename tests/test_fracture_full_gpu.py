@@ -5,9 +5,17 @@ delta = 4, critical energy from s0 = 1e-3 (reading R10 of the design notes),
 Full-size parity: the FP64 GPU path follows the FP64 oracle bit for bit in
 the integrity index through the first 250 steps (bonds start to break at
 about step 120); after the FP32 run's 4000 steps, one more step from its
-state takes the oracle's decisions on every node whose W is not within
-1e-4 Wc of the threshold; the damage counts of the final state are exact
-integers."""
+state takes the oracle's decisions on every node that is not borderline;
+the damage counts of the final state are exact integers.
+
+Borderline: the FP32 path evaluates W of Eq. 102 as T1 - 2 u.(C*(chi lam u))
++ u.(C*(chi lam)) u, three FFT convolutions whose rounding error scales with
+the size of the terms, not with W: |W32 - W| <~ c eps32 S(x) with
+S(x) = 1/2 alpha Σ_H (1/|xi|)(|u(x+xi)| + |u(x)|)^2 >= every term. With
+c = 64 (a forward and an inverse transform of ~2^19 points, eps32 log2 N
+each, and a factor 2 of slack) a node is borderline when |W - Wc| <= 64 eps32 S.
+At step 4000 |u| reaches ~0.1-0.2 grid units while W ~ Wc ~ 3e-6, so the band
+is a few per cent of Wc; it shrinks with |u|^2."""
 import math
 
 import numpy as np
@@ -78,9 +86,16 @@ def test_fracture_config3_full_size(pdm, oracle):
                                         1.0, dt, wc, 1)
     plans[False].step_verlet(u32, v32, lam32, b32, None, dt=dt, nsteps=1)
     lg = lam32.cpu().numpy()
-    clear = np.abs(W - wc) > 1e-4 * wc
+    off, ln = oracle.horizon(2, 1.0, delta)
+    umag = np.sqrt(us[0] ** 2 + us[1] ** 2)
+    S = np.zeros_like(umag)
+    for (o1, o2, _), r in zip(off, ln):
+        S += (np.roll(umag, (-int(o2), -int(o1)), axis=(0, 1)) + umag) ** 2 / r
+    S *= 0.5 * alpha
+    clear = np.abs(W - wc) > 64 * np.finfo(np.float32).eps * S
     assert np.array_equal(lg[clear], lo1[clear])
     assert np.sum(lg != lo1) <= np.sum(~clear)
+    assert np.sum(~clear & (cfg["chi"] == 1)) < 0.01 * np.sum(cfg["chi"])
 
     # (4) damage counts of the final state, exact
     nbo, _, do = oracle.damage(cfg["chi"], lg, 1.0, delta)
