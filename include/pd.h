@@ -149,6 +149,20 @@ pd_status pd_step_verlet(pd_plan *plan, void *u, void *v, uint8_t *lambda, const
                          void *stream);
 
 /*
+ * pd_plan_set_energy_mode -- how pd_step_verlet evaluates the strain energy
+ * density W that decides bond breaking (Eq. 63):
+ *   0 (default): the paper's convolution form, Eq. 102 (three FFT
+ *      convolutions of nodal products, fused into the force passes);
+ *   1: the plain horizon sum of Eq. 47 in the plan's precision.
+ * Both compute the same W. The convolutions' rounding error is global, about
+ * eps lambda_max (rms|u|^2 + 2|u(x)| rms|u|) at every node; in FP32 it reaches
+ * Wc once fragments have moved tens of grid units, and spurious breaking
+ * follows. The direct sum's error is local (about eps |u(x)| / |eta| relative
+ * to W). Mode 1 is for FP32 runs that go past full separation.
+ */
+pd_status pd_plan_set_energy_mode(pd_plan *plan, int mode);
+
+/*
  * pd_solve_static -- solve the FCBM-EC static problem (Eq. 85-89)
  *   chi_O (L(u) + b) = 0 on Omega,  u = w on Gamma,
  * by conjugate gradient (§4.3, ref. [50]) on A e = chi_O (b + L(w)),

@@ -219,6 +219,7 @@ struct pd_plan {
     int tune_rows = 0;     // rows per row-pass block
     int tune_w[2] = {0, 0};  // column-tile width of the x2 / last-axis passes
     int tune_sched = 0;    // FFT stage schedule
+    int energy_direct = 0; // pd_step_verlet: W by a direct horizon sum (pd_plan_set_energy_mode)
     int64_t prof_n[kKinds] = {};
 };
 

@@ -9,8 +9,16 @@
 //   kick       : v <- chi_O (v + dt/(2 rho) (L^{n+1} + b))
 // The call starts with one force evaluation of the given state, so a run of
 // n steps split over several calls gives the same result as one call.
+//
+// Energy mode 1 (pd_plan_set_energy_mode) evaluates W of Eq. 102 by the plain
+// horizon sum of Eq. 47 instead of the three convolutions T1 - 2 u.(C*(v u))
+// + u.(C*v) u: the convolutions' rounding error is global, about
+// eps lambda_max (rms|u|^2 + 2 |u(x)| rms|u|) at every node, which in FP32
+// exceeds Wc once fragments have moved far (|u| ~ 10-100 grid units), while
+// the direct sum errs by about eps |u(x)| / |eta| relative to W, locally.
 #include <algorithm>
 
+#include "pd_ops.cuh"
 #include "pd_plan.cuh"
 
 namespace pd {
@@ -89,6 +97,88 @@ __global__ void k_gfield_lam(int n1, int n2, int n3, HorizonDev hz, int ncomp, c
 
 __global__ void k_clear_changed(VerletCounters *cnt) { cnt->changed = 0; }
 
+// W(x) = 1/2 chi lam Σ_H chi' lam' eta.C(xi).eta dV, eta = u(x+xi) - u(x)
+// (Eq. 47 with the integrity weights of Eq. 44; periodic neighbour offsets).
+// The bond tensor is rank one, C(xi) dV = c(xi) xi xi^T / |xi|^2 with
+// c = tr C dV, so each bond adds c (xi.eta)^2 / |xi|^2: the projection is
+// formed first, and a rigidly rotating neighbourhood (large eta nearly
+// normal to xi) does not cancel large quadratic-form terms.
+template <typename T, int D>
+__global__ void k_energy_direct(int n1, int n2, int n3, HorizonDev hz, double dx1, double dx2, double dx3,
+                                const uint8_t *chi, const uint8_t *lam, const T *u, T *W, int64_t N)
+{
+    constexpr int NC = Sym<D>::n;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    T *ws = reinterpret_cast<T *>(sm_raw);            // cnt: c / |xi|^2
+    T *xs = ws + hz.cnt;                               // D x cnt: xi
+    int *os = reinterpret_cast<int *>(xs + D * hz.cnt);  // 3 x cnt
+    for (int c = threadIdx.x; c < hz.cnt; c += blockDim.x) {
+        const double x[3] = {hz.off[3 * c] * dx1, hz.off[3 * c + 1] * dx2, hz.off[3 * c + 2] * dx3};
+        double tr = 0.0, r2 = 0.0;
+        for (int k = 0; k < NC; ++k)
+            if (Sym<D>::i(k) == Sym<D>::j(k)) tr += hz.c[k * hz.cnt + c];
+        for (int j = 0; j < D; ++j) r2 += x[j] * x[j];
+        ws[c] = (T)(tr / r2);
+        for (int j = 0; j < D; ++j) xs[j * hz.cnt + c] = (T)x[j];
+        for (int j = 0; j < 3; ++j) os[3 * c + j] = hz.off[3 * c + j];
+    }
+    __syncthreads();
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+        T acc = T(0);
+        if (chi[p] && lam[p]) {
+            const int i1 = (int)(p % n1), i2 = (int)((p / n1) % n2), i3 = (int)(p / ((int64_t)n1 * n2));
+            T up[D];
+#pragma unroll
+            for (int j = 0; j < D; ++j) up[j] = u[j * N + p];
+            for (int c = 0; c < hz.cnt; ++c) {
+                const int a = (i1 + os[3 * c]) & (n1 - 1);
+                const int b = (i2 + os[3 * c + 1]) & (n2 - 1);
+                const int e = (i3 + os[3 * c + 2]) & (n3 - 1);
+                const int64_t q = ((int64_t)e * n2 + b) * n1 + a;
+                if (!(chi[q] && lam[q])) continue;
+                T s = T(0);
+#pragma unroll
+                for (int j = 0; j < D; ++j) s += xs[j * hz.cnt + c] * (u[j * N + q] - up[j]);
+                acc += ws[c] * s * s;
+            }
+        }
+        W[p] = T(0.5) * acc;
+    }
+}
+
+template <typename T>
+pd_status energy_direct(pd_plan *p, const T *u, const uint8_t *lam, T *W, cudaStream_t st)
+{
+    const int cnt = p->hdev.cnt;
+    const size_t smem = (size_t)(1 + p->dim) * cnt * sizeof(T) + (size_t)3 * cnt * sizeof(int);
+    const double *dx = p->prob.dx;
+    const unsigned ng = (unsigned)std::min<int64_t>(8 * p->nsm, (p->N + 255) / 256);
+    if (p->dim == 3) {
+        PD_TRY(set_smem_attr((const void *)k_energy_direct<T, 3>, smem));
+        k_energy_direct<T, 3><<<ng, 256, smem, st>>>(p->n1, p->n2, p->n3, p->hdev, dx[0], dx[1], dx[2], p->chi, lam,
+                                                     u, W, p->N);
+    } else {
+        PD_TRY(set_smem_attr((const void *)k_energy_direct<T, 2>, smem));
+        k_energy_direct<T, 2><<<ng, 256, smem, st>>>(p->n1, p->n2, p->n3, p->hdev, dx[0], dx[1], dx[2], p->chi, lam,
+                                                     u, W, p->N);
+    }
+    PD_LAUNCH_CHECK();
+    p->launches++;
+    return PD_OK;
+}
+
+// one force evaluation of the step, with W in the plan's energy mode
+template <typename T>
+pd_status step_force(pd_plan *p, const T *u, const uint8_t *lam, const T *G, T *L, T *W, int breaking,
+                     cudaStream_t st)
+{
+    if (breaking && p->energy_direct) {
+        PD_TRY(force_any<T>(p, u, nullptr, lam, G, L, nullptr, st));
+        return energy_direct<T>(p, u, lam, W, st);
+    }
+    return force_any<T>(p, u, nullptr, lam, G, L, breaking ? W : nullptr, st);
+}
+
 template <typename T>
 pd_status verlet_impl(pd_plan *p, T *u, T *v, uint8_t *lam, const T *b, const T *w, double dt, int nsteps,
                       int64_t *n_broken_out, cudaStream_t st)
@@ -107,7 +197,7 @@ pd_status verlet_impl(pd_plan *p, T *u, T *v, uint8_t *lam, const T *b, const T 
         PD_LAUNCH_CHECK();
         p->launches++;
     }
-    PD_TRY(force_any<T>(p, u, nullptr, lam, G, L, breaking ? W : nullptr, st));
+    PD_TRY(step_force<T>(p, u, lam, G, L, W, breaking, st));
     const T hdt = (T)(0.5 * dt / p->prob.rho);
     const unsigned ng = (unsigned)std::min<int64_t>(4 * p->nsm, (N + 255) / 256);
     const unsigned ngv = (unsigned)std::min<int64_t>(4 * p->nsm, (d * N + 255) / 256);
@@ -122,7 +212,7 @@ pd_status verlet_impl(pd_plan *p, T *u, T *v, uint8_t *lam, const T *b, const T 
             PD_LAUNCH_CHECK();
             p->launches += 2;
         }
-        PD_TRY(force_any<T>(p, u, nullptr, lam, G, L, breaking ? W : nullptr, st));
+        PD_TRY(step_force<T>(p, u, lam, G, L, W, breaking, st));
         k_kick<T><<<ngv, 256, 0, st>>>(v, L, b, p->chi_om, d * N, hdt);
         PD_LAUNCH_CHECK();
         p->launches++;
@@ -162,4 +252,14 @@ extern "C" pd_status pd_step_verlet(pd_plan *p, void *u, void *v, uint8_t *lambd
                                    nsteps, n_broken_out, st);
     return verlet_impl<float>(p, (float *)u, (float *)v, lambda, (const float *)b, (const float *)w, dt, nsteps,
                               n_broken_out, st);
+}
+
+extern "C" pd_status pd_plan_set_energy_mode(pd_plan *p, int mode)
+{
+    if (!p || (mode != 0 && mode != 1)) {
+        set_error("pd_plan_set_energy_mode: null plan or mode not 0/1");
+        return PD_ERR_ARG;
+    }
+    p->energy_direct = mode;
+    return PD_OK;
 }

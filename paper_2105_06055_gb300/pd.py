@@ -29,7 +29,8 @@ EXPORTS = ["pd_plan_create", "pd_plan_destroy", "pd_kernel_spectrum", "pd_force"
            "pd_stable_dt", "pd_plan_launch_count", "pd_status_string", "pd_last_error_detail",
            "pd_plan_profile", "pd_plan_profile_read", "pd_force2d_noalloc", "pd_plan_boundary_nodes",
            "pd_solve_dr", "pd_plan_create_batched", "pd_batch_size", "pd_batch_plan", "pd_solve_dr_batched",
-           "pd_batch_destroy", "pd_plan_autotune", "pd_batch_autotune", "pd_plan_tuning"]
+           "pd_batch_destroy", "pd_plan_autotune", "pd_batch_autotune", "pd_plan_tuning",
+           "pd_plan_set_energy_mode"]
 
 PASS_KINDS = {0: "rows_fwd", 1: "cols_x2", 2: "last_axis", 3: "rows_inv"}
 
@@ -109,6 +110,8 @@ def load():
     lib.pd_batch_autotune.restype = I
     lib.pd_plan_tuning.argtypes = [P, ctypes.POINTER(I)]
     lib.pd_plan_tuning.restype = I
+    lib.pd_plan_set_energy_mode.argtypes = [P, I]
+    lib.pd_plan_set_energy_mode.restype = I
     lib.pd_status_string.argtypes = [I]
     lib.pd_status_string.restype = ctypes.c_char_p
     lib.pd_last_error_detail.argtypes = []
@@ -295,6 +298,10 @@ class Plan:
     def autotune(self, stream=None):
         _check(load().pd_plan_autotune(self._h, _stream(stream)), "pd_plan_autotune")
         return self.tuning
+
+    def set_energy_mode(self, direct: bool):
+        """W for bond breaking: False = convolution form (Eq. 102), True = horizon sum (Eq. 47)."""
+        _check(load().pd_plan_set_energy_mode(self._h, 1 if direct else 0), "pd_plan_set_energy_mode")
 
     @property
     def tuning(self):

@@ -1,21 +1,29 @@
 """The dynamic brittle-fracture workload at full size: 1024 x 512 nodes,
-delta = 4, critical energy from s0 = 1e-3 (reading R10 of the design notes),
-4000 FP32 velocity-Verlet steps with bond breaking (Eq. 63, 83-84, 101-102).
+delta = 4, critical energy from the critical stretch s0 = 1e-3, constant
+traction layers, 4000 FP32 velocity-Verlet steps with bond breaking
+(Eq. 63, 83-84, 101-102).
 
-Full-size parity: the FP64 GPU path follows the FP64 oracle bit for bit in
-the integrity index through the first 250 steps (bonds start to break at
-about step 120); after the FP32 run's 4000 steps, one more step from its
-state takes the oracle's decisions on every node that is not borderline;
-the damage counts of the final state are exact integers.
+Full-size parity:
+  - FP64: the GPU path follows the FP64 oracle bit for bit in the integrity
+    index, in both energy modes (the convolution form of Eq. 102 and the
+    horizon sum of Eq. 47), through the first 250 steps (bonds start to break
+    at about step 120);
+  - FP32, energy mode 1: after 4000 steps, one more step from the run's
+    state takes the oracle's decisions on every node that is not borderline;
+    the final damage counts are exact integers.
 
-Borderline: the FP32 path evaluates W of Eq. 102 as T1 - 2 u.(C*(chi lam u))
-+ u.(C*(chi lam)) u, three FFT convolutions whose rounding error scales with
-the size of the terms, not with W: |W32 - W| <~ c eps32 S(x) with
-S(x) = 1/2 alpha Σ_H (1/|xi|)(|u(x+xi)| + |u(x)|)^2 >= every term. With
-c = 64 (a forward and an inverse transform of ~2^19 points, eps32 log2 N
-each, and a factor 2 of slack) a node is borderline when |W - Wc| <= 64 eps32 S.
-At step 4000 |u| reaches ~0.1-0.2 grid units while W ~ Wc ~ 3e-6, so the band
-is a few per cent of Wc; it shrinks with |u|^2."""
+Borderline (FP32, horizon-sum energy): eta = u' - u is one correctly rounded
+FP32 subtraction of the stored values and each bond adds
+(alpha/|xi|) (xi.eta)^2 / |xi|^2 with the projection xi.eta formed first, so a
+bond term errs by at most about 4 eps32 (alpha/|xi|) |xi^.eta| |eta| and the
+summation by |H| eps32 W: |W32 - W| <= 32 eps32 (S + 2 W) with
+S(x) = 1/2 chi lam Σ_H chi' lam' (alpha/|xi|) |xi^.eta| |eta| (a factor of
+about 4 to spare). A node is borderline when |W - Wc| is within that bound.
+
+(The convolution form in FP32 errs globally, by about
+eps32 lambda_max (rms|u|^2 + 2 |u(x)| rms|u|); in this run that exceeds Wc
+after about 1000 steps, when the broken halves fly apart, which is why the
+long FP32 run uses the horizon-sum energy.)"""
 import math
 
 import numpy as np
@@ -52,20 +60,23 @@ def test_fracture_config3_full_size(pdm, oracle):
                             _t(cfg["chi"], torch.uint8)) for fp64 in (True, False)}
     dt = 0.8 * plans[True].stable_dt
 
-    # (1) FP64 GPU path against the oracle through crack initiation
+    # (1) FP64 GPU path against the oracle through crack initiation, both energy modes
     n0 = 250
     uo, vo, lo, flo = oracle.verlet_damage(np.zeros((2,) + shape), np.zeros((2,) + shape), cfg["lam"], cfg["chi"],
                                            cfg["chi_omega"], b, cfg["w"], 1.0, delta, alpha, 1.0, dt, wc, n0)
     assert flo > 0
-    u = torch.zeros((2,) + shape, dtype=torch.float64, device=DEV)
-    v = torch.zeros_like(u)
-    lam = _t(cfg["lam"], torch.uint8)
-    nb = plans[True].step_verlet(u, v, lam, _t(b), None, dt=dt, nsteps=n0, count_broken=True)
-    assert nb == flo
-    assert np.array_equal(lam.cpu().numpy(), lo)
-    assert float(np.linalg.norm(u.cpu().numpy() - uo) / np.linalg.norm(uo)) < 1e-10
+    for direct in (False, True):
+        plans[True].set_energy_mode(direct)
+        u = torch.zeros((2,) + shape, dtype=torch.float64, device=DEV)
+        v = torch.zeros_like(u)
+        lam = _t(cfg["lam"], torch.uint8)
+        nb = plans[True].step_verlet(u, v, lam, _t(b), None, dt=dt, nsteps=n0, count_broken=True)
+        assert nb == flo
+        assert np.array_equal(lam.cpu().numpy(), lo)
+        assert float(np.linalg.norm(u.cpu().numpy() - uo) / np.linalg.norm(uo)) < 1e-10
 
-    # (2) the FP32 run of 4000 steps, broken counts every 100 steps
+    # (2) the FP32 run of 4000 steps (horizon-sum energy), broken counts every 100 steps
+    plans[False].set_energy_mode(True)
     u32 = torch.zeros((2,) + shape, dtype=torch.float32, device=DEV)
     v32 = torch.zeros_like(u32)
     lam32 = _t(cfg["lam"], torch.uint8)
@@ -76,7 +87,7 @@ def test_fracture_config3_full_size(pdm, oracle):
         total += plans[False].step_verlet(u32, v32, lam32, b32, None, dt=dt, nsteps=100, count_broken=True)
         hist.append(total)
         assert bool(torch.all(lam32 <= lam_prev))  # irreversible
-    assert hist[5] > 0 and hist[-1] > 4 * hist[5]  # the crack initiates and grows
+    assert hist[1] > 0 and hist[-1] > 4 * hist[1]  # the crack initiates and grows
     assert torch.isfinite(u32).all()
 
     # (3) one more step from the FP32 state: decisions against the oracle
@@ -87,15 +98,19 @@ def test_fracture_config3_full_size(pdm, oracle):
     plans[False].step_verlet(u32, v32, lam32, b32, None, dt=dt, nsteps=1)
     lg = lam32.cpu().numpy()
     off, ln = oracle.horizon(2, 1.0, delta)
-    umag = np.sqrt(us[0] ** 2 + us[1] ** 2)
-    S = np.zeros_like(umag)
+    live = ((cfg["chi"] == 1) & (ls == 1)).astype(np.float64)
+    S = np.zeros(shape)
     for (o1, o2, _), r in zip(off, ln):
-        S += (np.roll(umag, (-int(o2), -int(o1)), axis=(0, 1)) + umag) ** 2 / r
-    S *= 0.5 * alpha
-    clear = np.abs(W - wc) > 64 * np.finfo(np.float32).eps * S
+        sh = (-int(o2), -int(o1))
+        e0 = np.roll(us[0], sh, axis=(0, 1)) - us[0]
+        e1 = np.roll(us[1], sh, axis=(0, 1)) - us[1]
+        proj = np.abs(o1 * e0 + o2 * e1) / r
+        S += np.roll(live, sh, axis=(0, 1)) * proj * np.sqrt(e0 * e0 + e1 * e1) / r
+    S *= 0.5 * alpha * live
+    clear = np.abs(W - wc) > 32 * np.finfo(np.float32).eps * (S + 2 * np.abs(W))
     assert np.array_equal(lg[clear], lo1[clear])
     assert np.sum(lg != lo1) <= np.sum(~clear)
-    assert np.sum(~clear & (cfg["chi"] == 1)) < 0.01 * np.sum(cfg["chi"])
+    assert np.sum(~clear) < 1e-3 * np.sum(cfg["chi"])
 
     # (4) damage counts of the final state, exact
     nbo, _, do = oracle.damage(cfg["chi"], lg, 1.0, delta)
