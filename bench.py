@@ -8,7 +8,9 @@ w = 0) on the three node layers at the x1-low face, body-force layer
 b1 = sigma/delta (sigma = 1e-3) on the three layers at the x1-high face.
 One step = one complete static solve from u = 0 to a relative FP64 residual of
 1e-8: FP32 FFT-convolution CG with FP64 inner products inside FP64 iterative
-refinement (pd_solve_static).
+refinement (pd_solve_static). The plan's pass configuration is picked by the
+library's autotuner (pd_plan_autotune) before the warm-up, unless
+--no-autotune.
 
 Metric: force evaluations x nodes per second (each CG iteration and each FP64
 residual is one evaluation of the PD operator on all 128^3 nodes), plus the
@@ -161,7 +163,7 @@ def run_native(args, rank, world):
     chi = torch.tensor(cfg["chi"], device=dev)
     chi_om = torch.tensor(cfg["chi_omega"], device=dev)
     plan = pd.Plan(prob, chi, chi_om)
-    tuning = plan.autotune() if args.autotune else None
+    tuning = None if args.no_autotune else plan.autotune()
     b = torch.tensor(cfg["b"], dtype=torch.float64, device=dev)
     u = torch.zeros((3,) + shape, dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
@@ -400,7 +402,7 @@ def main():
     ap.add_argument("--n", type=int, default=N_GRID)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="static", choices=["static", "batched"])
-    ap.add_argument("--autotune", action="store_true", help="run the pass autotuner on the plan first")
+    ap.add_argument("--no-autotune", action="store_true", help="skip the pass autotuner (built-in tile heuristic)")
     ap.add_argument("--specimens", type=int, default=64)
     ap.add_argument("--profile-solve", type=int, default=0, metavar="K",
                     help="no timing: build the workload and run one solve capped at K CG iterations "
@@ -417,6 +419,8 @@ def main():
         dev = torch.device("cuda")
         plan = pd.Plan(pd.Problem(shape=cfg["shape"], delta=DELTA, model=pd.PD_LIN_STATE, nu=0.25, fp64=False),
                        torch.tensor(cfg["chi"], device=dev), torch.tensor(cfg["chi_omega"], device=dev))
+        if not args.no_autotune:
+            plan.autotune()
         u = torch.zeros((3,) + cfg["shape"], dtype=torch.float64, device=dev)
         it, rel, _ = plan.solve_static(u, torch.tensor(cfg["b"], dtype=torch.float64, device=dev), None,
                                        rtol=RTOL, max_iter=args.profile_solve, raise_on_fail=False)
