@@ -451,15 +451,13 @@ struct DrSpec {
         PD_TRY(launch_cols<T>(p, cmb, D == 3 ? 2 : 1, true, D, st));
         if (D == 3) PD_TRY((col_pass<T, D>(p, ob, true, st)));
         EpiDR<T, D> epi{e, v, rhs, F, p->chi, p->chi_om, m.gent, m.goff, p->red, p->N, p->n1, spec + ob * fs, fs};
-        RowGeom g;
-        LaunchCfg c;
-        row_cfg<T>(p, D, EpiDR<T, D>::kNF, EpiDR<T, D>::kNB, g, c);
-        if ((int64_t)c.grid.x > kDrPart) {
-            set_error("dynamic relaxation: %u row blocks exceed the reduction buffer", c.grid.x);
+        unsigned gepi = 0;
+        PD_TRY(launch_rows<T>(p, epi, st, &gepi));
+        if (gepi > (unsigned)kDrPart) {
+            set_error("dynamic relaxation: %u row blocks exceed the reduction buffer", gepi);
             return PD_ERR_SIZE;
         }
-        PD_TRY(launch_rows<T>(p, epi, st));
-        k_dr_finish<<<1, 1024, 0, st>>>(p->red, (int)c.grid.x);
+        k_dr_finish<<<1, 1024, 0, st>>>(p->red, (int)gepi);
         PD_LAUNCH_CHECK();
         p->launches++;
         return PD_OK;

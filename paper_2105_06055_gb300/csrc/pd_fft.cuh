@@ -197,13 +197,22 @@ __device__ __forceinline__ double block_sum_d(double v)
 
 struct RowGeom {
     int lgh;        // log2(n1/2): complex length of a packed row
-    int rows;       // rows per block
+    int rows;       // rows per tile
     int pitch;      // shared-memory pitch of a packed row (complex elements, even)
     int64_t nrows;  // n2 * n3 (multiple of rows)
     int lgl;        // log2 of the global twiddle table length
     int sched;      // FFT stage schedule (fft_smem)
     int *err;       // device status word (bounded-wait time-outs)
 };
+
+// Bytes of one pipeline stage of a row tile: FB packed-row slots, NF node
+// fields of T and NB byte fields, rounded up to 128 bytes.
+template <typename T>
+__host__ __device__ constexpr size_t row_stage_bytes(int FB, int NF, int NB, int rows, int pitch, int n1)
+{
+    return ((size_t)FB * rows * pitch * sizeof(cx<T>) + (size_t)NF * rows * n1 * sizeof(T) +
+            (((size_t)NB * rows * n1 + 15) & ~(size_t)15) + 127) & ~(size_t)127;
+}
 
 // Shared-memory views handed to the row ops.
 template <typename T>
@@ -258,9 +267,13 @@ struct op_node_acc<Op, std::void_t<decltype(Op::kNodeAcc)>> : std::bool_constant
 //   void sparse(ctx, tid, nthreads); void emit(ctx, rl, i1, s0, s1, acc)
 //   void block_done(acc): called by every thread at the end (block reductions);
 //        acc is an Op::Acc if the op declares that type, else a DSum
-// Data movement: one thread issues bulk async copies (cp.async.bulk) of the
-// tile's spectrum rows and node fields, completing on an mbarrier; twiddles
-// are copied to shared memory; outputs leave through coalesced stores.
+// Data movement: the kernel is persistent; each block walks the tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ... One thread issues the bulk async
+// copies (cp.async.bulk) of a tile's spectrum rows and node fields into one of
+// two shared-memory stages, completing on that stage's mbarrier: the copies of
+// the next tile are in flight while the current one is transformed. Twiddles
+// are copied to shared memory once; outputs leave through coalesced stores.
+// Block accumulators (acc) run over all tiles of the block.
 template <typename T, class Op>
 __global__ void __launch_bounds__(256) k_rows(RowGeom g, Op op, const cx<T> *__restrict__ tw)
 {
@@ -269,130 +282,167 @@ __global__ void __launch_bounds__(256) k_rows(RowGeom g, Op op, const cx<T> *__r
     constexpr int KO = FO > ST ? FO : ST;
     constexpr int FB = FI > KO ? FI : KO;
     static_assert(!(FO > 0 && ST > 0), "an op either stages outputs or transforms forward");
+    constexpr bool kLoad = FI > 0 || NF > 0 || NB > 0;
     const int H = 1 << g.lgh, n1 = 2 * H, nt = H >> kLgV, lg1 = g.lgh + 1;
     const int rows = g.rows, pitch = g.pitch;
-    const int64_t row0 = (int64_t)blockIdx.x * rows;
+    const int64_t ntiles = g.nrows / rows;
+    const size_t sbytes = row_stage_bytes<T>(FB, NF, NB, rows, pitch, n1);
     cx<T> *tws = reinterpret_cast<cx<T> *>(smem_raw);
-    cx<T> *spec = tws + n1;
-    T *nf = reinterpret_cast<T *>(spec + FB * rows * pitch);
-    uint8_t *nb = reinterpret_cast<uint8_t *>(nf + NF * rows * n1);
-    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(nb + ((NB * rows * n1 + 15) & ~15));
-    constexpr bool kLoad = FI > 0 || NF > 0 || NB > 0;
+    unsigned char *stage0 = smem_raw + (((size_t)n1 * sizeof(cx<T>) + 127) & ~(size_t)127);
+    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(stage0 + 2 * sbytes);
+    auto stage_spec = [&](int s) { return reinterpret_cast<cx<T> *>(stage0 + s * sbytes); };
+    auto stage_nf = [&](int s) { return reinterpret_cast<T *>(stage_spec(s) + FB * rows * pitch); };
+    auto stage_nb = [&](int s) { return reinterpret_cast<uint8_t *>(stage_nf(s) + NF * rows * n1); };
 
-    if (kLoad && threadIdx.x == 0) mbar_init(mbar, 1);
-    for (int i = threadIdx.x; i < n1; i += blockDim.x) tws[i] = tw[i << (g.lgl - lg1)];
-    __syncthreads();
-    if (kLoad && threadIdx.x == 0) {
+    // one thread: bulk copies of tile `tile` into stage s
+    auto issue = [&](int64_t tile, int s) {
+        const int64_t r0 = tile * rows;
+        cx<T> *spec = stage_spec(s);
+        T *nf = stage_nf(s);
+        uint8_t *nb = stage_nb(s);
         const unsigned bytes = (unsigned)(FI * rows * H * sizeof(cx<T>) + NF * rows * n1 * sizeof(T) + NB * rows * n1);
-        mbar_expect_tx(mbar, bytes);
+        mbar_expect_tx(&mbar[s], bytes);
 #pragma unroll
         for (int f = 0; f < FI; ++f)
             for (int r = 0; r < rows; ++r)
-                bulk_load(spec + (f * rows + r) * pitch, op.spec_in(f) + (row0 + r) * H, H * sizeof(cx<T>), mbar);
+                bulk_load(spec + (f * rows + r) * pitch, op.spec_in(f) + (r0 + r) * H, H * sizeof(cx<T>), &mbar[s]);
 #pragma unroll
         for (int k = 0; k < NF; ++k)
-            bulk_load(nf + k * rows * n1, op.nf_src(k) + row0 * n1, rows * n1 * sizeof(T), mbar);
+            bulk_load(nf + k * rows * n1, op.nf_src(k) + r0 * n1, rows * n1 * sizeof(T), &mbar[s]);
 #pragma unroll
-        for (int k = 0; k < NB; ++k) bulk_load(nb + k * rows * n1, op.nb_src(k) + row0 * n1, rows * n1, mbar);
-    }
-    if (kLoad && !mbar_wait(mbar, 0, g.err)) return;
-    const RowCtx<T> ctx{row0, rows, n1, pitch, spec, nf, nb};
-    const int jt = threadIdx.x % nt, rf = threadIdx.x / nt;  // FFT mapping: nt threads per row
+        for (int k = 0; k < NB; ++k) bulk_load(nb + k * rows * n1, op.nb_src(k) + r0 * n1, rows * n1, &mbar[s]);
+    };
 
-    if constexpr (FI > 0) {
-        // Unpack the half spectrum into Z(k) = E(k) + i O(k) (E, O: DFTs of the
-        // even / odd samples, times 2) and store conj(Z) for the inverse.
-#pragma unroll
-        for (int f = 0; f < FI; ++f) {
-            cx<T> *z = spec + (f * rows + rf) * pitch;
-            for (int k = jt; k <= H / 2; k += nt) {
-                if (k == 0) {
-                    const cx<T> p = z[0];  // (X(0), X(n1/2))
-                    z[0] = conjg(mk(p.x + p.y, p.x - p.y));
-                } else {
-                    const int kk = H - k;
-                    const cx<T> a = z[k], b = z[kk];
-                    const cx<T> w = tws[k];  // W^k, W = e^{-2 pi i / n1}
-                    // Z(k)  = (a + conj b) + i conj(W^k) (a - conj b)
-                    const cx<T> zk = (a + conjg(b)) + mul_i(cmul(conjg(w), a - conjg(b)));
-                    if (kk != k) {
-                        // Z(H-k) = (b + conj a) - i W^k (b - conj a)
-                        const cx<T> zkk = (b + conjg(a)) - mul_i(cmul(w, b - conjg(a)));
-                        z[kk] = conjg(zkk);
-                    }
-                    z[k] = conjg(zk);
-                }
+    if (kLoad && threadIdx.x == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+    }
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) tws[i] = tw[i << (g.lgl - lg1)];
+    __syncthreads();
+    int64_t t = blockIdx.x;
+    if (kLoad && threadIdx.x == 0 && t < ntiles) issue(t, 0);
+    unsigned phase = 0;  // bit s: parity of the next completion of stage s
+    const int jt = threadIdx.x % nt, rf = threadIdx.x / nt;  // FFT mapping: nt threads per row
+    typename op_acc<Op>::type acc;
+
+    for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
+        const int s = it & 1;
+        const int64_t tn = t + gridDim.x;
+        const bool pre = kLoad && tn < ntiles;
+        if (pre && threadIdx.x == 0) issue(tn, s ^ 1);
+        if constexpr (kLoad) {
+            const bool ok = mbar_wait(&mbar[s], (phase >> s) & 1u, g.err);
+            phase ^= 1u << s;
+            if (__syncthreads_or(!ok)) {
+                // give up: let the prefetch in flight land before the block exits
+                if (threadIdx.x == 0 && pre) mbar_wait(&mbar[s ^ 1], (phase >> (s ^ 1)) & 1u, g.err);
+                __syncthreads();
+                return;
             }
         }
-        __syncthreads();
+        const int64_t row0 = t * rows;
+        cx<T> *spec = stage_spec(s);
+        const RowCtx<T> ctx{row0, rows, n1, pitch, spec, stage_nf(s), stage_nb(s)};
+
+        if constexpr (FI > 0) {
+            // Unpack the half spectrum into Z(k) = E(k) + i O(k) (E, O: DFTs of the
+            // even / odd samples, times 2) and store conj(Z) for the inverse.
+#pragma unroll
+            for (int f = 0; f < FI; ++f) {
+                cx<T> *z = spec + (f * rows + rf) * pitch;
+                for (int k = jt; k <= H / 2; k += nt) {
+                    if (k == 0) {
+                        const cx<T> p = z[0];  // (X(0), X(n1/2))
+                        z[0] = conjg(mk(p.x + p.y, p.x - p.y));
+                    } else {
+                        const int kk = H - k;
+                        const cx<T> a = z[k], b = z[kk];
+                        const cx<T> w = tws[k];  // W^k, W = e^{-2 pi i / n1}
+                        // Z(k)  = (a + conj b) + i conj(W^k) (a - conj b)
+                        const cx<T> zk = (a + conjg(b)) + mul_i(cmul(conjg(w), a - conjg(b)));
+                        if (kk != k) {
+                            // Z(H-k) = (b + conj a) - i W^k (b - conj a)
+                            const cx<T> zkk = (b + conjg(a)) - mul_i(cmul(w, b - conjg(a)));
+                            z[kk] = conjg(zkk);
+                        }
+                        z[k] = conjg(zk);
+                    }
+                }
+            }
+            __syncthreads();
 #pragma unroll 1
-        for (int f = 0; f < FI; ++f) fft_smem<T>(spec + (f * rows + rf) * pitch, 1, g.lgh, jt, tws, lg1, false, false, g.sched);
-    }
-
-    typename op_acc<Op>::type acc;
-    // per-node work, lanes over consecutive packed slots (2 nodes each)
-    for (int idx = threadIdx.x; idx < rows * H; idx += blockDim.x) {
-        const int rl = idx >> g.lgh, n = idx & (H - 1);
-        T in0[FI > 0 ? FI : 1], in1[FI > 0 ? FI : 1];
-        T o0[KO > 0 ? KO : 1], o1[KO > 0 ? KO : 1];
-#pragma unroll
-        for (int f = 0; f < FI; ++f) {
-            const cx<T> w = spec[(f * rows + rl) * pitch + n];  // x[2n] = Re w, x[2n+1] = -Im w
-            in0[f] = w.x;
-            in1[f] = -w.y;
+            for (int f = 0; f < FI; ++f)
+                fft_smem<T>(spec + (f * rows + rf) * pitch, 1, g.lgh, jt, tws, lg1, false, false, g.sched);
         }
-        if constexpr (op_node_acc<Op>::value)
-            op.node2(ctx, rl, 2 * n, in0, in1, o0, o1, acc);
-        else
-            op.node2(ctx, rl, 2 * n, in0, in1, o0, o1);
-#pragma unroll
-        for (int f = 0; f < KO; ++f) spec[(f * rows + rl) * pitch + n] = mk(o0[f], o1[f]);
-    }
-    __syncthreads();
 
-    if constexpr (Op::kSparse) {
-        op.sparse(ctx, threadIdx.x, blockDim.x);
-        __syncthreads();
-    }
-    if constexpr (ST > 0) {
+        // per-node work, lanes over consecutive packed slots (2 nodes each)
         for (int idx = threadIdx.x; idx < rows * H; idx += blockDim.x) {
             const int rl = idx >> g.lgh, n = idx & (H - 1);
-            T s0[ST], s1[ST];
+            T in0[FI > 0 ? FI : 1], in1[FI > 0 ? FI : 1];
+            T o0[KO > 0 ? KO : 1], o1[KO > 0 ? KO : 1];
 #pragma unroll
-            for (int f = 0; f < ST; ++f) {
-                const cx<T> v = spec[(f * rows + rl) * pitch + n];
-                s0[f] = v.x;
-                s1[f] = v.y;
+            for (int f = 0; f < FI; ++f) {
+                const cx<T> w = spec[(f * rows + rl) * pitch + n];  // x[2n] = Re w, x[2n+1] = -Im w
+                in0[f] = w.x;
+                in1[f] = -w.y;
             }
-            op.emit(ctx, rl, 2 * n, s0, s1, acc);
-        }
-    }
-    op.block_done(acc);
-
-    if constexpr (FO > 0) {
-#pragma unroll 1
-        for (int f = 0; f < FO; ++f) fft_smem<T>(spec + (f * rows + rf) * pitch, 1, g.lgh, jt, tws, lg1, false, false, g.sched);
-        const T half = T(0.5);
+            if constexpr (op_node_acc<Op>::value)
+                op.node2(ctx, rl, 2 * n, in0, in1, o0, o1, acc);
+            else
+                op.node2(ctx, rl, 2 * n, in0, in1, o0, o1);
 #pragma unroll
-        for (int f = 0; f < FO; ++f) {
-            const cx<T> *z = spec + (f * rows + rf) * pitch;
-            cx<T> *dst = op.spec_out(f) + (row0 + rf) * H;
-            for (int k = jt; k <= H / 2; k += nt) {
-                if (k == 0) {
-                    const cx<T> z0 = z[0];
-                    dst[0] = mk(z0.x + z0.y, z0.x - z0.y);
-                } else {
-                    const int kk = H - k;
-                    const cx<T> a = z[k], b = z[kk];
-                    const cx<T> w = tws[k];
-                    // X(k) = 1/2 [(a + conj b) - i W^k (a - conj b)]
-                    dst[k] = scale((a + conjg(b)) - mul_i(cmul(w, a - conjg(b))), half);
-                    // X(H-k) = 1/2 [(b + conj a) + i conj(W^k) (b - conj a)]
-                    if (kk != k) dst[kk] = scale((b + conjg(a)) + mul_i(cmul(conjg(w), b - conjg(a))), half);
+            for (int f = 0; f < KO; ++f) spec[(f * rows + rl) * pitch + n] = mk(o0[f], o1[f]);
+        }
+        __syncthreads();
+
+        if constexpr (Op::kSparse) {
+            op.sparse(ctx, threadIdx.x, blockDim.x);
+            __syncthreads();
+        }
+        if constexpr (ST > 0) {
+            for (int idx = threadIdx.x; idx < rows * H; idx += blockDim.x) {
+                const int rl = idx >> g.lgh, n = idx & (H - 1);
+                T s0[ST], s1[ST];
+#pragma unroll
+                for (int f = 0; f < ST; ++f) {
+                    const cx<T> v = spec[(f * rows + rl) * pitch + n];
+                    s0[f] = v.x;
+                    s1[f] = v.y;
+                }
+                op.emit(ctx, rl, 2 * n, s0, s1, acc);
+            }
+        }
+
+        if constexpr (FO > 0) {
+#pragma unroll 1
+            for (int f = 0; f < FO; ++f)
+                fft_smem<T>(spec + (f * rows + rf) * pitch, 1, g.lgh, jt, tws, lg1, false, false, g.sched);
+            const T half = T(0.5);
+#pragma unroll
+            for (int f = 0; f < FO; ++f) {
+                const cx<T> *z = spec + (f * rows + rf) * pitch;
+                cx<T> *dst = op.spec_out(f) + (row0 + rf) * H;
+                for (int k = jt; k <= H / 2; k += nt) {
+                    if (k == 0) {
+                        const cx<T> z0 = z[0];
+                        dst[0] = mk(z0.x + z0.y, z0.x - z0.y);
+                    } else {
+                        const int kk = H - k;
+                        const cx<T> a = z[k], b = z[kk];
+                        const cx<T> w = tws[k];
+                        // X(k) = 1/2 [(a + conj b) - i W^k (a - conj b)]
+                        dst[k] = scale((a + conjg(b)) - mul_i(cmul(w, a - conjg(b))), half);
+                        // X(H-k) = 1/2 [(b + conj a) + i conj(W^k) (b - conj a)]
+                        if (kk != k) dst[kk] = scale((b + conjg(a)) + mul_i(cmul(conjg(w), b - conjg(a))), half);
+                    }
                 }
             }
         }
+        // the stage is rewritten by the async proxy two tiles on
+        fence_proxy_async();
+        __syncthreads();
     }
+    op.block_done(acc);
 }
 
 // ---------------------------------------------------------------------------

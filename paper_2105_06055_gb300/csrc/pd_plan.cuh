@@ -1,6 +1,8 @@
 // Plan object and launch helpers of the GB300 FCBM-EC library (private).
 #pragma once
 
+#include <algorithm>
+
 #include <vector>
 
 #include "pd_common.cuh"
@@ -242,7 +244,9 @@ inline const cx<float> *tw_buf<float>(const pd_plan *p) { return p->tw32; }
 template <>
 inline const cx<double> *tw_buf<double>(const pd_plan *p) { return p->tw64; }
 
-// Row-pass configuration: FB packed-row slots, NF node fields of T, NB byte fields.
+// Row-pass configuration: FB packed-row slots, NF node fields of T, NB byte
+// fields; two pipeline stages. c.grid is the tile count; launch_rows caps it
+// at the resident blocks (the kernel is persistent).
 template <typename T>
 inline void row_cfg(const pd_plan *p, int FB, int NF, int NB, RowGeom &g, LaunchCfg &c)
 {
@@ -250,10 +254,10 @@ inline void row_cfg(const pd_plan *p, int FB, int NF, int NB, RowGeom &g, Launch
     const int pad = nt < 16 ? (nt < 2 ? 2 : nt) : 0;  // keeps rows 16-byte aligned, spreads banks
     const int pitch = H + pad;
     auto smem_of = [&](int rows) {
-        return (size_t)n1 * sizeof(cx<T>) + (size_t)FB * rows * pitch * sizeof(cx<T>) +
-               (size_t)NF * rows * n1 * sizeof(T) + (((size_t)NB * rows * n1 + 15) & ~(size_t)15) + 16;
+        return (((size_t)n1 * sizeof(cx<T>) + 127) & ~(size_t)127) +
+               2 * row_stage_bytes<T>(FB, NF, NB, rows, pitch, n1) + 16;
     };
-    int rows = p->tune_rows > 0 ? p->tune_rows : 256 / nt;
+    int rows = p->tune_rows > 0 ? p->tune_rows : 128 / nt;
     if (rows < 1) rows = 1;
     while (rows > 1 && rows * nt > 256) rows >>= 1;  // k_rows launch bound
     while (rows > 1 && smem_of(rows) > 100 * 1024) rows >>= 1;
@@ -349,8 +353,11 @@ inline pd_status prof_end(pd_plan *p, cudaStream_t st)
     return PD_OK;
 }
 
+// Persistent row pass: as many blocks as fit on the GPU at once (at most one
+// per tile). *grid_out receives the block count (the number of block partial
+// sums an op with a block accumulator writes).
 template <typename T, class Op>
-pd_status launch_rows(pd_plan *p, const Op &op, cudaStream_t st)
+pd_status launch_rows(pd_plan *p, const Op &op, cudaStream_t st, unsigned *grid_out = nullptr)
 {
     RowGeom g;
     LaunchCfg c;
@@ -358,6 +365,11 @@ pd_status launch_rows(pd_plan *p, const Op &op, cudaStream_t st)
     constexpr int FB = Op::kFin > KO ? Op::kFin : KO;
     row_cfg<T>(p, FB, Op::kNF, Op::kNB, g, c);
     PD_TRY(set_smem_attr((const void *)k_rows<T, Op>, c.smem));
+    int per_sm = 0;
+    PD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows<T, Op>, (int)c.block.x, c.smem));
+    const int64_t cap = (int64_t)std::max(per_sm, 1) * p->nsm;
+    if ((int64_t)c.grid.x > cap) c.grid.x = (unsigned)cap;
+    if (grid_out) *grid_out = c.grid.x;
     PD_TRY(prof_begin(p, Op::kFin > 0 ? PASS_ROWS_INV : PASS_ROWS_FWD, st));
     k_rows<T, Op><<<c.grid, c.block, c.smem, st>>>(g, op, tw_buf<T>(p));
     PD_LAUNCH_CHECK();

@@ -352,23 +352,21 @@ struct Solver {
         cx<T> *spec = reinterpret_cast<cx<T> *>(spec_buf<T>(p));
         const int64_t fs = p->N / 2;
         const Model<T> m = model_view<T>(p);
-        RowGeom g;
-        LaunchCfg c;
-        row_cfg<T>(p, D, 0, 1, g, c);
-        if ((int64_t)c.grid.x > kPartB) {
-            set_error("pd_solve_static: %u row blocks exceed the reduction buffer", c.grid.x);
-            return PD_ERR_SIZE;
-        }
+        unsigned gpro = 0, gepi = 0;
         ProCG<T, D> pro{e, r, pv, q, p->mbits, p->red, p->N, p->n1, spec, fs};
-        PD_TRY(launch_rows<T>(p, pro, st));
+        PD_TRY(launch_rows<T>(p, pro, st, &gpro));
         if (D == 3) PD_TRY((col_pass<T, D>(p, 0, false, st)));
         const int ob = D == 3 ? D : 0;
         CombForce<T, D, false> cmb{m, ob};
         PD_TRY(launch_cols<T>(p, cmb, D == 3 ? 2 : 1, true, D, st));
         if (D == 3) PD_TRY((col_pass<T, D>(p, ob, true, st)));
         EpiCG<T, D> epi{pv, r, p->mbits, m.gent, m.goff, q, p->red, p->N, p->n1, spec + ob * fs, fs};
-        PD_TRY(launch_rows<T>(p, epi, st));
-        k_cg_finish_fused<<<1, 1024, 0, st>>>(p->red, (int)c.grid.x, (int)c.grid.x);
+        PD_TRY(launch_rows<T>(p, epi, st, &gepi));
+        if (gpro > (unsigned)kPartB || gepi > (unsigned)kPartB) {
+            set_error("pd_solve_static: %u / %u row blocks exceed the reduction buffer", gpro, gepi);
+            return PD_ERR_SIZE;
+        }
+        k_cg_finish_fused<<<1, 1024, 0, st>>>(p->red, (int)gpro, (int)gepi);
         PD_LAUNCH_CHECK();
         p->launches++;
         return PD_OK;
