@@ -71,4 +71,13 @@ __host__ __device__ __forceinline__ int ilog2(int v)
     return r;
 }
 
+// Grid coordinates of linear node p (x1 fastest; n1, n2 powers of two).
+__device__ __forceinline__ void node_coords(int64_t p, int n1, int n2, int &i1, int &i2, int &i3)
+{
+    const int l1 = __ffs(n1) - 1, l2 = __ffs(n2) - 1;
+    i1 = (int)(p & (n1 - 1));
+    i2 = (int)((p >> l1) & (n2 - 1));
+    i3 = (int)(p >> (l1 + l2));
+}
+
 }  // namespace pd

@@ -333,7 +333,7 @@ struct EpiDR {
                 Gv[q] = T(0);
             }
             sym_apply<T, D>(g.g, vv, Gv);
-            const int rl = (int)(g.p / n1 - c.row0), i1 = (int)(g.p % n1);
+            const int rl = (int)((g.p >> (__ffs(n1) - 1)) - c.row0), i1 = (int)(g.p & (n1 - 1));
 #pragma unroll
             for (int i = 0; i < D; ++i) c.stage(i, rl, i1) -= Gv[i];
         }

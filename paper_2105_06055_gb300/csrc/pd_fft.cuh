@@ -531,14 +531,21 @@ __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__r
     const int kyt = c0 >> g.lgh;  // 3D: the tile's k2
     const bool fyt = axis_is_z && kyt > (g.n2 >> 1);
     if constexpr (NTAB > 0) {
+        // lanes over the slice's columns (w + 1 <= 33: lane 0 also takes
+        // column 32), warps over (component, fold row); no integer division
         const int kyf = fyt ? g.n2 - kyt : kyt;
-        for (int i = threadIdx.x; i < NTAB * tcs; i += nthreads) {
-            const int comp = i / tcs, rem = i - comp * tcs;
-            const int rr = rem / tcols, cc = rem - rr * tcols;
-            const int kx = (cc == w) ? H : kx0 + cc;
-            const int64_t gi = axis_is_z ? ((int64_t)rr * ((g.n2 >> 1) + 1) + kyf) * (H + 1) + kx
-                                         : (int64_t)rr * (H + 1) + kx;
-            tab[i] = op.table(comp)[gi];
+        const int lane = threadIdx.x & 31, nwarp = nthreads >> 5;
+        const int64_t rstride = axis_is_z ? (int64_t)((g.n2 >> 1) + 1) * (H + 1) : (int64_t)(H + 1);
+        const int64_t roff = axis_is_z ? (int64_t)kyf * (H + 1) : 0;
+        for (int cr = threadIdx.x >> 5; cr < NTAB * trows; cr += nwarp) {
+            int comp = 0, rr = cr;
+            while (rr >= trows) {
+                rr -= trows;
+                ++comp;
+            }
+            const T *src = op.table(comp) + (int64_t)rr * rstride + roff;
+            T *dst = tab + comp * tcs + rr * tcols;
+            for (int cc = lane; cc < tcols; cc += 32) dst[cc] = src[(cc == w) ? H : kx0 + cc];
         }
     }
     if (!mbar_wait(mbar, 0, g.err)) return;

@@ -212,7 +212,7 @@ struct EpiForceSparse {
         for (int k = k0 + tid; k < k1; k += nthreads) {
             const GEntry<T> e = gent[k];
             const int64_t p = e.p;
-            const int rl = (int)(p / n1 - c.row0), i1 = (int)(p % n1);
+            const int rl = (int)((p >> (__ffs(n1) - 1)) - c.row0), i1 = (int)(p & (n1 - 1));
             T uu[D], Gu[D];
 #pragma unroll
             for (int j = 0; j < D; ++j) {

@@ -206,7 +206,8 @@ __global__ void k_state_fields(int n1, int n2, int n3, HorizonDev hz, const uint
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= N) return;
-    const int i1 = (int)(p % n1), i2 = (int)((p / n1) % n2), i3 = (int)(p / ((int64_t)n1 * n2));
+    int i1, i2, i3;
+    node_coords(p, n1, n2, i1, i2, i3);
     double q[3] = {0, 0, 0}, m = 0;
     if (chi[p]) {
         for (int c = 0; c < hz.cnt; ++c) {
@@ -302,7 +303,8 @@ __global__ void k_check_masks(int n1, int n2, int n3, int r1, int r2, int r3, co
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= N) return;
-    const int i1 = (int)(p % n1), i2 = (int)((p / n1) % n2), i3 = (int)(p / ((int64_t)n1 * n2));
+    int i1, i2, i3;
+    node_coords(p, n1, n2, i1, i2, i3);
     const uint8_t c = chi[p];
     if (c > 1) atomicOr(bad, 4);
     if (c) {

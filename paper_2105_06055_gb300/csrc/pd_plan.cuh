@@ -102,7 +102,8 @@ __global__ void k_gfield(int n1, int n2, int n3, HorizonDev hz, int ncomp, const
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= N) return;
-    const int i1 = (int)(p % n1), i2 = (int)((p / n1) % n2), i3 = (int)(p / ((int64_t)n1 * n2));
+    int i1, i2, i3;
+    node_coords(p, n1, n2, i1, i2, i3);
     Acc acc[6] = {0, 0, 0, 0, 0, 0};
     if (chi[p]) {
         const Acc vp = s ? (Acc)s[p] : Acc(1);

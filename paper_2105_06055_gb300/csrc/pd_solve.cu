@@ -238,7 +238,7 @@ struct EpiCG {
             for (int j = 0; j < U; ++j) {
                 if (kb + j * nthreads >= k1) break;
                 const int64_t p = e[j].p;
-                const int rl = (int)(p / n1 - c.row0), i1 = (int)(p % n1);
+                const int rl = (int)((p >> (__ffs(n1) - 1)) - c.row0), i1 = (int)(p & (n1 - 1));
                 T Gp[D];
 #pragma unroll
                 for (int qd = 0; qd < D; ++qd) Gp[qd] = T(0);

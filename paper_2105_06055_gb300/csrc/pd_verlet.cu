@@ -77,7 +77,8 @@ __global__ void k_gfield_lam(int n1, int n2, int n3, HorizonDev hz, int ncomp, c
     if (!force && !cnt->changed) return;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p < N) {
-        const int i1 = (int)(p % n1), i2 = (int)((p / n1) % n2), i3 = (int)(p / ((int64_t)n1 * n2));
+        int i1, i2, i3;
+        node_coords(p, n1, n2, i1, i2, i3);
         T acc[6] = {0, 0, 0, 0, 0, 0};
         if (chi[p]) {
             const T vp = lam[p] ? T(1) : T(0);
@@ -126,7 +127,8 @@ __global__ void k_energy_direct(int n1, int n2, int n3, HorizonDev hz, double dx
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
         T acc = T(0);
         if (chi[p] && lam[p]) {
-            const int i1 = (int)(p % n1), i2 = (int)((p / n1) % n2), i3 = (int)(p / ((int64_t)n1 * n2));
+            int i1, i2, i3;
+            node_coords(p, n1, n2, i1, i2, i3);
             T up[D];
 #pragma unroll
             for (int j = 0; j < D; ++j) up[j] = u[j * N + p];
