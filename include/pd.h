@@ -253,6 +253,11 @@ void pd_batch_destroy(pd_batch *batch);
 pd_status pd_plan_autotune(pd_plan *plan, void *stream);
 pd_status pd_batch_autotune(pd_batch *batch, void *stream);
 pd_status pd_plan_tuning(const pd_plan *plan, int *out4);
+/* Pin a pass configuration {rows, x2 width, last-axis width, schedule}: 0 or
+ * powers of two (rows <= 256, widths <= 32; 0 = heuristic), schedule 0/1;
+ * PD_ERR_ARG otherwise. The pass configuration functions still shrink a value
+ * that does not fit the grid or the shared memory. */
+pd_status pd_plan_set_tuning(pd_plan *plan, const int *in4);
 
 /*
  * pd_force_adjoint -- reverse-mode derivative of pd_force (bond model). The

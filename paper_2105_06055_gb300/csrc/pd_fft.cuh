@@ -531,21 +531,22 @@ __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__r
     const int kyt = c0 >> g.lgh;  // 3D: the tile's k2
     const bool fyt = axis_is_z && kyt > (g.n2 >> 1);
     if constexpr (NTAB > 0) {
-        // lanes over the slice's columns (w + 1 <= 33: lane 0 also takes
-        // column 32), warps over (component, fold row); no integer division
+        // flat loop over (component, fold row, column) with the column index in
+        // the low bits (vw = next power of two >= w + 1): no integer division,
+        // independent loads for the unrolled iterations
         const int kyf = fyt ? g.n2 - kyt : kyt;
-        const int lane = threadIdx.x & 31, nwarp = nthreads >> 5;
+        const int lgvw = 32 - __clz(tcols - 1), vw = 1 << lgvw;
         const int64_t rstride = axis_is_z ? (int64_t)((g.n2 >> 1) + 1) * (H + 1) : (int64_t)(H + 1);
         const int64_t roff = axis_is_z ? (int64_t)kyf * (H + 1) : 0;
-        for (int cr = threadIdx.x >> 5; cr < NTAB * trows; cr += nwarp) {
-            int comp = 0, rr = cr;
-            while (rr >= trows) {
-                rr -= trows;
-                ++comp;
-            }
-            const T *src = op.table(comp) + (int64_t)rr * rstride + roff;
-            T *dst = tab + comp * tcs + rr * tcols;
-            for (int cc = lane; cc < tcols; cc += 32) dst[cc] = src[(cc == w) ? H : kx0 + cc];
+        const float inv_trows = 1.0f / (float)trows;  // exact quotient for cr < 2^14
+        const int nv = NTAB * trows << lgvw;
+#pragma unroll 4
+        for (int i = threadIdx.x; i < nv; i += nthreads) {
+            const int cr = i >> lgvw, cc = i & (vw - 1);
+            const int comp = (int)(((float)cr + 0.5f) * inv_trows);
+            const int rr = cr - comp * trows;
+            if (cc < tcols)
+                tab[comp * tcs + rr * tcols + cc] = op.table(comp)[rr * rstride + roff + ((cc == w) ? H : kx0 + cc)];
         }
     }
     if (!mbar_wait(mbar, 0, g.err)) return;

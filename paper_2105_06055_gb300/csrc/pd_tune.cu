@@ -162,3 +162,25 @@ extern "C" pd_status pd_batch_autotune(pd_batch *B, void *stream)
     pd_batch_invalidate(B);
     return PD_OK;
 }
+
+extern "C" pd_status pd_plan_set_tuning(pd_plan *p, const int *in4)
+{
+    if (!p || !in4) {
+        set_error("pd_plan_set_tuning: null argument");
+        return PD_ERR_ARG;
+    }
+    const int r = in4[0], wx = in4[1], wl = in4[2], sc = in4[3];
+    auto pow2_or_zero = [](int v) { return v == 0 || (v > 0 && (v & (v - 1)) == 0); };
+    if (!pow2_or_zero(r) || r > 256 || !pow2_or_zero(wx) || wx > 32 || !pow2_or_zero(wl) || wl > 32 ||
+        (sc != 0 && sc != 1)) {
+        set_error("pd_plan_set_tuning: rows and widths must be 0 or powers of two (rows <= 256, widths <= 32), "
+                  "schedule 0 or 1");
+        return PD_ERR_ARG;
+    }
+    p->tune_rows = r;
+    p->tune_w[0] = wx;
+    p->tune_w[1] = wl;
+    p->tune_sched = sc;
+    drop_graphs(p);
+    return PD_OK;
+}

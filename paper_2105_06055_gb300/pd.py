@@ -30,7 +30,7 @@ EXPORTS = ["pd_plan_create", "pd_plan_destroy", "pd_kernel_spectrum", "pd_force"
            "pd_plan_profile", "pd_plan_profile_read", "pd_force2d_noalloc", "pd_plan_boundary_nodes",
            "pd_solve_dr", "pd_plan_create_batched", "pd_batch_size", "pd_batch_plan", "pd_solve_dr_batched",
            "pd_batch_destroy", "pd_plan_autotune", "pd_batch_autotune", "pd_plan_tuning",
-           "pd_plan_set_energy_mode"]
+           "pd_plan_set_energy_mode", "pd_plan_set_tuning"]
 
 PASS_KINDS = {0: "rows_fwd", 1: "cols_x2", 2: "last_axis", 3: "rows_inv"}
 
@@ -110,6 +110,8 @@ def load():
     lib.pd_batch_autotune.restype = I
     lib.pd_plan_tuning.argtypes = [P, ctypes.POINTER(I)]
     lib.pd_plan_tuning.restype = I
+    lib.pd_plan_set_tuning.argtypes = [P, ctypes.POINTER(I)]
+    lib.pd_plan_set_tuning.restype = I
     lib.pd_plan_set_energy_mode.argtypes = [P, I]
     lib.pd_plan_set_energy_mode.restype = I
     lib.pd_status_string.argtypes = [I]
@@ -302,6 +304,11 @@ class Plan:
     def set_energy_mode(self, direct: bool):
         """W for bond breaking: False = convolution form (Eq. 102), True = horizon sum (Eq. 47)."""
         _check(load().pd_plan_set_energy_mode(self._h, 1 if direct else 0), "pd_plan_set_energy_mode")
+
+    def set_tuning(self, rows=0, w_x2=0, w_last=0, sched=0):
+        """Pin a pass configuration (0 = built-in heuristic)."""
+        arr = (ctypes.c_int * 4)(int(rows), int(w_x2), int(w_last), int(sched))
+        _check(load().pd_plan_set_tuning(self._h, arr), "pd_plan_set_tuning")
 
     @property
     def tuning(self):
