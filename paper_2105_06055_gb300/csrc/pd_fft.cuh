@@ -531,22 +531,19 @@ __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__r
     const int kyt = c0 >> g.lgh;  // 3D: the tile's k2
     const bool fyt = axis_is_z && kyt > (g.n2 >> 1);
     if constexpr (NTAB > 0) {
-        // flat loop over (component, fold row, column) with the column index in
-        // the low bits (vw = next power of two >= w + 1): no integer division,
-        // independent loads for the unrolled iterations
+        // flat loop over the slice; the (component, fold row, column) split
+        // uses FP32 reciprocals, exact here (indices < 2^15, divisors <= 2^10 + 1)
         const int kyf = fyt ? g.n2 - kyt : kyt;
-        const int lgvw = 32 - __clz(tcols - 1), vw = 1 << lgvw;
         const int64_t rstride = axis_is_z ? (int64_t)((g.n2 >> 1) + 1) * (H + 1) : (int64_t)(H + 1);
         const int64_t roff = axis_is_z ? (int64_t)kyf * (H + 1) : 0;
-        const float inv_trows = 1.0f / (float)trows;  // exact quotient for cr < 2^14
-        const int nv = NTAB * trows << lgvw;
-#pragma unroll 4
-        for (int i = threadIdx.x; i < nv; i += nthreads) {
-            const int cr = i >> lgvw, cc = i & (vw - 1);
-            const int comp = (int)(((float)cr + 0.5f) * inv_trows);
-            const int rr = cr - comp * trows;
-            if (cc < tcols)
-                tab[comp * tcs + rr * tcols + cc] = op.table(comp)[rr * rstride + roff + ((cc == w) ? H : kx0 + cc)];
+        const float inv_tcs = 1.0f / (float)tcs, inv_tcols = 1.0f / (float)tcols;
+#pragma unroll 8
+        for (int i = threadIdx.x; i < NTAB * tcs; i += nthreads) {
+            const int comp = (int)(((float)i + 0.5f) * inv_tcs);
+            const int rem = i - comp * tcs;
+            const int rr = (int)(((float)rem + 0.5f) * inv_tcols);
+            const int cc = rem - rr * tcols;
+            tab[i] = op.table(comp)[rr * rstride + roff + ((cc == w) ? H : kx0 + cc)];
         }
     }
     if (!mbar_wait(mbar, 0, g.err)) return;
