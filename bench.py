@@ -163,7 +163,11 @@ def run_native(args, rank, world):
     chi = torch.tensor(cfg["chi"], device=dev)
     chi_om = torch.tensor(cfg["chi_omega"], device=dev)
     plan = pd.Plan(prob, chi, chi_om)
-    tuning = None if args.no_autotune else plan.autotune()
+    if args.tuning:
+        plan.set_tuning(*[int(v) for v in args.tuning.split(",")])
+        tuning = plan.tuning
+    else:
+        tuning = None if args.no_autotune else plan.autotune()
     b = torch.tensor(cfg["b"], dtype=torch.float64, device=dev)
     u = torch.zeros((3,) + shape, dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
@@ -403,6 +407,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="static", choices=["static", "batched"])
     ap.add_argument("--no-autotune", action="store_true", help="skip the pass autotuner (built-in tile heuristic)")
+    ap.add_argument("--tuning", default="", metavar="ROWS,WX2,WLAST,SCHED",
+                    help="pin a pass configuration instead of autotuning (e.g. the one a tuned run reported)")
     ap.add_argument("--specimens", type=int, default=64)
     ap.add_argument("--profile-solve", type=int, default=0, metavar="K",
                     help="no timing: build the workload and run one solve capped at K CG iterations "
@@ -419,7 +425,9 @@ def main():
         dev = torch.device("cuda")
         plan = pd.Plan(pd.Problem(shape=cfg["shape"], delta=DELTA, model=pd.PD_LIN_STATE, nu=0.25, fp64=False),
                        torch.tensor(cfg["chi"], device=dev), torch.tensor(cfg["chi_omega"], device=dev))
-        if not args.no_autotune:
+        if args.tuning:
+            plan.set_tuning(*[int(v) for v in args.tuning.split(",")])
+        elif not args.no_autotune:
             plan.autotune()
         u = torch.zeros((3,) + cfg["shape"], dtype=torch.float64, device=dev)
         it, rel, _ = plan.solve_static(u, torch.tensor(cfg["b"], dtype=torch.float64, device=dev), None,
