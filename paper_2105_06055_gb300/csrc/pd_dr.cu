@@ -52,7 +52,8 @@
 //   rows  : v, e update (needs c^{n-1}); x1 transform of chi v
 //   cols / last / cols : x2 transform, M^ multiply with x3, inverse (3D)
 //   rows  : inverse x1, F += chi_O L(v), block partials of e.Ae, e.e
-//           and ||F||^2; the last block to finish reduces them: c^n, ||F^n||^2
+//           and ||F||^2
+//   finish: c^n, ||F^n||^2
 // The state-based operator (dilatation round between the halves) runs the
 // update as separate vector kernels around the plain force.
 #include <algorithm>
@@ -76,7 +77,6 @@ enum {
     R_BN2 = 16, R_BN, R_TARGET, R_RN, R_ITOL2, R_C, R_FF, R_RHOINV, R_STEPS, R_MAXSTEPS, R_CYCLES,
     R_STATUS, R_GO, R_REL, R_BEST, R_SINCE, R_CSTEPS, R_RNPREV, R_SLOW, R_COUNT
 };
-constexpr int R_ARRIVE = 40;  // scalar slot holding the last-block arrival counter
 // R_STATUS values
 enum { DR_RUN = 0, DR_CONVERGED = 1, DR_MAXSTEPS = 2, DR_NONFINITE = 3, DR_TIMEOUT = 4, DR_CYCLES = 5,
        DR_STALLED = 6 };
@@ -85,7 +85,6 @@ __global__ void k_dr_start(double *red, double rho_inv, double max_steps)
 {
     double *s = red + kRedScal;
     for (int i = R_BN2; i < R_COUNT; ++i) s[i] = 0.0;
-    s[R_ARRIVE] = 0.0;
     s[R_RHOINV] = rho_inv;
     s[R_MAXSTEPS] = max_steps;
 }
@@ -201,14 +200,14 @@ __global__ void k_dr_ir_update(double *u, const T *e, const uint8_t *co, int64_t
         if (co[i]) u[i] += (double)e[i];
 }
 
-// Block partial triples (e.Ae, e.e, ||F||^2) -> c^n, ||F^n||^2 (all threads of one block)
-__device__ void dr_finish_block(double *red, int nparts)
+// Block partial triples (e.Ae, e.e, ||F||^2) -> c^n, ||F^n||^2
+__global__ void k_dr_finish(double *red, int nparts)
 {
     double a = 0.0, b = 0.0, f = 0.0;
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
-        a += __ldcg(red + kRedPart + 3 * i);
-        b += __ldcg(red + kRedPart + 3 * i + 1);
-        f += __ldcg(red + kRedPart + 3 * i + 2);
+        a += red[kRedPart + 3 * i];
+        b += red[kRedPart + 3 * i + 1];
+        f += red[kRedPart + 3 * i + 2];
     }
     a = block_sum_d(a);
     b = block_sum_d(b);
@@ -220,8 +219,6 @@ __device__ void dr_finish_block(double *red, int nparts)
         s[R_FF] = f;
     }
 }
-
-__global__ void k_dr_finish(double *red, int nparts) { dr_finish_block(red, nparts); }
 
 struct DrAcc {
     DSum num, den, ff;
@@ -236,24 +233,6 @@ __device__ __forceinline__ void write_partial3(double *red, const DrAcc &acc)
         red[kRedPart + 3 * blockIdx.x] = a;
         red[kRedPart + 3 * blockIdx.x + 1] = b;
         red[kRedPart + 3 * blockIdx.x + 2] = f;
-    }
-}
-
-// write_partial3, then the last block to arrive reduces all partials
-__device__ __forceinline__ void write_partial3_finish(double *red, const DrAcc &acc)
-{
-    __shared__ int last;
-    write_partial3(red, acc);
-    if (threadIdx.x == 0) {
-        __threadfence();
-        unsigned *cnt = reinterpret_cast<unsigned *>(red + kRedScal + R_ARRIVE);
-        last = atomicAdd(cnt, 1u) == gridDim.x - 1;
-        if (last) *cnt = 0u;
-    }
-    __syncthreads();
-    if (last) {
-        __threadfence();
-        dr_finish_block(red, (int)gridDim.x);
     }
 }
 
@@ -379,7 +358,7 @@ struct EpiDR {
             dr_accumulate<T>(acc, fb, rv[i].y, ev[i].y);
         }
     }
-    __device__ void block_done(DrAcc &acc) const { write_partial3_finish(red, acc); }
+    __device__ void block_done(DrAcc &acc) const { write_partial3(red, acc); }
 };
 
 // unfused step (state-based operator): v, e update ...
@@ -478,6 +457,9 @@ struct DrSpec {
             set_error("dynamic relaxation: %u row blocks exceed the reduction buffer", gepi);
             return PD_ERR_SIZE;
         }
+        k_dr_finish<<<1, 1024, 0, st>>>(p->red, (int)gepi);
+        PD_LAUNCH_CHECK();
+        p->launches++;
         return PD_OK;
     }
 
@@ -751,7 +733,7 @@ struct DrRunner {
             const double *h = host + i * R_COUNT;
             const int st = (int)h[R_STATUS];
             pd_plan *p = plans[i];
-            const int per = p->state_based ? 3 : (p->dim == 3 ? 5 : 3);
+            const int per = p->state_based ? 3 : (p->dim == 3 ? 6 : 4);
             p->launches += (int64_t)h[R_STEPS] * per + (int64_t)h[R_CYCLES] * 12;
             pd_status r = PD_OK;
             switch (st) {

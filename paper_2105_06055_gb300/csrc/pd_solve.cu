@@ -13,7 +13,7 @@
 // runs in FP64. CG inner products are accumulated per thread in compensated
 // FP32 (two-sum) and per block in FP64.
 //
-// One CG iteration is five fused passes; the vector
+// One CG iteration is five fused passes and one small kernel; the vector
 // updates of iteration i are applied in the first pass of iteration i+1, so
 // all reductions of an iteration happen in one place (r.q and q.q give the
 // next r.r before r is updated: (r - alpha q).(r - alpha q) = rr - 2 alpha rq
@@ -21,9 +21,8 @@
 //   rows  : e += alpha p, r -= alpha q, p = r + beta p (stored), partials of
 //           r.r, FFT_x1 of chi p
 //   cols / last / cols : FFT_x2, M^ multiply with FFT_x3, inverse (3D)
-//   rows  : inverse FFT_x1, q = -chi_O L(p) (stored), partials of p.q, r.q, q.q;
-//           the last block to finish reduces all partials: rr, alpha = rr / p.q,
-//           beta = (rr - 2 alpha rq + alpha^2 qq) / rr
+//   rows  : inverse FFT_x1, q = -chi_O L(p) (stored), partials of p.q, r.q, q.q
+//   finish: rr, alpha = rr / p.q, beta = (rr - 2 alpha rq + alpha^2 qq) / rr
 // After the last iteration one update kernel applies the pending e, r update.
 // All CG scalars stay on the device. Chunks of kChunk iterations are captured
 // once into a CUDA graph and replayed; the host reads the residual norm after
@@ -40,18 +39,15 @@ namespace {
 constexpr int kChunk = 16;       // CG iterations per graph replay
 constexpr int kPartB = 14400;    // fused iteration: r.r partials below, (p.q, r.q, q.q) triples above
 
-constexpr int S_ARRIVE = 40;   // scalar slot holding the last-block arrival counter
-
-// rr = sum of the first pass's partials; alpha, beta from the second pass's
-// triples. Run by the last block of the second pass to finish (all threads).
-__device__ void cg_finish_block(double *red, int na, int nb)
+// rr = sum of the first pass's partials; alpha, beta from the second pass's triples
+__global__ void k_cg_finish_fused(double *red, int na, int nb)
 {
     double rr = 0.0, pq = 0.0, rq = 0.0, qq = 0.0;
-    for (int i = threadIdx.x; i < na; i += blockDim.x) rr += __ldcg(red + kRedPart + i);
+    for (int i = threadIdx.x; i < na; i += blockDim.x) rr += red[kRedPart + i];
     for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-        pq += __ldcg(red + kRedPart + kPartB + 3 * i);
-        rq += __ldcg(red + kRedPart + kPartB + 3 * i + 1);
-        qq += __ldcg(red + kRedPart + kPartB + 3 * i + 2);
+        pq += red[kRedPart + kPartB + 3 * i];
+        rq += red[kRedPart + kPartB + 3 * i + 1];
+        qq += red[kRedPart + kPartB + 3 * i + 2];
     }
     rr = block_sum_d(rr);
     pq = block_sum_d(pq);
@@ -69,6 +65,7 @@ __device__ void cg_finish_block(double *red, int na, int nb)
         s[S_RR] = rn;  // r.r after this iteration's (pending) update
     }
 }
+
 
 // r = (T) r64, p = 0, e = 0, q = 0 ; partial r.r
 template <typename T>
@@ -207,7 +204,6 @@ struct EpiCG {
     int n1;
     const cx<T> *spec;
     int64_t fstride;
-    int na;  // blocks of the first pass (r.r partials)
     __device__ const cx<T> *spec_in(int f) const { return spec + f * fstride; }
     __device__ cx<T> *spec_out(int) const { return nullptr; }
     __device__ const T *nf_src(int) const { return nullptr; }
@@ -276,10 +272,8 @@ struct EpiCG {
             acc.qq.add(b * b);
         }
     }
-    // block partials; the last block to arrive finishes the iteration's scalars
     __device__ void block_done(CgAcc &acc) const
     {
-        __shared__ int last;
         const double x = block_sum_d(acc.pq.value());
         const double y = block_sum_d(acc.rq.value());
         const double z = block_sum_d(acc.qq.value());
@@ -288,15 +282,6 @@ struct EpiCG {
             o[0] = x;
             o[1] = y;
             o[2] = z;
-            __threadfence();
-            unsigned *cnt = reinterpret_cast<unsigned *>(red + kRedScal + S_ARRIVE);
-            last = atomicAdd(cnt, 1u) == gridDim.x - 1;
-            if (last) *cnt = 0u;
-        }
-        __syncthreads();
-        if (last) {
-            __threadfence();
-            cg_finish_block(red, na, (int)gridDim.x);
         }
     }
 };
@@ -375,16 +360,15 @@ struct Solver {
         CombForce<T, D, false> cmb{m, ob};
         PD_TRY(launch_cols<T>(p, cmb, D == 3 ? 2 : 1, true, D, st));
         if (D == 3) PD_TRY((col_pass<T, D>(p, ob, true, st)));
-        if (gpro > (unsigned)kPartB) {
-            set_error("pd_solve_static: %u row blocks exceed the reduction buffer", gpro);
-            return PD_ERR_SIZE;
-        }
-        EpiCG<T, D> epi{pv, r, p->mbits, m.gent, m.goff, q, p->red, p->N, p->n1, spec + ob * fs, fs, (int)gpro};
+        EpiCG<T, D> epi{pv, r, p->mbits, m.gent, m.goff, q, p->red, p->N, p->n1, spec + ob * fs, fs};
         PD_TRY(launch_rows<T>(p, epi, st, &gepi));
-        if (gepi > (unsigned)kPartB) {
-            set_error("pd_solve_static: %u row blocks exceed the reduction buffer", gepi);
+        if (gpro > (unsigned)kPartB || gepi > (unsigned)kPartB) {
+            set_error("pd_solve_static: %u / %u row blocks exceed the reduction buffer", gpro, gepi);
             return PD_ERR_SIZE;
         }
+        k_cg_finish_fused<<<1, 1024, 0, st>>>(p->red, (int)gpro, (int)gepi);
+        PD_LAUNCH_CHECK();
+        p->launches++;
         return PD_OK;
     }
 
@@ -428,7 +412,7 @@ struct Solver {
             p->ev_reserved = p->ev_used;  // keep the graph's event pairs
         }
         PD_CUDA_TRY(cudaGraphLaunch(p->cg_graph[gi], st));
-        p->launches += (int64_t)kChunk * (p->state_based ? 13 : (D == 3 ? 5 : 3));
+        p->launches += (int64_t)kChunk * (p->state_based ? 13 : (D == 3 ? 6 : 4));
         PD_CUDA_TRY(cudaStreamSynchronize(st));
         if (p->prof_on) PD_TRY(prof_harvest_range(p, p->cg_graph_ev[gi][0], p->cg_graph_ev[gi][1]));
         return PD_OK;
@@ -444,7 +428,6 @@ struct Solver {
         p->launches++;
         PD_TRY(finish(nb, S_RR, 0));
         PD_CUDA_TRY(cudaMemsetAsync(p->red + kRedScal + S_ALPHA, 0, 2 * sizeof(double), st));  // alpha, beta
-        PD_CUDA_TRY(cudaMemsetAsync(p->red + kRedScal + S_ARRIVE, 0, sizeof(double), st));
         int it = 0;
         double best = HUGE_VAL;
         int since_best = 0;
