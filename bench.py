@@ -20,6 +20,10 @@ Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|refere
 Under torchrun (N > 1) every rank solves its own copy (replicas: the problem
 does not shard) and rank 0 prints one JSON line.
 
+--workload force measures one FP32 bond-model force evaluation (pd_force) on
+an n^3 box (--n, e.g. 128/256/512; cube minus a centred ball, delta = 3) for the
+scale sweep, with per-pass times and roofline fractions.
+
 --workload batched measures the batched form instead: 64 uneven 2D bond-model
 specimens (sides 256..1024 padded to powers of two, delta 3..5, elliptical
 cutouts, seeded loads) solved to a relative FP64 residual of 1e-8 by dynamic
@@ -294,6 +298,117 @@ def run_native(args, rank, world):
     return result, cfg
 
 
+FORCE_PASS_BYTES = {  # algorithmic bytes per node of each FP32 pass of the bond force (d = 3)
+    "rows_fwd": 25.0,   # read u (12), chi (1); write 3 packed spectra (12)
+    "cols_x2": 24.0,    # read + write 3 spectra
+    "last_axis": 27.0,  # read + write 3 spectra, folded kernel table (6 floats per N/8 modes)
+    "rows_inv": 25.0,   # read 3 spectra (12), chi (1); write L (12); + 44 B per boundary node
+}
+
+
+def run_force(args):
+    import numpy as np
+    import torch
+
+    from paper_2105_06055_gb300 import build as pd_build
+    from paper_2105_06055_gb300 import inputs, pd
+
+    pd_build.build()
+    dev = torch.device("cuda")
+    n = args.n
+    shape = (n, n, n)
+    N = n ** 3
+    chi = inputs.cube_with_ball_mask(n)
+    u = inputs.separable_modes(shape, 4, max(n // 16, 2), 1e-3, seed=n, kmin=max(n // 32, 1)) * chi
+    plan = pd.Plan(pd.Problem(shape=shape, delta=DELTA, fp64=False), torch.tensor(chi, device=dev))
+    if args.tuning:
+        plan.set_tuning(*[int(v) for v in args.tuning.split(",")])
+        tuning = plan.tuning
+    else:
+        tuning = None if args.no_autotune else plan.autotune()
+    ud = torch.tensor(u, device=dev)
+    L = torch.empty_like(ud)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        plan.force(ud, L=L)
+    torch.cuda.synchronize()
+    plan.profile(True)
+    for _ in range(max(args.steps, 3)):
+        plan.force(ud, L=L)
+    torch.cuda.synchronize()
+    prof = plan.profile_read()
+    plan.profile(False)
+    launches0 = plan.launch_count
+    sampler = ClockSampler(None)
+    sampler.start()
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.force(ud, L=L)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    clocks = sampler.stop()
+    launches = plan.launch_count - launches0
+    peak, peak_kind = load_peaks()
+    nb = plan.boundary_nodes
+    passes = {}
+    for k, (ms, cnt) in prof.items():
+        if not cnt:
+            continue
+        per = ms / cnt
+        byt = FORCE_PASS_BYTES[k] * N + (44 * nb if k == "rows_inv" else 0)
+        passes[k] = {"us": 1e3 * per, "algorithmic_bytes": byt, "frac_of_measured_peak": byt / (per * 1e-3) / 1e9 / peak}
+    dom = max(passes, key=lambda k: passes[k]["us"] * (2 if k == "cols_x2" else 1))
+    t_ms = statistics.median(times)
+    # end to end: host u -> device, force, device L -> host
+    u_host = torch.tensor(u).pin_memory()
+    L_host = torch.empty_like(u_host).pin_memory()
+    e2e = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ud.copy_(u_host, non_blocking=True)
+        plan.force(ud, L=L)
+        L_host.copy_(L, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e.append(time.perf_counter() - t0)
+    out = {
+        "metric": f"PD force evals x nodes/sec (3D bond force evaluation, {n}^3)",
+        "value": N / (t_ms * 1e-3),
+        "unit": UNIT,
+        "n_gpus": 1,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": t_ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded separable smooth field, no dataset)",
+        "config": {"workload": f"3D linearized bond-based PD force evaluation (pd_force), {n}^3 box, cube minus "
+                               f"centred ball r={n // 4}, delta=3, E=1", "grid": [n, n, n],
+                   "l2": "256 MB L2 flush between steps"},
+        "passes": passes,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": passes[dom]["algorithmic_bytes"] /
+                     (passes[dom]["us"] * 1e-6) / 1e9, "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
+                     "frac": passes[dom]["frac_of_measured_peak"], "traffic": None},
+        "m2_end_to_end_hbm_frac": 25.0 * N / (t_ms * 1e-3) / (peak * 1e9),
+        "e2e": {"value": N / statistics.median(e2e), "unit": UNIT, "h2d_bytes_per_step": int(u_host.numel() * 4),
+                "d2h_bytes_per_step": int(L_host.numel() * 4)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "tuning": tuning,
+        "boundary_nodes": nb,
+    }
+    plan.close()
+    return out
+
+
 def run_batched(args):
     import numpy as np
     import torch
@@ -405,7 +520,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--n", type=int, default=N_GRID)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="static", choices=["static", "batched"])
+    ap.add_argument("--workload", default="static", choices=["static", "batched", "force"])
     ap.add_argument("--no-autotune", action="store_true", help="skip the pass autotuner (built-in tile heuristic)")
     ap.add_argument("--tuning", default="", metavar="ROWS,WX2,WLAST,SCHED",
                     help="pin a pass configuration instead of autotuning (e.g. the one a tuned run reported)")
@@ -442,6 +557,9 @@ def main():
 
     if args.workload == "batched":
         print(json.dumps(run_batched(args)))
+        return
+    if args.workload == "force":
+        print(json.dumps(run_force(args)))
         return
 
     if args.impl == "reference":

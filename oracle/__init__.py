@@ -67,6 +67,7 @@ def _load():
             lib.or_horizon.restype = I
             lib.or_force_bond.argtypes = [I, P, P, D, D, P, P, P, P]
             lib.or_energy_bond.argtypes = [I, P, P, D, D, P, P, P, P]
+            lib.or_force_bond_at.argtypes = [I, P, P, D, D, P, P, P, ctypes.c_int64, P]
             lib.or_damage.argtypes = [I, P, P, D, P, P, P, P, P]
             lib.or_force_lps.argtypes = [P, P, D, D, D, P, P, P, P, P]
             lib.or_force_bond_grad_s.argtypes = [I, P, P, D, D, P, P, P, P, P]
@@ -182,6 +183,19 @@ def force_bond(u, chi, dx, delta, alpha, s=None):
     L = np.empty_like(u)
     _load().or_force_bond(dim, _p(n), _p(_dx(dim, dx)), float(delta), float(alpha),
                           _p(chi), _p(s), _p(u), _p(L))
+    return L
+
+
+def force_bond_at(u, chi, dx, delta, alpha, nodes):
+    """force_bond evaluated only at the linear node indices ``nodes``; returns (d, len(nodes))."""
+    chi = _u8(chi)
+    dim, n = _grid(chi.shape)
+    u = _f64(u)
+    assert u.shape == (dim,) + chi.shape
+    nodes = np.ascontiguousarray(nodes, dtype=np.int64)
+    L = np.empty((dim, nodes.size), dtype=np.float64)
+    _load().or_force_bond_at(dim, _p(n), _p(_dx(dim, dx)), float(delta), float(alpha), _p(chi), _p(u),
+                             _p(nodes), int(nodes.size), _p(L))
     return L
 
 
@@ -348,6 +362,7 @@ PINS = {
     "alpha_bond": "energy of isotropic stretch vs classical elasticity; symbol vs Navier-Cauchy",
     "force_bond": "translation/rotation null space, affine interior, symbol, reciprocity, "
                   "all-pairs brute force, dense operator spectrum",
+    "force_bond_at": "all-pairs brute force at sampled nodes (3D); equals force_bond at those nodes",
     "energy_bond": "energy identity Σ W dV = -<u, L u> dV; isotropic-stretch closed form",
     "damage": "integer counts vs brute force; intact body d = 0",
     "force_lps": "translation/rotation null space, affine 2-delta interior, dilatation of "

@@ -166,6 +166,39 @@ void or_force_bond(int dim, const int *n, const double *dx, double delta, double
 }
 
 /*
+ * The same sum at selected nodes only (for checks on grids too large for a
+ * full evaluation): L[i * nsel + k] = L_i(nodes[k]).
+ */
+void or_force_bond_at(int dim, const int *n, const double *dx, double delta, double alpha,
+                      const uint8_t *chi, const double *u, const int64_t *nodes, int64_t nsel, double *L)
+{
+    horizon_t h;
+    build_horizon(dim, dx, delta, &h);
+    const int64_t N = (int64_t)n[0] * n[1] * n[2];
+    const double dV = dvol(dim, dx);
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < nsel; ++k) {
+        const int64_t p = nodes[k];
+        int i1 = (int)(p % n[0]), i2 = (int)((p / n[0]) % n[1]), i3 = (int)(p / ((int64_t)n[0] * n[1]));
+        double acc[3] = {0, 0, 0};
+        if (chi[p]) {
+            for (int c = 0; c < h.cnt; ++c) {
+                int64_t q = wrap_index(n, i1, i2, i3, &h.o[3 * c]);
+                if (!chi[q]) continue;
+                const double *xi = &h.xi[3 * c];
+                double r = h.len[c];
+                double coef = alpha * (1.0 / r) / (r * r);
+                double xe = 0.0;
+                for (int j = 0; j < dim; ++j) xe += xi[j] * (u[j * N + q] - u[j * N + p]);
+                for (int i = 0; i < dim; ++i) acc[i] += coef * xi[i] * xe;
+            }
+        }
+        for (int i = 0; i < dim; ++i) L[i * nsel + k] = chi[p] * acc[i] * dV;
+    }
+    free_horizon(&h);
+}
+
+/*
  * Strain energy density of the linearized bond model with bond breaking
  * (Eq. 47, EC form Eq. 102):  W(x) = 1/2 chi lam Σ_xi chi' lam' eta.C(xi).eta dV.
  * lam == NULL means lam = 1.

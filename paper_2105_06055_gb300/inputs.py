@@ -199,3 +199,29 @@ def batched_specimens(count=64, seed=0, nmin=256, nmax=1024, sizes=None):
         out.append(dict(shape=shape, n_body=n, dx=1.0, delta=delta, chi=chi,
                         chi_omega=np.stack([chi_om, chi_om]), b=b, w=np.zeros_like(b)))
     return out
+
+
+def cube_with_ball_mask(n, margin=3, radius_frac=0.25):
+    """chi of a cube [margin, n - margin)^3 minus a centred ball of radius
+    radius_frac * n, built by broadcasting (cheap at 512^3)."""
+    x = np.arange(n, dtype=np.float64)
+    c = (n - 1) / 2.0
+    inside = (x >= margin) & (x < n - margin)
+    r2 = ((x[None, None, :] - c) ** 2 + (x[None, :, None] - c) ** 2) + (x[:, None, None] - c) ** 2
+    chi = inside[:, None, None] & inside[None, :, None] & inside[None, None, :] & (r2 >= (radius_frac * n) ** 2)
+    return chi.astype(np.uint8)
+
+
+def separable_modes(shape, nterms, kmax, amp, seed, dtype=np.float32, kmin=1):
+    """Smooth vector field (3, *shape): per component a sum of nterms products
+    of 1D random sine waves (wave numbers kmin <= k <= kmax, random phases)
+    along x1, x2, x3, scaled to amplitude amp; separable, so cheap on large grids."""
+    g = rng(seed)
+    n3, n2, n1 = shape
+    out = np.zeros((3,) + tuple(shape), dtype=dtype)
+    for c in range(3):
+        for _ in range(nterms):
+            f = [np.sin(2 * math.pi * g.integers(kmin, kmax + 1) * np.arange(m) / m + g.uniform(0, 2 * math.pi))
+                 .astype(dtype) for m in (n1, n2, n3)]
+            out[c] += (amp / nterms) * (f[2][:, None, None] * f[1][None, :, None] * f[0][None, None, :])
+    return out

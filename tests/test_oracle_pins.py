@@ -228,6 +228,41 @@ def test_bond_matches_all_pairs_brute_force(oracle):
     assert _rel(L, ref) < 1e-13
 
 
+def test_bond_at_sampled_nodes_matches_brute_force(oracle):
+    """The sampled-node sum against a pure-Python all-pairs sum (3D, minimum
+    image, anisotropic spacing) and against the full evaluation."""
+    shape = (6, 7, 8)  # n3, n2, n1
+    delta = 1.9
+    dx = (1.0, 0.8, 0.9)
+    alpha = 0.61
+    g = inputs.rng(8)
+    chi = (g.random(shape) < 0.85).astype(np.uint8)
+    u = g.normal(size=(3,) + shape)
+    nodes = g.choice(chi.size, size=23, replace=False)
+    Ls = oracle.force_bond_at(u, chi, dx, delta, alpha, nodes)
+    n3, n2, n1 = shape
+    ref = np.zeros((3, nodes.size))
+    for k, p in enumerate(nodes):
+        a3, rem = divmod(int(p), n2 * n1)
+        a2, a1 = divmod(rem, n1)
+        if not chi[a3, a2, a1]:
+            continue
+        for b3 in range(n3):
+            for b2 in range(n2):
+                for b1 in range(n1):
+                    d = [(b1 - a1 + n1 // 2) % n1 - n1 // 2, (b2 - a2 + n2 // 2) % n2 - n2 // 2,
+                         (b3 - a3 + n3 // 2) % n3 - n3 // 2]
+                    xi = np.array([d[0] * dx[0], d[1] * dx[1], d[2] * dx[2]])
+                    r = float(np.linalg.norm(xi))
+                    if r == 0 or r > delta or not chi[b3, b2, b1]:
+                        continue
+                    eta = u[:, b3, b2, b1] - u[:, a3, a2, a1]
+                    ref[:, k] += alpha / r * np.outer(xi, xi) / r ** 2 @ eta * dx[0] * dx[1] * dx[2]
+    assert _rel(Ls, ref) < 1e-13
+    full = oracle.force_bond(u, chi, dx, delta, alpha).reshape(3, -1)[:, nodes]
+    assert np.array_equal(Ls, full)
+
+
 def test_bond_dense_operator_spectrum(oracle):
     """Assemble the operator on a tiny body: symmetric, negative semi-definite,
     null space = the 3 rigid motions of a connected 2D body."""
