@@ -202,16 +202,29 @@ struct RowGeom {
     int64_t nrows;  // n2 * n3 (multiple of rows)
     int lgl;        // log2 of the global twiddle table length
     int sched;      // FFT stage schedule (fft_smem)
+    int nstage;     // 2: the next tile's copies overlap this tile's work; 1: no overlap
     int *err;       // device status word (bounded-wait time-outs)
 };
 
-// Bytes of one pipeline stage of a row tile: FB packed-row slots, NF node
+// Bytes of one pipeline stage of a row tile: SB packed-row slots loaded by
+// the stage (the inverse passes' spectra; 0 for forward passes), NF node
 // fields of T and NB byte fields, rounded up to 128 bytes.
 template <typename T>
-__host__ __device__ constexpr size_t row_stage_bytes(int FB, int NF, int NB, int rows, int pitch, int n1)
+__host__ __device__ constexpr size_t row_stage_bytes(int SB, int NF, int NB, int rows, int pitch, int n1)
 {
-    return ((size_t)FB * rows * pitch * sizeof(cx<T>) + (size_t)NF * rows * n1 * sizeof(T) +
+    return ((size_t)SB * rows * pitch * sizeof(cx<T>) + (size_t)NF * rows * n1 * sizeof(T) +
             (((size_t)NB * rows * n1 + 15) & ~(size_t)15) + 127) & ~(size_t)127;
+}
+
+// Shared memory of a row pass: twiddles, a single transform workspace for
+// forward passes (FI = 0), and nstage pipeline stages.
+template <typename T>
+__host__ __device__ constexpr size_t row_smem_bytes(int FI, int FB, int NF, int NB, int rows, int pitch, int n1,
+                                                    int nstage)
+{
+    return (((size_t)n1 * sizeof(cx<T>) + 127) & ~(size_t)127) +
+           (FI > 0 ? 0 : (((size_t)FB * rows * pitch * sizeof(cx<T>) + 127) & ~(size_t)127)) +
+           (size_t)nstage * row_stage_bytes<T>(FI > 0 ? FB : 0, NF, NB, rows, pitch, n1) + 16;
 }
 
 // Shared-memory views handed to the row ops.
@@ -286,12 +299,21 @@ __global__ void __launch_bounds__(256) k_rows(RowGeom g, Op op, const cx<T> *__r
     const int H = 1 << g.lgh, n1 = 2 * H, nt = H >> kLgV, lg1 = g.lgh + 1;
     const int rows = g.rows, pitch = g.pitch;
     const int64_t ntiles = g.nrows / rows;
-    const size_t sbytes = row_stage_bytes<T>(FB, NF, NB, rows, pitch, n1);
+    // forward passes (FI = 0) load no spectra: one transform workspace, and
+    // the stages hold only the node fields
+    constexpr int SB = FI > 0 ? FB : 0;
+    const size_t sbytes = row_stage_bytes<T>(SB, NF, NB, rows, pitch, n1);
     cx<T> *tws = reinterpret_cast<cx<T> *>(smem_raw);
-    unsigned char *stage0 = smem_raw + (((size_t)n1 * sizeof(cx<T>) + 127) & ~(size_t)127);
-    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(stage0 + 2 * sbytes);
-    auto stage_spec = [&](int s) { return reinterpret_cast<cx<T> *>(stage0 + s * sbytes); };
-    auto stage_nf = [&](int s) { return reinterpret_cast<T *>(stage_spec(s) + FB * rows * pitch); };
+    unsigned char *after_tw = smem_raw + (((size_t)n1 * sizeof(cx<T>) + 127) & ~(size_t)127);
+    cx<T> *work = reinterpret_cast<cx<T> *>(after_tw);
+    unsigned char *stage0 =
+        after_tw + (FI > 0 ? 0 : (((size_t)FB * rows * pitch * sizeof(cx<T>) + 127) & ~(size_t)127));
+    const int ns = g.nstage;
+    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(stage0 + ns * sbytes);
+    auto stage_spec = [&](int s) {
+        return FI > 0 ? reinterpret_cast<cx<T> *>(stage0 + s * sbytes) : work;
+    };
+    auto stage_nf = [&](int s) { return reinterpret_cast<T *>(stage0 + s * sbytes + SB * rows * pitch * sizeof(cx<T>)); };
     auto stage_nb = [&](int s) { return reinterpret_cast<uint8_t *>(stage_nf(s) + NF * rows * n1); };
 
     // one thread: bulk copies of tile `tile` into stage s
@@ -315,7 +337,7 @@ __global__ void __launch_bounds__(256) k_rows(RowGeom g, Op op, const cx<T> *__r
 
     if (kLoad && threadIdx.x == 0) {
         mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
+        if (ns == 2) mbar_init(&mbar[1], 1);
     }
     for (int i = threadIdx.x; i < n1; i += blockDim.x) tws[i] = tw[i << (g.lgl - lg1)];
     __syncthreads();
@@ -326,10 +348,11 @@ __global__ void __launch_bounds__(256) k_rows(RowGeom g, Op op, const cx<T> *__r
     typename op_acc<Op>::type acc;
 
     for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
-        const int s = it & 1;
+        const int s = ns == 2 ? (it & 1) : 0;
         const int64_t tn = t + gridDim.x;
-        const bool pre = kLoad && tn < ntiles;
+        const bool pre = kLoad && ns == 2 && tn < ntiles;
         if (pre && threadIdx.x == 0) issue(tn, s ^ 1);
+        if (kLoad && ns == 1 && it > 0 && threadIdx.x == 0) issue(t, 0);
         if constexpr (kLoad) {
             const bool ok = mbar_wait(&mbar[s], (phase >> s) & 1u, g.err);
             phase ^= 1u << s;

@@ -222,6 +222,7 @@ struct pd_plan {
     int tune_rows = 0;     // rows per row-pass block
     int tune_w[2] = {0, 0};  // column-tile width of the x2 / last-axis passes
     int tune_sched = 0;    // FFT stage schedule
+    int tune_stages = 0;   // row-pass pipeline stages (1 or 2; 0: 2)
     int energy_direct = 0; // pd_step_verlet: W by a direct horizon sum (pd_plan_set_energy_mode)
     int64_t prof_n[kKinds] = {};
 };
@@ -249,15 +250,13 @@ inline const cx<double> *tw_buf<double>(const pd_plan *p) { return p->tw64; }
 // fields; two pipeline stages. c.grid is the tile count; launch_rows caps it
 // at the resident blocks (the kernel is persistent).
 template <typename T>
-inline void row_cfg(const pd_plan *p, int FB, int NF, int NB, RowGeom &g, LaunchCfg &c)
+inline void row_cfg(const pd_plan *p, int FI, int FB, int NF, int NB, RowGeom &g, LaunchCfg &c)
 {
     const int H = p->h, nt = H >> kLgV, n1 = 2 * H;
     const int pad = nt < 16 ? (nt < 2 ? 2 : nt) : 0;  // keeps rows 16-byte aligned, spreads banks
     const int pitch = H + pad;
-    auto smem_of = [&](int rows) {
-        return (((size_t)n1 * sizeof(cx<T>) + 127) & ~(size_t)127) +
-               2 * row_stage_bytes<T>(FB, NF, NB, rows, pitch, n1) + 16;
-    };
+    const int ns = p->tune_stages == 1 ? 1 : 2;
+    auto smem_of = [&](int rows) { return row_smem_bytes<T>(FI, FB, NF, NB, rows, pitch, n1, ns); };
     int rows = p->tune_rows > 0 ? p->tune_rows : 128 / nt;
     if (rows < 1) rows = 1;
     while (rows > 1 && rows * nt > 256) rows >>= 1;  // k_rows launch bound
@@ -269,6 +268,7 @@ inline void row_cfg(const pd_plan *p, int FB, int NF, int NB, RowGeom &g, Launch
     g.nrows = p->nrows;
     g.lgl = p->lgl;
     g.sched = p->tune_sched;
+    g.nstage = ns;
     g.err = p->dev_status;
     c.grid = dim3((unsigned)(p->nrows / rows));
     c.block = dim3(rows * nt);
@@ -364,7 +364,7 @@ pd_status launch_rows(pd_plan *p, const Op &op, cudaStream_t st, unsigned *grid_
     LaunchCfg c;
     constexpr int KO = Op::kFout > Op::kStage ? Op::kFout : Op::kStage;
     constexpr int FB = Op::kFin > KO ? Op::kFin : KO;
-    row_cfg<T>(p, FB, Op::kNF, Op::kNB, g, c);
+    row_cfg<T>(p, Op::kFin, FB, Op::kNF, Op::kNB, g, c);
     PD_TRY(set_smem_attr((const void *)k_rows<T, Op>, c.smem));
     int per_sm = 0;
     PD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows<T, Op>, (int)c.block.x, c.smem));

@@ -1,10 +1,11 @@
 // Autotuner for the FFT passes: picks, per plan, the rows per block of the
 // row passes, the tile width of the column passes (x2 and last axis) and the
-// FFT stage schedule (radix-4/2 remainder stage first or last) by timing the
+// FFT stage schedule (radix-4/2 remainder stage first or last) and the row
+// passes' pipeline depth (one or two shared-memory stages) by timing the
 // plan's own force evaluation on its workspace with CUDA events.
 //
 // The search is coordinate-wise from the built-in heuristic: schedule, rows,
-// last-axis width, x2 width; each candidate is timed as the median of five
+// stages, rows again, last-axis width, x2 width; each candidate is timed as the median of five
 // force evaluations after two untimed ones. Candidates are limited to the
 // shapes the passes accept (powers of two; at least one warp per row block;
 // shared memory within the pass's own limit, which the configuration
@@ -100,6 +101,8 @@ pd_status tune_plan(pd_plan *p, cudaStream_t caller)
     for (int r = std::max(1, 32 / nt); r * nt <= 256; r *= 2)
         if (p->nrows % r == 0) rows.push_back(r);
     best_of(&p->tune_rows, rows);
+    best_of(&p->tune_stages, {2, 1});
+    best_of(&p->tune_rows, rows);
     best_of(&p->tune_w[1], {32, 16, 8, 4});
     if (p->dim == 3) best_of(&p->tune_w[0], {32, 16, 8, 4});
     p->prof_on = prof;
@@ -123,16 +126,17 @@ extern "C" pd_status pd_plan_autotune(pd_plan *p, void *stream)
     return tune_plan(p, (cudaStream_t)stream);
 }
 
-extern "C" pd_status pd_plan_tuning(const pd_plan *p, int *out4)
+extern "C" pd_status pd_plan_tuning(const pd_plan *p, int *out5)
 {
-    if (!p || !out4) {
+    if (!p || !out5) {
         set_error("pd_plan_tuning: null argument");
         return PD_ERR_ARG;
     }
-    out4[0] = p->tune_rows;
-    out4[1] = p->tune_w[0];
-    out4[2] = p->tune_w[1];
-    out4[3] = p->tune_sched;
+    out5[0] = p->tune_rows;
+    out5[1] = p->tune_w[0];
+    out5[2] = p->tune_w[1];
+    out5[3] = p->tune_sched;
+    out5[4] = p->tune_stages;
     return PD_OK;
 }
 
@@ -156,6 +160,7 @@ extern "C" pd_status pd_batch_autotune(pd_batch *B, void *stream)
             p->tune_w[0] = it->second->tune_w[0];
             p->tune_w[1] = it->second->tune_w[1];
             p->tune_sched = it->second->tune_sched;
+            p->tune_stages = it->second->tune_stages;
             drop_graphs(p);
         }
     }
@@ -163,24 +168,25 @@ extern "C" pd_status pd_batch_autotune(pd_batch *B, void *stream)
     return PD_OK;
 }
 
-extern "C" pd_status pd_plan_set_tuning(pd_plan *p, const int *in4)
+extern "C" pd_status pd_plan_set_tuning(pd_plan *p, const int *in5)
 {
-    if (!p || !in4) {
+    if (!p || !in5) {
         set_error("pd_plan_set_tuning: null argument");
         return PD_ERR_ARG;
     }
-    const int r = in4[0], wx = in4[1], wl = in4[2], sc = in4[3];
+    const int r = in5[0], wx = in5[1], wl = in5[2], sc = in5[3], ns = in5[4];
     auto pow2_or_zero = [](int v) { return v == 0 || (v > 0 && (v & (v - 1)) == 0); };
     if (!pow2_or_zero(r) || r > 256 || !pow2_or_zero(wx) || wx > 32 || !pow2_or_zero(wl) || wl > 32 ||
-        (sc != 0 && sc != 1)) {
+        (sc != 0 && sc != 1) || ns < 0 || ns > 2) {
         set_error("pd_plan_set_tuning: rows and widths must be 0 or powers of two (rows <= 256, widths <= 32), "
-                  "schedule 0 or 1");
+                  "schedule 0 or 1, stages 0, 1 or 2");
         return PD_ERR_ARG;
     }
     p->tune_rows = r;
     p->tune_w[0] = wx;
     p->tune_w[1] = wl;
     p->tune_sched = sc;
+    p->tune_stages = ns;
     drop_graphs(p);
     return PD_OK;
 }
