@@ -222,18 +222,31 @@ struct EpiCG {
     {
         const int k0 = goff[c.row0], k1 = goff[c.row0 + c.rows];
         const int l1 = __ffs(n1) - 1;
-        for (int k = k0 + tid; k < k1; k += nthreads) {
-            const GEntry<T> e = gent[k];
-            T pp[D], Gp[D];
+        constexpr int U = 4;  // entries in flight per thread
+        for (int kb = k0 + tid; kb < k1; kb += U * nthreads) {
+            GEntry<T> e[U];
+            T pp[U][D];
 #pragma unroll
-            for (int qd = 0; qd < D; ++qd) {
-                pp[qd] = pv[qd * N + e.p];
-                Gp[qd] = T(0);
+            for (int j = 0; j < U; ++j)
+                if (kb + j * nthreads < k1) e[j] = gent[kb + j * nthreads];
+#pragma unroll
+            for (int j = 0; j < U; ++j)
+                if (kb + j * nthreads < k1) {
+#pragma unroll
+                    for (int qd = 0; qd < D; ++qd) pp[j][qd] = pv[qd * N + e[j].p];
+                }
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                if (kb + j * nthreads >= k1) break;
+                const int64_t p = e[j].p;
+                const int rl = (int)((p >> l1) - c.row0), i1 = (int)(p & (n1 - 1));
+                T Gp[D];
+#pragma unroll
+                for (int qd = 0; qd < D; ++qd) Gp[qd] = T(0);
+                sym_apply<T, D>(e[j].g, pp[j], Gp);
+#pragma unroll
+                for (int i = 0; i < D; ++i) c.stage(i, rl, i1) -= Gp[i];
             }
-            sym_apply<T, D>(e.g, pp, Gp);
-            const int rl = (int)((e.p >> l1) - c.row0), i1 = (int)(e.p & (n1 - 1));
-#pragma unroll
-            for (int i = 0; i < D; ++i) c.stage(i, rl, i1) -= Gp[i];
         }
     }
     __device__ __forceinline__ void emit(const RowCtx<T> &c, int rl, int i1, const T *s0, const T *s1,

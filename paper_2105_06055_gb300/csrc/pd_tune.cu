@@ -1,17 +1,17 @@
 // Autotuner for the FFT passes: picks, per plan, the rows per block of the
-// row passes, the tile width of the column passes (x2 and last axis) and the
-// FFT stage schedule (radix-4/2 remainder stage first or last) and the row
-// passes' pipeline depth (one or two shared-memory stages) by timing the
-// plan's own force evaluation on its workspace with CUDA events.
+// row passes, their pipeline depth (one or two shared-memory stages), the
+// tile width of the column passes (x2 and last axis) and the FFT stage
+// schedule (radix-4/2 remainder stage first or last) by timing the plan's own
+// force evaluation on its workspace with CUDA events.
 //
 // The search is coordinate-wise from the built-in heuristic: schedule, rows,
-// stages, rows again, last-axis width, x2 width; each candidate is timed as the median of five
-// force evaluations after two untimed ones. Candidates are limited to the
-// shapes the passes accept (powers of two; at least one warp per row block;
-// shared memory within the pass's own limit, which the configuration
-// functions enforce by shrinking the candidate). The transforms compute the
-// same values for every candidate (only the order of block partial sums in
-// the solvers' inner products changes).
+// stages, rows again, last-axis width, x2 width; each candidate is timed as
+// the median of nine force evaluations after three untimed ones. Candidates
+// are limited to the shapes the passes accept (powers of two; at least one
+// warp per row block; shared memory within the pass's own limit, which the
+// configuration functions enforce by shrinking the candidate). The
+// transforms compute the same values for every candidate (only the order of
+// block partial sums in the solvers' inner products changes).
 #include <algorithm>
 #include <map>
 #include <tuple>
@@ -43,9 +43,9 @@ pd_status time_force(pd_plan *p, cudaEvent_t e0, cudaEvent_t e1, float *ms_out)
     cudaStream_t st = p->own_stream;
     const T *u = (const T *)p->cg_e;
     T *L = (T *)p->cg_q;
-    for (int k = 0; k < 2; ++k) PD_TRY(force_plain<T>(p, u, nullptr, L, nullptr, st));
+    for (int k = 0; k < 3; ++k) PD_TRY(force_plain<T>(p, u, nullptr, L, nullptr, st));
     std::vector<float> t;
-    for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < 9; ++k) {
         PD_CUDA_TRY(cudaEventRecord(e0, st));
         PD_TRY(force_plain<T>(p, u, nullptr, L, nullptr, st));
         PD_CUDA_TRY(cudaEventRecord(e1, st));
@@ -55,7 +55,7 @@ pd_status time_force(pd_plan *p, cudaEvent_t e0, cudaEvent_t e1, float *ms_out)
         t.push_back(ms);
     }
     std::sort(t.begin(), t.end());
-    *ms_out = t[2];
+    *ms_out = t[4];
     return PD_OK;
 }
 
