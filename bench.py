@@ -131,19 +131,20 @@ MEASURED_TRAFFIC = {}
 def pass_bytes(kind, N, nbound, d=3, nc=6):
     """Algorithmic bytes of one launch of each FP32 pass of the fused CG
     iteration (d = 3 components; a packed half spectrum holds 4 bytes per node).
-      rows_fwd : read r, p (8d), chi (1); write p (4d) and d spectra (4d)
+      rows_fwd : read e, r, p, q (16d), mask bits (1); write e, r, p (12d) and
+                 d spectra (4d)
       cols_x2  : read + write d spectra
       last_axis: read + write d spectra, folded kernel table (nc floats per
                  folded mode, (n/2+1)^3 ~ N/8 modes)
-      rows_inv : read d spectra (4d), p (4d), chi (1), chi_Omega (d); write q
-                 (4d); boundary list (32 B per boundary node)"""
+      rows_inv : read d spectra (4d), p, r (8d), mask bits (1); write q (4d);
+                 boundary list (32 B per boundary node) and p there (4d)"""
     per_node = {
-        "rows_fwd": 16 * d + 1,
+        "rows_fwd": 32 * d + 1,
         "cols_x2": 8 * d,
         "last_axis": 8 * d + nc * 4 / 8.0,
-        "rows_inv": 12 * d + 1 + d,
+        "rows_inv": 16 * d + 1,
     }[kind]
-    extra = 32 * nbound if kind == "rows_inv" else 0
+    extra = (32 + 4 * d) * nbound if kind == "rows_inv" else 0
     return per_node * N + extra
 
 
