@@ -1,11 +1,12 @@
 // Autotuner for the FFT passes: picks, per plan, the rows per block of the
-// row passes, their pipeline depth (one or two shared-memory stages), the
+// row passes, their pipeline depth (one or two shared-memory stages) and
+// thread count (1, 2 or 4 threads per FFT thread), the
 // tile width of the column passes (x2 and last axis) and the FFT stage
 // schedule (radix-4/2 remainder stage first or last) by timing the plan's own
 // force evaluation on its workspace with CUDA events.
 //
 // The search is coordinate-wise from the built-in heuristic: schedule, rows,
-// stages, rows again, last-axis width, x2 width; each candidate is timed as
+// stages, threads, rows again, last-axis width, x2 width; each candidate is timed as
 // the median of nine force evaluations after three untimed ones. Candidates
 // are limited to the shapes the passes accept (powers of two; at least one
 // warp per row block; shared memory within the pass's own limit, which the
@@ -102,6 +103,7 @@ pd_status tune_plan(pd_plan *p, cudaStream_t caller)
         if (p->nrows % r == 0) rows.push_back(r);
     best_of(&p->tune_rows, rows);
     best_of(&p->tune_stages, {2, 1});
+    best_of(&p->tune_mult, {1, 2, 4});
     best_of(&p->tune_rows, rows);
     best_of(&p->tune_w[1], {32, 16, 8, 4});
     if (p->dim == 3) best_of(&p->tune_w[0], {32, 16, 8, 4});
@@ -126,17 +128,18 @@ extern "C" pd_status pd_plan_autotune(pd_plan *p, void *stream)
     return tune_plan(p, (cudaStream_t)stream);
 }
 
-extern "C" pd_status pd_plan_tuning(const pd_plan *p, int *out5)
+extern "C" pd_status pd_plan_tuning(const pd_plan *p, int *out6)
 {
-    if (!p || !out5) {
+    if (!p || !out6) {
         set_error("pd_plan_tuning: null argument");
         return PD_ERR_ARG;
     }
-    out5[0] = p->tune_rows;
-    out5[1] = p->tune_w[0];
-    out5[2] = p->tune_w[1];
-    out5[3] = p->tune_sched;
-    out5[4] = p->tune_stages;
+    out6[0] = p->tune_rows;
+    out6[1] = p->tune_w[0];
+    out6[2] = p->tune_w[1];
+    out6[3] = p->tune_sched;
+    out6[4] = p->tune_stages;
+    out6[5] = p->tune_mult;
     return PD_OK;
 }
 
@@ -161,6 +164,7 @@ extern "C" pd_status pd_batch_autotune(pd_batch *B, void *stream)
             p->tune_w[1] = it->second->tune_w[1];
             p->tune_sched = it->second->tune_sched;
             p->tune_stages = it->second->tune_stages;
+            p->tune_mult = it->second->tune_mult;
             drop_graphs(p);
         }
     }
@@ -168,18 +172,18 @@ extern "C" pd_status pd_batch_autotune(pd_batch *B, void *stream)
     return PD_OK;
 }
 
-extern "C" pd_status pd_plan_set_tuning(pd_plan *p, const int *in5)
+extern "C" pd_status pd_plan_set_tuning(pd_plan *p, const int *in6)
 {
-    if (!p || !in5) {
+    if (!p || !in6) {
         set_error("pd_plan_set_tuning: null argument");
         return PD_ERR_ARG;
     }
-    const int r = in5[0], wx = in5[1], wl = in5[2], sc = in5[3], ns = in5[4];
+    const int r = in6[0], wx = in6[1], wl = in6[2], sc = in6[3], ns = in6[4], mu = in6[5];
     auto pow2_or_zero = [](int v) { return v == 0 || (v > 0 && (v & (v - 1)) == 0); };
     if (!pow2_or_zero(r) || r > 256 || !pow2_or_zero(wx) || wx > 32 || !pow2_or_zero(wl) || wl > 32 ||
-        (sc != 0 && sc != 1) || ns < 0 || ns > 2) {
+        (sc != 0 && sc != 1) || ns < 0 || ns > 2 || !pow2_or_zero(mu) || mu > 4) {
         set_error("pd_plan_set_tuning: rows and widths must be 0 or powers of two (rows <= 256, widths <= 32), "
-                  "schedule 0 or 1, stages 0, 1 or 2");
+                  "schedule 0 or 1, stages 0, 1 or 2, thread multiple 0, 1, 2 or 4");
         return PD_ERR_ARG;
     }
     p->tune_rows = r;
@@ -187,6 +191,7 @@ extern "C" pd_status pd_plan_set_tuning(pd_plan *p, const int *in5)
     p->tune_w[1] = wl;
     p->tune_sched = sc;
     p->tune_stages = ns;
+    p->tune_mult = mu;
     drop_graphs(p);
     return PD_OK;
 }
