@@ -534,10 +534,15 @@ pd_status capture_graph_of(cudaStream_t st, cudaGraph_t *g)
 
 // Enqueue one specimen's whole solve on `st` (capturing); bs, bs2: idle
 // helper streams for the conditional bodies.
+struct DrLaunches {
+    int64_t pre = 0, chunk = 0, cycle = 0;  // kernels before the loop, per WHILE pass, per refinement block
+};
+
 pd_status capture_specimen(const DrSpec &S, double rtol, double max_steps, cudaStream_t st, cudaStream_t bs,
-                           cudaStream_t bs2)
+                           cudaStream_t bs2, DrLaunches *cnt)
 {
     pd_plan *p = S.p;
+    const int64_t l0 = p->launches;
     const double rho_inv = 1.0 / (0.25 * 1.05 * p->lam_max);
     k_dr_start<<<1, 1, 0, st>>>(p->red, rho_inv, max_steps);
     PD_LAUNCH_CHECK();
@@ -557,6 +562,8 @@ pd_status capture_specimen(const DrSpec &S, double rtol, double max_steps, cudaS
     PD_TRY(S.reset_any(st));
     cudaGraph_t wbody = nullptr;
     PD_TRY(add_conditional(st, hw, cudaGraphCondTypeWhile, &wbody));
+    cnt->pre = p->launches - l0 + 2;  // + start and check kernels
+    const int64_t l1 = p->launches;
 
     // WHILE body: K steps, cycle check, IF(cycle over) { refinement }
     PD_CUDA_TRY(cudaStreamBeginCaptureToGraph(bs, wbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
@@ -574,6 +581,8 @@ pd_status capture_specimen(const DrSpec &S, double rtol, double max_steps, cudaS
             s = PD_ERR_CUDA;
         }
     }
+    cnt->chunk = p->launches - l1 + 1;  // + check kernel
+    const int64_t l2 = p->launches;
     if (s == PD_OK) s = add_conditional(bs, hif, cudaGraphCondTypeIf, &ibody);
     if (s == PD_OK) {
         if (cudaStreamBeginCaptureToGraph(bs2, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
@@ -599,6 +608,8 @@ pd_status capture_specimen(const DrSpec &S, double rtol, double max_steps, cudaS
             }
         }
     }
+    cnt->cycle = p->launches - l2 + 1;  // + check kernel
+    p->launches = l0;                  // captured, not yet run
     cudaGraph_t dummy = nullptr;
     const cudaError_t e1 = cudaStreamEndCapture(bs, &dummy);
     if (s == PD_OK && e1 != cudaSuccess) {
@@ -622,6 +633,7 @@ struct DrRunner {
     double key_rtol = 0.0;
     int key_iter = 0;
     double *host = nullptr;  // pinned, plans.size() x R_COUNT
+    std::vector<DrLaunches> counts;
 
     pd_status init(const std::vector<pd_plan *> &ps)
     {
@@ -664,6 +676,7 @@ struct DrRunner {
             exec = nullptr;
         }
         std::vector<int> prof(n);
+        counts.assign(n, DrLaunches());
         for (size_t i = 0; i < n; ++i) {
             prof[i] = plans[i]->prof_on;
             plans[i]->prof_on = 0;  // no event nodes inside conditional bodies
@@ -684,7 +697,7 @@ struct DrRunner {
                 }
                 DrSpec S{p, u[i], b[i], w ? w[i] : nullptr, (int64_t)p->dim * p->N, 0};
                 S.nb = (unsigned)std::min<int64_t>(kUpdBlocks, (S.nvec + 255) / 256);
-                s = capture_specimen(S, rtol, msteps, p->own_stream, bs, bs2);
+                s = capture_specimen(S, rtol, msteps, p->own_stream, bs, bs2, &counts[i]);
                 if (s == PD_OK && (cudaEventRecord(ev_join[i], p->own_stream) != cudaSuccess ||
                                    cudaStreamWaitEvent(ms, ev_join[i], 0) != cudaSuccess))
                     s = PD_ERR_CUDA;
@@ -733,8 +746,8 @@ struct DrRunner {
             const double *h = host + i * R_COUNT;
             const int st = (int)h[R_STATUS];
             pd_plan *p = plans[i];
-            const int per = p->state_based ? 3 : (p->dim == 3 ? 6 : 4);
-            p->launches += (int64_t)h[R_STEPS] * per + (int64_t)h[R_CYCLES] * 12;
+            const DrLaunches &c = counts[i];
+            p->launches += c.pre + (int64_t)h[R_STEPS] / kDrChunk * c.chunk + (int64_t)h[R_CYCLES] * c.cycle;
             pd_status r = PD_OK;
             switch (st) {
                 case DR_CONVERGED: r = PD_OK; break;

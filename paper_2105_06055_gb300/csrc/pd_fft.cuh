@@ -495,6 +495,8 @@ struct ColGeom {
     int lb;      // rows per TMA box (<= 256, divides L)
     int outer;   // outer extent: n3 for the x2 pass, 1 for the last axis
     int sched;   // FFT stage schedule (fft_smem)
+    int tmode;   // tiles: 0 all (c0 = block w), 1 3D last axis without the kx = 0
+                 // tiles, 2 3D last axis, only the kx = 0 tiles (with mirror)
     int *err;    // device status word (bounded-wait time-outs)
 };
 
@@ -529,16 +531,23 @@ __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__r
     const int L = 1 << g.lgl;
     const int w = g.w, ncol = w + g.mirror;  // threads: ncol x (L / kV)
     const int col = threadIdx.x % ncol, jt = threadIdx.x / ncol;
-    const int c0 = blockIdx.x * w;
-    const int o = blockIdx.y;
     const int H = 1 << g.lgh;
+    int c0;
+    if (g.tmode == 1) {
+        const int per = (H >> g.lgw) - 1;  // tiles of a k2 row after its kx = 0 tile
+        c0 = ((int)blockIdx.x / per) * H + w * (1 + (int)blockIdx.x % per);
+    } else {
+        c0 = g.tmode == 2 ? (int)blockIdx.x * H : (int)blockIdx.x * w;
+    }
+    const int o = blockIdx.y;
     const int nthreads = blockDim.x;
     const int fsz = L * w;
     cx<T> *tws = reinterpret_cast<cx<T> *>(smem_raw);  // W_L^i, i < L
     cx<T> *tile = tws + L;
     cx<T> *mir = tile + FB * fsz;
     constexpr int NTAB = (MODE == 2) ? Op::kTab : 0;
-    const int trows = L / 2 + 1, tcols = w + 1, tcs = trows * tcols;  // table slice [comp][fold row][kx]
+    // table slice [comp][fold row][kx]; the kx = n1/2 column only where the tile holds kx = 0
+    const int trows = L / 2 + 1, tcols = w + (g.tmode == 1 ? 0 : 1), tcs = trows * tcols;
     T *tab = reinterpret_cast<T *>(mir + (g.mirror ? FI * L * 2 : 0));
     unsigned long long *mbar = reinterpret_cast<unsigned long long *>(tab + ((NTAB * tcs + 1) & ~1));
 

@@ -214,6 +214,7 @@ struct pd_plan {
     cudaGraphExec_t cg_graph[2] = {nullptr, nullptr};
     int cg_graph_prof[2] = {0, 0};
     int cg_graph_ev[2][2] = {{0, 0}, {0, 0}};
+    int64_t cg_graph_launches[2] = {0, 0};  // kernel launches per replay
     double *host_scal = nullptr;    // pinned host copy of the solver scalars
     cudaStream_t own_stream = nullptr;  // plan stream for captured work (never the legacy stream)
     cudaEvent_t ev_join[2] = {nullptr, nullptr};
@@ -279,23 +280,28 @@ inline void row_cfg(const pd_plan *p, int FI, int FB, int NF, int NB, RowGeom &g
 }
 
 // Column-pass configuration: axis 1 = x2, axis 2 = x3 (3D); FB fields in the
-// tile, FI of them with a mirror column.
+// tile, FI of them with a mirror column. The 3D last-axis pass runs as two
+// launches with one tile width: tmode 1 (tiles without kx = 0: no mirror
+// column, no kx = n1/2 table column) and tmode 2 (the kx = 0 tile of each k2
+// row, with the mirror column of -k2).
 template <typename T>
-inline void col_cfg(const pd_plan *p, int axis, bool last, int FB, int FI, int NTAB, ColGeom &g, LaunchCfg &c,
-                    int64_t &inner)
+inline void col_cfg(const pd_plan *p, int axis, bool last, int FB, int FI, int NTAB, int tmode, ColGeom &g,
+                    LaunchCfg &c, int64_t &inner)
 {
     const int H = p->h;
     const int L = axis == 1 ? p->n2 : p->n3;
     const int nt = L >> kLgV;
-    const int mirror = (p->dim == 3 && last) ? 1 : 0;
+    const bool split = p->dim == 3 && last;
+    const int wmirror = split ? 1 : 0;  // the width must also fit the kx = 0 tiles
+    const int mirror = tmode == 2 ? 1 : 0;
     inner = axis == 1 ? (int64_t)H : (int64_t)p->n2 * H;
-    auto smem_of = [&](int w) {
-        const size_t tab = (((size_t)NTAB * (L / 2 + 1) * (w + 1) + 1) & ~(size_t)1) * sizeof(T);
+    auto smem_of = [&](int w, int mir, int tc) {
+        const size_t tab = (((size_t)NTAB * (L / 2 + 1) * tc + 1) & ~(size_t)1) * sizeof(T);
         return (size_t)L * sizeof(cx<T>) + (size_t)FB * L * w * sizeof(cx<T>) +
-               (mirror ? (size_t)FI * L * 2 * sizeof(cx<T>) : 0) + tab + 16;
+               (mir ? (size_t)FI * L * 2 * sizeof(cx<T>) : 0) + tab + 16;
     };
     int w = p->tune_w[last ? 1 : 0] > 0 ? p->tune_w[last ? 1 : 0] : 32;
-    while (w > 2 && ((w + mirror) * nt > 512 || smem_of(w) > 100 * 1024 || (H % w))) w >>= 1;
+    while (w > 2 && ((w + wmirror) * nt > 512 || smem_of(w, wmirror, w + 1) > 100 * 1024 || (H % w))) w >>= 1;
     g.lgl = ilog2(L);
     g.w = w;
     g.lgw = ilog2(w);
@@ -306,10 +312,13 @@ inline void col_cfg(const pd_plan *p, int axis, bool last, int FB, int FI, int N
     g.lb = L < 256 ? L : 256;
     g.outer = axis == 1 ? p->n3 : 1;
     g.sched = p->tune_sched;
+    g.tmode = split ? tmode : 0;
     g.err = p->dev_status;
-    c.grid = dim3((unsigned)(inner / w), (unsigned)g.outer);
+    unsigned gx = (unsigned)(inner / w);
+    if (split) gx = tmode == 2 ? (unsigned)p->n2 : (unsigned)(p->n2 * (H / w - 1));
+    c.grid = dim3(gx, (unsigned)g.outer);
     c.block = dim3((w + mirror) * nt);
-    c.smem = smem_of(w);
+    c.smem = smem_of(w, mirror, w + (split && tmode == 1 ? 0 : 1));
 }
 
 pd_status set_smem_attr(const void *func, size_t smem);
@@ -397,26 +406,30 @@ constexpr int op_tab()
 template <typename T, class Op>
 pd_status launch_cols(pd_plan *p, const Op &op, int axis, bool last, int F, cudaStream_t st)
 {
-    ColGeom g;
-    LaunchCfg c;
-    int64_t inner = 0;
-    col_cfg<T>(p, axis, last, F, Op::kFin, Op::kMode == 2 ? op_tab<Op>() : 0, g, c, inner);
-    const int L = 1 << g.lgl;
-    const unsigned long long dims[3] = {(unsigned long long)(2 * inner), (unsigned long long)L,
-                                        (unsigned long long)g.outer * spec_slots<T>(p)};
-    const unsigned long long strides[2] = {(unsigned long long)(2 * inner * sizeof(T)),
-                                           (unsigned long long)(2 * inner * L * sizeof(T))};
-    const unsigned box_t[3] = {(unsigned)(2 * g.w), (unsigned)g.lb, 1u};
-    const unsigned box_m[3] = {4u, (unsigned)g.lb, 1u};
-    CUtensorMap tmt, tmm;
-    PD_TRY(encode_tmap_3d(&tmt, spec_buf<T>(p), sizeof(T) == 8, dims, strides, box_t));
-    PD_TRY(encode_tmap_3d(&tmm, spec_buf<T>(p), sizeof(T) == 8, dims, strides, box_m));
-    PD_TRY(set_smem_attr((const void *)k_cols<T, Op>, c.smem));
+    const bool split = p->dim == 3 && last;
     PD_TRY(prof_begin(p, last ? PASS_LAST : PASS_COLS, st));
-    k_cols<T, Op><<<c.grid, c.block, c.smem, st>>>(g, op, tw_buf<T>(p), axis == 2 ? 1 : 0, tmt, tmm);
-    PD_LAUNCH_CHECK();
+    for (int tmode = split ? 1 : 0; tmode <= (split ? 2 : 0); ++tmode) {
+        ColGeom g;
+        LaunchCfg c;
+        int64_t inner = 0;
+        col_cfg<T>(p, axis, last, F, Op::kFin, Op::kMode == 2 ? op_tab<Op>() : 0, tmode, g, c, inner);
+        if (c.grid.x == 0) continue;  // one tile per k2 row: no tmode-1 tiles
+        const int L = 1 << g.lgl;
+        const unsigned long long dims[3] = {(unsigned long long)(2 * inner), (unsigned long long)L,
+                                            (unsigned long long)g.outer * spec_slots<T>(p)};
+        const unsigned long long strides[2] = {(unsigned long long)(2 * inner * sizeof(T)),
+                                               (unsigned long long)(2 * inner * L * sizeof(T))};
+        const unsigned box_t[3] = {(unsigned)(2 * g.w), (unsigned)g.lb, 1u};
+        const unsigned box_m[3] = {4u, (unsigned)g.lb, 1u};
+        CUtensorMap tmt, tmm;
+        PD_TRY(encode_tmap_3d(&tmt, spec_buf<T>(p), sizeof(T) == 8, dims, strides, box_t));
+        PD_TRY(encode_tmap_3d(&tmm, spec_buf<T>(p), sizeof(T) == 8, dims, strides, box_m));
+        PD_TRY(set_smem_attr((const void *)k_cols<T, Op>, c.smem));
+        k_cols<T, Op><<<c.grid, c.block, c.smem, st>>>(g, op, tw_buf<T>(p), axis == 2 ? 1 : 0, tmt, tmm);
+        PD_LAUNCH_CHECK();
+        p->launches++;
+    }
     PD_TRY(prof_end(p, st));
-    p->launches++;
     return PD_OK;
 }
 

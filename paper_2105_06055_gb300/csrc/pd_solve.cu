@@ -386,6 +386,7 @@ struct Solver {
         if (!p->cg_graph[gi]) {
             if (p->prof_on) PD_TRY(prof_harvest(p));
             const int ev0 = p->ev_used;
+            const int64_t l0 = p->launches;  // launches recorded by the capture = launches per replay
             cudaGraph_t graph = nullptr;
             PD_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
             pd_status s = PD_OK;
@@ -410,10 +411,12 @@ struct Solver {
             p->cg_graph_prof[gi] = p->prof_on;
             p->cg_graph_ev[gi][0] = ev0;
             p->cg_graph_ev[gi][1] = p->ev_used;
+            p->cg_graph_launches[gi] = p->launches - l0;
+            p->launches = l0;
             p->ev_reserved = p->ev_used;  // keep the graph's event pairs
         }
         PD_CUDA_TRY(cudaGraphLaunch(p->cg_graph[gi], st));
-        p->launches += (int64_t)kChunk * (p->state_based ? 13 : (D == 3 ? 6 : 4));
+        p->launches += p->cg_graph_launches[gi];
         PD_CUDA_TRY(cudaStreamSynchronize(st));
         if (p->prof_on) PD_TRY(prof_harvest_range(p, p->cg_graph_ev[gi][0], p->cg_graph_ev[gi][1]));
         return PD_OK;

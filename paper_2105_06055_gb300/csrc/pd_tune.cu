@@ -1,12 +1,11 @@
 // Autotuner for the FFT passes: picks, per plan, the rows per block of the
-// row passes, their pipeline depth (one or two shared-memory stages) and
-// thread count (1, 2 or 4 threads per FFT thread), the
+// row passes and their pipeline depth (one or two shared-memory stages), the
 // tile width of the column passes (x2 and last axis) and the FFT stage
 // schedule (radix-4/2 remainder stage first or last) by timing the plan's own
 // force evaluation on its workspace with CUDA events.
 //
-// The search is coordinate-wise from the built-in heuristic: schedule, rows,
-// stages, threads, rows again, last-axis width, x2 width; each candidate is timed as
+// The search covers rows x stages jointly, then the schedule, the last-axis
+// width and the x2 width one at a time; each candidate is timed as
 // the median of nine force evaluations after three untimed ones. Candidates
 // are limited to the shapes the passes accept (powers of two; at least one
 // warp per row block; shared memory within the pass's own limit, which the
@@ -93,18 +92,34 @@ pd_status tune_plan(pd_plan *p, cudaStream_t caller)
         }
         *knob = best;
     };
-    // schedule: only lengths that are not powers of 8 have a remainder stage
+    // rows per tile and pipeline depth jointly (they interact through shared
+    // memory), then the schedule and the column widths one at a time
     const int H = p->h;
+    const int nt = H >> kLgV;
+    {
+        float tbest = 1e30f;
+        int rbest = p->tune_rows, sbest = p->tune_stages;
+        for (int r = std::max(1, 32 / nt); r * nt <= 256 && s == PD_OK; r *= 2) {
+            if (p->nrows % r) continue;
+            for (int ns : {2, 1}) {
+                p->tune_rows = r;
+                p->tune_stages = ns;
+                float ms = 0.f;
+                s = time_cfg(p, e0, e1, &ms);
+                if (s != PD_OK) break;
+                if (ms < tbest) {
+                    tbest = ms;
+                    rbest = r;
+                    sbest = ns;
+                }
+            }
+        }
+        p->tune_rows = rbest;
+        p->tune_stages = sbest;
+    }
+    // schedule: only lengths that are not powers of 8 have a remainder stage
     const bool rem = (ilog2(H) % kLgV) || (ilog2(p->n2) % kLgV) || (p->dim == 3 && (ilog2(p->n3) % kLgV));
     if (rem) best_of(&p->tune_sched, {0, 1});
-    const int nt = H >> kLgV;
-    std::vector<int> rows;
-    for (int r = std::max(1, 32 / nt); r * nt <= 256; r *= 2)
-        if (p->nrows % r == 0) rows.push_back(r);
-    best_of(&p->tune_rows, rows);
-    best_of(&p->tune_stages, {2, 1});
-    best_of(&p->tune_mult, {1, 2, 4});
-    best_of(&p->tune_rows, rows);
     best_of(&p->tune_w[1], {32, 16, 8, 4});
     if (p->dim == 3) best_of(&p->tune_w[0], {32, 16, 8, 4});
     p->prof_on = prof;
