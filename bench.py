@@ -9,8 +9,8 @@ b1 = sigma/delta (sigma = 1e-3) on the three layers at the x1-high face.
 One step = one complete static solve from u = 0 to a relative FP64 residual of
 1e-8: FP32 FFT-convolution CG with FP64 inner products inside FP64 iterative
 refinement (pd_solve_static). The plan's pass configuration is picked by the
-library's autotuner (pd_plan_autotune) before the warm-up, unless
---no-autotune.
+library's autotuner timing the solver's own CG iterations
+(pd_plan_autotune_solve) before the warm-up, unless --no-autotune.
 
 Metric: force evaluations x nodes per second (each CG iteration and each FP64
 residual is one evaluation of the PD operator on all 128^3 nodes), plus the
@@ -172,7 +172,7 @@ def run_native(args, rank, world):
         plan.set_tuning(*[int(v) for v in args.tuning.split(",")])
         tuning = plan.tuning
     else:
-        tuning = None if args.no_autotune else plan.autotune()
+        tuning = None if args.no_autotune else plan.autotune(solve=True)
     b = torch.tensor(cfg["b"], dtype=torch.float64, device=dev)
     u = torch.zeros((3,) + shape, dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
@@ -544,7 +544,7 @@ def main():
         if args.tuning:
             plan.set_tuning(*[int(v) for v in args.tuning.split(",")])
         elif not args.no_autotune:
-            plan.autotune()
+            plan.autotune(solve=True)
         u = torch.zeros((3,) + cfg["shape"], dtype=torch.float64, device=dev)
         it, rel, _ = plan.solve_static(u, torch.tensor(cfg["b"], dtype=torch.float64, device=dev), None,
                                        rtol=RTOL, max_iter=args.profile_solve, raise_on_fail=False)

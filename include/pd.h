@@ -252,6 +252,10 @@ void pd_batch_destroy(pd_batch *batch);
  * thread multiple} (0 = heuristic) to out6.
  */
 pd_status pd_plan_autotune(pd_plan *plan, void *stream);
+/* The same search timing a chunk of 16 iterations of the static solver's CG
+ * (pd_solve_static's unit of work) instead of a force evaluation; uses the
+ * plan's solver workspace. */
+pd_status pd_plan_autotune_solve(pd_plan *plan, void *stream);
 pd_status pd_batch_autotune(pd_batch *batch, void *stream);
 pd_status pd_plan_tuning(const pd_plan *plan, int *out6);
 /* Pin a pass configuration {rows, x2 width, last-axis width, schedule,

@@ -29,6 +29,7 @@
 // each chunk.
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "pd_force_impl.cuh"
 #include "pd_solver_common.cuh"
@@ -470,6 +471,65 @@ struct Solver {
 }  // namespace pd
 
 using namespace pd;
+
+namespace pd {
+namespace {
+
+// r64 = chi_O sin(2 pi (i1 + 2 i2 + 3 i3) / 64): a fixed right-hand side for timing
+__global__ void k_tune_rhs(double *r, const uint8_t *co, int n1, int n2, int64_t N, int d)
+{
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (int64_t)d * N;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = q % N;
+        int i1, i2, i3;
+        node_coords(p, n1, n2, i1, i2, i3);
+        r[q] = co[q] ? sinpi((double)(i1 + 2 * i2 + 3 * i3 + (int)(q / N)) / 32.0) : 0.0;
+    }
+}
+
+}  // namespace
+
+// Time of one captured chunk of CG iterations (the static solver's unit of
+// work) in the plan's current pass configuration; for the autotuner.
+pd_status time_cg_chunk(pd_plan *p, cudaEvent_t e0, cudaEvent_t e1, float *ms_out)
+{
+    Solver S;
+    S.p = p;
+    S.st = p->own_stream;
+    S.nvec = (int64_t)p->dim * p->N;
+    S.nb = (unsigned)std::min<int64_t>(kUpdBlocks, (S.nvec + 255) / 256);
+    k_tune_rhs<<<S.nb, 256, 0, S.st>>>(p->r64, p->chi_om, p->n1, p->n2, p->N, p->dim);
+    PD_LAUNCH_CHECK();
+    std::vector<float> t;
+    for (int rep = 0; rep < 4; ++rep) {
+        // restart from the same state; the first replay also captures the graph
+        if (p->prob.fp64) {
+            k_cg_init<double><<<S.nb, 256, 0, S.st>>>(p->r64, (double *)p->cg_r, (double *)p->cg_p,
+                                                      (double *)p->cg_e, (double *)p->cg_q, S.nvec, p->red);
+        } else {
+            k_cg_init<float><<<S.nb, 256, 0, S.st>>>(p->r64, (float *)p->cg_r, (float *)p->cg_p,
+                                                     (float *)p->cg_e, (float *)p->cg_q, S.nvec, p->red);
+        }
+        PD_LAUNCH_CHECK();
+        PD_TRY(S.finish(S.nb, S_RR, 0));
+        PD_CUDA_TRY(cudaMemsetAsync(p->red + kRedScal + S_ALPHA, 0, 2 * sizeof(double), S.st));
+        PD_CUDA_TRY(cudaEventRecord(e0, S.st));
+        if (p->prob.fp64)
+            PD_TRY(p->dim == 3 ? (S.chunk<double, 3>()) : (S.chunk<double, 2>()));
+        else
+            PD_TRY(p->dim == 3 ? (S.chunk<float, 3>()) : (S.chunk<float, 2>()));
+        PD_CUDA_TRY(cudaEventRecord(e1, S.st));
+        PD_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        PD_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0) t.push_back(ms);
+    }
+    std::sort(t.begin(), t.end());
+    *ms_out = t[t.size() / 2];
+    return PD_OK;
+}
+
+}  // namespace pd
 
 extern "C" pd_status pd_solve_static(pd_plan *p, double *u, const double *b, const double *w, double rtol,
                                      int max_iter, int *iters_out, double *relres_out, void *stream)

@@ -2,7 +2,8 @@
 // row passes and their pipeline depth (one or two shared-memory stages), the
 // tile width of the column passes (x2 and last axis) and the FFT stage
 // schedule (radix-4/2 remainder stage first or last) by timing the plan's own
-// force evaluation on its workspace with CUDA events.
+// force evaluation (pd_plan_autotune) or a chunk of its static solver's CG
+// iterations (pd_plan_autotune_solve) on its workspace with CUDA events.
 //
 // The search covers rows x stages jointly, then the schedule, the last-axis
 // width and the x2 width one at a time; each candidate is timed as
@@ -25,6 +26,10 @@ struct pd_batch;
 void pd_batch_invalidate(pd_batch *B);
 extern "C" pd_plan *pd_batch_plan(pd_batch *B, int i);
 extern "C" int pd_batch_size(const pd_batch *B);
+
+namespace pd {
+pd_status time_cg_chunk(pd_plan *p, cudaEvent_t e0, cudaEvent_t e1, float *ms_out);
+}
 
 namespace {
 
@@ -59,12 +64,18 @@ pd_status time_force(pd_plan *p, cudaEvent_t e0, cudaEvent_t e1, float *ms_out)
     return PD_OK;
 }
 
-pd_status time_cfg(pd_plan *p, cudaEvent_t e0, cudaEvent_t e1, float *ms)
+// what the search times: 0 a force evaluation, 1 a chunk of static-solver
+// CG iterations (its graph is recaptured for every candidate)
+pd_status time_cfg(pd_plan *p, int target, cudaEvent_t e0, cudaEvent_t e1, float *ms)
 {
+    if (target == 1) {
+        drop_graphs(p);
+        return time_cg_chunk(p, e0, e1, ms);
+    }
     return p->prob.fp64 ? time_force<double>(p, e0, e1, ms) : time_force<float>(p, e0, e1, ms);
 }
 
-pd_status tune_plan(pd_plan *p, cudaStream_t caller)
+pd_status tune_plan(pd_plan *p, cudaStream_t caller, int target = 0)
 {
     PD_CUDA_TRY(cudaEventRecord(p->ev_join[0], caller));
     PD_CUDA_TRY(cudaStreamWaitEvent(p->own_stream, p->ev_join[0], 0));
@@ -83,7 +94,7 @@ pd_status tune_plan(pd_plan *p, cudaStream_t caller)
         for (int c : cands) {
             *knob = c;
             float ms = 0.f;
-            s = time_cfg(p, e0, e1, &ms);
+            s = time_cfg(p, target, e0, e1, &ms);
             if (s != PD_OK) return;
             if (ms < tbest) {
                 tbest = ms;
@@ -105,7 +116,7 @@ pd_status tune_plan(pd_plan *p, cudaStream_t caller)
                 p->tune_rows = r;
                 p->tune_stages = ns;
                 float ms = 0.f;
-                s = time_cfg(p, e0, e1, &ms);
+                s = time_cfg(p, target, e0, e1, &ms);
                 if (s != PD_OK) break;
                 if (ms < tbest) {
                     tbest = ms;
@@ -141,6 +152,15 @@ extern "C" pd_status pd_plan_autotune(pd_plan *p, void *stream)
         return PD_ERR_ARG;
     }
     return tune_plan(p, (cudaStream_t)stream);
+}
+
+extern "C" pd_status pd_plan_autotune_solve(pd_plan *p, void *stream)
+{
+    if (!p) {
+        set_error("pd_plan_autotune_solve: null plan");
+        return PD_ERR_ARG;
+    }
+    return tune_plan(p, (cudaStream_t)stream, 1);
 }
 
 extern "C" pd_status pd_plan_tuning(const pd_plan *p, int *out6)

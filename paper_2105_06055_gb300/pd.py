@@ -30,7 +30,7 @@ EXPORTS = ["pd_plan_create", "pd_plan_destroy", "pd_kernel_spectrum", "pd_force"
            "pd_plan_profile", "pd_plan_profile_read", "pd_force2d_noalloc", "pd_plan_boundary_nodes",
            "pd_solve_dr", "pd_plan_create_batched", "pd_batch_size", "pd_batch_plan", "pd_solve_dr_batched",
            "pd_batch_destroy", "pd_plan_autotune", "pd_batch_autotune", "pd_plan_tuning",
-           "pd_plan_set_energy_mode", "pd_plan_set_tuning"]
+           "pd_plan_set_energy_mode", "pd_plan_set_tuning", "pd_plan_autotune_solve"]
 
 PASS_KINDS = {0: "rows_fwd", 1: "cols_x2", 2: "last_axis", 3: "rows_inv"}
 
@@ -106,6 +106,8 @@ def load():
     lib.pd_batch_destroy.restype = None
     lib.pd_plan_autotune.argtypes = [P, P]
     lib.pd_plan_autotune.restype = I
+    lib.pd_plan_autotune_solve.argtypes = [P, P]
+    lib.pd_plan_autotune_solve.restype = I
     lib.pd_batch_autotune.argtypes = [P, P]
     lib.pd_batch_autotune.restype = I
     lib.pd_plan_tuning.argtypes = [P, ctypes.POINTER(I)]
@@ -297,8 +299,13 @@ class Plan:
             raise PDError(st, "pd_solve_dr")
         return int(it.value), float(rr.value), st
 
-    def autotune(self, stream=None):
-        _check(load().pd_plan_autotune(self._h, _stream(stream)), "pd_plan_autotune")
+    def autotune(self, stream=None, solve=False):
+        """Pick the pass configuration by timing force evaluations, or (solve=True)
+        chunks of the static solver's CG iterations."""
+        if solve:
+            _check(load().pd_plan_autotune_solve(self._h, _stream(stream)), "pd_plan_autotune_solve")
+        else:
+            _check(load().pd_plan_autotune(self._h, _stream(stream)), "pd_plan_autotune")
         return self.tuning
 
     def set_energy_mode(self, direct: bool):

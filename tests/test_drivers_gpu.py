@@ -225,3 +225,23 @@ def test_force_adjoint(pdm, oracle, dim, fp64):
     assert _rel(gu.double().cpu().numpy(), gu_ref) < tol
     assert _rel(gs.double().cpu().numpy(), gs_ref) < tol
     plan.close()
+
+
+def test_static_after_solver_autotune(pdm):
+    """Tuning the passes on the solver's own CG chunk changes no result beyond
+    the order of the inner-product partial sums."""
+    cfg = inputs.cube_with_cavity(n=64)
+    shape = cfg["shape"]
+    sols = []
+    for tune in (False, True):
+        prob = pdm.Problem(shape=shape, delta=3.0, model=pdm.PD_LIN_STATE, nu=0.25, fp64=False)
+        plan = pdm.Plan(prob, _t(cfg["chi"], torch.uint8), _t(cfg["chi_omega"], torch.uint8))
+        if tune:
+            tun = plan.autotune(solve=True)
+            assert tun["rows"] > 0 and tun["w_last"] > 0 and tun["stages"] in (1, 2)
+        u = torch.zeros((3,) + shape, dtype=torch.float64, device=DEV)
+        it, rel, st = plan.solve_static(u, _t(cfg["b"]), None, rtol=1e-8, max_iter=20000)
+        assert st == 0 and rel <= 1e-8
+        sols.append(u.cpu().numpy())
+        plan.close()
+    assert _rel(sols[1], sols[0]) < 1e-6
