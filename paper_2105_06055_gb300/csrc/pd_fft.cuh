@@ -93,43 +93,37 @@ __device__ __forceinline__ void dft_reg(cx<T> *v)
 
 // One radix-R Stockham stage of a length-n transform stored at s[e * stride].
 // Thread jt (of nt = n/kV) handles butterflies j = jt + b nt, b < kV/R.
-// tw[i] = e^{-2 pi i i / 2^lgl}. Ends with a block-wide barrier; threads with
-// active = false only take part in the barriers.
+// tw[i] = e^{-2 pi i i / 2^lgl}. Ends with a block-wide barrier.
 template <typename T, int R>
 __device__ __forceinline__ void fft_stage(cx<T> *s, int stride, int n, int ns, int lgnsr, int jt,
-                                          int nt, const cx<T> *__restrict__ tw, int lgl, bool cin, bool cout,
-                                          bool active)
+                                          int nt, const cx<T> *__restrict__ tw, int lgl, bool cin, bool cout)
 {
     static_assert(R <= kV, "radix larger than the values per thread");
     constexpr int B = kV / R;
     cx<T> v[kV];
     const int q = n / R;
-    if (active) {
 #pragma unroll
-        for (int b = 0; b < B; ++b) {
-            const int j = jt + b * nt;
+    for (int b = 0; b < B; ++b) {
+        const int j = jt + b * nt;
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const cx<T> x = s[(j + r * q) * stride];
-                v[b * R + r] = cin ? conjg(x) : x;
-            }
+        for (int r = 0; r < R; ++r) {
+            const cx<T> x = s[(j + r * q) * stride];
+            v[b * R + r] = cin ? conjg(x) : x;
         }
     }
     __syncthreads();
-    if (active) {
 #pragma unroll
-        for (int b = 0; b < B; ++b) {
-            const int j = jt + b * nt;
-            const int k = j & (ns - 1);
-            if (ns > 1) {
+    for (int b = 0; b < B; ++b) {
+        const int j = jt + b * nt;
+        const int k = j & (ns - 1);
+        if (ns > 1) {
 #pragma unroll
-                for (int r = 1; r < R; ++r) v[b * R + r] = cmul(v[b * R + r], tw[(r * k) << (lgl - lgnsr)]);
-            }
-            dft_reg<T, R>(&v[b * R]);
-            const int o = (j - k) * R + k;
-#pragma unroll
-            for (int r = 0; r < R; ++r) s[(o + r * ns) * stride] = cout ? conjg(v[b * R + r]) : v[b * R + r];
+            for (int r = 1; r < R; ++r) v[b * R + r] = cmul(v[b * R + r], tw[(r * k) << (lgl - lgnsr)]);
         }
+        dft_reg<T, R>(&v[b * R]);
+        const int o = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) s[(o + r * ns) * stride] = cout ? conjg(v[b * R + r]) : v[b * R + r];
     }
     __syncthreads();
 }
@@ -142,7 +136,7 @@ __device__ __forceinline__ void fft_stage(cx<T> *s, int stride, int n, int ns, i
 template <typename T>
 __device__ __forceinline__ void fft_smem(cx<T> *s, int stride, int lgn, int jt,
                                          const cx<T> *__restrict__ tw, int lgl, bool cin = false,
-                                         bool cout = false, int sched = 0, bool active = true)
+                                         bool cout = false, int sched = 0)
 {
     const int n = 1 << lgn, nt = n >> kLgV;
     int ns = 1, lgns = 0, rem = lgn;
@@ -152,9 +146,9 @@ __device__ __forceinline__ void fft_smem(cx<T> *s, int stride, int lgn, int jt,
         const bool first = (lgns == 0), last = (rem == lr);
         const bool ci = cin && first, co = cout && last;
         switch (lr) {
-            case 3: fft_stage<T, 8>(s, stride, n, ns, lgns + 3, jt, nt, tw, lgl, ci, co, active); break;
-            case 2: fft_stage<T, 4>(s, stride, n, ns, lgns + 2, jt, nt, tw, lgl, ci, co, active); break;
-            default: fft_stage<T, 2>(s, stride, n, ns, lgns + 1, jt, nt, tw, lgl, ci, co, active); break;
+            case 3: fft_stage<T, 8>(s, stride, n, ns, lgns + 3, jt, nt, tw, lgl, ci, co); break;
+            case 2: fft_stage<T, 4>(s, stride, n, ns, lgns + 2, jt, nt, tw, lgl, ci, co); break;
+            default: fft_stage<T, 2>(s, stride, n, ns, lgns + 1, jt, nt, tw, lgl, ci, co); break;
         }
         ns <<= lr;
         lgns += lr;
@@ -350,11 +344,7 @@ __global__ void __launch_bounds__(256) k_rows(RowGeom g, Op op, const cx<T> *__r
     int64_t t = blockIdx.x;
     if (kLoad && threadIdx.x == 0 && t < ntiles) issue(t, 0);
     unsigned phase = 0;  // bit s: parity of the next completion of stage s
-    // FFT mapping: nt threads per row; a block may carry more threads than
-    // rows x nt (more loads in flight in the node phases), the extra ones
-    // only pass the transforms' barriers
-    const int jt = threadIdx.x % nt, rf = threadIdx.x / nt;
-    const bool fft_on = rf < rows;
+    const int jt = threadIdx.x % nt, rf = threadIdx.x / nt;  // FFT mapping: nt threads per row
     typename op_acc<Op>::type acc;
 
     for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
@@ -381,7 +371,7 @@ __global__ void __launch_bounds__(256) k_rows(RowGeom g, Op op, const cx<T> *__r
             // Unpack the half spectrum into Z(k) = E(k) + i O(k) (E, O: DFTs of the
             // even / odd samples, times 2) and store conj(Z) for the inverse.
 #pragma unroll
-            for (int f = 0; f < FI && fft_on; ++f) {
+            for (int f = 0; f < FI; ++f) {
                 cx<T> *z = spec + (f * rows + rf) * pitch;
                 for (int k = jt; k <= H / 2; k += nt) {
                     if (k == 0) {
@@ -405,8 +395,7 @@ __global__ void __launch_bounds__(256) k_rows(RowGeom g, Op op, const cx<T> *__r
             __syncthreads();
 #pragma unroll 1
             for (int f = 0; f < FI; ++f)
-                fft_smem<T>(spec + (f * rows + (fft_on ? rf : 0)) * pitch, 1, g.lgh, jt, tws, lg1, false, false,
-                            g.sched, fft_on);
+                fft_smem<T>(spec + (f * rows + rf) * pitch, 1, g.lgh, jt, tws, lg1, false, false, g.sched);
         }
 
         // per-node work, lanes over consecutive packed slots (2 nodes each)
@@ -450,11 +439,10 @@ __global__ void __launch_bounds__(256) k_rows(RowGeom g, Op op, const cx<T> *__r
         if constexpr (FO > 0) {
 #pragma unroll 1
             for (int f = 0; f < FO; ++f)
-                fft_smem<T>(spec + (f * rows + (fft_on ? rf : 0)) * pitch, 1, g.lgh, jt, tws, lg1, false, false,
-                            g.sched, fft_on);
+                fft_smem<T>(spec + (f * rows + rf) * pitch, 1, g.lgh, jt, tws, lg1, false, false, g.sched);
             const T half = T(0.5);
 #pragma unroll
-            for (int f = 0; f < FO && fft_on; ++f) {
+            for (int f = 0; f < FO; ++f) {
                 const cx<T> *z = spec + (f * rows + rf) * pitch;
                 cx<T> *dst = op.spec_out(f) + (row0 + rf) * H;
                 for (int k = jt; k <= H / 2; k += nt) {

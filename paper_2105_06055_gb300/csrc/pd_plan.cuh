@@ -224,7 +224,6 @@ struct pd_plan {
     int tune_w[2] = {0, 0};  // column-tile width of the x2 / last-axis passes
     int tune_sched = 0;    // FFT stage schedule
     int tune_stages = 0;   // row-pass pipeline stages (1 or 2; 0: 2)
-    int tune_mult = 0;     // row-pass threads per block as a multiple of rows x (n1/16) (0: 1)
     int energy_direct = 0; // pd_step_verlet: W by a direct horizon sum (pd_plan_set_energy_mode)
     int64_t prof_n[kKinds] = {};
 };
@@ -273,9 +272,7 @@ inline void row_cfg(const pd_plan *p, int FI, int FB, int NF, int NB, RowGeom &g
     g.nstage = ns;
     g.err = p->dev_status;
     c.grid = dim3((unsigned)(p->nrows / rows));
-    int mult = p->tune_mult > 0 ? p->tune_mult : 1;  // threads per block = rows x nt x mult
-    while (mult > 1 && rows * nt * mult > 256) mult >>= 1;
-    c.block = dim3(rows * nt * mult);
+    c.block = dim3(rows * nt);
     c.smem = smem_of(rows);
 }
 

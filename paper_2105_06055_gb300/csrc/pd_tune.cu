@@ -163,18 +163,17 @@ extern "C" pd_status pd_plan_autotune_solve(pd_plan *p, void *stream)
     return tune_plan(p, (cudaStream_t)stream, 1);
 }
 
-extern "C" pd_status pd_plan_tuning(const pd_plan *p, int *out6)
+extern "C" pd_status pd_plan_tuning(const pd_plan *p, int *out5)
 {
-    if (!p || !out6) {
+    if (!p || !out5) {
         set_error("pd_plan_tuning: null argument");
         return PD_ERR_ARG;
     }
-    out6[0] = p->tune_rows;
-    out6[1] = p->tune_w[0];
-    out6[2] = p->tune_w[1];
-    out6[3] = p->tune_sched;
-    out6[4] = p->tune_stages;
-    out6[5] = p->tune_mult;
+    out5[0] = p->tune_rows;
+    out5[1] = p->tune_w[0];
+    out5[2] = p->tune_w[1];
+    out5[3] = p->tune_sched;
+    out5[4] = p->tune_stages;
     return PD_OK;
 }
 
@@ -199,7 +198,6 @@ extern "C" pd_status pd_batch_autotune(pd_batch *B, void *stream)
             p->tune_w[1] = it->second->tune_w[1];
             p->tune_sched = it->second->tune_sched;
             p->tune_stages = it->second->tune_stages;
-            p->tune_mult = it->second->tune_mult;
             drop_graphs(p);
         }
     }
@@ -207,18 +205,18 @@ extern "C" pd_status pd_batch_autotune(pd_batch *B, void *stream)
     return PD_OK;
 }
 
-extern "C" pd_status pd_plan_set_tuning(pd_plan *p, const int *in6)
+extern "C" pd_status pd_plan_set_tuning(pd_plan *p, const int *in5)
 {
-    if (!p || !in6) {
+    if (!p || !in5) {
         set_error("pd_plan_set_tuning: null argument");
         return PD_ERR_ARG;
     }
-    const int r = in6[0], wx = in6[1], wl = in6[2], sc = in6[3], ns = in6[4], mu = in6[5];
+    const int r = in5[0], wx = in5[1], wl = in5[2], sc = in5[3], ns = in5[4];
     auto pow2_or_zero = [](int v) { return v == 0 || (v > 0 && (v & (v - 1)) == 0); };
     if (!pow2_or_zero(r) || r > 256 || !pow2_or_zero(wx) || wx > 32 || !pow2_or_zero(wl) || wl > 32 ||
-        (sc != 0 && sc != 1) || ns < 0 || ns > 2 || !pow2_or_zero(mu) || mu > 4) {
+        (sc != 0 && sc != 1) || ns < 0 || ns > 2) {
         set_error("pd_plan_set_tuning: rows and widths must be 0 or powers of two (rows <= 256, widths <= 32), "
-                  "schedule 0 or 1, stages 0, 1 or 2, thread multiple 0, 1, 2 or 4");
+                  "schedule 0 or 1, stages 0, 1 or 2");
         return PD_ERR_ARG;
     }
     p->tune_rows = r;
@@ -226,7 +224,6 @@ extern "C" pd_status pd_plan_set_tuning(pd_plan *p, const int *in6)
     p->tune_w[1] = wl;
     p->tune_sched = sc;
     p->tune_stages = ns;
-    p->tune_mult = mu;
     drop_graphs(p);
     return PD_OK;
 }
