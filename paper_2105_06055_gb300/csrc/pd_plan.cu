@@ -526,6 +526,9 @@ void pd_plan_destroy(pd_plan *p)
     for (int k = 0; k < 2; ++k)
         if (p->ev_join[k]) cudaEventDestroy(p->ev_join[k]);
     if (p->own_stream) cudaStreamDestroy(p->own_stream);
+    if (p->aux_stream) cudaStreamDestroy(p->aux_stream);
+    for (int k = 0; k < 2; ++k)
+        if (p->ev_fork[k]) cudaEventDestroy(p->ev_fork[k]);
     delete p;
 }
 
@@ -808,6 +811,9 @@ static pd_status plan_create_impl(const pd_problem *pr, const uint8_t *chi_B, co
     PD_CUDA_TRY(cudaStreamCreateWithFlags(&p->own_stream, cudaStreamNonBlocking));
     PD_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_join[0], cudaEventDisableTiming));
     PD_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_join[1], cudaEventDisableTiming));
+    PD_CUDA_TRY(cudaStreamCreateWithFlags(&p->aux_stream, cudaStreamNonBlocking));
+    PD_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_fork[0], cudaEventDisableTiming));
+    PD_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_fork[1], cudaEventDisableTiming));
 
     // spectra and scratch
     if (!pr->fp64) {

@@ -218,6 +218,9 @@ struct pd_plan {
     double *host_scal = nullptr;    // pinned host copy of the solver scalars
     cudaStream_t own_stream = nullptr;  // plan stream for captured work (never the legacy stream)
     cudaEvent_t ev_join[2] = {nullptr, nullptr};
+    // second stream: the kx = 0 tiles of the 3D last-axis pass run beside the others
+    cudaStream_t aux_stream = nullptr;
+    cudaEvent_t ev_fork[2] = {nullptr, nullptr};
     double prof_ms[kKinds] = {};
     // pass configuration picked by pd_plan_autotune (0: built-in heuristic)
     int tune_rows = 0;     // rows per row-pass block
@@ -290,7 +293,7 @@ inline void col_cfg(const pd_plan *p, int axis, bool last, int FB, int FI, int N
     const int nt = L >> kLgV;
     const bool split = p->dim == 3 && last;
     const int wmirror = split ? 1 : 0;  // the width must also fit the kx = 0 tiles
-    const int mirror = tmode == 2 ? 1 : 0;
+    const int mirror = (tmode == 2 || (split && tmode == 0)) ? 1 : 0;  // tmode 0 + split: one launch, all tiles
     inner = axis == 1 ? (int64_t)H : (int64_t)p->n2 * H;
     auto smem_of = [&](int w, int mir, int tc) {
         const size_t tab = (((size_t)NTAB * (L / 2 + 1) * tc + 1) & ~(size_t)1) * sizeof(T);
@@ -312,7 +315,7 @@ inline void col_cfg(const pd_plan *p, int axis, bool last, int FB, int FI, int N
     g.tmode = split ? tmode : 0;
     g.err = p->dev_status;
     unsigned gx = (unsigned)(inner / w);
-    if (split) gx = tmode == 2 ? (unsigned)p->n2 : (unsigned)(p->n2 * (H / w - 1));
+    if (split && tmode != 0) gx = tmode == 2 ? (unsigned)p->n2 : (unsigned)(p->n2 * (H / w - 1));
     c.grid = dim3(gx, (unsigned)g.outer);
     c.block = dim3((w + mirror) * nt);
     c.smem = smem_of(w, mirror, w + (split && tmode == 1 ? 0 : 1));
@@ -403,9 +406,18 @@ constexpr int op_tab()
 template <typename T, class Op>
 pd_status launch_cols(pd_plan *p, const Op &op, int axis, bool last, int F, cudaStream_t st)
 {
-    const bool split = p->dim == 3 && last;
+    // The 3D last-axis pass runs as two launches: the kx = 0 tiles (one per k2
+    // row, with the mirror column) on the plan's second stream beside the
+    // other tiles on `st` (fork and join by events; inside a stream capture
+    // they become parallel graph branches).
+    const bool split = p->dim == 3 && last && p->aux_stream;
     PD_TRY(prof_begin(p, last ? PASS_LAST : PASS_COLS, st));
-    for (int tmode = split ? 1 : 0; tmode <= (split ? 2 : 0); ++tmode) {
+    if (split) {
+        PD_CUDA_TRY(cudaEventRecord(p->ev_fork[0], st));
+        PD_CUDA_TRY(cudaStreamWaitEvent(p->aux_stream, p->ev_fork[0], 0));
+    }
+    for (int tmode = split ? 2 : 0; tmode >= (split ? 1 : 0); --tmode) {
+        cudaStream_t ls = (split && tmode == 2) ? p->aux_stream : st;
         ColGeom g;
         LaunchCfg c;
         int64_t inner = 0;
@@ -422,9 +434,13 @@ pd_status launch_cols(pd_plan *p, const Op &op, int axis, bool last, int F, cuda
         PD_TRY(encode_tmap_3d(&tmt, spec_buf<T>(p), sizeof(T) == 8, dims, strides, box_t));
         PD_TRY(encode_tmap_3d(&tmm, spec_buf<T>(p), sizeof(T) == 8, dims, strides, box_m));
         PD_TRY(set_smem_attr((const void *)k_cols<T, Op>, c.smem));
-        k_cols<T, Op><<<c.grid, c.block, c.smem, st>>>(g, op, tw_buf<T>(p), axis == 2 ? 1 : 0, tmt, tmm);
+        k_cols<T, Op><<<c.grid, c.block, c.smem, ls>>>(g, op, tw_buf<T>(p), axis == 2 ? 1 : 0, tmt, tmm);
         PD_LAUNCH_CHECK();
         p->launches++;
+    }
+    if (split) {
+        PD_CUDA_TRY(cudaEventRecord(p->ev_fork[1], p->aux_stream));
+        PD_CUDA_TRY(cudaStreamWaitEvent(st, p->ev_fork[1], 0));
     }
     PD_TRY(prof_end(p, st));
     return PD_OK;
