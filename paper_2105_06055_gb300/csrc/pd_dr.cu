@@ -680,6 +680,7 @@ struct DrRunner {
         for (size_t i = 0; i < n; ++i) {
             prof[i] = plans[i]->prof_on;
             plans[i]->prof_on = 0;  // no event nodes inside conditional bodies
+            plans[i]->no_fork = 1;  // and no second stream
         }
         cudaGraph_t graph = nullptr;
         pd_status s = PD_OK;
@@ -708,7 +709,10 @@ struct DrRunner {
                 s = PD_ERR_CUDA;
             }
         }
-        for (size_t i = 0; i < n; ++i) plans[i]->prof_on = prof[i];
+        for (size_t i = 0; i < n; ++i) {
+            plans[i]->prof_on = prof[i];
+            plans[i]->no_fork = 0;
+        }
         if (s != PD_OK) {
             if (graph) cudaGraphDestroy(graph);
             if (s == PD_ERR_CUDA && !*pd_last_error_detail()) set_error("dynamic relaxation: graph build failed");

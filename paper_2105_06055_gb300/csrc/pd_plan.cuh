@@ -221,6 +221,7 @@ struct pd_plan {
     // second stream: the kx = 0 tiles of the 3D last-axis pass run beside the others
     cudaStream_t aux_stream = nullptr;
     cudaEvent_t ev_fork[2] = {nullptr, nullptr};
+    int no_fork = 0;  // set while capturing into conditional-node bodies (single stream there)
     double prof_ms[kKinds] = {};
     // pass configuration picked by pd_plan_autotune (0: built-in heuristic)
     int tune_rows = 0;     // rows per row-pass block
@@ -409,15 +410,18 @@ pd_status launch_cols(pd_plan *p, const Op &op, int axis, bool last, int F, cuda
     // The 3D last-axis pass runs as two launches: the kx = 0 tiles (one per k2
     // row, with the mirror column) on the plan's second stream beside the
     // other tiles on `st` (fork and join by events; inside a stream capture
-    // they become parallel graph branches).
-    const bool split = p->dim == 3 && last && p->aux_stream;
+    // they become parallel graph branches). Bodies of conditional graph nodes
+    // are captured from one stream only (no_fork): there the two launches
+    // follow each other.
+    const bool split = p->dim == 3 && last;
+    const bool fork = split && p->aux_stream && !p->no_fork;
     PD_TRY(prof_begin(p, last ? PASS_LAST : PASS_COLS, st));
-    if (split) {
+    if (fork) {
         PD_CUDA_TRY(cudaEventRecord(p->ev_fork[0], st));
         PD_CUDA_TRY(cudaStreamWaitEvent(p->aux_stream, p->ev_fork[0], 0));
     }
     for (int tmode = split ? 2 : 0; tmode >= (split ? 1 : 0); --tmode) {
-        cudaStream_t ls = (split && tmode == 2) ? p->aux_stream : st;
+        cudaStream_t ls = (fork && tmode == 2) ? p->aux_stream : st;
         ColGeom g;
         LaunchCfg c;
         int64_t inner = 0;
@@ -438,7 +442,7 @@ pd_status launch_cols(pd_plan *p, const Op &op, int axis, bool last, int F, cuda
         PD_LAUNCH_CHECK();
         p->launches++;
     }
-    if (split) {
+    if (fork) {
         PD_CUDA_TRY(cudaEventRecord(p->ev_fork[1], p->aux_stream));
         PD_CUDA_TRY(cudaStreamWaitEvent(st, p->ev_fork[1], 0));
     }
