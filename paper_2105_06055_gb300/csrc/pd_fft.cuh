@@ -287,8 +287,18 @@ struct op_node_acc<Op, std::void_t<decltype(Op::kNodeAcc)>> : std::bool_constant
 // the next tile are in flight while the current one is transformed. Twiddles
 // are copied to shared memory once; outputs leave through coalesced stores.
 // Block accumulators (acc) run over all tiles of the block.
+// Row ops may declare kMinBlocks (resident 256-thread blocks per SM the
+// compiler must allow, i.e. a register cap of 256 / kMinBlocks per thread).
+template <class Op, class = void>
+struct op_min_blocks : std::integral_constant<int, 1> {
+};
+template <class Op>
+struct op_min_blocks<Op, std::void_t<decltype(Op::kMinBlocks)>> : std::integral_constant<int, Op::kMinBlocks> {
+};
+
 template <typename T, class Op>
-__global__ void __launch_bounds__(256) k_rows(RowGeom g, Op op, const cx<T> *__restrict__ tw)
+__global__ void __launch_bounds__(256, op_min_blocks<Op>::value) k_rows(RowGeom g, Op op,
+                                                                       const cx<T> *__restrict__ tw)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     constexpr int FI = Op::kFin, FO = Op::kFout, NF = Op::kNF, NB = Op::kNB, ST = Op::kStage;

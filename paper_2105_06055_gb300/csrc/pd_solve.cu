@@ -194,6 +194,7 @@ template <typename T, int D>
 struct EpiCG {
     static constexpr int kFin = D, kFout = 0, kStage = D, kNF = 0, kNB = 1;
     static constexpr bool kSparse = true;
+    static constexpr int kMinBlocks = 4;  // <= 64 registers: more resident warps
     using Acc = CgAcc;
     const T *pv, *r;
     const uint8_t *bits;
@@ -223,7 +224,7 @@ struct EpiCG {
     {
         const int k0 = goff[c.row0], k1 = goff[c.row0 + c.rows];
         const int l1 = __ffs(n1) - 1;
-        constexpr int U = 4;  // entries in flight per thread
+        constexpr int U = 2;  // entries in flight per thread
         for (int kb = k0 + tid; kb < k1; kb += U * nthreads) {
             GEntry<T> e[U];
             T pp[U][D];
