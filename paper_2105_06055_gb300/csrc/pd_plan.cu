@@ -333,7 +333,7 @@ __global__ void k_gcount(int n1, int64_t nrows, const uint8_t *chi, const double
 }
 
 __global__ void k_gfill(int n1, int64_t nrows, const uint8_t *chi, const double *G, int nc, int64_t N, const int *off,
-                        GEntry<double> *e64, GEntry<float> *e32)
+                        GEntry<double> *e64, GEntry<float> *e32, int *gidx)
 {
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= nrows) return;
@@ -353,6 +353,7 @@ __global__ void k_gfill(int n1, int64_t nrows, const uint8_t *chi, const double 
         a.p = b.p = p;
         e64[k] = a;
         e32[k] = b;
+        gidx[p] = k;
         ++k;
     }
 }
@@ -513,7 +514,7 @@ void pd_plan_destroy(pd_plan *p)
 {
     if (!p) return;
     void *ptrs[] = {p->chi, p->chi_om, p->mbits, p->hoff, p->mhat64, p->mhat32, p->ghat64, p->ghat32, p->G64, p->G32,
-                    p->goff, p->gent64, p->gent32,
+                    p->goff, p->gidx, p->gent64, p->gent32,
                     p->qt64, p->m3inv64, p->qt32, p->m3inv32, p->tw64, p->tw32, p->spec32, p->spec64,
                     p->work, p->red};
     for (void *q : ptrs)
@@ -761,8 +762,10 @@ static pd_status plan_create_impl(const pd_problem *pr, const uint8_t *chi_B, co
         PD_CUDA_TRY(cudaMemcpyAsync(p->goff, cnt.data(), sizeof(int) * (size_t)(nr + 1), cudaMemcpyHostToDevice, st));
         PD_TRY(dalloc(p, &p->gent64, sizeof(GEntry<double>) * (size_t)std::max<int64_t>(acc, 1)));
         PD_TRY(dalloc(p, &p->gent32, sizeof(GEntry<float>) * (size_t)std::max<int64_t>(acc, 1)));
+        PD_TRY(dalloc(p, &p->gidx, sizeof(int) * N));
+        PD_CUDA_TRY(cudaMemsetAsync(p->gidx, 0xff, sizeof(int) * N, st));  // -1
         k_gfill<<<nblk(nr, 128), 128, 0, st>>>(n1, nr, p->chi, p->G64, nc, N, p->goff, (GEntry<double> *)p->gent64,
-                                              (GEntry<float> *)p->gent32);
+                                              (GEntry<float> *)p->gent32, p->gidx);
         PD_LAUNCH_CHECK();
         PD_CUDA_TRY(cudaStreamSynchronize(st));
     }

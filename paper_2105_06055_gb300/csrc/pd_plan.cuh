@@ -177,6 +177,7 @@ struct pd_plan {
     double *G64 = nullptr;         // ncomp x N
     float *G32 = nullptr;
     int *goff = nullptr;           // nrows + 1: boundary-node list offsets per row
+    int *gidx = nullptr;           // N: entry of the node in the boundary list, or -1
     void *gent64 = nullptr;        // GEntry<double>[ngent]
     void *gent32 = nullptr;        // GEntry<float>[ngent]
     int64_t ngent = 0;

@@ -188,18 +188,19 @@ struct CgAcc {
     DSum pq, rq, qq;
 };
 
-// rows, inverse: L = chi y staged, boundary fix-up with G p, q = -chi_O L,
-// block partials of p.q, r.q, q.q
+// rows, inverse: L = chi y - G p (G from the boundary list, looked up per node
+// with the p already in registers), q = -chi_O L, block partials of p.q,
+// r.q, q.q
 template <typename T, int D>
 struct EpiCG {
     static constexpr int kFin = D, kFout = 0, kStage = D, kNF = 0, kNB = 1;
-    static constexpr bool kSparse = true;
+    static constexpr bool kSparse = false;
     static constexpr int kMinBlocks = 4;  // <= 64 registers: more resident warps
     using Acc = CgAcc;
     const T *pv, *r;
     const uint8_t *bits;
     const GEntry<T> *gent;
-    const int *goff;
+    const int *gidx;
     T *q;
     double *red;
     int64_t N;
@@ -220,52 +221,53 @@ struct EpiCG {
             o1[i] = v1 * in1[i];
         }
     }
-    __device__ void sparse(const RowCtx<T> &c, int tid, int nthreads) const
-    {
-        const int k0 = goff[c.row0], k1 = goff[c.row0 + c.rows];
-        const int l1 = __ffs(n1) - 1;
-        constexpr int U = 2;  // entries in flight per thread
-        for (int kb = k0 + tid; kb < k1; kb += U * nthreads) {
-            GEntry<T> e[U];
-            T pp[U][D];
-#pragma unroll
-            for (int j = 0; j < U; ++j)
-                if (kb + j * nthreads < k1) e[j] = gent[kb + j * nthreads];
-#pragma unroll
-            for (int j = 0; j < U; ++j)
-                if (kb + j * nthreads < k1) {
-#pragma unroll
-                    for (int qd = 0; qd < D; ++qd) pp[j][qd] = pv[qd * N + e[j].p];
-                }
-#pragma unroll
-            for (int j = 0; j < U; ++j) {
-                if (kb + j * nthreads >= k1) break;
-                const int64_t p = e[j].p;
-                const int rl = (int)((p >> l1) - c.row0), i1 = (int)(p & (n1 - 1));
-                T Gp[D];
-#pragma unroll
-                for (int qd = 0; qd < D; ++qd) Gp[qd] = T(0);
-                sym_apply<T, D>(e[j].g, pp[j], Gp);
-#pragma unroll
-                for (int i = 0; i < D; ++i) c.stage(i, rl, i1) -= Gp[i];
-            }
-        }
-    }
+    __device__ void sparse(const RowCtx<T> &, int, int) const {}
     __device__ __forceinline__ void emit(const RowCtx<T> &c, int rl, int i1, const T *s0, const T *s1,
                                          CgAcc &acc) const
     {
         const int64_t p = (c.row0 + rl) * n1 + i1;
         const unsigned b0 = c.b(0, rl, i1), b1 = c.b(0, rl, i1 + 1);
+        const int2 gi = *reinterpret_cast<const int2 *>(gidx + p);
         typename vec2<T>::type pp[D], rr[D];
 #pragma unroll
         for (int i = 0; i < D; ++i) {
             pp[i] = load2(pv + i * N + p);
             rr[i] = load2(r + i * N + p);
         }
+        T L0[D], L1[D];
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-            const T a = ((b0 >> (1 + i)) & 1) ? -s0[i] : T(0);
-            const T b = ((b1 >> (1 + i)) & 1) ? -s1[i] : T(0);
+            L0[i] = s0[i];
+            L1[i] = s1[i];
+        }
+        if (gi.x >= 0) {
+            const GEntry<T> e = gent[gi.x];
+            T x[D], y[D];
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                x[i] = pp[i].x;
+                y[i] = T(0);
+            }
+            sym_apply<T, D>(e.g, x, y);
+#pragma unroll
+            for (int i = 0; i < D; ++i) L0[i] -= y[i];
+        }
+        if (gi.y >= 0) {
+            const GEntry<T> e = gent[gi.y];
+            T x[D], y[D];
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                x[i] = pp[i].y;
+                y[i] = T(0);
+            }
+            sym_apply<T, D>(e.g, x, y);
+#pragma unroll
+            for (int i = 0; i < D; ++i) L1[i] -= y[i];
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const T a = ((b0 >> (1 + i)) & 1) ? -L0[i] : T(0);
+            const T b = ((b1 >> (1 + i)) & 1) ? -L1[i] : T(0);
             store2(q + i * N + p, a, b);
             acc.pq.add(pp[i].x * a);
             acc.pq.add(pp[i].y * b);
@@ -363,7 +365,7 @@ struct Solver {
         CombForce<T, D, false> cmb{m, ob};
         PD_TRY(launch_cols<T>(p, cmb, D == 3 ? 2 : 1, true, D, st));
         if (D == 3) PD_TRY((col_pass<T, D>(p, ob, true, st)));
-        EpiCG<T, D> epi{pv, r, p->mbits, m.gent, m.goff, q, p->red, p->N, p->n1, spec + ob * fs, fs};
+        EpiCG<T, D> epi{pv, r, p->mbits, m.gent, p->gidx, q, p->red, p->N, p->n1, spec + ob * fs, fs};
         PD_TRY(launch_rows<T>(p, epi, st, &gepi));
         if (gpro > (unsigned)kPartB || gepi > (unsigned)kPartB) {
             set_error("pd_solve_static: %u / %u row blocks exceed the reduction buffer", gpro, gepi);
