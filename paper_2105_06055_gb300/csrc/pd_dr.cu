@@ -295,13 +295,13 @@ struct ProDR {
 template <typename T, int D>
 struct EpiDR {
     static constexpr int kFin = D, kFout = 0, kStage = D, kNF = 0, kNB = 1 + D;
-    static constexpr bool kSparse = true;
+    static constexpr bool kSparse = false;
     using Acc = DrAcc;
     const T *e, *v, *rhs;
     T *F;
     const uint8_t *chi, *co;
     const GEntry<T> *gent;
-    const int *goff;
+    const int *gidx;
     double *red;
     int64_t N;
     int n1;
@@ -321,27 +321,34 @@ struct EpiDR {
             o1[i] = m1 * in1[i];
         }
     }
-    __device__ void sparse(const RowCtx<T> &c, int tid, int nthreads) const
+    __device__ void sparse(const RowCtx<T> &, int, int) const {}
+    // L -= G v at a boundary node (entry k of the list)
+    __device__ __forceinline__ void fix(int64_t p, int k, T *s) const
     {
-        const int k0 = goff[c.row0], k1 = goff[c.row0 + c.rows];
-        for (int k = k0 + tid; k < k1; k += nthreads) {
-            const GEntry<T> g = gent[k];
-            T vv[D], Gv[D];
+        const GEntry<T> g = gent[k];
+        T vv[D], Gv[D];
 #pragma unroll
-            for (int q = 0; q < D; ++q) {
-                vv[q] = v[q * N + g.p];
-                Gv[q] = T(0);
-            }
-            sym_apply<T, D>(g.g, vv, Gv);
-            const int rl = (int)((g.p >> (__ffs(n1) - 1)) - c.row0), i1 = (int)(g.p & (n1 - 1));
-#pragma unroll
-            for (int i = 0; i < D; ++i) c.stage(i, rl, i1) -= Gv[i];
+        for (int q = 0; q < D; ++q) {
+            vv[q] = v[q * N + p];
+            Gv[q] = T(0);
         }
+        sym_apply<T, D>(g.g, vv, Gv);
+#pragma unroll
+        for (int i = 0; i < D; ++i) s[i] -= Gv[i];
     }
     __device__ __forceinline__ void emit(const RowCtx<T> &c, int rl, int i1, const T *s0, const T *s1,
                                          DrAcc &acc) const
     {
         const int64_t p = (c.row0 + rl) * n1 + i1;
+        const int2 gi = *reinterpret_cast<const int2 *>(gidx + p);
+        T a[D], b[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            a[i] = s0[i];
+            b[i] = s1[i];
+        }
+        if (gi.x >= 0) fix(p, gi.x, a);
+        if (gi.y >= 0) fix(p + 1, gi.y, b);
         typename vec2<T>::type ev[D], rv[D], fv[D];
 #pragma unroll
         for (int i = 0; i < D; ++i) {
@@ -351,8 +358,8 @@ struct EpiDR {
         }
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-            const T fa = c.b(1 + i, rl, i1) ? fv[i].x + s0[i] : T(0);
-            const T fb = c.b(1 + i, rl, i1 + 1) ? fv[i].y + s1[i] : T(0);
+            const T fa = c.b(1 + i, rl, i1) ? fv[i].x + a[i] : T(0);
+            const T fb = c.b(1 + i, rl, i1 + 1) ? fv[i].y + b[i] : T(0);
             store2(F + i * N + p, fa, fb);
             dr_accumulate<T>(acc, fa, rv[i].x, ev[i].x);
             dr_accumulate<T>(acc, fb, rv[i].y, ev[i].y);
@@ -450,7 +457,7 @@ struct DrSpec {
         CombForce<T, D, false> cmb{m, ob};
         PD_TRY(launch_cols<T>(p, cmb, D == 3 ? 2 : 1, true, D, st));
         if (D == 3) PD_TRY((col_pass<T, D>(p, ob, true, st)));
-        EpiDR<T, D> epi{e, v, rhs, F, p->chi, p->chi_om, m.gent, m.goff, p->red, p->N, p->n1, spec + ob * fs, fs};
+        EpiDR<T, D> epi{e, v, rhs, F, p->chi, p->chi_om, m.gent, p->gidx, p->red, p->N, p->n1, spec + ob * fs, fs};
         unsigned gepi = 0;
         PD_TRY(launch_rows<T>(p, epi, st, &gepi));
         if (gepi > (unsigned)kDrPart) {

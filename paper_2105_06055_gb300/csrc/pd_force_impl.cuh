@@ -34,7 +34,7 @@ pd_status force_bond_pipeline(pd_plan *p, const T *u, const T *s, const uint8_t 
     if constexpr (SPARSE) {
         static_assert(WM == W_NONE, "the boundary-node list is for the plan weight chi_B");
         const Model<T> m = model_view<T>(p);
-        EpiForceSparse<T, D, ENERGY> epi{u, p->chi, m.gent, m.goff, L, W, p->N, p->n1, spec + ob * fs, fs};
+        EpiForceSparse<T, D, ENERGY> epi{u, p->chi, m.gent, p->gidx, L, W, p->N, p->n1, spec + ob * fs, fs};
         PD_TRY(launch_rows<T>(p, epi, st));
     } else {
         EpiForceDense<T, D, ENERGY, WM> epi{u, s, lam, p->chi, G, L, W, p->N, p->n1, spec + ob * fs, fs};

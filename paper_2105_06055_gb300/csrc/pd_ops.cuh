@@ -166,18 +166,18 @@ struct CombForce {
 // ---------------------------------------------------------------------------
 // Inverse epilogue, plan weight (v = chi_B): sparse boundary field
 //   node2 : L_i = chi y_i, W = 1/2 chi (y_T - 2 u.y)  (staged)
-//   sparse: L_i -= G_ij u_j, W += 1/2 u.G.u at the boundary nodes
-//   emit  : write the staged rows
+//   emit  : at boundary nodes (gidx >= 0) L_i -= G_ij u_j, W += 1/2 u.G.u with
+//           G from the boundary list; write the rows
 // ---------------------------------------------------------------------------
 template <typename T, int D, bool ENERGY>
 struct EpiForceSparse {
     static constexpr int kFin = D + (ENERGY ? 1 : 0), kFout = 0, kStage = D + (ENERGY ? 1 : 0);
     static constexpr int kNF = ENERGY ? D : 0, kNB = 1;
-    static constexpr bool kSparse = true;
+    static constexpr bool kSparse = false;
     const T *u;
     const uint8_t *chi;
     const GEntry<T> *gent;
-    const int *goff;
+    const int *gidx;
     T *L;
     T *W;
     int64_t N;
@@ -206,38 +206,45 @@ struct EpiForceSparse {
         node1(c, rl, i1, in0, o0);
         node1(c, rl, i1 + 1, in1, o1);
     }
-    __device__ void sparse(const RowCtx<T> &c, int tid, int nthreads) const
+    __device__ void sparse(const RowCtx<T> &, int, int) const {}
+    // boundary correction of one node (entry k of the list)
+    __device__ __forceinline__ void fix(const RowCtx<T> &c, int rl, int i1, int64_t p, int k, T *s) const
     {
-        const int k0 = goff[c.row0], k1 = goff[c.row0 + c.rows];
-        for (int k = k0 + tid; k < k1; k += nthreads) {
-            const GEntry<T> e = gent[k];
-            const int64_t p = e.p;
-            const int rl = (int)((p >> (__ffs(n1) - 1)) - c.row0), i1 = (int)(p & (n1 - 1));
-            T uu[D], Gu[D];
+        const GEntry<T> e = gent[k];
+        T uu[D], Gu[D];
 #pragma unroll
-            for (int j = 0; j < D; ++j) {
-                uu[j] = u[j * N + p];
-                Gu[j] = T(0);
-            }
-            sym_apply<T, D>(e.g, uu, Gu);
+        for (int j = 0; j < D; ++j) {
+            uu[j] = ENERGY ? c.f(j, rl, i1) : u[j * N + p];
+            Gu[j] = T(0);
+        }
+        sym_apply<T, D>(e.g, uu, Gu);
 #pragma unroll
-            for (int i = 0; i < D; ++i) c.stage(i, rl, i1) -= Gu[i];
-            if constexpr (ENERGY) {
-                T ugu = T(0);
+        for (int i = 0; i < D; ++i) s[i] -= Gu[i];
+        if constexpr (ENERGY) {
+            T ugu = T(0);
 #pragma unroll
-                for (int i = 0; i < D; ++i) ugu += uu[i] * Gu[i];
-                c.stage(D, rl, i1) += T(0.5) * ugu;
-            }
+            for (int i = 0; i < D; ++i) ugu += uu[i] * Gu[i];
+            s[D] += T(0.5) * ugu;
         }
     }
     __device__ __forceinline__ void emit(const RowCtx<T> &c, int rl, int i1, const T *s0, const T *s1,
                                          DSum &) const
     {
         const int64_t p = (c.row0 + rl) * n1 + i1;
+        const int2 gi = *reinterpret_cast<const int2 *>(gidx + p);
+        constexpr int S = D + (ENERGY ? 1 : 0);
+        T a[S], b[S];
 #pragma unroll
-        for (int i = 0; i < D; ++i) store2(L + i * N + p, s0[i], s1[i]);
+        for (int i = 0; i < S; ++i) {
+            a[i] = s0[i];
+            b[i] = s1[i];
+        }
+        if (gi.x >= 0) fix(c, rl, i1, p, gi.x, a);
+        if (gi.y >= 0) fix(c, rl, i1 + 1, p + 1, gi.y, b);
+#pragma unroll
+        for (int i = 0; i < D; ++i) store2(L + i * N + p, a[i], b[i]);
         if constexpr (ENERGY) {
-            if (W) store2(W + p, s0[D], s1[D]);
+            if (W) store2(W + p, a[D], b[D]);
         }
     }
     __device__ void block_done(DSum &) const {}
