@@ -200,18 +200,16 @@ __global__ void k_dr_ir_update(double *u, const T *e, const uint8_t *co, int64_t
         if (co[i]) u[i] += (double)e[i];
 }
 
-// Block partial triples (e.Ae, e.e, ||F||^2) -> c^n, ||F^n||^2
-__global__ void k_dr_finish(double *red, int nparts)
+// Block partial triples (e.Ae, e.e, ||F||^2) -> c^n, ||F^n||^2 (one block of kFinishThreads)
+__global__ void __launch_bounds__(kFinishThreads) k_dr_finish(double *red, int nparts)
 {
-    double a = 0.0, b = 0.0, f = 0.0;
+    double a = 0.0, b = 0.0, f = 0.0, z = 0.0;
     for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
         a += red[kRedPart + 3 * i];
         b += red[kRedPart + 3 * i + 1];
         f += red[kRedPart + 3 * i + 2];
     }
-    a = block_sum_d(a);
-    b = block_sum_d(b);
-    f = block_sum_d(f);
+    block_sum4(a, b, f, z);
     if (threadIdx.x == 0) {
         double *s = red + kRedScal;
         const double q = b > 0.0 ? a / b * s[R_RHOINV] : 0.0;
@@ -442,7 +440,7 @@ struct DrSpec {
             PD_TRY(force_plain<T>(p, v, nullptr, L, nullptr, st));
             k_dr_post<T><<<nb, 256, 0, st>>>(L, e, rhs, F, p->chi_om, nvec, p->red);
             PD_LAUNCH_CHECK();
-            k_dr_finish<<<1, 1024, 0, st>>>(p->red, (int)nb);
+            k_dr_finish<<<1, kFinishThreads, 0, st>>>(p->red, (int)nb);
             PD_LAUNCH_CHECK();
             p->launches += 3;
             return PD_OK;
@@ -464,7 +462,7 @@ struct DrSpec {
             set_error("dynamic relaxation: %u row blocks exceed the reduction buffer", gepi);
             return PD_ERR_SIZE;
         }
-        k_dr_finish<<<1, 1024, 0, st>>>(p->red, (int)gepi);
+        k_dr_finish<<<1, kFinishThreads, 0, st>>>(p->red, (int)gepi);
         PD_LAUNCH_CHECK();
         p->launches++;
         return PD_OK;

@@ -41,7 +41,9 @@ constexpr int kChunk = 16;       // CG iterations per graph replay
 constexpr int kPartB = 14400;    // fused iteration: r.r partials below, (p.q, r.q, q.q) triples above
 
 // rr = sum of the first pass's partials; alpha, beta from the second pass's triples
-__global__ void k_cg_finish_fused(double *red, int na, int nb)
+// rr = sum of the first pass's partials; alpha, beta from the second pass's
+// triples (one block of kFinishThreads)
+__global__ void __launch_bounds__(kFinishThreads) k_cg_finish_fused(double *red, int na, int nb)
 {
     double rr = 0.0, pq = 0.0, rq = 0.0, qq = 0.0;
     for (int i = threadIdx.x; i < na; i += blockDim.x) rr += red[kRedPart + i];
@@ -50,10 +52,7 @@ __global__ void k_cg_finish_fused(double *red, int na, int nb)
         rq += red[kRedPart + kPartB + 3 * i + 1];
         qq += red[kRedPart + kPartB + 3 * i + 2];
     }
-    rr = block_sum_d(rr);
-    pq = block_sum_d(pq);
-    rq = block_sum_d(rq);
-    qq = block_sum_d(qq);
+    block_sum4(rr, pq, rq, qq);
     if (threadIdx.x == 0) {
         double *s = red + kRedScal;
         if (!isfinite(rr) || !isfinite(pq) || !isfinite(rq) || !isfinite(qq)) s[S_FLAG] = 1.0;
@@ -66,7 +65,6 @@ __global__ void k_cg_finish_fused(double *red, int na, int nb)
         s[S_RR] = rn;  // r.r after this iteration's (pending) update
     }
 }
-
 
 // r = (T) r64, p = 0, e = 0, q = 0 ; partial r.r
 template <typename T>
@@ -371,7 +369,7 @@ struct Solver {
             set_error("pd_solve_static: %u / %u row blocks exceed the reduction buffer", gpro, gepi);
             return PD_ERR_SIZE;
         }
-        k_cg_finish_fused<<<1, 1024, 0, st>>>(p->red, (int)gpro, (int)gepi);
+        k_cg_finish_fused<<<1, kFinishThreads, 0, st>>>(p->red, (int)gpro, (int)gepi);
         PD_LAUNCH_CHECK();
         p->launches++;
         return PD_OK;

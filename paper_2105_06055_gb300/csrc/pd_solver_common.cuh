@@ -13,6 +13,37 @@ namespace {
 constexpr int kUpdBlocks = 1024;  // blocks of the vector kernels
 enum { S_RR = 0, S_PQ, S_ALPHA, S_BETA, S_RRNEW, S_NORM, S_BN, S_FLAG, S_COUNT };
 
+// Sum of four doubles per thread over a block of kFinishThreads threads
+// (valid in thread 0): warp shuffles, one shared-memory exchange.
+constexpr int kFinishThreads = 256;
+__device__ __forceinline__ void block_sum4(double &a, double &b, double &c, double &d)
+{
+    __shared__ double sh[4][kFinishThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+        c += __shfl_down_sync(0xffffffffu, c, o);
+        d += __shfl_down_sync(0xffffffffu, d, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        sh[0][wid] = a;
+        sh[1][wid] = b;
+        sh[2][wid] = c;
+        sh[3][wid] = d;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a = b = c = d = 0.0;
+        for (int k = 0; k < kFinishThreads / 32; ++k) {
+            a += sh[0][k];
+            b += sh[1][k];
+            c += sh[2][k];
+            d += sh[3][k];
+        }
+    }
+}
+
 __device__ __forceinline__ void write_partial(double *red, double v)
 {
     const double t = block_sum_d(v);
