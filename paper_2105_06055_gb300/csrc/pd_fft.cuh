@@ -91,24 +91,28 @@ __device__ __forceinline__ void dft_reg(cx<T> *v)
     }
 }
 
-// One radix-R Stockham stage of a length-n transform stored at s[e * stride].
-// Thread jt (of nt = n/kV) handles butterflies j = jt + b nt, b < kV/R.
-// tw[i] = e^{-2 pi i i / 2^lgl}. Ends with a block-wide barrier.
-template <typename T, int R>
-__device__ __forceinline__ void fft_stage(cx<T> *s, int stride, int n, int ns, int lgnsr, int jt,
+// One radix-R Stockham stage of F length-n transforms, field f stored at
+// s[f * fstride + e * stride]. Thread jt (of nt = n/kV) handles butterflies
+// j = jt + b nt, b < kV/R, of every field (the twiddles are loaded once for
+// all fields). tw[i] = e^{-2 pi i i / 2^lgl}. Ends with a block-wide barrier.
+template <typename T, int R, int F>
+__device__ __forceinline__ void fft_stage(cx<T> *s, int fstride, int stride, int n, int ns, int lgnsr, int jt,
                                           int nt, const cx<T> *__restrict__ tw, int lgl, bool cin, bool cout)
 {
     static_assert(R <= kV, "radix larger than the values per thread");
     constexpr int B = kV / R;
-    cx<T> v[kV];
+    cx<T> v[F][kV];
     const int q = n / R;
 #pragma unroll
-    for (int b = 0; b < B; ++b) {
-        const int j = jt + b * nt;
+    for (int f = 0; f < F; ++f) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const cx<T> x = s[(j + r * q) * stride];
-            v[b * R + r] = cin ? conjg(x) : x;
+        for (int b = 0; b < B; ++b) {
+            const int j = jt + b * nt;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const cx<T> x = s[f * fstride + (j + r * q) * stride];
+                v[f][b * R + r] = cin ? conjg(x) : x;
+            }
         }
     }
     __syncthreads();
@@ -116,25 +120,44 @@ __device__ __forceinline__ void fft_stage(cx<T> *s, int stride, int n, int ns, i
     for (int b = 0; b < B; ++b) {
         const int j = jt + b * nt;
         const int k = j & (ns - 1);
-        if (ns > 1) {
-#pragma unroll
-            for (int r = 1; r < R; ++r) v[b * R + r] = cmul(v[b * R + r], tw[(r * k) << (lgl - lgnsr)]);
-        }
-        dft_reg<T, R>(&v[b * R]);
         const int o = (j - k) * R + k;
+        if constexpr (F == 1) {
+            if (ns > 1) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) s[(o + r * ns) * stride] = cout ? conjg(v[b * R + r]) : v[b * R + r];
+                for (int r = 1; r < R; ++r) v[0][b * R + r] = cmul(v[0][b * R + r], tw[(r * k) << (lgl - lgnsr)]);
+            }
+            dft_reg<T, R>(&v[0][b * R]);
+#pragma unroll
+            for (int r = 0; r < R; ++r) s[(o + r * ns) * stride] = cout ? conjg(v[0][b * R + r]) : v[0][b * R + r];
+        } else {
+            cx<T> w[R];
+            if (ns > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) w[r] = tw[(r * k) << (lgl - lgnsr)];
+            }
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                if (ns > 1) {
+#pragma unroll
+                    for (int r = 1; r < R; ++r) v[f][b * R + r] = cmul(v[f][b * R + r], w[r]);
+                }
+                dft_reg<T, R>(&v[f][b * R]);
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    s[f * fstride + (o + r * ns) * stride] = cout ? conjg(v[f][b * R + r]) : v[f][b * R + r];
+            }
+        }
     }
     __syncthreads();
 }
 
-// Forward DFT of length 2^lgn (>= 16) in shared memory, in place: stages of
-// radix 8 and one stage of radix 4 or 2 for the remainder, which comes last
-// (schedule 0) or first (schedule 1). With cin the input is conjugated as it
-// is read, with cout the output as it is written (IDFT(x) =
-// conj(DFT(conj(x))) costs no extra pass).
-template <typename T>
-__device__ __forceinline__ void fft_smem(cx<T> *s, int stride, int lgn, int jt,
+// Forward DFTs of length 2^lgn (>= 16) of F fields (field f at s + f *
+// fstride) in shared memory, in place: stages of radix 8 and one stage of
+// radix 4 or 2 for the remainder, which comes last (schedule 0) or first
+// (schedule 1). With cin the input is conjugated as it is read, with cout the
+// output as it is written (IDFT(x) = conj(DFT(conj(x))) costs no extra pass).
+template <typename T, int F = 1>
+__device__ __forceinline__ void fft_smem(cx<T> *s, int fstride, int stride, int lgn, int jt,
                                          const cx<T> *__restrict__ tw, int lgl, bool cin = false,
                                          bool cout = false, int sched = 0)
 {
@@ -146,15 +169,31 @@ __device__ __forceinline__ void fft_smem(cx<T> *s, int stride, int lgn, int jt,
         const bool first = (lgns == 0), last = (rem == lr);
         const bool ci = cin && first, co = cout && last;
         switch (lr) {
-            case 3: fft_stage<T, 8>(s, stride, n, ns, lgns + 3, jt, nt, tw, lgl, ci, co); break;
-            case 2: fft_stage<T, 4>(s, stride, n, ns, lgns + 2, jt, nt, tw, lgl, ci, co); break;
-            default: fft_stage<T, 2>(s, stride, n, ns, lgns + 1, jt, nt, tw, lgl, ci, co); break;
+            case 3: fft_stage<T, 8, F>(s, fstride, stride, n, ns, lgns + 3, jt, nt, tw, lgl, ci, co); break;
+            case 2: fft_stage<T, 4, F>(s, fstride, stride, n, ns, lgns + 2, jt, nt, tw, lgl, ci, co); break;
+            default: fft_stage<T, 2, F>(s, fstride, stride, n, ns, lgns + 1, jt, nt, tw, lgl, ci, co); break;
         }
         ns <<= lr;
         lgns += lr;
         rem -= lr;
     }
 }
+
+// F transforms in sweeps of up to MG fields at a time (one barrier pair per
+// stage and sweep instead of per stage and field; MG x 8 complex values live
+// per thread)
+template <typename T, int F, int MG>
+__device__ __forceinline__ void fft_fields(cx<T> *s, int fstride, int stride, int lgn, int jt,
+                                           const cx<T> *__restrict__ tw, int lgl, bool cin, bool cout, int sched)
+{
+    if constexpr (F > 0) {
+        constexpr int G = F < MG ? F : MG;
+        fft_smem<T, G>(s, fstride, stride, lgn, jt, tw, lgl, cin, cout, sched);
+        if constexpr (F > G)
+            fft_fields<T, F - G, MG>(s + G * fstride, fstride, stride, lgn, jt, tw, lgl, cin, cout, sched);
+    }
+}
+constexpr int kColFieldGroup = 3;  // column passes
 
 // ---------------------------------------------------------------------------
 // Compensated FP32 accumulation (Knuth two-sum): sums of FP32 products carried
@@ -405,7 +444,7 @@ __global__ void __launch_bounds__(256, op_min_blocks<Op>::value) k_rows(RowGeom 
             __syncthreads();
 #pragma unroll 1
             for (int f = 0; f < FI; ++f)
-                fft_smem<T>(spec + (f * rows + rf) * pitch, 1, g.lgh, jt, tws, lg1, false, false, g.sched);
+                fft_smem<T>(spec + (f * rows + rf) * pitch, 0, 1, g.lgh, jt, tws, lg1, false, false, g.sched);
         }
 
         // per-node work, lanes over consecutive packed slots (2 nodes each)
@@ -449,7 +488,7 @@ __global__ void __launch_bounds__(256, op_min_blocks<Op>::value) k_rows(RowGeom 
         if constexpr (FO > 0) {
 #pragma unroll 1
             for (int f = 0; f < FO; ++f)
-                fft_smem<T>(spec + (f * rows + rf) * pitch, 1, g.lgh, jt, tws, lg1, false, false, g.sched);
+                fft_smem<T>(spec + (f * rows + rf) * pitch, 0, 1, g.lgh, jt, tws, lg1, false, false, g.sched);
             const T half = T(0.5);
 #pragma unroll
             for (int f = 0; f < FO; ++f) {
@@ -597,9 +636,9 @@ __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__r
     auto colbase = [&](int f) -> cx<T> * { return is_m ? (mir + f * L * 2) : (tile + f * fsz + col); };
 
     constexpr int FPRE = (MODE == 2) ? Op::kPre : 0;
-#pragma unroll 1
-    for (int f = FPRE; f < FI; ++f)
-        fft_smem<T>(colbase(f), cstride, g.lgl, jt, tws, g.lgl, MODE == 1, MODE == 1, g.sched);
+    const int fstr = is_m ? L * 2 : fsz;  // field stride of this thread's column
+    fft_fields<T, FI - FPRE, kColFieldGroup>(colbase(FPRE), fstr, cstride, g.lgl, jt, tws, g.lgl, MODE == 1,
+                                              MODE == 1, g.sched);
 
     if constexpr (MODE == 2 && Op::kStoreIn) {
         fence_proxy_async();
@@ -705,8 +744,7 @@ __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__r
             }
             __syncthreads();
         }
-#pragma unroll 1
-        for (int f = 0; f < FO; ++f) fft_smem<T>(colbase(f), cstride, g.lgl, jt, tws, g.lgl, false, true, g.sched);
+        fft_fields<T, FO, kColFieldGroup>(colbase(0), fstr, cstride, g.lgl, jt, tws, g.lgl, false, true, g.sched);
     }
 
     // ---- store
