@@ -193,7 +193,9 @@ __device__ __forceinline__ void fft_fields(cx<T> *s, int fstride, int stride, in
             fft_fields<T, F - G, MG>(s + G * fstride, fstride, stride, lgn, jt, tw, lgl, cin, cout, sched);
     }
 }
-constexpr int kColFieldGroup = 3;  // column passes
+// column passes: grouped sweeps pay for the spectral-combine passes; the plain
+// transforms keep one field per sweep (fewer registers, more resident warps)
+constexpr int kCombFieldGroup = 3;
 
 // ---------------------------------------------------------------------------
 // Compensated FP32 accumulation (Knuth two-sum): sums of FP32 products carried
@@ -637,8 +639,8 @@ __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__r
 
     constexpr int FPRE = (MODE == 2) ? Op::kPre : 0;
     const int fstr = is_m ? L * 2 : fsz;  // field stride of this thread's column
-    fft_fields<T, FI - FPRE, kColFieldGroup>(colbase(FPRE), fstr, cstride, g.lgl, jt, tws, g.lgl, MODE == 1,
-                                              MODE == 1, g.sched);
+    fft_fields<T, FI - FPRE, MODE == 2 ? kCombFieldGroup : 1>(colbase(FPRE), fstr, cstride, g.lgl, jt, tws, g.lgl,
+                                                              MODE == 1, MODE == 1, g.sched);
 
     if constexpr (MODE == 2 && Op::kStoreIn) {
         fence_proxy_async();
@@ -744,7 +746,7 @@ __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__r
             }
             __syncthreads();
         }
-        fft_fields<T, FO, kColFieldGroup>(colbase(0), fstr, cstride, g.lgl, jt, tws, g.lgl, false, true, g.sched);
+        fft_fields<T, FO, kCombFieldGroup>(colbase(0), fstr, cstride, g.lgl, jt, tws, g.lgl, false, true, g.sched);
     }
 
     // ---- store
