@@ -125,7 +125,11 @@ class ClockSampler:
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
 # committed ncu summaries; None when the kernel changed after the capture.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    "rows_inv": (99.6e6, "profiles/k_rows_EpiCG_static_solve_128cube.md"),
+    "last_axis": (42.4e6, "profiles/k_rows_EpiCG_static_solve_128cube.md"),
+    "rows_fwd": (145.2e6, "profiles/k_rows_EpiCG_static_solve_128cube.md"),
+}
 
 
 def pass_bytes(kind, N, nbound, d=3, nc=6):
