@@ -686,6 +686,7 @@ struct DrRunner {
             prof[i] = plans[i]->prof_on;
             plans[i]->prof_on = 0;  // no event nodes inside conditional bodies
             plans[i]->no_fork = 1;  // and no second stream
+            plans[i]->pdl = 0;      // nor programmatic launches
         }
         cudaGraph_t graph = nullptr;
         pd_status s = PD_OK;
@@ -717,6 +718,7 @@ struct DrRunner {
         for (size_t i = 0; i < n; ++i) {
             plans[i]->prof_on = prof[i];
             plans[i]->no_fork = 0;
+            plans[i]->pdl = 1;
         }
         if (s != PD_OK) {
             if (graph) cudaGraphDestroy(graph);

@@ -392,6 +392,10 @@ __global__ void __launch_bounds__(256, op_min_blocks<Op>::value) k_rows(RowGeom 
     }
     for (int i = threadIdx.x; i < n1; i += blockDim.x) tws[i] = tw[i << (g.lgl - lg1)];
     __syncthreads();
+    // everything above reads plan constants only; the op's fields come from
+    // the preceding pass
+    pdl_wait();
+    pdl_trigger();
     int64_t t = blockIdx.x;
     if (kLoad && threadIdx.x == 0 && t < ntiles) issue(t, 0);
     unsigned phase = 0;  // bit s: parity of the next completion of stage s
@@ -597,19 +601,8 @@ __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__r
     if (threadIdx.x == 0) mbar_init(mbar, 1);
     for (int i = threadIdx.x; i < L; i += nthreads) tws[i] = tw[i << (g.lgtw - g.lgl)];
     __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned bytes = (unsigned)(FI * fsz * sizeof(cx<T>) + (mcol >= 0 ? FI * L * 2 * sizeof(cx<T>) : 0));
-        mbar_expect_tx(mbar, bytes);
-#pragma unroll
-        for (int f = 0; f < FI; ++f) {
-            const int z = o + op.slot_in(f) * g.outer;
-            for (int l0 = 0; l0 < L; l0 += g.lb) {
-                tma_load_3d(tile + f * fsz + l0 * w, &tmt, 2 * c0, l0, z, mbar);
-                if (mcol >= 0) tma_load_3d(mir + f * L * 2 + l0 * 2, &tmm, 2 * mcol, l0, z, mbar);
-            }
-        }
-    }
-    // kernel-table slice of this tile (overlaps the TMA loads)
+    // kernel-table slice of this tile (plan constants: fetched before the wait
+    // for the preceding pass, overlapping its tail)
     const int kx0 = axis_is_z ? (c0 & (H - 1)) : c0;
     const int kyt = c0 >> g.lgh;  // 3D: the tile's k2
     const bool fyt = axis_is_z && kyt > (g.n2 >> 1);
@@ -627,6 +620,20 @@ __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__r
             const int rr = (int)(((float)rem + 0.5f) * inv_tcols);
             const int cc = rem - rr * tcols;
             tab[i] = op.table(comp)[rr * rstride + roff + ((cc == w) ? H : kx0 + cc)];
+        }
+    }
+    pdl_trigger();
+    if (threadIdx.x == 0) {
+        pdl_wait();  // the tiles are the preceding pass's output; only thread 0 touches global data
+        const unsigned bytes = (unsigned)(FI * fsz * sizeof(cx<T>) + (mcol >= 0 ? FI * L * 2 * sizeof(cx<T>) : 0));
+        mbar_expect_tx(mbar, bytes);
+#pragma unroll
+        for (int f = 0; f < FI; ++f) {
+            const int z = o + op.slot_in(f) * g.outer;
+            for (int l0 = 0; l0 < L; l0 += g.lb) {
+                tma_load_3d(tile + f * fsz + l0 * w, &tmt, 2 * c0, l0, z, mbar);
+                if (mcol >= 0) tma_load_3d(mir + f * L * 2 + l0 * 2, &tmm, 2 * mcol, l0, z, mbar);
+            }
         }
     }
     if (!mbar_wait(mbar, 0, g.err)) return;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <algorithm>
+#include <utility>
 
 #include <vector>
 
@@ -223,6 +224,7 @@ struct pd_plan {
     cudaStream_t aux_stream = nullptr;
     cudaEvent_t ev_fork[2] = {nullptr, nullptr};
     int no_fork = 0;  // set while capturing into conditional-node bodies (single stream there)
+    int pdl = 1;      // pass kernels launched as programmatic dependents (griddepcontrol)
     double prof_ms[kKinds] = {};
     // pass configuration picked by pd_plan_autotune (0: built-in heuristic)
     int tune_rows = 0;     // rows per row-pass block
@@ -368,6 +370,32 @@ inline pd_status prof_end(pd_plan *p, cudaStream_t st)
     return PD_OK;
 }
 
+// Launch with the programmatic-stream-serialization attribute when pdl is set:
+// the kernel may start while its predecessor in the stream finishes and waits
+// for it with griddepcontrol.wait (every pass kernel does, before it touches
+// data of the preceding pass).
+template <typename... KArgs, typename... Args>
+inline pd_status launch_k(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                          Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl ? attr : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+    if (e != cudaSuccess) {
+        set_error("kernel launch failed: %s", cudaGetErrorString(e));
+        return PD_ERR_CUDA;
+    }
+    return PD_OK;
+}
+
 // Persistent row pass: as many blocks as fit on the GPU at once (at most one
 // per tile). *grid_out receives the block count (the number of block partial
 // sums an op with a block accumulator writes).
@@ -386,8 +414,7 @@ pd_status launch_rows(pd_plan *p, const Op &op, cudaStream_t st, unsigned *grid_
     if ((int64_t)c.grid.x > cap) c.grid.x = (unsigned)cap;
     if (grid_out) *grid_out = c.grid.x;
     PD_TRY(prof_begin(p, Op::kFin > 0 ? PASS_ROWS_INV : PASS_ROWS_FWD, st));
-    k_rows<T, Op><<<c.grid, c.block, c.smem, st>>>(g, op, tw_buf<T>(p));
-    PD_LAUNCH_CHECK();
+    PD_TRY(launch_k(p->pdl != 0, k_rows<T, Op>, c.grid, c.block, c.smem, st, g, op, tw_buf<T>(p)));
     PD_TRY(prof_end(p, st));
     p->launches++;
     return PD_OK;
@@ -439,8 +466,8 @@ pd_status launch_cols(pd_plan *p, const Op &op, int axis, bool last, int F, cuda
         PD_TRY(encode_tmap_3d(&tmt, spec_buf<T>(p), sizeof(T) == 8, dims, strides, box_t));
         PD_TRY(encode_tmap_3d(&tmm, spec_buf<T>(p), sizeof(T) == 8, dims, strides, box_m));
         PD_TRY(set_smem_attr((const void *)k_cols<T, Op>, c.smem));
-        k_cols<T, Op><<<c.grid, c.block, c.smem, ls>>>(g, op, tw_buf<T>(p), axis == 2 ? 1 : 0, tmt, tmm);
-        PD_LAUNCH_CHECK();
+        PD_TRY(launch_k(p->pdl != 0, k_cols<T, Op>, c.grid, c.block, c.smem, ls, g, op, tw_buf<T>(p),
+                        axis == 2 ? 1 : 0, tmt, tmm));
         p->launches++;
     }
     if (fork) {

@@ -45,6 +45,8 @@ constexpr int kPartB = 14400;    // fused iteration: r.r partials below, (p.q, r
 // triples (one block of kFinishThreads)
 __global__ void __launch_bounds__(kFinishThreads) k_cg_finish_fused(double *red, int na, int nb)
 {
+    pdl_wait();
+    pdl_trigger();
     double rr = 0.0, pq = 0.0, rq = 0.0, qq = 0.0;
     for (int i = threadIdx.x; i < na; i += blockDim.x) rr += red[kRedPart + i];
     for (int i = threadIdx.x; i < nb; i += blockDim.x) {
@@ -369,8 +371,8 @@ struct Solver {
             set_error("pd_solve_static: %u / %u row blocks exceed the reduction buffer", gpro, gepi);
             return PD_ERR_SIZE;
         }
-        k_cg_finish_fused<<<1, kFinishThreads, 0, st>>>(p->red, (int)gpro, (int)gepi);
-        PD_LAUNCH_CHECK();
+        PD_TRY(launch_k(p->pdl != 0, k_cg_finish_fused, dim3(1), dim3(kFinishThreads), 0, st, p->red, (int)gpro,
+                        (int)gepi));
         p->launches++;
         return PD_OK;
     }
