@@ -527,7 +527,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="static", choices=["static", "batched", "force"])
     ap.add_argument("--no-autotune", action="store_true", help="skip the pass autotuner (built-in tile heuristic)")
-    ap.add_argument("--tuning", default="", metavar="ROWS,WX2,WLAST,SCHED[,STAGES]",
+    ap.add_argument("--tuning", default="", metavar="ROWS,WX2,WLAST,SCHED[,STAGES[,STAGES_INV]]",
                     help="pin a pass configuration instead of autotuning (e.g. the one a tuned run reported)")
     ap.add_argument("--specimens", type=int, default=64)
     ap.add_argument("--profile-solve", type=int, default=0, metavar="K",

@@ -247,8 +247,8 @@ void pd_batch_destroy(pd_batch *batch);
  * calls use the chosen configuration. Synchronises the stream.
  * pd_batch_autotune tunes one plan per distinct grid/precision/operator of a
  * batch and gives the others the same configuration.
- * pd_plan_tuning writes {rows, x2 width, last-axis width, schedule, stages}
- * (0 = heuristic) to out5.
+ * pd_plan_tuning writes {rows, x2 width, last-axis width, schedule, stages,
+ * inverse-pass stages} (0 = heuristic) to out6.
  */
 pd_status pd_plan_autotune(pd_plan *plan, void *stream);
 /* The same search timing a chunk of 16 iterations of the static solver's CG
@@ -256,13 +256,14 @@ pd_status pd_plan_autotune(pd_plan *plan, void *stream);
  * plan's solver workspace. */
 pd_status pd_plan_autotune_solve(pd_plan *plan, void *stream);
 pd_status pd_batch_autotune(pd_batch *batch, void *stream);
-pd_status pd_plan_tuning(const pd_plan *plan, int *out5);
+pd_status pd_plan_tuning(const pd_plan *plan, int *out6);
 /* Pin a pass configuration {rows, x2 width, last-axis width, schedule,
- * stages}: rows and widths 0 or powers of two (rows <= 256, widths <= 32;
- * 0 = heuristic), schedule 0/1, row-pass pipeline stages 0 (= 2), 1 or 2;
+ * stages, inverse-pass stages}: rows and widths 0 or powers of two (rows <=
+ * 256, widths <= 32; 0 = heuristic), schedule 0/1, row-pass pipeline stages
+ * 0 (= 2), 1 or 2, inverse-pass stages 0 (= as the forward passes), 1 or 2;
  * PD_ERR_ARG otherwise. The pass configuration functions still shrink a value
  * that does not fit the grid or the shared memory. */
-pd_status pd_plan_set_tuning(pd_plan *plan, const int *in5);
+pd_status pd_plan_set_tuning(pd_plan *plan, const int *in6);
 
 /*
  * pd_force_adjoint -- reverse-mode derivative of pd_force (bond model). The

@@ -231,6 +231,7 @@ struct pd_plan {
     int tune_w[2] = {0, 0};  // column-tile width of the x2 / last-axis passes
     int tune_sched = 0;    // FFT stage schedule
     int tune_stages = 0;   // row-pass pipeline stages (1 or 2; 0: 2)
+    int tune_stages_inv = 0;  // the same for the inverse row passes (0: as tune_stages)
     int energy_direct = 0; // pd_step_verlet: W by a direct horizon sum (pd_plan_set_energy_mode)
     int64_t prof_n[kKinds] = {};
 };
@@ -263,7 +264,8 @@ inline void row_cfg(const pd_plan *p, int FI, int FB, int NF, int NB, RowGeom &g
     const int H = p->h, nt = H >> kLgV, n1 = 2 * H;
     const int pad = nt < 16 ? (nt < 2 ? 2 : nt) : 0;  // keeps rows 16-byte aligned, spreads banks
     const int pitch = H + pad;
-    const int ns = p->tune_stages == 1 ? 1 : 2;
+    const int ns_fwd = p->tune_stages == 1 ? 1 : 2;
+    const int ns = (FI > 0 && p->tune_stages_inv > 0) ? p->tune_stages_inv : ns_fwd;
     auto smem_of = [&](int rows) { return row_smem_bytes<T>(FI, FB, NF, NB, rows, pitch, n1, ns); };
     int rows = p->tune_rows > 0 ? p->tune_rows : 128 / nt;
     if (rows < 1) rows = 1;

@@ -5,8 +5,8 @@
 // force evaluation (pd_plan_autotune) or a chunk of its static solver's CG
 // iterations (pd_plan_autotune_solve) on its workspace with CUDA events.
 //
-// The search covers rows x stages jointly, then the schedule, the last-axis
-// width and the x2 width one at a time; each candidate is timed as
+// The search covers rows x stages jointly, then the inverse passes' stages,
+// the schedule, the last-axis width and the x2 width one at a time; each candidate is timed as
 // the median of nine force evaluations after three untimed ones. Candidates
 // are limited to the shapes the passes accept (powers of two; at least one
 // warp per row block; shared memory within the pass's own limit, which the
@@ -128,6 +128,7 @@ pd_status tune_plan(pd_plan *p, cudaStream_t caller, int target = 0)
         p->tune_rows = rbest;
         p->tune_stages = sbest;
     }
+    best_of(&p->tune_stages_inv, {1, 2});
     // schedule: only lengths that are not powers of 8 have a remainder stage
     const bool rem = (ilog2(H) % kLgV) || (ilog2(p->n2) % kLgV) || (p->dim == 3 && (ilog2(p->n3) % kLgV));
     if (rem) best_of(&p->tune_sched, {0, 1});
@@ -163,17 +164,18 @@ extern "C" pd_status pd_plan_autotune_solve(pd_plan *p, void *stream)
     return tune_plan(p, (cudaStream_t)stream, 1);
 }
 
-extern "C" pd_status pd_plan_tuning(const pd_plan *p, int *out5)
+extern "C" pd_status pd_plan_tuning(const pd_plan *p, int *out6)
 {
-    if (!p || !out5) {
+    if (!p || !out6) {
         set_error("pd_plan_tuning: null argument");
         return PD_ERR_ARG;
     }
-    out5[0] = p->tune_rows;
-    out5[1] = p->tune_w[0];
-    out5[2] = p->tune_w[1];
-    out5[3] = p->tune_sched;
-    out5[4] = p->tune_stages;
+    out6[0] = p->tune_rows;
+    out6[1] = p->tune_w[0];
+    out6[2] = p->tune_w[1];
+    out6[3] = p->tune_sched;
+    out6[4] = p->tune_stages;
+    out6[5] = p->tune_stages_inv;
     return PD_OK;
 }
 
@@ -198,6 +200,7 @@ extern "C" pd_status pd_batch_autotune(pd_batch *B, void *stream)
             p->tune_w[1] = it->second->tune_w[1];
             p->tune_sched = it->second->tune_sched;
             p->tune_stages = it->second->tune_stages;
+            p->tune_stages_inv = it->second->tune_stages_inv;
             drop_graphs(p);
         }
     }
@@ -205,16 +208,16 @@ extern "C" pd_status pd_batch_autotune(pd_batch *B, void *stream)
     return PD_OK;
 }
 
-extern "C" pd_status pd_plan_set_tuning(pd_plan *p, const int *in5)
+extern "C" pd_status pd_plan_set_tuning(pd_plan *p, const int *in6)
 {
-    if (!p || !in5) {
+    if (!p || !in6) {
         set_error("pd_plan_set_tuning: null argument");
         return PD_ERR_ARG;
     }
-    const int r = in5[0], wx = in5[1], wl = in5[2], sc = in5[3], ns = in5[4];
+    const int r = in6[0], wx = in6[1], wl = in6[2], sc = in6[3], ns = in6[4], ni = in6[5];
     auto pow2_or_zero = [](int v) { return v == 0 || (v > 0 && (v & (v - 1)) == 0); };
     if (!pow2_or_zero(r) || r > 256 || !pow2_or_zero(wx) || wx > 32 || !pow2_or_zero(wl) || wl > 32 ||
-        (sc != 0 && sc != 1) || ns < 0 || ns > 2) {
+        (sc != 0 && sc != 1) || ns < 0 || ns > 2 || ni < 0 || ni > 2) {
         set_error("pd_plan_set_tuning: rows and widths must be 0 or powers of two (rows <= 256, widths <= 32), "
                   "schedule 0 or 1, stages 0, 1 or 2");
         return PD_ERR_ARG;
@@ -224,6 +227,7 @@ extern "C" pd_status pd_plan_set_tuning(pd_plan *p, const int *in5)
     p->tune_w[1] = wl;
     p->tune_sched = sc;
     p->tune_stages = ns;
+    p->tune_stages_inv = ni;
     drop_graphs(p);
     return PD_OK;
 }

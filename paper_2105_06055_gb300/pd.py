@@ -312,17 +312,18 @@ class Plan:
         """W for bond breaking: False = convolution form (Eq. 102), True = horizon sum (Eq. 47)."""
         _check(load().pd_plan_set_energy_mode(self._h, 1 if direct else 0), "pd_plan_set_energy_mode")
 
-    def set_tuning(self, rows=0, w_x2=0, w_last=0, sched=0, stages=0):
+    def set_tuning(self, rows=0, w_x2=0, w_last=0, sched=0, stages=0, stages_inv=0):
         """Pin a pass configuration (0 = built-in heuristic)."""
-        arr = (ctypes.c_int * 5)(int(rows), int(w_x2), int(w_last), int(sched), int(stages))
+        arr = (ctypes.c_int * 6)(int(rows), int(w_x2), int(w_last), int(sched), int(stages), int(stages_inv))
         _check(load().pd_plan_set_tuning(self._h, arr), "pd_plan_set_tuning")
 
     @property
     def tuning(self):
-        """{rows, w_x2, w_last, sched, stages} picked by autotune (0 = built-in heuristic)."""
-        out = (ctypes.c_int * 5)()
+        """{rows, w_x2, w_last, sched, stages, stages_inv} picked by autotune (0 = built-in heuristic)."""
+        out = (ctypes.c_int * 6)()
         _check(load().pd_plan_tuning(self._h, out), "pd_plan_tuning")
-        return {"rows": out[0], "w_x2": out[1], "w_last": out[2], "sched": out[3], "stages": out[4]}
+        return {"rows": out[0], "w_x2": out[1], "w_last": out[2], "sched": out[3], "stages": out[4],
+                "stages_inv": out[5]}
 
     def force_adjoint(self, u, gL, s=None, want_gu=True, want_gs=True, stream=None):
         u = self._field(u, self.dim, "u")
