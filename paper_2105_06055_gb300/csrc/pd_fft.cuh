@@ -328,16 +328,6 @@ struct op_node_acc<Op, std::void_t<decltype(Op::kNodeAcc)>> : std::bool_constant
 // the next tile are in flight while the current one is transformed. Twiddles
 // are copied to shared memory once; outputs leave through coalesced stores.
 // Block accumulators (acc) run over all tiles of the block.
-// Row ops may declare prefetch(row0, rows, tid, nthreads): called at the start
-// of each tile, before its bulk copies complete, to start the node fields the
-// op reads later towards L2.
-template <class Op, class = void>
-struct op_has_prefetch : std::false_type {
-};
-template <class Op>
-struct op_has_prefetch<Op, std::void_t<decltype(&Op::prefetch)>> : std::true_type {
-};
-
 // Row ops may declare kMinBlocks (resident 256-thread blocks per SM the
 // compiler must allow, i.e. a register cap of 256 / kMinBlocks per thread).
 template <class Op, class = void>
@@ -418,7 +408,6 @@ __global__ void __launch_bounds__(256, op_min_blocks<Op>::value) k_rows(RowGeom 
         const bool pre = kLoad && ns == 2 && tn < ntiles;
         if (pre && threadIdx.x == 0) issue(tn, s ^ 1);
         if (kLoad && ns == 1 && it > 0 && threadIdx.x == 0) issue(t, 0);
-        if constexpr (op_has_prefetch<Op>::value) op.prefetch(t * rows, rows, threadIdx.x, blockDim.x);
         if constexpr (kLoad) {
             const bool ok = mbar_wait(&mbar[s], (phase >> s) & 1u, g.err);
             phase ^= 1u << s;

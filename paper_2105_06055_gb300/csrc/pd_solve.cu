@@ -222,20 +222,6 @@ struct EpiCG {
         }
     }
     __device__ void sparse(const RowCtx<T> &, int, int) const {}
-    // p, r and the boundary index of the tile's rows towards L2 while the
-    // tile's spectra arrive and are transformed
-    __device__ __forceinline__ void prefetch(int64_t row0, int rows, int tid, int nthreads) const
-    {
-        const int64_t base = row0 * n1, len = (int64_t)rows * n1;  // nodes
-        const int lines = (int)((len * sizeof(T) + 127) / 128);
-        for (int k = tid; k < 2 * D * lines; k += nthreads) {
-            const int v = k / lines, l = k - v * lines;
-            const T *src = (v < D ? pv + v * N : r + (v - D) * N) + base;
-            prefetch_l2(reinterpret_cast<const char *>(src) + 128 * l);
-        }
-        const int glines = (int)((len * sizeof(int) + 127) / 128);
-        for (int k = tid; k < glines; k += nthreads) prefetch_l2(reinterpret_cast<const char *>(gidx + base) + 128 * k);
-    }
     __device__ __forceinline__ void emit(const RowCtx<T> &c, int rl, int i1, const T *s0, const T *s1,
                                          CgAcc &acc) const
     {
