@@ -174,3 +174,23 @@ def test_dr_batched_config4_full_size(pdm, oracle):
                                  ("bond", oracle.alpha_bond(2, 1.0, c["delta"])))
     assert np.linalg.norm(res) / np.linalg.norm(c["chi_omega"] * c["b"]) <= 1.5e-8
     batch.close()
+
+
+def test_tuning_and_mode_arguments_are_checked(pdm):
+    """Bad pass configurations and energy modes are rejected with PD_ERR_ARG and
+    leave the plan usable; a pinned configuration round-trips."""
+    shape = (64, 64)
+    chi = inputs.box_mask(shape, (4, 4), (60, 60))
+    plan = pdm.Plan(pdm.Problem(shape=shape, delta=3.0), _t(chi, torch.uint8))
+    for bad in [(3, 0, 0, 0, 0, 0), (0, 64, 0, 0, 0, 0), (0, 0, 6, 0, 0, 0), (0, 0, 0, 2, 0, 0),
+                (0, 0, 0, 0, 3, 0), (0, 0, 0, 0, 0, -1)]:
+        with pytest.raises(pdm.PDError) as ei:
+            plan.set_tuning(*bad)
+        assert ei.value.status == -1
+    assert pdm.load().pd_plan_set_energy_mode(plan._h, 2) == -1  # modes are 0 and 1
+    plan.set_tuning(8, 0, 8, 1, 1, 2)
+    assert plan.tuning == {"rows": 8, "w_x2": 0, "w_last": 8, "sched": 1, "stages": 1, "stages_inv": 2}
+    u = torch.tensor(inputs.sine_modes(shape, 2, 1e-3, 2, 1) * chi, dtype=torch.float32, device=DEV)
+    L = plan.force(u)
+    assert torch.isfinite(L).all()
+    plan.close()
