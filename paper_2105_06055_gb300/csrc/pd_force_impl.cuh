@@ -68,7 +68,7 @@ __device__ __forceinline__ void load_ghat(const Model<T> &m, const SpecIdx<T> &s
 // Slots: 0-2 chi u_j (x1, x2 transformed), 3 S, 4 theta, 5-7 fully transformed
 // chi u_j, 0-2 again for the outputs (every 3D last-axis pass writes slots it
 // does not read).
-// last axis, round 1: transform chi u_j (kept in slots 5-7), S = Σ -i ghat_i X_i
+// last axis, first combine: transform chi u_j (kept in slots 5-7), S = Σ -i ghat_i X_i
 template <typename T>
 struct CombTheta {
     static constexpr int kFin = 3, kFout = 1, kMode = 2, kPre = 0, kTab = 3;
@@ -128,7 +128,7 @@ struct RowTheta {
     __device__ void block_done(DSum &) const {}
 };
 
-// last axis, round 2: Y_i = M^_ij X_j + i ka ghat_i Theta
+// last axis, second combine: Y_i = M^_ij X_j + i ka ghat_i Theta
 template <typename T>
 struct CombState {
     static constexpr int kFin = 4, kFout = 3, kMode = 2, kPre = 3, kTab = 9;
