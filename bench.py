@@ -132,6 +132,22 @@ MEASURED_TRAFFIC = {
 }
 
 
+def max_over_ranks(value, world, device=None):
+    """The largest of one float per rank (a replicated job takes as long as its
+    slowest rank); `value` itself when there is one rank."""
+    if world <= 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, t_max_ms):
+    """Whole-job throughput: every rank processes units_per_rank in the job time."""
+    return world * units_per_rank / (t_max_ms * 1e-3)
+
+
 def pass_bytes(kind, N, nbound, d=3, nc=6):
     """Algorithmic bytes of one launch of each FP32 pass of the fused CG
     iteration (d = 3 components; a packed half spectrum holds 4 bytes per node).
@@ -235,12 +251,8 @@ def run_native(args, rank, world):
     plan.profile(False)
     evals_per_step = prof["rows_inv"][1] / args.steps  # one inverse row pass per force evaluation
     total_ms = sum(times)
-    t_max = total_ms
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * evals_per_step * args.steps * N / (t_max * 1e-3)
+    t_max = max_over_ranks(total_ms, world, dev)
+    value = job_rate(evals_per_step * args.steps * N, world, t_max)
 
     # dominant pass and its roofline
     peak, peak_kind = load_peaks()
@@ -523,7 +535,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--n", type=int, default=N_GRID)
+    ap.add_argument("--n", "--grid", dest="n", type=int, default=N_GRID)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="static", choices=["static", "batched", "force"])
     ap.add_argument("--no-autotune", action="store_true", help="skip the pass autotuner (built-in tile heuristic)")
