@@ -508,6 +508,11 @@ def run_batched(args):
     return out
 
 
+def oracle_threads(t):
+    import oracle
+    oracle.set_threads(t)
+
+
 def oracle_sample(n, nevals, threads=None):
     """Time the FP64 oracle's state-based force on the same workload (host cores)."""
     import numpy as np
@@ -626,6 +631,12 @@ def main():
             result["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                       "sample": f"2 FP64 direct-sum state-based force evaluations of the "
                                                 f"{args.n}^3 workload ({dt:.1f} s)"}
+            # the same on one host core (one evaluation)
+            v1, _, dt1 = oracle_sample(args.n, 1, threads=1)
+            oracle_threads(cores)
+            result["cpu_baseline"]["value_1_core"] = v1
+            result["cpu_baseline"]["sample_1_core"] = (f"1 FP64 direct-sum evaluation of the {args.n}^3 workload on "
+                                                       f"one thread ({dt1:.1f} s)")
         print(json.dumps(result))
     if world > 1:
         torch.distributed.barrier()
