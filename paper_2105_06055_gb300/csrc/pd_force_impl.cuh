@@ -55,16 +55,6 @@ pd_status force_bond_pipeline(pd_plan *p, const T *u, const T *s, const uint8_t 
 // ghat_i = dV gamma_i / N.
 // ---------------------------------------------------------------------------
 
-template <typename T>
-__device__ __forceinline__ void load_ghat(const Model<T> &m, const SpecIdx<T> &s, T *g)
-{
-    const T *t = m.ghat + s.idx;
-    const int64_t fs = m.fold_sz;
-    g[0] = t[0];
-    g[1] = s.fy ? -t[fs] : t[fs];
-    g[2] = s.fz ? -t[2 * fs] : t[2 * fs];
-}
-
 // Slots: 0-2 chi u_j (x1, x2 transformed), 3 S, 4 theta, 5-7 fully transformed
 // chi u_j, 0-2 again for the outputs (every 3D last-axis pass writes slots it
 // does not read).

@@ -46,46 +46,6 @@ struct Model {
     T ka;              // (3 kappa - 5 mu)/m0 (state-based)
 };
 
-// Folded-table lookup of a symmetric kernel spectrum at mode (kx, ky, kz),
-// kx in [0, n1/2]. Off-diagonal components are odd in each of their two axes.
-template <typename T>
-struct SpecIdx {
-    int64_t idx;
-    bool fy, fz;
-};
-
-template <typename T>
-__device__ __forceinline__ SpecIdx<T> spec_index(const Model<T> &m, int kx, int ky, int kz)
-{
-    SpecIdx<T> r;
-    r.fy = ky > m.ky_half;
-    r.fz = kz > m.kz_half;
-    const int kyf = r.fy ? m.n2 - ky : ky;
-    const int kzf = r.fz ? m.n3 - kz : kz;
-    r.idx = ((int64_t)kzf * (m.ky_half + 1) + kyf) * (m.h + 1) + kx;
-    return r;
-}
-
-// Component order: 2D 11,22,12; 3D 11,22,33,12,13,23.
-template <typename T>
-__device__ __forceinline__ void load_mhat(const Model<T> &m, const SpecIdx<T> &s, T *M /*3x3*/)
-{
-    const T *t = m.mhat + s.idx;
-    const int64_t fs = m.fold_sz;
-    if (m.dim == 2) {
-        const T m11 = t[0], m22 = t[fs], m12 = s.fy ? -t[2 * fs] : t[2 * fs];
-        M[0] = m11; M[1] = m12; M[3] = m12; M[4] = m22;
-    } else {
-        const T m11 = t[0], m22 = t[fs], m33 = t[2 * fs];
-        const T m12 = s.fy ? -t[3 * fs] : t[3 * fs];
-        const T m13 = s.fz ? -t[4 * fs] : t[4 * fs];
-        const T m23 = (s.fy != s.fz) ? -t[5 * fs] : t[5 * fs];
-        M[0] = m11; M[1] = m12; M[2] = m13;
-        M[3] = m12; M[4] = m22; M[5] = m23;
-        M[6] = m13; M[7] = m23; M[8] = m33;
-    }
-}
-
 struct HorizonDev {
     const int *off;   // 3 x cnt
     const double *c;  // ncomp x cnt: C_ij(xi) dV
