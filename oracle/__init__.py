@@ -18,11 +18,18 @@ Contents
     FP64 conjugate gradient on the EC static residual (Eq. 89), and model
     constants (§5.1, §5.2).
 
+Every sum takes the bond's quadrature weight from the horizon: the constant dV
+of the paper's examples, or, after ``set_volume_rule(1)`` (or inside
+``with partial_volumes():``), the linear partial-volume weight beta(|xi|) dV
+that §4.1.1 allows in place of dV (the rule of Hu, Ha and Bobaru).
+
 Every function here is FP64. Parity status of each function is listed in the
-``PINS`` table at the bottom, which the pin tests import.
+``PINS`` table at the bottom (the tests that hold each pin are in
+``tests/test_oracle_pins.py`` and ``tests/test_partial_volume_pins.py``).
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import math
 import os
@@ -63,7 +70,9 @@ def _load():
             I, D = ctypes.c_int, ctypes.c_double
             lib.or_num_threads.restype = I
             lib.or_set_threads.argtypes = [I]
-            lib.or_horizon.argtypes = [I, P, D, I, P, P]
+            lib.or_horizon.argtypes = [I, P, D, I, P, P, P]
+            lib.or_set_volume_rule.argtypes = [I]
+            lib.or_volume_rule.restype = I
             lib.or_horizon.restype = I
             lib.or_force_bond.argtypes = [I, P, P, D, D, P, P, P, P]
             lib.or_energy_bond.argtypes = [I, P, P, D, D, P, P, P, P]
@@ -106,16 +115,45 @@ def set_threads(t: int) -> None:
 # Model constants (§3.1, §3.3, §5.1, §5.2)
 # ----------------------------------------------------------------------------
 
-def horizon(dim: int, dx, delta: float):
-    """Integer offsets o (|H| x 3) and lengths |xi| of the horizon (R1, R2)."""
+def set_volume_rule(rule: int) -> None:
+    """Quadrature weight of every later call: 0 the constant dV of the paper's
+    examples (§4.1.1), 1 linear partial volumes beta(|xi|) dV (reading R3)."""
+    if rule not in (0, 1):
+        raise ValueError("volume rule is 0 (constant) or 1 (partial volumes)")
+    _load().or_set_volume_rule(int(rule))
+
+
+def volume_rule() -> int:
+    return int(_load().or_volume_rule())
+
+
+@contextlib.contextmanager
+def partial_volumes(on: bool = True):
+    """Run the enclosed oracle calls under the partial-volume rule (or not)."""
+    old = volume_rule()
+    set_volume_rule(1 if on else 0)
+    try:
+        yield
+    finally:
+        set_volume_rule(old)
+
+
+def horizon(dim: int, dx, delta: float, weights: bool = False):
+    """Integer offsets o (|H| x 3) and lengths |xi| of the horizon (R1, R2);
+    with ``weights`` also each bond's quadrature weight relative to dV (1, or
+    beta(|xi|) under the partial-volume rule)."""
     lib = _load()
     d = _dx(dim, dx)
+    reach = delta + 0.5 * d[0] if volume_rule() == 1 else delta
     cap = 1
     for a in range(dim):
-        cap *= 2 * int(math.floor(delta / d[a] + 1e-9)) + 1
+        cap *= 2 * int(math.floor(reach / d[a] + 1e-9)) + 1
     off = np.zeros((cap, 3), dtype=np.int32)
     ln = np.zeros(cap, dtype=np.float64)
-    cnt = lib.or_horizon(dim, _p(d), float(delta), cap, _p(off), _p(ln))
+    vol = np.zeros(cap, dtype=np.float64)
+    cnt = lib.or_horizon(dim, _p(d), float(delta), cap, _p(off), _p(ln), _p(vol))
+    if weights:
+        return off[:cnt].copy(), ln[:cnt].copy(), vol[:cnt].copy()
     return off[:cnt].copy(), ln[:cnt].copy()
 
 
@@ -140,9 +178,9 @@ def lps_constants(E: float, nu: float, dx, delta: float):
     ka = (3 kappa - 5 mu)/m0, cb = 30 mu/m0.
     """
     d = _dx(3, dx)
-    _, ln = horizon(3, d, delta)
+    _, ln, vol = horizon(3, d, delta, weights=True)
     dV = float(d[0] * d[1] * d[2])
-    m0 = float(np.sum(ln)) * dV  # omega |xi|^2 = |xi|
+    m0 = float(np.sum(vol * ln)) * dV  # omega |xi|^2 = |xi|
     kappa = E / (3.0 * (1.0 - 2.0 * nu))
     mu = E / (2.0 * (1.0 + nu))
     return (3.0 * kappa - 5.0 * mu) / m0, 30.0 * mu / m0, m0
@@ -156,9 +194,9 @@ def wc_from_stretch(dim: int, dx, delta: float, alpha: float, s0: float) -> floa
     for omega = 1/|xi|, and W_c = 1/2 alpha s0^2 dV Σ_H |xi|.
     """
     d = _dx(dim, dx)
-    _, ln = horizon(dim, d, delta)
+    _, ln, vol = horizon(dim, d, delta, weights=True)
     dV = float(np.prod(d[:dim]))
-    return 0.5 * alpha * s0 * s0 * dV * float(np.sum(ln))
+    return 0.5 * alpha * s0 * s0 * dV * float(np.sum(vol * ln))
 
 
 # ----------------------------------------------------------------------------
@@ -371,4 +409,6 @@ PINS = {
     "symbol_bond": "single-mode displacement through force_bond",
     "verlet_damage": "energy conservation without damage, time reversibility",
     "cg_static": "FP64 residual of the returned solution",
+    "partial_volumes": "weighted lattice moments vs the ball integrals (closed forms), long-wave symbol vs "
+                       "Navier-Cauchy, all-pairs brute force, invariants, family counts vs lattice count",
 }

@@ -19,7 +19,12 @@
  *   R1  horizon membership |xi| <= delta (Eq. 48), tested as
  *       sum_k (i_k dx_k)^2 <= delta^2 (1 + 1e-12)
  *   R2  the self-bond xi = 0 is excluded (C is singular there)
- *   R3  constant quadrature weight dV = dx1 dx2 dx3 (no partial volumes, §4.1.1)
+ *   R3  quadrature weight dV = dx1 dx2 dx3 (§4.1.1); under the partial-volume
+ *       rule (or_set_volume_rule(1), §4.1.1 remark on partially covered cells)
+ *       each bond's weight is beta(|xi|) dV with the linear rule of Hu, Ha and
+ *       Bobaru (PA-HHB in Seleson's 2014 comparison of one-point quadratures):
+ *       beta = min(1, (delta + h/2 - |xi|) / h) for |xi| < delta + h/2, cubic
+ *       cells of side h; the family is then every offset with beta > 0
  *   R4  the "P u" / "(C*chi) u" term enters with a minus sign: it comes from
  *       (u'_j - u_j) in Eq. 17-18; Eq. 38, 92, 93 print a plus
  *   R5  state-based kernels use the bulk m0 (Eq. 35 over a full horizon); the
@@ -47,37 +52,55 @@ typedef struct {
     int *o;      /* cnt x 3 integer offsets */
     double *xi;  /* cnt x 3 physical offsets */
     double *len; /* |xi| */
+    double *vol; /* quadrature weight of the bond relative to dV: 1, or beta(|xi|) */
 } horizon_t;
 
-/* Horizon offsets: all lattice vectors xi != 0 with |xi| <= delta (R1, R2). */
+/* 0: constant dV (the paper's examples); 1: linear partial volumes (R3). */
+static int g_volume_rule = 0;
+
+/*
+ * Horizon offsets: all lattice vectors xi != 0 with |xi| <= delta (R1, R2), or,
+ * under the partial-volume rule, with |xi| < delta + h/2, where a cell of side
+ * h centred at x + xi is partly covered by the ball of radius delta (R3).
+ */
 static int build_horizon(int dim, const double *dx, double delta, horizon_t *h)
 {
+    const int pv = g_volume_rule == 1;
+    const double hc = dx[0];
+    const double reach = pv ? delta + 0.5 * hc : delta;
     int r[3] = {0, 0, 0};
-    for (int a = 0; a < dim; ++a) r[a] = (int)floor(delta / dx[a] + 1e-9);
+    for (int a = 0; a < dim; ++a)
+        r[a] = pv ? (int)floor(reach / dx[a] * (1.0 - 1e-12)) : (int)floor(delta / dx[a] + 1e-9);
     int cap = (2 * r[0] + 1) * (2 * r[1] + 1) * (2 * r[2] + 1);
     h->o = (int *)malloc(sizeof(int) * 3 * cap);
     h->xi = (double *)malloc(sizeof(double) * 3 * cap);
     h->len = (double *)malloc(sizeof(double) * cap);
+    h->vol = (double *)malloc(sizeof(double) * cap);
     h->cnt = 0;
-    double d2max = delta * delta * (1.0 + 1e-12);
+    double d2max = pv ? reach * reach * (1.0 - 1e-12) : delta * delta * (1.0 + 1e-12);
     for (int k = -r[2]; k <= r[2]; ++k)
         for (int j = -r[1]; j <= r[1]; ++j)
             for (int i = -r[0]; i <= r[0]; ++i) {
                 if (i == 0 && j == 0 && k == 0) continue;
                 double x0 = i * dx[0], x1 = j * dx[1], x2 = (dim == 3) ? k * dx[2] : 0.0;
                 double d2 = x0 * x0 + x1 * x1 + x2 * x2;
-                if (d2 > d2max) continue;
+                if (pv ? !(d2 < d2max) : d2 > d2max) continue;
                 int c = h->cnt++;
                 h->o[3 * c] = i; h->o[3 * c + 1] = j; h->o[3 * c + 2] = k;
                 h->xi[3 * c] = x0; h->xi[3 * c + 1] = x1; h->xi[3 * c + 2] = x2;
                 h->len[c] = sqrt(d2);
+                h->vol[c] = 1.0;
+                if (pv) {
+                    double b = (reach - h->len[c]) / hc;
+                    h->vol[c] = b < 1.0 ? b : 1.0;
+                }
             }
     return h->cnt;
 }
 
 static void free_horizon(horizon_t *h)
 {
-    free(h->o); free(h->xi); free(h->len);
+    free(h->o); free(h->xi); free(h->len); free(h->vol);
 }
 
 static inline int64_t wrap_index(const int *n, int i1, int i2, int i3, const int *o)
@@ -112,8 +135,19 @@ void or_set_threads(int t)
 #endif
 }
 
-/* Number of horizon offsets and the offsets themselves (cap entries max). */
-int or_horizon(int dim, const double *dx, double delta, int cap, int *off_out, double *len_out)
+/* Volume rule of every later call: 0 constant dV, 1 linear partial volumes (R3). */
+void or_set_volume_rule(int rule)
+{
+    g_volume_rule = rule == 1 ? 1 : 0;
+}
+
+int or_volume_rule(void)
+{
+    return g_volume_rule;
+}
+
+/* Number of horizon offsets, the offsets, lengths and weights (cap entries max). */
+int or_horizon(int dim, const double *dx, double delta, int cap, int *off_out, double *len_out, double *vol_out)
 {
     horizon_t h;
     int cnt = build_horizon(dim, dx, delta, &h);
@@ -122,6 +156,7 @@ int or_horizon(int dim, const double *dx, double delta, int cap, int *off_out, d
         off_out[3 * c + 1] = h.o[3 * c + 1];
         off_out[3 * c + 2] = h.o[3 * c + 2];
         if (len_out) len_out[c] = h.len[c];
+        if (vol_out) vol_out[c] = h.vol[c];
     }
     free_horizon(&h);
     return cnt;
@@ -154,7 +189,7 @@ void or_force_bond(int dim, const int *n, const double *dx, double delta, double
                 if (wq == 0.0) continue;
                 const double *xi = &h.xi[3 * c];
                 double r = h.len[c];
-                double coef = alpha * (1.0 / r) / (r * r) * wq; /* alpha omega / |xi|^2 */
+                double coef = alpha * (1.0 / r) / (r * r) * wq * h.vol[c]; /* alpha omega / |xi|^2 */
                 double xe = 0.0;                                 /* xi . eta */
                 for (int j = 0; j < dim; ++j) xe += xi[j] * (u[j * N + q] - u[j * N + p]);
                 for (int i = 0; i < dim; ++i) acc[i] += coef * xi[i] * xe;
@@ -187,7 +222,7 @@ void or_force_bond_at(int dim, const int *n, const double *dx, double delta, dou
                 if (!chi[q]) continue;
                 const double *xi = &h.xi[3 * c];
                 double r = h.len[c];
-                double coef = alpha * (1.0 / r) / (r * r);
+                double coef = alpha * (1.0 / r) / (r * r) * h.vol[c];
                 double xe = 0.0;
                 for (int j = 0; j < dim; ++j) xe += xi[j] * (u[j * N + q] - u[j * N + p]);
                 for (int i = 0; i < dim; ++i) acc[i] += coef * xi[i] * xe;
@@ -223,7 +258,7 @@ void or_energy_bond(int dim, const int *n, const double *dx, double delta, doubl
                 double r = h.len[c];
                 double xe = 0.0;
                 for (int j = 0; j < dim; ++j) xe += xi[j] * (u[j * N + q] - u[j * N + p]);
-                acc += alpha * (1.0 / r) / (r * r) * xe * xe; /* eta.C.eta */
+                acc += alpha * (1.0 / r) / (r * r) * h.vol[c] * xe * xe; /* eta.C.eta */
             }
         }
         W[p] = 0.5 * acc * dV;
@@ -237,6 +272,8 @@ void or_energy_bond(int dim, const int *n, const double *dx, double delta, doubl
  *   beta(x) = chi Σ_xi chi'           (initial in-body bonds, integer)
  *   nb(x)   = chi Σ_xi chi' (1 - lam lam')
  *   d(x)    = nb / beta   (0 where beta = 0)
+ * The sums run over the family; under the partial-volume rule a partly covered
+ * bond still counts as one bond (the counts are integers).
  */
 void or_damage(int dim, const int *n, const double *dx, double delta,
                const uint8_t *chi, const uint8_t *lam, int32_t *nb, int32_t *beta, double *d)
@@ -293,10 +330,10 @@ void or_force_lps(const int *n, const double *dx, double delta, double ka, doubl
                 if (!chi[q]) continue;
                 const double *xi = &h.xi[3 * c];
                 double r = h.len[c], om = 1.0 / r;
-                msum += om * r * r;
+                msum += om * r * r * h.vol[c];
                 double xe = 0.0;
                 for (int j = 0; j < dim; ++j) xe += xi[j] * (u[j * N + q] - u[j * N + p]);
-                tsum += om * xe;
+                tsum += om * xe * h.vol[c];
             }
         }
         mm[p] = chi[p] ? msum * dV : 0.0;
@@ -315,7 +352,7 @@ void or_force_lps(const int *n, const double *dx, double delta, double ka, doubl
                 double xe = 0.0;
                 for (int j = 0; j < dim; ++j) xe += xi[j] * (u[j * N + q] - u[j * N + p]);
                 for (int i = 0; i < dim; ++i)
-                    acc[i] += ka * om * xi[i] * (th[p] + th[q]) + cb * om * xi[i] * xe / (r * r);
+                    acc[i] += h.vol[c] * (ka * om * xi[i] * (th[p] + th[q]) + cb * om * xi[i] * xe / (r * r));
             }
         }
         for (int i = 0; i < dim; ++i) L[i * N + p] = chi[p] ? acc[i] * dV : 0.0;
@@ -354,7 +391,7 @@ void or_force_bond_grad_s(int dim, const int *n, const double *dx, double delta,
                 if (wq == 0.0) continue;
                 const double *xi = &h.xi[3 * c];
                 double r = h.len[c];
-                double coef = alpha * (1.0 / r) / (r * r) * wq;
+                double coef = alpha * (1.0 / r) / (r * r) * wq * h.vol[c];
                 double xu = 0.0, xp = 0.0;
                 for (int j = 0; j < dim; ++j) {
                     xu += xi[j] * (u[j * N + q] - u[j * N + p]);
@@ -386,7 +423,7 @@ void or_symbol_bond(int dim, const int *n, const double *dx, double delta, doubl
         for (int a = 0; a < dim; ++a) ph += k[a] * h.o[3 * c + a] / (double)n[a];
         double w = 1.0 - cos(2.0 * M_PI * ph);
         double r = h.len[c];
-        double coef = alpha * (1.0 / r) / (r * r) * w * dV;
+        double coef = alpha * (1.0 / r) / (r * r) * w * h.vol[c] * dV;
         for (int i = 0; i < dim; ++i)
             for (int j = 0; j < dim; ++j) M[3 * i + j] += coef * h.xi[3 * c + i] * h.xi[3 * c + j];
     }
