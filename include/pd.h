@@ -71,6 +71,16 @@ typedef struct {
     double rho;      /* mass density (Eq. 1), used by pd_step_verlet              */
     double Wc;       /* critical strain energy density (Eq. 40, 63); <= 0: no damage */
     int fp64;        /* 0: FP32 fields and FFTs; 1: FP64 fields and FFTs          */
+    int volume_rule; /* quadrature weight of a bond (§4.1.1, remark on cells only
+                        partly covered by the horizon): 0 the constant dV of the
+                        paper's examples; 1 linear partial volumes, weight
+                        beta(|xi|) dV with beta = min(1, (delta + h/2 - |xi|)/h)
+                        for |xi| < delta + h/2 (Hu, Ha and Bobaru's rule), which
+                        needs cubic cells (all dx equal to h, else PD_ERR_ARG).
+                        Part of the kernel C(xi), so the convolution structure and
+                        every entry point are unchanged; the family (and the
+                        damage counts of pd_damage) then holds every offset with
+                        beta > 0, and the body must stay that far from the faces */
 } pd_problem;
 
 typedef struct pd_plan pd_plan;  /* opaque; owns spectra, masks and workspace */
@@ -297,8 +307,9 @@ pd_status pd_damage(pd_plan *plan, const uint8_t *lambda, int32_t *nb, void *d, 
  * the allocator, a plug-in with a fixed memory budget) and so cannot create a
  * pd_plan. Same operator and result as pd_plan_create + pd_force with s = NULL
  * and W = NULL.
- *   problem: dim = 2, model = PD_LIN_BOND, fp64 = 0; grid rules as for
- *            pd_plan_create, and n[0] * n[1] <= 65536 nodes, horizon <= 512 bonds
+ *   problem: dim = 2, model = PD_LIN_BOND, fp64 = 0, volume_rule = 0 (else
+ *            PD_ERR_ARG); grid rules as for pd_plan_create, and
+ *            n[0] * n[1] <= 65536 nodes, horizon <= 512 bonds
  *            (else PD_ERR_SIZE, nothing enqueued).
  *   chi_B:   device, N bytes (0/1, body at least delta from the box faces,
  *            checked: PD_ERR_ARG otherwise). u: device, 2 x N floats.

@@ -170,6 +170,10 @@ extern "C" pd_status pd_force2d_noalloc(const pd_problem *pr, const uint8_t *chi
         set_error("pd_force2d_noalloc: delta, E and dx must be positive");
         return PD_ERR_ARG;
     }
+    if (pr->volume_rule != 0) {
+        set_error("pd_force2d_noalloc: constant dV only (volume_rule 0); use pd_plan_create for partial volumes");
+        return PD_ERR_ARG;
+    }
     const int r1 = (int)std::floor(pr->delta / pr->dx[0] + 1e-9), r2 = (int)std::floor(pr->delta / pr->dx[1] + 1e-9);
     if (r1 < 1 || 2 * r1 + 2 > n1 || 2 * r2 + 2 > n2) {
         set_error("pd_force2d_noalloc: horizon of %d x %d cells does not fit the grid", r1, r2);

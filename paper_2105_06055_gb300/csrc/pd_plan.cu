@@ -398,16 +398,32 @@ struct HostHorizon {
     int cnt = 0;
 };
 
-// Horizon offsets (0 < |xi| <= delta, tolerance 1e-12 relative on delta^2) and
-// per-bond kernel values (omega = 1/|xi|):
-//   C_ij = kc xi_i xi_j / |xi|^3 dV, g_i = xi_i / |xi| dV, omega|xi|^2 dV = |xi| dV.
+// Reach of the family along axis a in cells: offsets with |xi| <= delta
+// (tolerance 1e-12 relative on delta^2), or, with partial volumes, every
+// offset whose cell the ball of radius delta still covers in part,
+// |xi| < delta + h/2.
+int family_radius(const pd_problem *pr, int a)
+{
+    if (pr->volume_rule == 1) return (int)std::floor((pr->delta + 0.5 * pr->dx[0]) / pr->dx[a] * (1.0 - 1e-12));
+    return (int)std::floor(pr->delta / pr->dx[a] + 1e-9);
+}
+
+// Horizon offsets and per-bond kernel values (omega = 1/|xi|):
+//   C_ij = kc xi_i xi_j / |xi|^3 w, g_i = xi_i / |xi| w, omega|xi|^2 w = |xi| w,
+// with the bond's quadrature weight w = dV, or beta(|xi|) dV under the linear
+// partial-volume rule (Hu, Ha and Bobaru): beta = min(1, (delta + h/2 - |xi|)/h)
+// on cubic cells of side h; the weight is part of the kernel, so every
+// convolution stays a convolution (§4.1.1).
 HostHorizon make_horizon(const pd_plan *p, double kc)
 {
     HostHorizon h;
     const int dim = p->dim;
+    const bool pv = p->prob.volume_rule == 1;
+    const double hc = p->prob.dx[0];
+    const double reach = pv ? p->prob.delta + 0.5 * hc : p->prob.delta;
     int r[3] = {0, 0, 0};
-    for (int a = 0; a < dim; ++a) r[a] = (int)std::floor(p->prob.delta / p->prob.dx[a] + 1e-9);
-    const double d2max = p->prob.delta * p->prob.delta * (1.0 + 1e-12);
+    for (int a = 0; a < dim; ++a) r[a] = family_radius(&p->prob, a);
+    const double d2max = pv ? reach * reach * (1.0 - 1e-12) : p->prob.delta * p->prob.delta * (1.0 + 1e-12);
     const double dV = p->dV;
     std::vector<double> xi;
     for (int k = -r[2]; k <= r[2]; ++k)
@@ -416,7 +432,7 @@ HostHorizon make_horizon(const pd_plan *p, double kc)
                 if (!i && !j && !k) continue;
                 const double x[3] = {i * p->prob.dx[0], j * p->prob.dx[1], dim == 3 ? k * p->prob.dx[2] : 0.0};
                 const double s2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
-                if (s2 > d2max) continue;
+                if (pv ? !(s2 < d2max) : s2 > d2max) continue;
                 h.off.push_back(i);
                 h.off.push_back(j);
                 h.off.push_back(k);
@@ -434,12 +450,13 @@ HostHorizon make_horizon(const pd_plan *p, double kc)
     for (int c = 0; c < h.cnt; ++c) {
         const double *x = &xi[3 * c];
         const double rr = std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+        const double w = pv ? dV * std::min(1.0, (reach - rr) / hc) : dV;
         for (int q = 0; q < nc; ++q) {
             const int a = dim == 3 ? ci[q] : ci2[q], b = dim == 3 ? cj[q] : cj2[q];
-            h.c[(size_t)q * h.cnt + c] = kc * x[a] * x[b] / (rr * rr * rr) * dV;
+            h.c[(size_t)q * h.cnt + c] = kc * x[a] * x[b] / (rr * rr * rr) * w;
         }
-        for (int i = 0; i < 3; ++i) h.g[(size_t)i * h.cnt + c] = x[i] / rr * dV;
-        h.w2[c] = rr * dV;
+        for (int i = 0; i < 3; ++i) h.g[(size_t)i * h.cnt + c] = x[i] / rr * w;
+        h.w2[c] = rr * w;
     }
     return h;
 }
@@ -586,13 +603,22 @@ static pd_status plan_create_impl(const pd_problem *pr, const uint8_t *chi_B, co
                   pr->n[0], pr->n[1], pr->n[2]);
         return PD_ERR_SIZE;
     }
+    if (pr->volume_rule != 0 && pr->volume_rule != 1) {
+        set_error("volume_rule must be 0 (constant dV) or 1 (partial volumes), got %d", pr->volume_rule);
+        return PD_ERR_ARG;
+    }
     int r[3] = {0, 0, 0};
     for (int a = 0; a < dim; ++a) {
         if (!(pr->dx[a] > 0)) {
             set_error("dx[%d] must be positive", a);
             return PD_ERR_ARG;
         }
-        r[a] = (int)std::floor(pr->delta / pr->dx[a] + 1e-9);
+        if (pr->volume_rule == 1 && std::fabs(pr->dx[a] - pr->dx[0]) > 1e-12 * pr->dx[0]) {
+            set_error("partial volumes need cubic cells (dx[%d] = %g differs from dx[0] = %g)", a, pr->dx[a],
+                      pr->dx[0]);
+            return PD_ERR_ARG;
+        }
+        r[a] = family_radius(pr, a);
     }
     if (r[0] < 1 || 2 * r[0] + 2 > n1 || 2 * r[1] + 2 > n2 || (dim == 3 && 2 * r[2] + 2 > n3)) {
         set_error("horizon of %d x %d x %d cells does not fit the grid", r[0], r[1], r[2]);
@@ -689,7 +715,7 @@ static pd_status plan_create_impl(const pd_problem *pr, const uint8_t *chi_B, co
             return PD_ERR_ARG;
         }
         if (hbad & 1) {
-            set_error("the body must stay at least delta away from the box faces (chi_B = 1 within delta of a face)");
+            set_error("the body must stay at least delta (delta + h/2 with partial volumes) away from the box faces");
             return PD_ERR_ARG;
         }
         if (hbad & 2) {

@@ -47,7 +47,7 @@ class _Problem(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("dx", ctypes.c_double * 3),
                 ("delta", ctypes.c_double), ("model", ctypes.c_int), ("E", ctypes.c_double),
                 ("nu", ctypes.c_double), ("rho", ctypes.c_double), ("Wc", ctypes.c_double),
-                ("fp64", ctypes.c_int)]
+                ("fp64", ctypes.c_int), ("volume_rule", ctypes.c_int)]
 
 
 def load():
@@ -150,6 +150,7 @@ class Problem:
     rho: float = 1.0
     Wc: float = 0.0
     fp64: bool = False
+    volume_rule: int = 0           # 0 constant dV (§4.1.1); 1 linear partial volumes (cubic cells)
 
     def to_c(self) -> _Problem:
         p = _Problem()
@@ -165,6 +166,7 @@ class Problem:
         p.model = int(self.model)
         p.E, p.nu, p.rho, p.Wc = float(self.E), float(self.nu), float(self.rho), float(self.Wc)
         p.fp64 = 1 if self.fp64 else 0
+        p.volume_rule = int(self.volume_rule)
         return p
 
     @property

@@ -43,3 +43,44 @@ def test_library_exports_every_declared_symbol():
 def test_binding_names_match_header():
     from paper_2105_06055_gb300 import pd
     assert set(pd.EXPORTS) == _declared()
+
+
+def test_problem_struct_layout_matches_header(tmp_path):
+    """The binding's ctypes pd_problem has the size and field offsets that a C
+    compiler gives the header's struct (the struct crosses the ABI by pointer)."""
+    from paper_2105_06055_gb300 import pd
+    fields = [f[0] for f in pd._Problem._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"pd.h\"\nint main(void){\n"
+                   + 'printf("%zu\\n", sizeof(pd_problem));\n'
+                   + "".join(f'printf("%zu\\n", offsetof(pd_problem, {f}));\n' for f in fields)
+                   + "return 0;}\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert got[0] == ctypes.sizeof(pd._Problem)
+    assert got[1:] == [getattr(pd._Problem, f).offset for f in fields]
+
+
+def test_volume_rule_arguments_are_checked_on_the_host():
+    """The quadrature-rule and cell-shape checks return PD_ERR_ARG before any
+    device work, so they run without a GPU."""
+    from paper_2105_06055_gb300 import build, pd
+    build.build()
+    lib = pd.load()
+    buf = (ctypes.c_uint8 * 64)()
+    ptr = ctypes.cast(buf, ctypes.c_void_p)
+
+    def create(**kw):
+        prob = pd.Problem(shape=(64, 64), delta=3.0, **kw).to_c()
+        h = ctypes.c_void_p()
+        st = lib.pd_plan_create(ctypes.byref(prob), ptr, None, None, ctypes.byref(h))
+        return st, lib.pd_last_error_detail().decode()
+
+    st, msg = create(volume_rule=2)
+    assert st == -1 and "volume_rule" in msg
+    st, msg = create(volume_rule=1, dx=(1.0, 1.1))
+    assert st == -1 and "cubic cells" in msg
+    prob = pd.Problem(shape=(64, 64), delta=3.0, volume_rule=1).to_c()
+    st = lib.pd_force2d_noalloc(ctypes.byref(prob), ptr, ptr, ptr, None)
+    assert st == -1 and "volume_rule" in lib.pd_last_error_detail().decode()
