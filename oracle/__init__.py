@@ -12,7 +12,8 @@ Contents
     the linearized bond model (Eq. 17-18, 75, 100), its strain energy density
     (Eq. 47, 102), damage counts (Eq. 12, 44, reading R11), the linearized
     state-based solid (Eq. 33-39, 92-94), the node-weight gradient of the bond
-    operator, and the periodic Fourier symbol (Eq. 57).
+    operator, the periodic Fourier symbol (Eq. 57), and the nonlinear
+    rotation-invariant bond model with its energy density (§3.2, Eq. 19-22).
   * Python drivers written step by step in the paper's order: velocity-Verlet
     with embedded constraint and energy-based bond breaking (Eq. 63, 83-84),
     FP64 conjugate gradient on the EC static residual (Eq. 89), and model
@@ -76,6 +77,8 @@ def _load():
             lib.or_horizon.restype = I
             lib.or_force_bond.argtypes = [I, P, P, D, D, P, P, P, P]
             lib.or_energy_bond.argtypes = [I, P, P, D, D, P, P, P, P]
+            lib.or_force_nl.argtypes = [I, P, P, D, D, P, P, P, P]
+            lib.or_energy_nl.argtypes = [I, P, P, D, D, P, P, P, P]
             lib.or_force_bond_at.argtypes = [I, P, P, D, D, P, P, P, ctypes.c_int64, P]
             lib.or_damage.argtypes = [I, P, P, D, P, P, P, P, P]
             lib.or_force_lps.argtypes = [P, P, D, D, D, P, P, P, P, P]
@@ -249,6 +252,29 @@ def energy_bond(u, chi, dx, delta, alpha, lam=None):
     return W
 
 
+def force_nonlinear(u, chi, dx, delta, alpha, lam=None):
+    """Nonlinear rotation-invariant bond model (§3.2, Eq. 19-22):
+    L = chi lam Σ chi' lam' c/2 (|xi+eta|^2 - |xi|^2)(xi+eta) dV, c = alpha/|xi|^3."""
+    chi = _u8(chi)
+    dim, n = _grid(chi.shape)
+    u = _f64(u)
+    lam = None if lam is None else _u8(lam)
+    L = np.empty_like(u)
+    _load().or_force_nl(dim, _p(n), _p(_dx(dim, dx)), float(delta), float(alpha), _p(chi), _p(lam), _p(u), _p(L))
+    return L
+
+
+def energy_nonlinear(u, chi, dx, delta, alpha, lam=None):
+    """W = chi lam Σ chi' lam' c/8 (|xi+eta|^2 - |xi|^2)^2 dV (the potential of Eq. 21)."""
+    chi = _u8(chi)
+    dim, n = _grid(chi.shape)
+    u = _f64(u)
+    lam = None if lam is None else _u8(lam)
+    W = np.empty(chi.shape, dtype=np.float64)
+    _load().or_energy_nl(dim, _p(n), _p(_dx(dim, dx)), float(delta), float(alpha), _p(chi), _p(lam), _p(u), _p(W))
+    return W
+
+
 def damage(chi, lam, dx, delta):
     """(nb, beta, d): broken in-body bonds, initial in-body bonds, damage index
     (Eq. 12 with mu = lam lam', Eq. 44; reading R11)."""
@@ -409,6 +435,10 @@ PINS = {
     "symbol_bond": "single-mode displacement through force_bond",
     "verlet_damage": "energy conservation without damage, time reversibility",
     "cg_static": "FP64 residual of the returned solution",
+    "force_nonlinear": "finite rigid rotations give zero force (the linearized model does not), small-"
+                       "displacement limit = force_bond, -grad of the total energy, total force zero, all-pairs "
+                       "brute force, the convolutional form of Eq. 26 evaluated with numpy FFTs",
+    "energy_nonlinear": "small-displacement limit = energy_bond (Eq. 47); zero under finite rigid rotations",
     "partial_volumes": "weighted lattice moments vs the ball integrals (closed forms), long-wave symbol vs "
                        "Navier-Cauchy, all-pairs brute force, invariants, family counts vs lattice count",
 }

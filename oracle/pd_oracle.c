@@ -267,6 +267,89 @@ void or_energy_bond(int dim, const int *n, const double *dx, double delta, doubl
 }
 
 /*
+ * Nonlinear, rotation-invariant bond model (§3.2, Eq. 19-22) with the
+ * embedded-constraint cut (Eq. 75) and a bond factor lam lam' (Eq. 44):
+ *   f(xi, eta) = alpha omega |xi| (s + 3/2 s^2 + 1/2 s^3) (xi + eta)/|xi + eta|,
+ *   s = (|xi + eta| - |xi|)/|xi|        (bond strain, Eq. 20),
+ * which the paper rewrites (Eq. 21) as
+ *   f = c(xi)/2 (|xi + eta|^2 - |xi|^2)(xi + eta),  c = alpha omega / |xi|^2,
+ * a polynomial in eta (the form summed here, no square roots of |xi + eta|).
+ *   L(x) = chi lam Σ_xi chi' lam' f(xi, u' - u) dV.
+ * lam == NULL means lam = 1. omega = 1/|xi|.
+ */
+void or_force_nl(int dim, const int *n, const double *dx, double delta, double alpha,
+                 const uint8_t *chi, const uint8_t *lam, const double *u, double *L)
+{
+    horizon_t h;
+    build_horizon(dim, dx, delta, &h);
+    const int64_t N = (int64_t)n[0] * n[1] * n[2];
+    const double dV = dvol(dim, dx);
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < N; ++p) {
+        int i1 = (int)(p % n[0]), i2 = (int)((p / n[0]) % n[1]), i3 = (int)(p / ((int64_t)n[0] * n[1]));
+        double acc[3] = {0, 0, 0};
+        int wx = chi[p] && (lam ? lam[p] : 1);
+        if (wx) {
+            for (int c = 0; c < h.cnt; ++c) {
+                int64_t q = wrap_index(n, i1, i2, i3, &h.o[3 * c]);
+                if (!(chi[q] && (lam ? lam[q] : 1))) continue;
+                const double *xi = &h.xi[3 * c];
+                double r = h.len[c];
+                double cc = alpha * (1.0 / r) / (r * r) * h.vol[c];
+                double y[3] = {0, 0, 0}, yy = 0.0; /* y = xi + eta */
+                for (int j = 0; j < dim; ++j) {
+                    y[j] = xi[j] + (u[j * N + q] - u[j * N + p]);
+                    yy += y[j] * y[j];
+                }
+                double g = 0.5 * cc * (yy - r * r);
+                for (int i = 0; i < dim; ++i) acc[i] += g * y[i];
+            }
+        }
+        for (int i = 0; i < dim; ++i) L[i * N + p] = wx * acc[i] * dV;
+    }
+    free_horizon(&h);
+}
+
+/*
+ * Energy density of the same model: f is the gradient in eta of the pairwise
+ * potential w(xi, eta) = c/8 (|xi + eta|^2 - |xi|^2)^2, and
+ *   W(x) = chi lam Σ_xi chi' lam' w(xi, u' - u) dV,
+ * which for small eta is 1/2 Σ eta.C.eta dV, the density of Eq. 47 (R9).
+ */
+void or_energy_nl(int dim, const int *n, const double *dx, double delta, double alpha,
+                  const uint8_t *chi, const uint8_t *lam, const double *u, double *W)
+{
+    horizon_t h;
+    build_horizon(dim, dx, delta, &h);
+    const int64_t N = (int64_t)n[0] * n[1] * n[2];
+    const double dV = dvol(dim, dx);
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < N; ++p) {
+        int i1 = (int)(p % n[0]), i2 = (int)((p / n[0]) % n[1]), i3 = (int)(p / ((int64_t)n[0] * n[1]));
+        double acc = 0.0;
+        int wx = chi[p] && (lam ? lam[p] : 1);
+        if (wx) {
+            for (int c = 0; c < h.cnt; ++c) {
+                int64_t q = wrap_index(n, i1, i2, i3, &h.o[3 * c]);
+                if (!(chi[q] && (lam ? lam[q] : 1))) continue;
+                const double *xi = &h.xi[3 * c];
+                double r = h.len[c];
+                double cc = alpha * (1.0 / r) / (r * r) * h.vol[c];
+                double yy = 0.0;
+                for (int j = 0; j < dim; ++j) {
+                    double yj = xi[j] + (u[j * N + q] - u[j * N + p]);
+                    yy += yj * yj;
+                }
+                double d = yy - r * r;
+                acc += 0.125 * cc * d * d;
+            }
+        }
+        W[p] = acc * dV;
+    }
+    free_horizon(&h);
+}
+
+/*
  * Broken-bond count and damage index (Eq. 12 with mu = lam lam' (Eq. 44) and the
  * bond cut of Eq. 75; reading R11):
  *   beta(x) = chi Σ_xi chi'           (initial in-body bonds, integer)
