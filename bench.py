@@ -577,16 +577,13 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
 
-    if args.workload == "batched":
-        print(json.dumps(run_batched(args)))
-        return
-    if args.workload == "force":
-        print(json.dumps(run_force(args)))
-        return
-
     if args.impl == "reference":
         # the reference arm is the FP64 oracle on the host cores; rank 0 only
         if rank != 0:
+            return
+        if args.workload != "static":
+            print(json.dumps({"impl": "reference", "unavailable": f"the oracle arm times the static workload only "
+                                                                  f"(asked for --workload {args.workload})"}))
             return
         value, cores, dt = oracle_sample(args.n, 1)  # warm-up (page-in, thread spin-up)
         samples = []
@@ -619,6 +616,13 @@ def main():
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         }
         print(json.dumps(out))
+        return
+
+    if args.workload == "batched":
+        print(json.dumps(run_batched(args)))
+        return
+    if args.workload == "force":
+        print(json.dumps(run_force(args)))
         return
 
     import torch

@@ -225,3 +225,34 @@ def separable_modes(shape, nterms, kmax, amp, seed, dtype=np.float32, kmin=1):
                  .astype(dtype) for m in (n1, n2, n3)]
             out[c] += (amp / nterms) * (f[2][:, None, None] * f[1][None, :, None] * f[0][None, None, :])
     return out
+
+
+def plate_with_hole_level(level, n0=32, delta=3.0, hole_frac=0.125, sigma=1e-3, angle=0.3):
+    """One resolution level of a 2D static body fixed in physical units, for an
+    m-convergence study (§5.1, Eq. 99): box [0, n0)^2 with dx = 2^-level, so
+    n = n0 2^level nodes per side and m = delta / dx = delta 2^level.
+
+    Body: delta <= x1, x2 < n0 - delta minus a centred disk of radius
+    hole_frac * n0; clamp (chi_Omega = 0, w = 0) on delta <= x1 < 2 delta;
+    body-force layer b = sigma / delta (cos angle, sin angle) on
+    n0 - 2 delta <= x1 < n0 - delta. Every node of level k is a node of level
+    k + 1 (x = i dx), so successive levels compare on the coarser nodes."""
+    dx = 2.0 ** -level
+    n = int(n0 * 2 ** level)
+    shape = (n, n)
+    x1, x2 = coords(shape, dx)
+    eps = 1e-9 * dx
+    L = float(n0)
+    c = L / 2.0
+    inside = (x1 >= delta - eps) & (x1 < L - delta - eps) & (x2 >= delta - eps) & (x2 < L - delta - eps)
+    hole = (x1 - c) ** 2 + (x2 - c) ** 2 < (hole_frac * L) ** 2
+    chi = (inside & ~hole).astype(np.uint8)
+    clamp = (x1 < 2 * delta - eps) & (chi == 1)
+    chi_om = chi.copy()
+    chi_om[clamp] = 0
+    b = np.zeros((2,) + shape, dtype=np.float64)
+    layer = (x1 >= L - 2 * delta - eps) & (chi == 1)
+    b[0][layer] = sigma / delta * math.cos(angle)
+    b[1][layer] = sigma / delta * math.sin(angle)
+    return dict(shape=shape, dx=dx, delta=delta, m=delta / dx, chi=chi,
+                chi_omega=np.stack([chi_om, chi_om]), b=b, w=np.zeros_like(b))

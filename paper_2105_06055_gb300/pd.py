@@ -229,6 +229,8 @@ class Plan:
         if t.dtype != dt or not t.is_cuda or tuple(t.shape) != shape or not t.is_contiguous():
             raise ValueError(f"{name}: expected a contiguous CUDA {dt} tensor of shape {shape}, got "
                              f"{t.dtype} {tuple(t.shape)} (cuda={t.is_cuda}, contiguous={t.is_contiguous()})")
+        if t.device != self.device:
+            raise ValueError(f"{name}: tensor on {t.device}, the plan's buffers are on {self.device}")
         return t
 
     def close(self):
