@@ -180,7 +180,10 @@ pd_status pd_plan_set_energy_mode(pd_plan *plan, int mode);
  * FP32 plan: the inner CG runs on FP32 FFT convolutions with FP64 inner
  * products; an outer iterative refinement recomputes the residual
  * r = chi_O (b + L(u)) with the FP64 operator and stops when
- * ||r||_2 <= rtol ||chi_O b||_2. FP64 plan: plain CG on the FP64 operator.
+ * ||r||_2 <= rtol ||chi_O b||_2, or, for a problem driven by w alone
+ * (chi_O b = 0), when ||r||_2 <= rtol times the residual of the initial guess
+ * (for u = 0 on Omega that is ||chi_O L(w)||_2, the norm of the right-hand
+ * side). FP64 plan: plain CG on the FP64 operator.
  * u:  device, d x N, FP64 regardless of the plan's precision; in: initial
  *     guess (values on Gamma are replaced by w), out: solution.
  * b, w: device, d x N, FP64 (w may be NULL for w = 0).

@@ -387,23 +387,28 @@ def cg_static(chi, chi_omega, b, w, dx, delta, op, rtol=1e-12, max_iter=100000):
     """FP64 conjugate gradient for the EC static problem (Eq. 85-89, §5.1).
 
     Unknowns are u on Omega (chi_O = 1); u = w on Gamma (reading R14/R15).
-    The system chi_O (L(u) + b) = 0 with u = e + w, e = 0 off Omega, is
-    A e = r0 with A e = -chi_O L(chi_O e) (symmetric positive definite on Omega)
-    and r0 = chi_O (b + L(w)). Unpreconditioned CG from e = 0 [50].
-    Returns (u, iterations, relative residual ||chi_O(L(u)+b)|| / ||chi_O b||).
+    The system chi_O (L(u) + b) = 0 with u = e + (1 - chi_O) w, e = 0 off
+    Omega, is A e = r0 with A e = -chi_O L(chi_O e) (symmetric positive
+    definite on Omega) and r0 = chi_O (b + L((1 - chi_O) w)); values of w on
+    Omega play no part. Unpreconditioned CG from e = 0 [50].
+    Returns (u, iterations, relative residual ||chi_O(L(u)+b)|| / ||chi_O b||);
+    when chi_O b = 0 (a problem driven by w alone) the residual is relative to
+    the right-hand side ||r0|| = ||chi_O L((1 - chi_O) w)|| instead.
     """
     co = np.asarray(chi_omega, dtype=np.float64)
-    w = _f64(w)
+    wg = (1.0 - co) * _f64(w)  # w enters on Gamma only (Eq. 87-88)
     b = _f64(b)
 
     def A(e):
         return -co * _apply(op, co * e, chi, dx, delta)
 
-    r = co * (b + _apply(op, w, chi, dx, delta))
+    r = co * (b + _apply(op, wg, chi, dx, delta))
     e = np.zeros_like(r)
     p = r.copy()
     rr = float(np.vdot(r, r))
     bn = math.sqrt(float(np.vdot(co * b, co * b)))
+    if bn == 0.0:
+        bn = math.sqrt(rr) if rr > 0.0 else 1.0
     it = 0
     while it < max_iter and math.sqrt(rr) > rtol * bn:
         q = A(p)
@@ -414,7 +419,7 @@ def cg_static(chi, chi_omega, b, w, dx, delta, op, rtol=1e-12, max_iter=100000):
         p = r + (rr_new / rr) * p
         rr = rr_new
         it += 1
-    u = co * e + (1.0 - co) * w
+    u = co * e + wg
     res = static_residual(u, chi, chi_omega, b, dx, delta, op)
     return u, it, math.sqrt(float(np.vdot(res, res))) / bn
 

@@ -36,7 +36,8 @@
 // plan's FFT convolutions (FP32 on an FP32 plan) inside an iterative
 // refinement whose residual R(u) = chi_O (b + L(u)) is recomputed with the
 // FP64 operator; each relaxation cycle reduces ||F|| by 1e-3 (never below
-// half the target) and the solve stops when ||R(u)|| <= rtol ||chi_O b||.
+// half the target) and the solve stops when ||R(u)|| <= rtol ||chi_O b|| (the
+// initial ||R|| when chi_O b = 0).
 //
 // Device-side control: per specimen the graph holds
 //   [bc, FP64 residual, check -> W] WHILE(W) { K relaxation steps,
@@ -96,13 +97,16 @@ __global__ void k_dr_ir_check(double *red, const int *dev_status, cudaGraphCondi
                               double rtol)
 {
     double *s = red + kRedScal;
+    const double rn = sqrt(s[R_RN]);
     if (first) {
-        s[R_BN] = sqrt(s[R_BN2]);
-        s[R_TARGET] = rtol * (s[R_BN] > 0.0 ? s[R_BN] : 1.0);
+        // the residual is relative to ||chi_O b||; a problem driven by the
+        // prescribed w alone (b = 0 on Omega) takes the initial residual instead
+        const double rn0 = (rn > 0.0 && isfinite(rn)) ? rn : 1.0;
+        s[R_BN] = s[R_BN2] > 0.0 ? sqrt(s[R_BN2]) : rn0;
+        s[R_TARGET] = rtol * s[R_BN];
         s[R_RNPREV] = HUGE_VAL;
     }
-    const double rn = sqrt(s[R_RN]);
-    if (isfinite(rn)) s[R_REL] = s[R_BN] > 0.0 ? rn / s[R_BN] : rn;
+    if (isfinite(rn)) s[R_REL] = rn / s[R_BN];
     // a cycle that did not halve the residual counts as slow; two in a row stall
     s[R_SLOW] = (rn > 0.5 * s[R_RNPREV]) ? s[R_SLOW] + 1.0 : 0.0;
     s[R_RNPREV] = rn;

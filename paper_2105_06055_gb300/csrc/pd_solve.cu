@@ -562,15 +562,21 @@ extern "C" pd_status pd_solve_static(pd_plan *p, double *u, const double *b, con
     p->launches++;
     PD_TRY(S.finish(S.nb, S_BN, 0));
     PD_TRY(S.read_scalars());
-    const double bn = std::sqrt(S.hs()[S_BN]);
+    // the residual is relative to ||chi_O b||; a problem driven by the
+    // prescribed w alone (b = 0 on Omega) takes the initial residual instead
+    double scale = std::sqrt(S.hs()[S_BN]);
     int total = 0;
     double rel = 0.0;
     pd_status result = PD_ERR_NOT_CONVERGED;
-    const double target = rtol * (bn > 0 ? bn : 1.0);
+    double target = 0.0;
     for (int outer = 0; outer < 64; ++outer) {
         double rn = 0.0;
         PD_TRY(S.residual(u, b, &rn));
-        rel = bn > 0 ? rn / bn : rn;
+        if (outer == 0) {
+            if (!(scale > 0)) scale = (rn > 0 && std::isfinite(rn)) ? rn : 1.0;
+            target = rtol * scale;
+        }
+        rel = rn / scale;
         if (rn <= target) {
             result = PD_OK;
             break;

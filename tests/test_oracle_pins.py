@@ -497,3 +497,35 @@ def test_cg_static_residual(oracle):
     assert rel < 1e-11 and it > 10
     # the body is pulled along +x1 at the loaded end
     assert u[0][12, 19] > 0
+
+
+def test_cg_static_driven_by_prescribed_displacement(oracle):
+    """No body force: the load is the prescribed w on both clamped layers (a
+    stretch of the bar). The residual is then relative to ||chi_O L(w)||; the
+    solution keeps w on Gamma, satisfies equilibrium on Omega to that
+    tolerance, and is invariant under adding a rigid translation to w."""
+    shape = (24, 40)
+    chi = inputs.box_mask(shape, (3, 3), (37, 21))
+    x1, _ = inputs.coords(shape)
+    left = (x1 >= 3) & (x1 < 6) & (chi == 1)
+    right = (x1 >= 34) & (x1 < 37) & (chi == 1)
+    co = chi.copy()
+    co[left | right] = 0
+    chio = np.stack([co, co])
+    w = np.zeros((2,) + shape)
+    w[0][right] = 1e-3 * 30
+    b = np.zeros_like(w)
+    delta = 3.0
+    alpha = oracle.alpha_bond(2, 1.0, delta)
+    u, it, rel = oracle.cg_static(chi, chio, b, w, 1.0, delta, ("bond", alpha), rtol=1e-12)
+    assert rel < 1e-11 and it > 10
+    assert np.array_equal(u[:, co == 0], w[:, co == 0])
+    L = oracle.force_bond(u, chi, 1.0, delta, alpha)
+    r0 = chio * oracle.force_bond(w, chi, 1.0, delta, alpha)
+    assert np.linalg.norm(chio * L) < 1e-11 * np.linalg.norm(r0)
+    # stretched along +x1: monotone along the bar's axis on the centre line
+    assert np.all(np.diff(u[0][12, 6:34]) > 0)
+    # a rigid translation of the whole prescribed field translates the solution
+    t = np.array([0.3, -0.2]).reshape(2, 1, 1)
+    ut, _, _ = oracle.cg_static(chi, chio, b, w + t * chi, 1.0, delta, ("bond", alpha), rtol=1e-12)
+    assert np.allclose((ut - t * chi)[:, chi == 1], u[:, chi == 1], rtol=0, atol=1e-10)
