@@ -513,8 +513,9 @@ def oracle_threads(t):
     oracle.set_threads(t)
 
 
-def oracle_sample(n, nevals, threads=None):
-    """Time the FP64 oracle's state-based force on the same workload (host cores)."""
+def oracle_sample(n, nevals, threads=None, min_seconds=0.0):
+    """Time the FP64 oracle's state-based force on the same workload (host cores):
+    at least nevals evaluations, and more until min_seconds have passed."""
     import numpy as np
 
     import oracle
@@ -527,11 +528,13 @@ def oracle_sample(n, nevals, threads=None):
     ka, cb, _ = oracle.lps_constants(1.0, 0.25, 1.0, DELTA)
     u = inputs.sine_modes(cfg["shape"], 4, 1e-3, 3, 5)
     t0 = time.perf_counter()
-    for _ in range(nevals):
+    k = 0
+    while k < nevals or time.perf_counter() - t0 < min_seconds:
         oracle.force_lps(u, cfg["chi"], 1.0, DELTA, ka, cb)
+        k += 1
     dt = time.perf_counter() - t0
     N = n ** 3
-    return nevals * N / dt, oracle.num_threads(), dt
+    return k * N / dt, oracle.num_threads(), dt
 
 
 def main():
@@ -631,10 +634,11 @@ def main():
     result, cfg = run_native(args, rank, world)
     if rank == 0:
         if not args.no_cpu_baseline:
-            v, cores, dt = oracle_sample(args.n, 2)
+            v, cores, dt = oracle_sample(args.n, 2, min_seconds=2.0)
+            k = int(round(v * dt / args.n ** 3))
             result["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                      "sample": f"2 FP64 direct-sum state-based force evaluations of the "
-                                                f"{args.n}^3 workload ({dt:.1f} s)"}
+                                      "sample": f"{k} FP64 direct-sum state-based force evaluations of the "
+                                                f"{args.n}^3 workload ({dt:.1f} s on {cores} threads)"}
             # the same on one host core (one evaluation)
             v1, _, dt1 = oracle_sample(args.n, 1, threads=1)
             oracle_threads(cores)
