@@ -12,7 +12,10 @@ CPU only).
   * the convolutional form of Eq. 26 with the embedded-constraint mask: every
     monomial of f in u(x) and u(x + xi) becomes a correlation of a kernel
     (C_ij, a_i = c xi_i or c, Eq. 24) with a masked field, evaluated with numpy
-    FFTs, and the sum equals the direct sum.
+    FFTs, and the sum equals the direct sum;
+  * the field plan for the GPU passes (12 forward and 21 inverse half spectra
+    in 3D, with the pure correlations combined in spectral space) gives the
+    same force.
 """
 import math
 
@@ -212,4 +215,98 @@ def test_convolutional_form_eq26(oracle, dim, pv):
     with oracle.partial_volumes(pv):
         ref = oracle.force_nonlinear(u, chi, 1.0, delta, alpha, lam=lam)
         L = _eq26(oracle, u, chi, lam, 1.0, delta, alpha)
+    assert _rel(L, ref) < 1e-11
+
+
+def _spectral_passes(oracle, u, chi, lam, dx, delta, alpha):
+    """The decomposition planned for the GPU passes, on numpy half spectra:
+    forward w u_j (d), w u_i u_j (d(d+1)/2), w |u|^2 u_i (d) with w = chi lam;
+    one spectral combination per component for the terms of Eq. 26 that are
+    pure correlations, plus the inverse fields a_m*(w u_n) (d^2),
+    c*(w u_i u_j) (d(d+1)/2), c*(w u_j) (d); the correlations with w alone are
+    plan-time fields. Correlation with an even real kernel multiplies by its
+    (real) spectrum, with the odd a_i by the conjugate of its (imaginary) one."""
+    dim = u.shape[0]
+    shape = u.shape[1:]
+    off, ln, vol = oracle.horizon(dim, dx, delta, weights=True)
+    dV = dx ** dim
+    cK = np.zeros(shape)
+    aK = np.zeros((dim,) + shape)
+    CK = np.zeros((dim, dim) + shape)
+    for o, r, b in zip(off, ln, vol):
+        idx = tuple(int(o[dim - 1 - a]) % shape[a] for a in range(dim))
+        xi = o[:dim] * dx
+        c = alpha / r ** 3 * b * dV
+        cK[idx] += c
+        for i in range(dim):
+            aK[(i,) + idx] += c * xi[i]
+            for j in range(dim):
+                CK[(i, j) + idx] += c * xi[i] * xi[j]
+    F = np.fft.rfftn
+    axes_shape = shape
+
+    def Fi(X):
+        return np.fft.irfftn(X, s=axes_shape, axes=tuple(range(dim)))
+
+    cH = np.conj(F(cK))
+    aH = [np.conj(F(aK[i])) for i in range(dim)]
+    CH = [[np.conj(F(CK[i, j])) for j in range(dim)] for i in range(dim)]
+    # the kernel spectra have the parities the passes rely on
+    assert np.max(np.abs(cH.imag)) < 1e-12 * np.max(np.abs(cH))
+    for i in range(dim):
+        assert np.max(np.abs(aH[i].real)) < 1e-12 * np.max(np.abs(aH[i]))
+    w = (chi * lam).astype(float)
+    X = [F(w * u[j]) for j in range(dim)]
+    Y = {(i, j): F(w * u[i] * u[j]) for i in range(dim) for j in range(i, dim)}
+
+    def Yf(i, j):
+        return Y[(min(i, j), max(i, j))]
+
+    uu = np.sum(u * u, axis=0)
+    Z = [F(w * uu * u[i]) for i in range(dim)]
+    Yt = sum(Yf(j, j) for j in range(dim))
+    assert len(X) + len(Y) + len(Z) == (12 if dim == 3 else 7)
+    # inverse fields
+    P = [Fi(sum(CH[i][j] * X[j] for j in range(dim)) + sum(aH[j] * Yf(j, i) for j in range(dim))
+            + 0.5 * aH[i] * Yt + 0.5 * cH * Z[i]) for i in range(dim)]
+    A = [[Fi(aH[m] * X[n]) for n in range(dim)] for m in range(dim)]
+    B = {k: Fi(cH * v) for k, v in Y.items()}
+    Cc = [Fi(cH * X[j]) for j in range(dim)]
+    assert len(P) + dim * dim + len(B) + len(Cc) == (21 if dim == 3 else 11)
+
+    def Bf(i, j):
+        return B[(min(i, j), max(i, j))]
+
+    # plan-time correlations with w alone
+    Fw = F(w)
+    SC = [[Fi(CH[i][j] * Fw) for j in range(dim)] for i in range(dim)]
+    Sa = [Fi(aH[j] * Fw) for j in range(dim)]
+    Sc = Fi(cH * Fw)
+    # epilogue per node
+    L = np.zeros_like(u)
+    trA = sum(A[j][j] for j in range(dim))
+    trB = sum(Bf(j, j) for j in range(dim))
+    for i in range(dim):
+        t = P[i] - sum(SC[i][j] * u[j] for j in range(dim))
+        t = t - u[i] * trA - sum(A[j][i] * u[j] for j in range(dim)) + u[i] * sum(Sa[j] * u[j] for j in range(dim))
+        t = t - sum(A[i][j] * u[j] for j in range(dim)) + 0.5 * Sa[i] * uu
+        t = t - 0.5 * trB * u[i] - sum(Bf(i, j) * u[j] for j in range(dim))
+        t = t + u[i] * sum(Cc[j] * u[j] for j in range(dim)) + 0.5 * Cc[i] * uu - 0.5 * Sc * uu * u[i]
+        L[i] = w * t
+    return L
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_spectral_decomposition_for_the_passes(oracle, dim):
+    """12 forward and 21 inverse fields in 3D (7 and 11 in 2D) reproduce the
+    direct sum; this is the field plan of the GPU passes for this model."""
+    shape = (24, 32) if dim == 2 else (14, 16, 18)
+    chi = _blob(shape, 12, margin=4)
+    g = inputs.rng(13)
+    lam = (g.random(shape) < 0.9).astype(np.uint8)
+    u = 0.3 * g.normal(size=(dim,) + shape)
+    delta = 3.0 if dim == 2 else 2.5
+    alpha = oracle.alpha_bond(dim, 1.0, delta)
+    ref = oracle.force_nonlinear(u, chi, 1.0, delta, alpha, lam=lam)
+    L = _spectral_passes(oracle, u, chi, lam, 1.0, delta, alpha)
     assert _rel(L, ref) < 1e-11
