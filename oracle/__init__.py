@@ -344,7 +344,10 @@ def verlet_damage(u, v, lam, chi, chi_omega, b, w, dx, delta, alpha, rho, dt, wc
         lam^{n+1} = lam^n [ W(u^n, lam^n) <= wc ]          (irreversible)
         a^{n+1}  = L(u^{n+1}, lam^{n+1}) + b
         v^{n+1}  = chi_O { v^n + dt/(2 rho) (a^n + a^{n+1}) }
-    chi_omega has shape (d, *grid); w and b have shape (d, *grid).
+    chi_omega has shape (d, *grid); w and b have shape (d, *grid). For a
+    time-varying volume constraint w may instead be a function of the step
+    index giving the prescribed field at the end of that step: u^{n+1} takes
+    w(n + 1) on Gamma (t = (n + 1) dt).
     Returns (u, v, lam, flips) with flips = nodes whose lam went 1 -> 0.
     """
     u = _f64(u).copy()
@@ -352,13 +355,13 @@ def verlet_damage(u, v, lam, chi, chi_omega, b, w, dx, delta, alpha, rho, dt, wc
     lam = _u8(lam).copy()
     co = np.asarray(chi_omega, dtype=np.float64)
     b = _f64(b)
-    w = _f64(w)
+    w_at = w if callable(w) else (lambda n, w0=_f64(w): w0)
     L = force_bond(u, chi, dx, delta, alpha, s=lam.astype(np.float64))
     W = energy_bond(u, chi, dx, delta, alpha, lam=lam)
     flips = 0
-    for _ in range(nsteps):
+    for n in range(nsteps):
         a0 = L + b
-        u = co * (u + dt * (v + dt / (2.0 * rho) * a0)) + (1.0 - co) * w
+        u = co * (u + dt * (v + dt / (2.0 * rho) * a0)) + (1.0 - co) * _f64(w_at(n + 1))
         new_lam = (lam.astype(bool) & (W <= wc)).astype(np.uint8)
         flips += int(np.sum(lam.astype(np.int64) - new_lam.astype(np.int64)))
         lam = new_lam

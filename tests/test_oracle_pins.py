@@ -529,3 +529,34 @@ def test_cg_static_driven_by_prescribed_displacement(oracle):
     t = np.array([0.3, -0.2]).reshape(2, 1, 1)
     ut, _, _ = oracle.cg_static(chi, chio, b, w + t * chi, 1.0, delta, ("bond", alpha), rtol=1e-12)
     assert np.allclose((ut - t * chi)[:, chi == 1], u[:, chi == 1], rtol=0, atol=1e-10)
+
+
+def test_verlet_time_varying_constraint(oracle):
+    """A prescribed field given per step: a constant one reproduces the array
+    form bit for bit, and a body moving rigidly at v0 whose Gamma layer is
+    prescribed as w(t) = v0 t stays a rigid translation (no force, no broken
+    bond, u = v0 t, v = v0 on Omega)."""
+    shape = (24, 28)
+    chi = inputs.box_mask(shape, (4, 4), (24, 20))
+    x1, _ = inputs.coords(shape)
+    co = chi.copy()
+    co[(x1 >= 4) & (x1 < 7)] = 0
+    chio = np.stack([co, co])
+    delta = 3.0
+    alpha = oracle.alpha_bond(2, 1.0, delta)
+    g = inputs.rng(17)
+    u0 = 1e-3 * g.normal(size=(2,) + shape) * chi
+    w = 1e-3 * g.normal(size=(2,) + shape) * (chi - co)
+    z = np.zeros_like(u0)
+    dt = 0.3
+    ra = oracle.verlet_damage(u0, z, chi, chi, chio, z, w, 1.0, delta, alpha, 1.0, dt, 1e300, 12)
+    rc = oracle.verlet_damage(u0, z, chi, chi, chio, z, lambda n: w, 1.0, delta, alpha, 1.0, dt, 1e300, 12)
+    for a, c in zip(ra[:3], rc[:3]):
+        assert np.array_equal(a, c)
+    v0 = np.array([2e-3, -1e-3]).reshape(2, 1, 1)
+    nsteps = 20
+    u, v, lam, flips = oracle.verlet_damage(z, v0 * chio, chi, chi, chio, z, lambda n: v0 * (n * dt) * chi,
+                                            1.0, delta, alpha, 1.0, dt, 1e-12, nsteps)
+    assert flips == 0 and np.array_equal(lam, chi)
+    assert np.allclose(u[:, chi == 1], (v0 * nsteps * dt * np.ones((2,) + shape))[:, chi == 1], rtol=0, atol=1e-15)
+    assert np.allclose(v[:, co == 1], (v0 * np.ones((2,) + shape))[:, co == 1], rtol=0, atol=1e-15)
