@@ -560,3 +560,65 @@ def test_verlet_time_varying_constraint(oracle):
     assert flips == 0 and np.array_equal(lam, chi)
     assert np.allclose(u[:, chi == 1], (v0 * nsteps * dt * np.ones((2,) + shape))[:, chi == 1], rtol=0, atol=1e-15)
     assert np.allclose(v[:, co == 1], (v0 * np.ones((2,) + shape))[:, co == 1], rtol=0, atol=1e-15)
+
+
+def _bar_periodic_in_x2():
+    """Bar along x1 that fills the periodic x2 direction (the oracle has no
+    margin rule there), Gamma layers of delta = 3 nodes at both x1 ends, mirror
+    planes halfway between the last Gamma and the first Omega layer."""
+    shape = (16, 64)
+    chi = inputs.box_mask(shape, (3, 0), (61, 16))
+    x1, x2 = inputs.coords(shape)
+    left = (x1 >= 3) & (x1 < 6)
+    right = (x1 >= 58) & (x1 < 61)
+    xl, xr = 5.5, 57.5
+    co1 = chi.copy()
+    co1[left | right] = 0
+    co2 = chi.copy()
+    co2[left] = 0
+    n1 = shape[1]
+    node = (x2 * n1).astype(np.int64)
+    mir = -np.ones((2,) + shape, dtype=np.int64)
+    mir[0][left] = (node + (2 * xl - x1).astype(np.int64))[left]
+    mir[0][right] = (node + (2 * xr - x1).astype(np.int64))[right]
+    mir[1][left] = mir[0][left]
+    return shape, chi, np.stack([co1, co2]), mir, x1, xl, xr, left, right
+
+
+def test_mirror_constraints_reproduce_a_uniform_stretch(oracle):
+    """§5.1: the mirror-based constraint approximates the local boundary
+    condition better than the naive one. For a uniform stretch it is exact:
+    u1 = eps (x1 - xl), u2 = 0 extends oddly through both mirror planes and has
+    zero force everywhere; the naive constraint (u = g on the whole layer)
+    leaves boundary layers. The coupled solve also satisfies the mirror
+    relation exactly and is the fixed point of the per-iteration update the
+    paper describes (here averaged with the previous value to converge)."""
+    shape, chi, chio, mir, x1, xl, xr, left, right = _bar_periodic_in_x2()
+    delta = 3.0
+    op = ("bond", oracle.alpha_bond(2, 1.0, delta))
+    eps = 1e-3
+    g = np.zeros((2,) + shape)
+    g[0][right] = eps * (xr - xl)
+    b = np.zeros_like(g)
+    u, it, rel = oracle.static_mirror(chi, chio, b, g, mir, 1.0, delta, op, rtol=1e-13)
+    assert rel < 1e-11 and it > 0
+    exact = np.stack([eps * (x1 - xl) * chi, np.zeros(shape)])
+    assert np.max(np.abs(u - exact)) < 1e-10 * np.max(np.abs(exact))
+    gam = (chio == 0) & chi.astype(bool)[None]
+    flat = u.reshape(2, -1)
+    for c in range(2):
+        assert np.array_equal(u[c][gam[c]], 2 * g[c][gam[c]] - flat[c][mir[c][gam[c]]])
+    # the naive constraint: u = g on the whole Gamma layer
+    un, _, reln = oracle.cg_static(chi, chio, b, g, 1.0, delta, op, rtol=1e-13)
+    om = chio[0] == 1
+    assert np.max(np.abs(un[0][om] - exact[0][om])) > 1e-3 * np.max(np.abs(exact[0]))
+    # fixed point of w <- 2 g - u(mirror), averaged
+    w = g.copy()
+    for _ in range(60):
+        uf, _, _ = oracle.cg_static(chi, chio, b, w, 1.0, delta, op, rtol=1e-13)
+        ff = uf.reshape(2, -1)
+        wn = w.copy()
+        for c in range(2):
+            wn[c][gam[c]] = 2 * g[c][gam[c]] - ff[c][mir[c][gam[c]]]
+        w = 0.5 * (w + wn)
+    assert np.max(np.abs(uf - u)) < 1e-8 * np.max(np.abs(u))
