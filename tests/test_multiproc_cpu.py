@@ -65,3 +65,15 @@ def test_reference_arm_under_torchrun_two_ranks():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["n_gpus"] == 2
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_pass_bytes_match_the_per_node_figures():
+    """The roofline's algorithmic bytes per launch: 97 / 24 / 27 / 49 B per node
+    for the forward row, x2, last-axis and inverse row passes of the FP32 CG
+    iteration (d = 3), plus 44 B per boundary node in the inverse row pass."""
+    import bench
+    N = 128 ** 3
+    assert bench.pass_bytes("rows_fwd", N, 0) == 97 * N
+    assert bench.pass_bytes("cols_x2", N, 0) == 24 * N
+    assert bench.pass_bytes("last_axis", N, 0) == 27 * N
+    assert bench.pass_bytes("rows_inv", N, 1000) == 49 * N + 44 * 1000
