@@ -272,7 +272,7 @@ pd_status pd_batch_autotune(pd_batch *batch, void *stream);
 pd_status pd_plan_tuning(const pd_plan *plan, int *out6);
 /* Pin a pass configuration {rows, x2 width, last-axis width, schedule,
  * stages, inverse-pass stages}: rows and widths 0 or powers of two (rows <=
- * 256, widths <= 32; 0 = heuristic), schedule 0/1, row-pass pipeline stages
+ * 256, widths 2..32; 0 = heuristic), schedule 0/1, row-pass pipeline stages
  * 0 (= 2), 1 or 2, inverse-pass stages 0 (= as the forward passes), 1 or 2;
  * PD_ERR_ARG otherwise. The pass configuration functions still shrink a value
  * that does not fit the grid or the shared memory. */

@@ -216,9 +216,11 @@ extern "C" pd_status pd_plan_set_tuning(pd_plan *p, const int *in6)
     }
     const int r = in6[0], wx = in6[1], wl = in6[2], sc = in6[3], ns = in6[4], ni = in6[5];
     auto pow2_or_zero = [](int v) { return v == 0 || (v > 0 && (v & (v - 1)) == 0); };
-    if (!pow2_or_zero(r) || r > 256 || !pow2_or_zero(wx) || wx > 32 || !pow2_or_zero(wl) || wl > 32 ||
-        (sc != 0 && sc != 1) || ns < 0 || ns > 2 || ni < 0 || ni > 2) {
-        set_error("pd_plan_set_tuning: rows and widths must be 0 or powers of two (rows <= 256, widths <= 32), "
+    // a column tile is at least 2 complex values wide: its first column, and so the
+    // x coordinate of every tensor copy, is then a multiple of 16 bytes
+    if (!pow2_or_zero(r) || r > 256 || !pow2_or_zero(wx) || wx == 1 || wx > 32 || !pow2_or_zero(wl) || wl == 1 ||
+        wl > 32 || (sc != 0 && sc != 1) || ns < 0 || ns > 2 || ni < 0 || ni > 2) {
+        set_error("pd_plan_set_tuning: rows and widths must be 0 or powers of two (rows <= 256, widths 2..32), "
                   "schedule 0 or 1, stages 0, 1 or 2");
         return PD_ERR_ARG;
     }

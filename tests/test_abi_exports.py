@@ -84,3 +84,19 @@ def test_volume_rule_arguments_are_checked_on_the_host():
     prob = pd.Problem(shape=(64, 64), delta=3.0, volume_rule=1).to_c()
     st = lib.pd_force2d_noalloc(ctypes.byref(prob), ptr, ptr, ptr, None)
     assert st == -1 and "volume_rule" in lib.pd_last_error_detail().decode()
+
+
+def test_tuning_widths_are_checked_on_the_host():
+    """pd_plan_set_tuning refuses a column-tile width of 1 (and other bad values)
+    before it touches the plan: a one-column tile would start tensor copies off
+    a 16-byte boundary."""
+    from paper_2105_06055_gb300 import build, pd
+    build.build()
+    lib = pd.load()
+    dummy = (ctypes.c_uint8 * 4096)()  # never read: the arguments are refused first
+    for bad in [(0, 1, 0, 0, 0, 0), (0, 0, 1, 0, 0, 0), (0, 64, 0, 0, 0, 0), (3, 0, 0, 0, 0, 0),
+                (0, 0, 0, 2, 0, 0), (0, 0, 0, 0, 3, 0)]:
+        arr = (ctypes.c_int * 6)(*bad)
+        assert lib.pd_plan_set_tuning(ctypes.cast(dummy, ctypes.c_void_p), arr) == -1, bad
+    assert "widths 2..32" in lib.pd_last_error_detail().decode()
+    assert not any(dummy)
