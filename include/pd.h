@@ -275,7 +275,8 @@ pd_status pd_plan_tuning(const pd_plan *plan, int *out6);
  * 256, widths 2..32; 0 = heuristic), schedule 0/1, row-pass pipeline stages
  * 0 (= 2), 1 or 2, inverse-pass stages 0 (= as the forward passes), 1 or 2;
  * PD_ERR_ARG otherwise. The pass configuration functions still shrink a value
- * that does not fit the grid or the shared memory. */
+ * that does not fit the grid or the shared memory, and raise rows to fill at
+ * least one warp per row-pass block. */
 pd_status pd_plan_set_tuning(pd_plan *plan, const int *in6);
 
 /*

@@ -229,6 +229,9 @@ inline void row_cfg(const pd_plan *p, int FI, int FB, int NF, int NB, RowGeom &g
     auto smem_of = [&](int rows) { return row_smem_bytes<T>(FI, FB, NF, NB, rows, pitch, n1, ns); };
     int rows = p->tune_rows > 0 ? p->tune_rows : 128 / nt;
     if (rows < 1) rows = 1;
+    // whole warps: the epilogues' block reductions shuffle over full warps
+    // (the heuristic and the autotuner never go below; a pinned value could)
+    if (rows * nt < 32) rows = 32 / nt;
     while (rows > 1 && rows * nt > 256) rows >>= 1;  // k_rows launch bound
     while (rows > 1 && smem_of(rows) > 100 * 1024) rows >>= 1;
     while (p->nrows % rows) rows >>= 1;
