@@ -81,6 +81,15 @@ typedef struct {
                         every entry point are unchanged; the family (and the
                         damage counts of pd_damage) then holds every offset with
                         beta > 0, and the body must stay that far from the faces */
+    double s0;       /* critical bond stretch (bond model; used when Wc <= 0 and
+                        s0 > 0): the plan takes Wc = 1/2 alpha s0^2 dV Σ_H w|xi|,
+                        the Eq. 47 energy density of a fully bonded node under the
+                        isotropic stretch u = s0 x (every bond then has
+                        eta.C.eta = alpha s0^2 |xi| for omega = 1/|xi|; w is the
+                        bond's quadrature weight relative to dV). The paper's
+                        failure criterion is energy based (§3.4, Eq. 40-44, 51);
+                        this maps a stretch criterion onto it. Negative values,
+                        or s0 > 0 with the state-based model: PD_ERR_ARG      */
 } pd_problem;
 
 typedef struct pd_plan pd_plan;  /* opaque; owns spectra, masks and workspace */
@@ -321,13 +330,32 @@ pd_status pd_damage(pd_plan *plan, const uint8_t *lambda, int32_t *nb, void *d, 
  * All intermediates live in one fixed 2 MiB __device__ array inside the
  * library, held by every GPU that loads it until the process exits. The first
  * call on each device looks up that array's device address; make it before
- * any stream capture. The call waits on `stream` for the mask check, then
- * enqueues the force passes and returns. Every call reuses the same array, so
+ * any stream capture. The call synchronises `stream` once (it reads the mask
+ * check back to the host), then enqueues the force passes and returns. Every call reuses the same array, so
  * calls that overlap on the GPU (from several streams or threads) race; the
  * caller must serialise them.
  */
 pd_status pd_force2d_noalloc(const pd_problem *problem, const uint8_t *chi_B, const float *u, float *L,
                              void *stream);
+
+/* Critical strain energy density the plan uses for bond breaking (Eq. 63):
+ * problem.Wc when it is > 0, else the value derived from problem.s0 (see
+ * pd_problem), else 0 (no breaking). Host FP64. */
+double pd_plan_critical_energy(const pd_plan *plan);
+
+/*
+ * pd_plan_inject_stall -- test hook for the failure handling of bounded
+ * device waits. The next row pass of the given kind launched on the plan
+ * (0: forward, 3: inverse; see pd_plan_profile) has its first block issue none
+ * of its bulk copies, so that block's wait on its copy barrier gives up after
+ * the library's limit (2 s), sets the plan's device status word and the block
+ * exits; the rest of the pass runs normally. pd_solve_static then returns
+ * PD_ERR_TIMEOUT at its next check (after the CG chunk, at most 16
+ * iterations). Nothing faults or hangs; the plan stays usable (each solve
+ * clears the status word). One-shot: the word is cleared by the block that
+ * takes it. Synchronous (writes one word to device memory).
+ */
+pd_status pd_plan_inject_stall(pd_plan *plan, int kind);
 
 /* Bytes of device memory owned by the plan. */
 int64_t pd_plan_workspace_bytes(const pd_plan *plan);

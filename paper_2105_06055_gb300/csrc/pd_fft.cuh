@@ -245,6 +245,9 @@ struct RowGeom {
     int sched;      // FFT stage schedule (fft_smem)
     int nstage;     // 2: the next tile's copies overlap this tile's work; 1: no overlap
     int *err;       // device status word (bounded-wait time-outs)
+    int *inject;    // failure-handling test hook (device word or null): when it
+                    // holds 1 + this pass's kind (0 forward, 3 inverse), block 0
+                    // clears it and issues no copies, so its bounded wait runs out
 };
 
 // Bytes of one pipeline stage of a row tile: SB packed-row slots loaded by
@@ -397,7 +400,13 @@ __global__ void __launch_bounds__(256, op_min_blocks<Op>::value) k_rows(RowGeom 
     pdl_wait();
     pdl_trigger();
     int64_t t = blockIdx.x;
-    if (kLoad && threadIdx.x == 0 && t < ntiles) issue(t, 0);
+    // test hook: one-shot, so a pass captured in a graph stalls on one replay only
+    bool stall = false;
+    if (kLoad && g.inject && blockIdx.x == 0 && threadIdx.x == 0) {
+        const int kind = FI > 0 ? 3 : 0;
+        stall = atomicCAS(g.inject, kind + 1, 0) == kind + 1;
+    }
+    if (kLoad && threadIdx.x == 0 && t < ntiles && !stall) issue(t, 0);
     unsigned phase = 0;  // bit s: parity of the next completion of stage s
     const int jt = threadIdx.x % nt, rf = threadIdx.x / nt;  // FFT mapping: nt threads per row
     typename op_acc<Op>::type acc;
@@ -405,9 +414,9 @@ __global__ void __launch_bounds__(256, op_min_blocks<Op>::value) k_rows(RowGeom 
     for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
         const int s = ns == 2 ? (it & 1) : 0;
         const int64_t tn = t + gridDim.x;
-        const bool pre = kLoad && ns == 2 && tn < ntiles;
+        const bool pre = kLoad && ns == 2 && tn < ntiles && !stall;
         if (pre && threadIdx.x == 0) issue(tn, s ^ 1);
-        if (kLoad && ns == 1 && it > 0 && threadIdx.x == 0) issue(t, 0);
+        if (kLoad && ns == 1 && it > 0 && threadIdx.x == 0 && !stall) issue(t, 0);
         if constexpr (kLoad) {
             const bool ok = mbar_wait(&mbar[s], (phase >> s) & 1u, g.err);
             phase ^= 1u << s;

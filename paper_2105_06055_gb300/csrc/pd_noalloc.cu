@@ -21,7 +21,9 @@
 // kernel spectrum, boundary field, twiddles, spectra), so nothing depends on
 // the previous call's contents; the only values that must start at zero, the
 // mask-check flag and the passes' wait-status word, are cleared at the start of
-// each call. All calls share the
+// each call. The call reads the mask-check flag back to the host, so it
+// synchronises `stream` once before it enqueues the force passes (a wrong mask
+// is then an argument error, not a device fault). All calls share the
 // one array: calls that overlap on the GPU (other streams, other host
 // threads) race on it and must be serialised by the caller.
 #include <cmath>
@@ -273,6 +275,12 @@ extern "C" pd_status pd_force2d_noalloc(const pd_problem *pr, const uint8_t *chi
     p.spec32_slots = 2;
     p.dev_status = flag + 1;
     p.hdev = hd;
+    {
+        // persistent row-pass grids are sized by the SM count (a query, no allocation)
+        int dev = 0;
+        PD_CUDA_TRY(cudaGetDevice(&dev));
+        PD_CUDA_TRY(cudaDeviceGetAttribute(&p.nsm, cudaDevAttrMultiProcessorCount, dev));
+    }
     const pd_status s = force_bond_pipeline<float, 2, false, W_NONE, false>(&p, u, nullptr, nullptr, G, L, nullptr, st);
     // the stack plan owns nothing: detach its views before it goes out of scope
     p.chi = nullptr;

@@ -467,6 +467,19 @@ extern "C" {
 
 const char *pd_last_error_detail(void) { return g_err; }
 
+double pd_plan_critical_energy(const pd_plan *p) { return p ? p->wc : 0.0; }
+
+pd_status pd_plan_inject_stall(pd_plan *p, int kind)
+{
+    if (!p || (kind != 0 && kind != 3)) {
+        set_error("pd_plan_inject_stall: null plan or kind not 0 (forward row pass) or 3 (inverse row pass)");
+        return PD_ERR_ARG;
+    }
+    const int v = kind + 1;
+    PD_CUDA_TRY(cudaMemcpy(p->inject, &v, sizeof(int), cudaMemcpyHostToDevice));
+    return PD_OK;
+}
+
 const char *pd_status_string(pd_status s)
 {
     switch (s) {
@@ -603,6 +616,10 @@ static pd_status plan_create_impl(const pd_problem *pr, const uint8_t *chi_B, co
                   pr->n[0], pr->n[1], pr->n[2]);
         return PD_ERR_SIZE;
     }
+    if (!(pr->s0 >= 0) || (pr->s0 > 0 && pr->model != PD_LIN_BOND)) {
+        set_error("s0 must be >= 0, and is defined for the bond model only (got %g)", pr->s0);
+        return PD_ERR_ARG;
+    }
     if (pr->volume_rule != 0 && pr->volume_rule != 1) {
         set_error("volume_rule must be 0 (constant dV) or 1 (partial volumes), got %d", pr->volume_rule);
         return PD_ERR_ARG;
@@ -663,6 +680,17 @@ static pd_status plan_create_impl(const pd_problem *pr, const uint8_t *chi_B, co
     p->state_based = (pr->model == PD_LIN_STATE && p->ka != 0.0) ? 1 : 0;
     HostHorizon hz = make_horizon(p, p->alpha);
     p->hcount = hz.cnt;
+    // critical energy density (Eq. 63): given, or that of a fully bonded node
+    // under the isotropic stretch u = s0 x, W = 1/2 Σ_H eta.C.eta w with
+    // eta = s0 xi, i.e. 1/2 alpha s0^2 Σ_H |xi| w (omega = 1/|xi|; hz0.w2 holds
+    // |xi| w, w = the bond's quadrature weight dV or beta dV)
+    if (pr->Wc > 0) {
+        p->wc = pr->Wc;
+    } else if (pr->s0 > 0) {
+        double sl = 0.0;
+        for (int c = 0; c < hz0.cnt; ++c) sl += hz0.w2[c];
+        p->wc = 0.5 * p->alpha * pr->s0 * pr->s0 * sl;
+    }
 
     const int64_t N = p->N;
     const int nc = p->ncomp;
@@ -698,6 +726,7 @@ static pd_status plan_create_impl(const pd_problem *pr, const uint8_t *chi_B, co
     // reduction scratch; the last 64 bytes hold the device status word
     PD_TRY(dalloc(p, &p->red, sizeof(double) * 65536));
     p->dev_status = reinterpret_cast<int *>(p->red + 65536 - 8);  // last 64 bytes
+    p->inject = p->dev_status + 1;
     PD_CUDA_TRY(cudaMemsetAsync(p->dev_status, 0, 64, st));
 
     // mask checks

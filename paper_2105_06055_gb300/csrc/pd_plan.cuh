@@ -124,6 +124,7 @@ struct pd_plan {
     double dV, alpha;   // bond constant (or 30 mu / m0 for the state-based C)
     double ka, m0;      // state-based constants
     double lam_max;     // largest eigenvalue of the periodic symbol
+    double wc = 0.0;    // critical energy density of bond breaking (problem Wc, or from s0)
     int state_based;    // model == PD_LIN_STATE && ka != 0 (dilatation round needed)
     int hcount;
     // device memory
@@ -150,6 +151,7 @@ struct pd_plan {
     void *spec64 = nullptr;        // spec64_slots x N doubles
     int spec32_slots = 0, spec64_slots = 0;
     int *dev_status = nullptr;     // device status word (bounded-wait time-outs)
+    int *inject = nullptr;         // row-pass stall word (pd_plan_inject_stall), next to dev_status
     void *work = nullptr;          // one allocation carved into the scratch fields below
     size_t work_bytes = 0;
     // scratch fields (plan precision T unless noted)
@@ -243,6 +245,7 @@ inline void row_cfg(const pd_plan *p, int FI, int FB, int NF, int NB, RowGeom &g
     g.sched = p->tune_sched;
     g.nstage = ns;
     g.err = p->dev_status;
+    g.inject = p->inject;
     c.grid = dim3((unsigned)(p->nrows / rows));
     c.block = dim3(rows * nt);
     c.smem = smem_of(rows);

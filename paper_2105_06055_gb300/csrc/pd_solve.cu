@@ -39,6 +39,7 @@ namespace {
 
 constexpr int kChunk = 16;       // CG iterations per graph replay
 constexpr int kPartB = 14400;    // fused iteration: r.r partials below, (p.q, r.q, q.q) triples above
+constexpr int kHostStatus = 32;  // slot of the pinned host scalars that receives the device status word
 
 // rr = sum of the first pass's partials; alpha, beta from the second pass's triples
 // rr = sum of the first pass's partials; alpha, beta from the second pass's
@@ -309,8 +310,11 @@ struct Solver {
     pd_status copy_scalars()
     {
         PD_CUDA_TRY(cudaMemcpyAsync(hs(), p->red + kRedScal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, st));
+        // the device status word (bounded-wait time-outs) rides along
+        PD_CUDA_TRY(cudaMemcpyAsync(hs() + kHostStatus, p->dev_status, sizeof(int), cudaMemcpyDeviceToHost, st));
         return PD_OK;
     }
+    int dev_status() const { return *reinterpret_cast<const int *>(hs() + kHostStatus); }
     pd_status read_scalars()
     {
         PD_TRY(copy_scalars());
@@ -327,6 +331,10 @@ struct Solver {
         p->launches++;
         PD_TRY(finish(nb, S_NORM, 0));
         PD_TRY(read_scalars());
+        if (dev_status()) {  // a pass that gave up leaves its tiles unwritten: report that first
+            set_error("pd_solve_static: a bounded device wait timed out (status %d)", dev_status());
+            return PD_ERR_TIMEOUT;
+        }
         *rn = std::sqrt(hs()[S_NORM]);
         if (!std::isfinite(*rn)) {
             set_error("pd_solve_static: non-finite residual");
@@ -443,6 +451,10 @@ struct Solver {
             PD_TRY((chunk<T, D>()));
             it += kChunk;
             const double rn = std::sqrt(hs()[S_RR]);
+            if (dev_status()) {
+                set_error("pd_solve_static: a bounded device wait timed out (status %d)", dev_status());
+                return PD_ERR_TIMEOUT;
+            }
             if (hs()[S_FLAG] == 1.0) {
                 set_error("pd_solve_static: non-finite CG scalar");
                 return PD_ERR_NONFINITE;

@@ -190,7 +190,7 @@ pd_status verlet_impl(pd_plan *p, T *u, T *v, uint8_t *lam, const T *b, const T 
     T *L = (T *)p->cg_q;
     T *W = (T *)p->theta;
     T *G = lam ? (T *)p->Gw : (sizeof(T) == 8 ? (T *)p->G64 : (T *)p->G32);
-    const int breaking = (lam && p->prob.Wc > 0) ? 1 : 0;
+    const int breaking = (lam && p->wc > 0) ? 1 : 0;
     VerletCounters *cnt = reinterpret_cast<VerletCounters *>(p->red + kRedVerlet);
     PD_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(VerletCounters), st));
     const unsigned nbl = (unsigned)((N + 127) / 128);
@@ -205,7 +205,7 @@ pd_status verlet_impl(pd_plan *p, T *u, T *v, uint8_t *lam, const T *b, const T 
     const unsigned ngv = (unsigned)std::min<int64_t>(4 * p->nsm, (d * N + 255) / 256);
     for (int s = 0; s < nsteps; ++s) {
         k_kick_drift<T><<<ng, 256, 0, st>>>(u, v, lam, L, b, w, W, p->chi, p->chi_om, d, N, hdt, (T)dt,
-                                            (T)p->prob.Wc, breaking, cnt);
+                                            (T)p->wc, breaking, cnt);
         PD_LAUNCH_CHECK();
         p->launches++;
         if (breaking) {

@@ -30,7 +30,8 @@ EXPORTS = ["pd_plan_create", "pd_plan_destroy", "pd_kernel_spectrum", "pd_force"
            "pd_plan_profile", "pd_plan_profile_read", "pd_force2d_noalloc", "pd_plan_boundary_nodes",
            "pd_solve_dr", "pd_plan_create_batched", "pd_batch_size", "pd_batch_plan", "pd_solve_dr_batched",
            "pd_batch_destroy", "pd_plan_autotune", "pd_batch_autotune", "pd_plan_tuning",
-           "pd_plan_set_energy_mode", "pd_plan_set_tuning", "pd_plan_autotune_solve"]
+           "pd_plan_set_energy_mode", "pd_plan_set_tuning", "pd_plan_autotune_solve", "pd_plan_critical_energy",
+           "pd_plan_inject_stall"]
 
 PASS_KINDS = {0: "rows_fwd", 1: "cols_x2", 2: "last_axis", 3: "rows_inv"}
 
@@ -47,7 +48,7 @@ class _Problem(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("dx", ctypes.c_double * 3),
                 ("delta", ctypes.c_double), ("model", ctypes.c_int), ("E", ctypes.c_double),
                 ("nu", ctypes.c_double), ("rho", ctypes.c_double), ("Wc", ctypes.c_double),
-                ("fp64", ctypes.c_int), ("volume_rule", ctypes.c_int)]
+                ("fp64", ctypes.c_int), ("volume_rule", ctypes.c_int), ("s0", ctypes.c_double)]
 
 
 def load():
@@ -84,6 +85,10 @@ def load():
     lib.pd_plan_boundary_nodes.restype = I64
     lib.pd_stable_dt.argtypes = [P]
     lib.pd_stable_dt.restype = D
+    lib.pd_plan_critical_energy.argtypes = [P]
+    lib.pd_plan_critical_energy.restype = D
+    lib.pd_plan_inject_stall.argtypes = [P, I]
+    lib.pd_plan_inject_stall.restype = I
     lib.pd_plan_profile.argtypes = [P, I]
     lib.pd_plan_profile.restype = I
     lib.pd_plan_profile_read.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(I64)]
@@ -151,6 +156,7 @@ class Problem:
     Wc: float = 0.0
     fp64: bool = False
     volume_rule: int = 0           # 0 constant dV (§4.1.1); 1 linear partial volumes (cubic cells)
+    s0: float = 0.0                # critical stretch; the plan derives Wc from it when Wc <= 0
 
     def to_c(self) -> _Problem:
         p = _Problem()
@@ -167,6 +173,7 @@ class Problem:
         p.E, p.nu, p.rho, p.Wc = float(self.E), float(self.nu), float(self.rho), float(self.Wc)
         p.fp64 = 1 if self.fp64 else 0
         p.volume_rule = int(self.volume_rule)
+        p.s0 = float(self.s0)
         return p
 
     @property
@@ -379,7 +386,15 @@ class Plan:
     def boundary_nodes(self):
         return int(load().pd_plan_boundary_nodes(self._h))
 
+    def inject_stall(self, kind: int):
+        """Failure-handling test hook (pd_plan_inject_stall): the next row pass
+        of this kind (0 forward, 3 inverse) has one block whose wait runs out."""
+        _check(load().pd_plan_inject_stall(self._h, int(kind)), "pd_plan_inject_stall")
+
     @property
+    def critical_energy(self):
+        return float(load().pd_plan_critical_energy(self._h))
+
     def stable_dt(self):
         return float(load().pd_stable_dt(self._h))
 

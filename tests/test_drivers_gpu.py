@@ -48,9 +48,10 @@ def test_static_cube_with_cavity_small(pdm, oracle, fp64, nu):
     res = oracle.static_residual(ug, cfg["chi"], cfg["chi_omega"], cfg["b"], 1.0, 3.0, op)
     bn = np.linalg.norm(cfg["chi_omega"] * cfg["b"])
     assert np.linalg.norm(res) / bn <= 1.5e-8
-    uo, _, relo = oracle.cg_static(cfg["chi"], cfg["chi_omega"], cfg["b"], cfg["w"], 1.0, 3.0, op, rtol=1e-12)
-    assert relo < 1e-11
-    assert _rel(ug, uo) < 2e-6
+    uo, _, relo = oracle.cg_static(cfg["chi"], cfg["chi_omega"], cfg["b"], cfg["w"], 1.0, 3.0, op, rtol=1e-13)
+    assert relo < 1e-12
+    # the displacement itself, element by element, to the static-solve target
+    assert _rel(ug, uo) < 1e-8
     assert np.all(ug[:, cfg["chi_omega"][0] == 0] == 0)
     plan.close()
 
@@ -78,7 +79,12 @@ def test_static_2d_bond_fp64_with_prescribed_w(pdm, oracle):
 
 def test_static_config2_full_size(pdm, oracle):
     """128^3 cube with spherical cavity, FP32 FFTs + FP64 refinement to 1e-8;
-    the returned u is checked with the oracle's FP64 operator."""
+    the returned u is checked with the oracle's FP64 operator (residual) and
+    element by element against the oracle's own FP64 CG solution from u = 0
+    (relative L2 <= 1e-8). At nu = 1/4 the state-based operator is the bond
+    operator with constant 30 mu / m0 (3 kappa - 5 mu = 0; pinned on the CPU by
+    test_lps_reduces_to_bond_at_quarter_poisson), which the oracle evaluates at half the
+    cost, so its reference solve uses that form."""
     cfg = inputs.cube_with_cavity(n=128)
     shape = cfg["shape"]
     prob = pdm.Problem(shape=shape, delta=3.0, model=pdm.PD_LIN_STATE, nu=0.25, fp64=False)
@@ -92,6 +98,10 @@ def test_static_config2_full_size(pdm, oracle):
     bn = np.linalg.norm(cfg["chi_omega"] * cfg["b"])
     assert np.linalg.norm(res) / bn <= 1.5e-8
     plan.close()
+    uo, ito, relo = oracle.cg_static(cfg["chi"], cfg["chi_omega"], cfg["b"], cfg["w"], 1.0, 3.0, ("bond", cb),
+                                     rtol=1e-12)
+    assert relo < 1e-11
+    assert _rel(u.cpu().numpy(), uo) < 1e-8
 
 
 # --------------------------------------------------------------------------

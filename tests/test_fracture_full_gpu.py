@@ -56,8 +56,11 @@ def test_fracture_config3_full_size(pdm, oracle):
     assert abs(alpha - 9.0 / (64.0 * math.pi)) < 1e-15
     wc = oracle.wc_from_stretch(2, 1.0, delta, alpha, 1e-3)
     b = cfg["b"] * (0.242 * math.sqrt(wc))
-    plans = {fp64: pdm.Plan(pdm.Problem(shape=shape, delta=delta, rho=1.0, Wc=wc, nu=1.0 / 3.0, fp64=fp64),
+    # the critical stretch goes to the library, which derives Wc itself
+    plans = {fp64: pdm.Plan(pdm.Problem(shape=shape, delta=delta, rho=1.0, s0=1e-3, nu=1.0 / 3.0, fp64=fp64),
                             _t(cfg["chi"], torch.uint8)) for fp64 in (True, False)}
+    for p in plans.values():
+        assert abs(p.critical_energy / wc - 1.0) < 1e-14
     dt = 0.8 * plans[True].stable_dt
 
     # (1) FP64 GPU path against the oracle through crack initiation, both energy modes

@@ -105,6 +105,54 @@ def test_bond_symbol_long_wave_is_navier(oracle, dim):
         assert _rel(M, Mn) < 0.06, (kvec, M, Mn)
 
 
+def _lattice_moments(dim, delta):
+    """Brute-force lattice sums over 0 < |xi| <= delta (unit spacing), written
+    out here from the definition: S1 = Σ xi1^4/|xi|^3, S2 = Σ xi1^2 xi2^2/|xi|^3."""
+    r = int(math.floor(delta))
+    ax = np.arange(-r, r + 1, dtype=float)
+    g = np.meshgrid(*([ax] * dim), indexing="ij")
+    x1, x2 = g[0].ravel(), g[1].ravel()
+    rr = np.sqrt(sum(a.ravel() ** 2 for a in g))
+    keep = (rr > 0) & (rr <= delta * (1 + 1e-12))
+    x1, x2, rr = x1[keep], x2[keep], rr[keep]
+    return float(np.sum(x1 ** 4 / rr ** 3)), float(np.sum(x1 ** 2 * x2 ** 2 / rr ** 3))
+
+
+@pytest.mark.parametrize("dim,delta", [(2, 3.0), (2, 4.0), (2, 7.5), (3, 3.0), (3, 4.0), (3, 6.0)])
+def test_bond_constant_against_navier_with_lattice_moments(oracle, dim, delta):
+    """The bond constant is tied to E to the precision of the long-wave limit.
+
+    For a long wave k e1 the symbol is M(k) = dV Σ_H C(xi)(1 - cos k.xi)
+    ~ 1/2 alpha k^2 (S1, S2) on the diagonal, with the lattice moments S1, S2
+    above (omega = 1/|xi|). Navier-Cauchy elasticity asks for lam + 2 mu and
+    mu, which the continuum calibration reaches with the ball moments
+    B1 = int xi1^4/|xi|^3 = pi delta^4/5 (3D) or pi delta^3/4 (2D) and
+    B2 = pi delta^4/15 (3D) or pi delta^3/12 (2D). So the discrete symbol must
+    equal (lam + 2 mu) k^2 S1/B1 and mu k^2 S2/B2, with lam = mu = 2E/5 (3D,
+    nu = 1/4) or plane stress lam + 2 mu = 9E/8, mu = 3E/8 (2D, nu = 1/3). The
+    lattice moments carry the whole quadrature error, so the check holds to
+    the O(k^2 delta^2) remainder of the long-wave expansion (1e-5 here) at any
+    horizon: a bond constant off by 1% fails it."""
+    E = 1.0
+    n = 16384
+    shape = (n,) * dim
+    alpha = oracle.alpha_bond(dim, E, delta)
+    S1, S2 = _lattice_moments(dim, delta)
+    if dim == 3:
+        B1, B2 = math.pi * delta ** 4 / 5.0, math.pi * delta ** 4 / 15.0
+        lam2mu, mu = 6.0 * E / 5.0, 2.0 * E / 5.0
+    else:
+        B1, B2 = math.pi * delta ** 3 / 4.0, math.pi * delta ** 3 / 12.0
+        lam2mu, mu = 9.0 * E / 8.0, 3.0 * E / 8.0
+    k = np.zeros(dim)
+    k[0] = 1.0
+    kap = 2 * math.pi / n
+    M = oracle.symbol_bond(shape, 1.0, delta, alpha, k)
+    assert abs(M[0, 0] / (lam2mu * kap ** 2 * S1 / B1) - 1.0) < 1e-5
+    assert abs(M[1, 1] / (mu * kap ** 2 * S2 / B2) - 1.0) < 1e-5
+    assert abs(M[0, 1]) < 1e-12 * abs(M[0, 0])
+
+
 def test_wc_closed_form(oracle):
     """W of a fully bonded node under u = s0 x equals 1/2 alpha s0^2 dV Σ|xi| (R10)."""
     shape = (40, 40)
