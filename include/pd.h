@@ -344,6 +344,23 @@ pd_status pd_force2d_noalloc(const pd_problem *problem, const uint8_t *chi_B, co
 double pd_plan_critical_energy(const pd_plan *plan);
 
 /*
+ * pd_plan_set_affine_split -- accuracy option of pd_force for FP32 fields
+ * with a large affine part (bond model; 1 on, 0 off, the default). The FFT
+ * convolution's rounding error grows with the norm of the transformed field
+ * (about eps ||chi u|| lam_max), while the force of an affine field
+ * a = A x + t is known exactly: chi Σ_H chi' C_ij(xi) A_jk xi_k dV (Eq. 17-18
+ * with u' - u = A xi), nonzero only within delta of the body's boundary. With
+ * the option on, pd_force (s = NULL, W = NULL) fits a by least squares over
+ * the body (one reduction over u), transforms u - a only and adds the force of
+ * a at the boundary nodes from a plan-time moment table; the fit's
+ * coefficients are rounded so that a is evaluated exactly, and the result is
+ * the same operator applied to u. Cost: one extra read of u per call. Other
+ * calls (weights, W, the solvers) are unchanged. PD_ERR_ARG for the
+ * state-based model or a body without a full-rank set of nodes.
+ */
+pd_status pd_plan_set_affine_split(pd_plan *plan, int on);
+
+/*
  * pd_plan_inject_stall -- test hook for the failure handling of bounded
  * device waits. The next row pass of the given kind launched on the plan
  * (0: forward, 3: inverse; see pd_plan_profile) has its first block issue none

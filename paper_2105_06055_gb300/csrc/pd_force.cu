@@ -3,7 +3,7 @@
 
 namespace pd {
 template <typename T>
-pd_status force_plain(pd_plan *p, const T *u, const T *s, T *L, T *W, cudaStream_t st);
+pd_status force_public(pd_plan *p, const T *u, const T *s, T *L, T *W, cudaStream_t st);
 }  // namespace pd
 
 using namespace pd;
@@ -20,6 +20,6 @@ extern "C" pd_status pd_force(pd_plan *p, const void *u, const void *s, void *L,
     }
     cudaStream_t st = (cudaStream_t)stream;
     if (p->prob.fp64)
-        return force_plain<double>(p, (const double *)u, (const double *)s, (double *)L, (double *)W, st);
-    return force_plain<float>(p, (const float *)u, (const float *)s, (float *)L, (float *)W, st);
+        return force_public<double>(p, (const double *)u, (const double *)s, (double *)L, (double *)W, st);
+    return force_public<float>(p, (const float *)u, (const float *)s, (float *)L, (float *)W, st);
 }

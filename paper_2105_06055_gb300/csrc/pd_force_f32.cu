@@ -6,4 +6,5 @@ template pd_status weight_gfield<float>(pd_plan *, const float *, const uint8_t 
 template pd_status force_any<float>(pd_plan *, const float *, const float *, const uint8_t *, const float *, float *, float *,
                                    cudaStream_t);
 template pd_status force_plain<float>(pd_plan *, const float *, const float *, float *, float *, cudaStream_t);
+template pd_status force_public<float>(pd_plan *, const float *, const float *, float *, float *, cudaStream_t);
 }  // namespace pd

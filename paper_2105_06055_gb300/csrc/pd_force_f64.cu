@@ -6,4 +6,5 @@ template pd_status weight_gfield<double>(pd_plan *, const double *, const uint8_
 template pd_status force_any<double>(pd_plan *, const double *, const double *, const uint8_t *, const double *, double *, double *,
                                    cudaStream_t);
 template pd_status force_plain<double>(pd_plan *, const double *, const double *, double *, double *, cudaStream_t);
+template pd_status force_public<double>(pd_plan *, const double *, const double *, double *, double *, cudaStream_t);
 }  // namespace pd

@@ -17,14 +17,36 @@ static inline unsigned nblk_f(int64_t n, int b = 256) { return (unsigned)((n + b
 
 // SPARSE: the epilogue takes the plan's boundary-node list of G (weight chi_B);
 // otherwise the dense G passed in (weight chi_B, chi_B s or chi_B lam).
-template <typename T, int D, bool ENERGY, int WM, bool SPARSE = (WM == W_NONE)>
+// Fit of the affine split (pd_affine.cuh): block sums over the body, then the
+// exact-form coefficients in the plan's coefficient buffer.
+template <typename T, int D>
+pd_status affine_fit(pd_plan *p, const T *u, cudaStream_t st, AffineView<T> *view)
+{
+    constexpr int kBlocks = 296;  // 2 x 148 SMs' worth; the sums are a small part of the evaluation
+    AffFitArgs fa;
+    for (int i = 0; i < 16; ++i) fa.inv[i] = p->aff_inv[i];
+    for (int k = 0; k < 3; ++k) fa.emax[k] = p->aff_emax[k];
+    fa.nblk = kBlocks;
+    const int lg1 = ilog2(p->n1), lg2 = ilog2(p->n2);
+    PD_TRY(launch_k(p->pdl != 0, k_aff_sums<T, D>, dim3(kBlocks), dim3(256), 0, st, u, (const uint8_t *)p->chi, lg1,
+                    lg2, p->aff_c[0], p->aff_c[1], p->aff_c[2], p->N, p->red));
+    T *coef = reinterpret_cast<T *>(p->aff_coef);
+    PD_TRY(launch_k(p->pdl != 0, k_aff_fit<T, D>, dim3(1), dim3(256), 0, st, (const double *)p->red, fa, coef));
+    p->launches += 2;
+    *view = AffineView<T>{coef, p->aff_c[0], p->aff_c[1], p->aff_c[2], lg1, lg2};
+    return PD_OK;
+}
+
+template <typename T, int D, bool ENERGY, int WM, bool SPARSE = (WM == W_NONE), bool AFF = false>
 pd_status force_bond_pipeline(pd_plan *p, const T *u, const T *s, const uint8_t *lam, const T *G, T *L, T *W,
                               cudaStream_t st)
 {
     cx<T> *spec = reinterpret_cast<cx<T> *>(spec_buf<T>(p));
     const int64_t fs = p->N / 2;
     constexpr int FI = D + (ENERGY ? Sym<D>::n : 0), FO = D + (ENERGY ? 1 : 0);
-    ProForce<T, D, ENERGY, WM> pro{u, s, lam, p->chi, p->N, spec, fs};
+    AffineView<T> av{};
+    if constexpr (AFF) PD_TRY((affine_fit<T, D>(p, u, st, &av)));
+    ProForce<T, D, ENERGY, WM, AFF> pro{u, s, lam, p->chi, p->N, spec, fs, av};
     PD_TRY(launch_rows<T>(p, pro, st));
     if (D == 3) PD_TRY((col_pass<T, FI>(p, 0, false, st)));
     const int ob = D == 3 ? FI : 0;
@@ -34,7 +56,8 @@ pd_status force_bond_pipeline(pd_plan *p, const T *u, const T *s, const uint8_t 
     if constexpr (SPARSE) {
         static_assert(WM == W_NONE, "the boundary-node list is for the plan weight chi_B");
         const Model<T> m = model_view<T>(p);
-        EpiForceSparse<T, D, ENERGY> epi{u, p->chi, m.gent, p->gidx, L, W, p->N, p->n1, spec + ob * fs, fs};
+        EpiForceSparse<T, D, ENERGY, AFF> epi{u, p->chi, m.gent, p->gidx, L, W, p->N, p->n1, spec + ob * fs, fs,
+                                              av, reinterpret_cast<const T *>(p->aff_tab)};
         PD_TRY(launch_rows<T>(p, epi, st));
     } else {
         EpiForceDense<T, D, ENERGY, WM> epi{u, s, lam, p->chi, G, L, W, p->N, p->n1, spec + ob * fs, fs};
@@ -290,6 +313,17 @@ pd_status force_plain(pd_plan *p, const T *u, const T *s, T *L, T *W, cudaStream
         G = Gs;
     }
     return force_any<T>(p, u, s, nullptr, G, L, W, st);
+}
+
+// pd_force: force_plain, or with the affine split when the plan has it on and
+// the call is the plain bond force in the plan's precision (pd_affine.cuh)
+template <typename T>
+pd_status force_public(pd_plan *p, const T *u, const T *s, T *L, T *W, cudaStream_t st)
+{
+    const bool aff = p->affine_split && !p->state_based && !s && !W && sizeof(T) == (p->prob.fp64 ? 8 : 4);
+    if (!aff) return force_plain<T>(p, u, s, L, W, st);
+    if (p->dim == 2) return force_bond_pipeline<T, 2, false, W_NONE, true, true>(p, u, s, nullptr, nullptr, L, W, st);
+    return force_bond_pipeline<T, 3, false, W_NONE, true, true>(p, u, s, nullptr, nullptr, L, W, st);
 }
 
 }  // namespace pd

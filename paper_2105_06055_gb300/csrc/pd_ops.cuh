@@ -13,6 +13,7 @@
 // subtracts G u at the listed nodes before the rows are written.
 #pragma once
 
+#include "pd_affine.cuh"
 #include "pd_plan.cuh"
 
 namespace pd {
@@ -87,8 +88,10 @@ enum WeightMode { W_NONE = 0, W_S = 1, W_LAM = 2 };
 // ---------------------------------------------------------------------------
 // Forward prologue: fields v u_j (D) [and v u_i u_j (ncomp) when ENERGY]
 // ---------------------------------------------------------------------------
-template <typename T, int D, bool ENERGY, int WM>
+// AFF: transform u - a instead of u, a the exact affine fit (pd_affine.cuh)
+template <typename T, int D, bool ENERGY, int WM, bool AFF = false>
 struct ProForce {
+    static_assert(!AFF || (!ENERGY && WM == W_NONE), "the affine split is for the plain force");
     static constexpr int kFin = 0, kFout = D + (ENERGY ? Sym<D>::n : 0);
     static constexpr int kNF = D + (WM == W_S ? 1 : 0), kNB = 1 + (WM == W_LAM ? 1 : 0), kStage = 0;
     static constexpr bool kSparse = false;
@@ -99,6 +102,7 @@ struct ProForce {
     int64_t N;
     cx<T> *spec;
     int64_t fstride;
+    AffineView<T> aff;
     __device__ const cx<T> *spec_in(int) const { return nullptr; }
     __device__ cx<T> *spec_out(int f) const { return spec + f * fstride; }
     __device__ const T *nf_src(int k) const { return k < D ? u + k * N : s; }
@@ -110,10 +114,15 @@ struct ProForce {
         if constexpr (WM == W_LAM) v *= c.b(1, rl, i1) ? T(1) : T(0);
         T uu[D];
 #pragma unroll
-        for (int j = 0; j < D; ++j) {
-            uu[j] = c.f(j, rl, i1);
-            out[j] = v * uu[j];
+        for (int j = 0; j < D; ++j) uu[j] = c.f(j, rl, i1);
+        if constexpr (AFF) {
+            T a[D];
+            aff.at(i1, c.row0 + rl, D, a);
+#pragma unroll
+            for (int j = 0; j < D; ++j) uu[j] -= a[j];
         }
+#pragma unroll
+        for (int j = 0; j < D; ++j) out[j] = v * uu[j];
         if constexpr (ENERGY) {
 #pragma unroll
             for (int q = 0; q < Sym<D>::n; ++q) out[D + q] = v * uu[Sym<D>::i(q)] * uu[Sym<D>::j(q)];
@@ -169,8 +178,11 @@ struct CombForce {
 //   emit  : at boundary nodes (gidx >= 0) L_i -= G_ij u_j, W += 1/2 u.G.u with
 //           G from the boundary list; write the rows
 // ---------------------------------------------------------------------------
-template <typename T, int D, bool ENERGY>
+// AFF: the transforms saw u - a; G applies to u - a and the exact L(a) is
+// added from the boundary entry's moment row
+template <typename T, int D, bool ENERGY, bool AFF = false>
 struct EpiForceSparse {
+    static_assert(!AFF || !ENERGY, "the affine split is for the plain force");
     static constexpr int kFin = D + (ENERGY ? 1 : 0), kFout = 0, kStage = D + (ENERGY ? 1 : 0);
     static constexpr int kNF = ENERGY ? D : 0, kNB = 1;
     static constexpr bool kSparse = false;
@@ -184,6 +196,8 @@ struct EpiForceSparse {
     int n1;
     const cx<T> *spec;
     int64_t fstride;
+    AffineView<T> aff;
+    const T *atab;  // [entries][Sym<D>::n * D]
     __device__ const cx<T> *spec_in(int f) const { return spec + f * fstride; }
     __device__ cx<T> *spec_out(int) const { return nullptr; }
     __device__ const T *nf_src(int k) const { return u + k * N; }
@@ -216,6 +230,15 @@ struct EpiForceSparse {
         for (int j = 0; j < D; ++j) {
             uu[j] = ENERGY ? c.f(j, rl, i1) : u[j * N + p];
             Gu[j] = T(0);
+        }
+        if constexpr (AFF) {
+            T a[D], La[D];
+            aff.at(i1, c.row0 + rl, D, a);
+#pragma unroll
+            for (int j = 0; j < D; ++j) uu[j] -= a[j];
+            aff_force<T, D>(aff.coef, atab + (int64_t)k * (Sym<D>::n * D), La);
+#pragma unroll
+            for (int i = 0; i < D; ++i) s[i] += La[i];
         }
         sym_apply<T, D>(e.g, uu, Gu);
 #pragma unroll

@@ -358,6 +358,58 @@ __global__ void k_gfill(int n1, int64_t nrows, const uint8_t *chi, const double 
     }
 }
 
+// Body moments about the node (c0, c1, c2): Σ chi, Σ chi e_k, Σ chi e_k e_l
+// (e = i - c; order S0, e1, e2, e3, 11, 22, 33, 12, 13, 23), block partials.
+// The sums are of integers below 2^53, so they are exact in FP64.
+__global__ void __launch_bounds__(256) k_body_moments(int n1, int n2, const uint8_t *chi, int c0, int c1, int c2,
+                                                      int64_t N, double *part)
+{
+    double a[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+        if (!chi[p]) continue;
+        int i1, i2, i3;
+        node_coords(p, n1, n2, i1, i2, i3);
+        const double e[3] = {(double)(i1 - c0), (double)(i2 - c1), (double)(i3 - c2)};
+        a[0] += 1.0;
+        for (int k = 0; k < 3; ++k) a[1 + k] += e[k];
+        a[4] += e[0] * e[0];
+        a[5] += e[1] * e[1];
+        a[6] += e[2] * e[2];
+        a[7] += e[0] * e[1];
+        a[8] += e[0] * e[2];
+        a[9] += e[1] * e[2];
+    }
+    for (int v = 0; v < 10; ++v) {
+        const double t = block_sum_d(a[v]);
+        if (threadIdx.x == 0) part[(int64_t)blockIdx.x * 10 + v] = t;
+    }
+}
+
+// Affine-split moments per boundary entry: M_(q)k = Σ_H chi(x+xi) C_q(xi) dV o_k
+// (C_q in Sym order with its quadrature weight, o the integer offset), FP64 sums.
+template <typename T>
+__global__ void k_aff_table(int n1, int n2, int n3, HorizonDev hz, int nc, int dim, const uint8_t *chi,
+                            const GEntry<double> *gent, int64_t ngent, T *tab)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ngent) return;
+    const int64_t p = gent[k].p;
+    int i1, i2, i3;
+    node_coords(p, n1, n2, i1, i2, i3);
+    double acc[18];
+    for (int v = 0; v < 18; ++v) acc[v] = 0.0;
+    for (int c = 0; c < hz.cnt; ++c) {
+        const int o[3] = {hz.off[3 * c], hz.off[3 * c + 1], hz.off[3 * c + 2]};
+        const int a = (i1 + o[0]) & (n1 - 1), b = (i2 + o[1]) & (n2 - 1), e = (i3 + o[2]) & (n3 - 1);
+        if (!chi[((int64_t)e * n2 + b) * n1 + a]) continue;
+        for (int q = 0; q < nc; ++q) {
+            const double cq = hz.c[(int64_t)q * hz.cnt + c];
+            for (int kk = 0; kk < dim; ++kk) acc[q * dim + kk] += cq * (double)o[kk];
+        }
+    }
+    for (int v = 0; v < nc * dim; ++v) tab[k * nc * dim + v] = (T)acc[v];
+}
+
 template <typename Tout>
 __global__ void k_convert(const double *in, Tout *out, int64_t n)
 {
@@ -469,6 +521,20 @@ const char *pd_last_error_detail(void) { return g_err; }
 
 double pd_plan_critical_energy(const pd_plan *p) { return p ? p->wc : 0.0; }
 
+pd_status pd_plan_set_affine_split(pd_plan *p, int on)
+{
+    if (!p || (on != 0 && on != 1)) {
+        set_error("pd_plan_set_affine_split: null plan or value not 0/1");
+        return PD_ERR_ARG;
+    }
+    if (on && (p->prob.model != PD_LIN_BOND || !p->aff_ok)) {
+        set_error("pd_plan_set_affine_split: bond model with a body that spans the grid's dimensions only");
+        return PD_ERR_ARG;
+    }
+    p->affine_split = on;
+    return PD_OK;
+}
+
 pd_status pd_plan_inject_stall(pd_plan *p, int kind)
 {
     if (!p || (kind != 0 && kind != 3)) {
@@ -544,7 +610,7 @@ void pd_plan_destroy(pd_plan *p)
 {
     if (!p) return;
     void *ptrs[] = {p->chi, p->chi_om, p->mbits, p->hoff, p->mhat64, p->mhat32, p->ghat64, p->ghat32, p->G64, p->G32,
-                    p->goff, p->gidx, p->gent64, p->gent32,
+                    p->goff, p->gidx, p->gent64, p->gent32, p->aff_tab, p->aff_coef,
                     p->qt64, p->m3inv64, p->qt32, p->m3inv32, p->tw64, p->tw32, p->spec32, p->spec64,
                     p->work, p->red};
     for (void *q : ptrs)
@@ -581,6 +647,86 @@ pd_status pd_plan_create(const pd_problem *pr, const uint8_t *chi_B, const uint8
         return s;
     }
     *out = p;
+    return PD_OK;
+}
+
+// Plan-time part of the affine split of pd_force (pd_affine.cuh): the body's
+// centre node and the inverse of the normal matrix of the least-squares
+// affine fit, the bound on the node offsets, the coefficient buffer and the
+// boundary moment table.
+static pd_status affine_setup(pd_plan *p, cudaStream_t st)
+{
+    const int dim = p->dim;
+    constexpr int kBlk = 256;
+    double *part = p->red;  // free at plan time
+    double mom[10];
+    auto moments = [&](int c0, int c1, int c2) -> pd_status {
+        k_body_moments<<<kBlk, 256, 0, st>>>(p->n1, p->n2, p->chi, c0, c1, c2, p->N, part);
+        PD_LAUNCH_CHECK();
+        std::vector<double> h((size_t)kBlk * 10);
+        PD_CUDA_TRY(cudaMemcpyAsync(h.data(), part, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st));
+        PD_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int v = 0; v < 10; ++v) {
+            mom[v] = 0.0;
+            for (int b = 0; b < kBlk; ++b) mom[v] += h[(size_t)b * 10 + v];
+        }
+        return PD_OK;
+    };
+    PD_TRY(moments(0, 0, 0));
+    const int n[3] = {p->n1, p->n2, p->n3};
+    for (int k = 0; k < 3; ++k) {
+        p->aff_c[k] = (k < dim && mom[0] > 0) ? (int)std::lround(mom[1 + k] / mom[0]) : 0;
+        p->aff_emax[k] = k < dim ? (double)std::max(p->aff_c[k], n[k] - 1 - p->aff_c[k]) : 0.0;
+    }
+    PD_TRY(moments(p->aff_c[0], p->aff_c[1], p->aff_c[2]));
+    // normal matrix [[S0, Se^T], [Se, See]] and its inverse (Gauss-Jordan, partial pivoting)
+    const int M = dim + 1;
+    const int sidx[3][3] = {{4, 7, 8}, {7, 5, 9}, {8, 9, 6}};
+    double a[4][8] = {};
+    for (int r = 0; r < M; ++r) {
+        for (int c = 0; c < M; ++c)
+            a[r][c] = (r == 0 && c == 0) ? mom[0] : (r == 0 ? mom[c] : (c == 0 ? mom[r] : mom[sidx[r - 1][c - 1]]));
+        a[r][M + r] = 1.0;
+    }
+    double scale = 0.0;
+    for (int r = 0; r < M; ++r) scale = std::max(scale, std::fabs(a[r][r]));
+    p->aff_ok = scale > 0 ? 1 : 0;
+    for (int c = 0; c < M && p->aff_ok; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < M; ++r)
+            if (std::fabs(a[r][c]) > std::fabs(a[piv][c])) piv = r;
+        if (!(std::fabs(a[piv][c]) > 1e-9 * scale)) {
+            p->aff_ok = 0;  // the body spans no full-rank affine space (a line or a point)
+            break;
+        }
+        for (int j = 0; j < 2 * M; ++j) std::swap(a[c][j], a[piv][j]);
+        const double d = a[c][c];
+        for (int j = 0; j < 2 * M; ++j) a[c][j] /= d;
+        for (int r = 0; r < M; ++r) {
+            if (r == c) continue;
+            const double f = a[r][c];
+            for (int j = 0; j < 2 * M; ++j) a[r][j] -= f * a[c][j];
+        }
+    }
+    for (int r = 0; r < M; ++r)
+        for (int c = 0; c < M; ++c) p->aff_inv[r * M + c] = a[r][M + c];
+    PD_TRY(dalloc(p, &p->aff_coef, sizeof(double) * 32));
+    PD_CUDA_TRY(cudaMemsetAsync(p->aff_coef, 0, sizeof(double) * 32, st));
+    const int nv = p->ncomp * dim;
+    const int64_t ng = std::max<int64_t>(p->ngent, 1);
+    if (p->prob.fp64) {
+        PD_TRY(dalloc(p, &p->aff_tab, sizeof(double) * nv * ng));
+        k_aff_table<double><<<nblk(ng, 128), 128, 0, st>>>(p->n1, p->n2, p->n3, p->hdev, p->ncomp, dim, p->chi,
+                                                           (const GEntry<double> *)p->gent64, p->ngent,
+                                                           (double *)p->aff_tab);
+    } else {
+        PD_TRY(dalloc(p, &p->aff_tab, sizeof(float) * nv * ng));
+        k_aff_table<float><<<nblk(ng, 128), 128, 0, st>>>(p->n1, p->n2, p->n3, p->hdev, p->ncomp, dim, p->chi,
+                                                          (const GEntry<double> *)p->gent64, p->ngent,
+                                                          (float *)p->aff_tab);
+    }
+    PD_LAUNCH_CHECK();
+    PD_CUDA_TRY(cudaStreamSynchronize(st));
     return PD_OK;
 }
 
@@ -824,6 +970,7 @@ static pd_status plan_create_impl(const pd_problem *pr, const uint8_t *chi_B, co
         PD_LAUNCH_CHECK();
         PD_CUDA_TRY(cudaStreamSynchronize(st));
     }
+    if (pr->model == PD_LIN_BOND) PD_TRY(affine_setup(p, st));
     if (pr->model == PD_LIN_STATE) {
         PD_TRY(dalloc(p, &p->qt64, sizeof(double) * 3 * N));
         PD_TRY(dalloc(p, &p->m3inv64, sizeof(double) * N));

@@ -142,6 +142,17 @@ struct pd_plan {
     int *gidx = nullptr;           // N: entry of the node in the boundary list, or -1
     void *gent64 = nullptr;        // GEntry<double>[ngent]
     void *gent32 = nullptr;        // GEntry<float>[ngent]
+    // affine split of pd_force (pd_plan_set_affine_split): per boundary entry the
+    // moments M_(ij)k = Σ_H chi(x+xi) C_ij(xi) dV o_k (o = integer offset), in the
+    // plan's precision, [ngent][ncomp * dim]; the fitted coefficients; the body's
+    // moment inverse and centre (host)
+    void *aff_tab = nullptr;
+    void *aff_coef = nullptr;      // 32 values of the plan's precision
+    int affine_split = 0;
+    int aff_ok = 0;                // body moments invertible
+    int aff_c[3] = {0, 0, 0};      // centre node (integer grid indices)
+    double aff_inv[16] = {};       // inverse of the (d+1)^2 normal matrix of the least-squares fit
+    double aff_emax[3] = {0, 0, 0};
     int64_t ngent = 0;
     double *qt64 = nullptr, *m3inv64 = nullptr;  // state-based
     float *qt32 = nullptr, *m3inv32 = nullptr;

@@ -31,7 +31,7 @@ EXPORTS = ["pd_plan_create", "pd_plan_destroy", "pd_kernel_spectrum", "pd_force"
            "pd_solve_dr", "pd_plan_create_batched", "pd_batch_size", "pd_batch_plan", "pd_solve_dr_batched",
            "pd_batch_destroy", "pd_plan_autotune", "pd_batch_autotune", "pd_plan_tuning",
            "pd_plan_set_energy_mode", "pd_plan_set_tuning", "pd_plan_autotune_solve", "pd_plan_critical_energy",
-           "pd_plan_inject_stall"]
+           "pd_plan_inject_stall", "pd_plan_set_affine_split"]
 
 PASS_KINDS = {0: "rows_fwd", 1: "cols_x2", 2: "last_axis", 3: "rows_inv"}
 
@@ -89,6 +89,8 @@ def load():
     lib.pd_plan_critical_energy.restype = D
     lib.pd_plan_inject_stall.argtypes = [P, I]
     lib.pd_plan_inject_stall.restype = I
+    lib.pd_plan_set_affine_split.argtypes = [P, I]
+    lib.pd_plan_set_affine_split.restype = I
     lib.pd_plan_profile.argtypes = [P, I]
     lib.pd_plan_profile.restype = I
     lib.pd_plan_profile_read.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(I64)]
@@ -386,6 +388,11 @@ class Plan:
     def boundary_nodes(self):
         return int(load().pd_plan_boundary_nodes(self._h))
 
+    def set_affine_split(self, on: bool):
+        """pd_force on fields with a large affine part: transform u - a (a the
+        least-squares affine fit) and add the exact force of a (pd_plan_set_affine_split)."""
+        _check(load().pd_plan_set_affine_split(self._h, 1 if on else 0), "pd_plan_set_affine_split")
+
     def inject_stall(self, kind: int):
         """Failure-handling test hook (pd_plan_inject_stall): the next row pass
         of this kind (0 forward, 3 inverse) has one block whose wait runs out."""
@@ -395,6 +402,7 @@ class Plan:
     def critical_energy(self):
         return float(load().pd_plan_critical_energy(self._h))
 
+    @property
     def stable_dt(self):
         return float(load().pd_stable_dt(self._h))
 

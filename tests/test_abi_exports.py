@@ -100,3 +100,10 @@ def test_tuning_widths_are_checked_on_the_host():
         assert lib.pd_plan_set_tuning(ctypes.cast(dummy, ctypes.c_void_p), arr) == -1, bad
     assert "widths 2..32" in lib.pd_last_error_detail().decode()
     assert not any(dummy)
+
+
+def test_binding_plan_queries_are_properties():
+    """Plan queries that the tests and the bench read as attributes stay properties."""
+    from paper_2105_06055_gb300 import pd
+    for name in ("stable_dt", "critical_energy", "boundary_nodes", "launch_count", "workspace_bytes", "tuning"):
+        assert isinstance(getattr(pd.Plan, name), property), name

@@ -66,20 +66,73 @@ def _conditioning(oracle, shape, chi, u, L, delta, alpha):
     return float(np.linalg.norm(chi * u) * lam / np.linalg.norm(L))
 
 
+def _force_split(pdm, shape, chi, u, delta, fp64, dx=1.0):
+    """pd_force with the affine split on (pd_plan_set_affine_split)."""
+    dev = torch.device("cuda")
+    plan = pdm.Plan(pdm.Problem(shape=shape, dx=dx, delta=delta, fp64=fp64), torch.tensor(chi, device=dev))
+    plan.set_affine_split(True)
+    out = plan.force(torch.tensor(u, dtype=torch.float64 if fp64 else torch.float32, device=dev))
+    torch.cuda.synchronize()
+    plan.close()
+    return out.double().cpu().numpy()
+
+
 def test_plate_2d_single_eval_fp32(pdm, oracle):
-    """Same input on the FP32 path. Its affine part makes kappa ~ 440, so the
-    error bound is 4 eps32 kappa; the sine (deformation) part alone, kappa ~ 36,
-    meets the 1e-5 force tolerance."""
+    """Same input on the FP32 path, against the oracle on the same FP32 input.
+    With the affine split the transforms see only the deformation part (the
+    exact force of the fitted affine part is added at the boundary nodes), and
+    the 1e-5 force tolerance holds on the full input. Without it the affine
+    part makes kappa ~ 440 and the error is only bounded by 4 eps32 kappa; the
+    sine (deformation) part alone, kappa ~ 36, meets 1e-5 either way."""
     cfg = inputs.plate_2d_single_eval(n=128, margin=16, seed=0)
     alpha = oracle.alpha_bond(2, 1.0, 3.0)
-    ref = oracle.force_bond(cfg["u"], cfg["chi"], 1.0, 3.0, alpha)
+    u32 = cfg["u"].astype(np.float32)
+    ref = oracle.force_bond(u32, cfg["chi"], 1.0, 3.0, alpha)
+    Lsplit = _force_split(pdm, cfg["shape"], cfg["chi"], u32, 3.0, False)
+    assert _rel(Lsplit, ref) < FP32_TOL
+    assert np.all(Lsplit[:, cfg["chi"] == 0] == 0)
     kappa = _conditioning(oracle, cfg["shape"], cfg["chi"], cfg["u"], ref, 3.0, alpha)
-    L = _run_force(pdm, cfg["shape"], cfg["chi"], cfg["u"], 3.0, False)
+    L = _run_force(pdm, cfg["shape"], cfg["chi"], u32, 3.0, False)
     assert _rel(L, ref) < 4 * 2.0 ** -24 * kappa
-    us = inputs.sine_modes(cfg["shape"], 8, 1e-3, 4, 0)
+    us = inputs.sine_modes(cfg["shape"], 8, 1e-3, 4, 0).astype(np.float32)
     refs = oracle.force_bond(us, cfg["chi"], 1.0, 3.0, alpha)
     Ls = _run_force(pdm, cfg["shape"], cfg["chi"], us, 3.0, False)
     assert _rel(Ls, refs) < FP32_TOL
+
+
+@pytest.mark.parametrize("fp64", [True, False])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_affine_split_matches_oracle(pdm, oracle, fp64, dim):
+    """The affine split is the same operator: FP64 agrees with the oracle to
+    rounding, FP32 meets 1e-5 on a strain-dominated field (uniform strain of
+    1e-2 over a ragged body, plus smooth modes of 1e-4 and a translation)."""
+    g = inputs.rng(21 + dim)
+    shape = (32, 64) if dim == 2 else (32, 32, 64)
+    dx = (1.0, 1.25) if dim == 2 else 1.0
+    m = 5
+    chi = inputs.box_mask(shape, (m,) * dim, tuple(s - m for s in shape[::-1]))
+    chi[g.random(shape) < 0.05] = 0
+    A = g.uniform(-1e-2, 1e-2, size=(dim, dim))
+    x = inputs.coords(shape, 1.0)
+    u = np.stack([sum(A[j, k] * x[k] for k in range(dim)) + 0.3 for j in range(dim)])
+    u = u + inputs.sine_modes(shape, 4, 1e-4, 3, 9)
+    if not fp64:
+        u = u.astype(np.float32)
+    alpha = oracle.alpha_bond(dim, 1.0, 3.0)
+    ref = oracle.force_bond(u, chi, dx, 3.0, alpha)
+    L = _force_split(pdm, shape, chi, u, 3.0, fp64, dx=dx)
+    assert _rel(L, ref) < (FP64_TOL if fp64 else FP32_TOL)
+
+
+def test_affine_split_refused_for_the_state_based_model(pdm):
+    dev = torch.device("cuda")
+    shape = (32, 32, 32)
+    chi = inputs.box_mask(shape, (4, 4, 4), (28, 28, 28))
+    plan = pdm.Plan(pdm.Problem(shape=shape, delta=3.0, model=pdm.PD_LIN_STATE, nu=0.4),
+                    torch.tensor(chi, device=dev))
+    with pytest.raises(pdm.PDError, match="PD_ERR_ARG"):
+        plan.set_affine_split(True)
+    plan.close()
 
 
 @pytest.mark.parametrize("shape,delta,dx", [((16, 32), 2.0, 1.0), ((64, 32), 3.0, 1.0),
