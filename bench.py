@@ -208,14 +208,15 @@ def run_native(args, rank, world):
     for _ in range(args.warmup):
         one_solve()
     torch.cuda.synchronize()
-    # one untimed profiled solve finds the dominant pass kind; the timed region
-    # then brackets only that kind with events (fewer graph event nodes)
+    # one untimed profiled solve: per-pass event times of every pass kind and
+    # the dominant kind (the timed region below carries no profiling events)
     plan.profile(True)
     one_solve()
     torch.cuda.synchronize()
     calib = plan.profile_read()
     plan.profile(False)
     dom_name = max(calib.items(), key=lambda kv: kv[1][0])[0]
+    evals_per_solve = calib["rows_inv"][1]  # one inverse row pass per force evaluation
 
     uuid = None
     try:
@@ -225,7 +226,6 @@ def run_native(args, rank, world):
     except Exception:
         uuid = None
     sampler = ClockSampler(uuid)
-    plan.profile(True, kinds=[dom_name, "rows_inv"])
     launches0 = plan.launch_count
     times = []
     its = []
@@ -247,26 +247,39 @@ def run_native(args, rank, world):
         rels.append(rel)
     clocks = sampler.stop()
     launches = plan.launch_count - launches0
-    prof = plan.profile_read()
-    plan.profile(False)
-    evals_per_step = prof["rows_inv"][1] / args.steps  # one inverse row pass per force evaluation
+    evals_per_step = float(evals_per_solve)
     total_ms = sum(times)
     t_max = max_over_ranks(total_ms, world, dev)
     value = job_rate(evals_per_step * args.steps * N, world, t_max)
 
-    # dominant pass and its roofline
+    # dominant pass: its average launch time from CUDA events recorded on the
+    # plan's stream around every launch of that kind, over two more solves
+    plan.profile(True, kinds=[dom_name])
+    for _ in range(2):
+        flush.fill_(1.0)
+        one_solve()
+    torch.cuda.synchronize()
+    dom_ms, dom_n = plan.profile_read()[dom_name]
+    plan.profile(False)
     peak, peak_kind = load_peaks()
-    dom_ms, dom_n = prof[dom_name]
-    bytes_per_launch = pass_bytes(dom_name, N, plan.boundary_nodes)
-    achieved = bytes_per_launch / (dom_ms / dom_n * 1e-3) / 1e9
+    bytes_alg = pass_bytes(dom_name, N, plan.boundary_nodes)
+    traffic = MEASURED_TRAFFIC.get(dom_name, (None, None))
+    t_launch = dom_ms / dom_n * 1e-3
+    # the fraction counts the bytes the kernel really moves: the measured DRAM
+    # traffic where a capture of the current kernel exists, never more than the
+    # algorithmic bytes
+    bytes_used = min(bytes_alg, traffic[0]) if traffic[0] else bytes_alg
+    achieved = bytes_used / t_launch / 1e9
     t_eval_ms = total_ms / (evals_per_step * args.steps)
     m2 = 25.0 * N / (t_eval_ms * 1e-3) / (peak * 1e9)
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: every step copies b
+    # in and u out (pinned host memory), the same L2 flush before each step
     b_host = torch.tensor(cfg["b"], dtype=torch.float64).pin_memory()
     u_host = torch.empty((3,) + shape, dtype=torch.float64).pin_memory()
     e2e_times = []
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(args.steps):
+        flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         b.copy_(b_host, non_blocking=True)
@@ -299,12 +312,16 @@ def run_native(args, rank, world):
             "ms_per_force_eval": t_eval_ms,
             "m2_end_to_end_hbm_frac": m2,
             "passes_ms_per_launch": {k: (v[0] / v[1] if v[1] else None) for k, v in calib.items()},
-            "passes_note": "per-pass times from one untimed profiled solve (all passes bracketed by events)",
+            "passes_note": "per-pass times from one untimed profiled solve (all passes bracketed by events); "
+                           "the timed steps carry no profiling events",
             "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
                          "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": (MEASURED_TRAFFIC[dom_name][0] if dom_name in MEASURED_TRAFFIC else None),
-                         "traffic_source": (MEASURED_TRAFFIC[dom_name][1] if dom_name in MEASURED_TRAFFIC else None),
-                         "algorithmic_bytes_per_launch": bytes_per_launch},
+                         "traffic": traffic[0], "traffic_source": traffic[1],
+                         "algorithmic_bytes_per_launch": bytes_alg,
+                         "frac_algorithmic": bytes_alg / t_launch / 1e9 / peak,
+                         "launch_us": 1e6 * t_launch,
+                         "bytes_note": "frac uses min(measured DRAM traffic, algorithmic bytes) per launch; "
+                                       "launch_us from CUDA events on the plan's stream over two solves"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(b_host.numel() * 8),
                     "d2h_bytes_per_step": int(u_host.numel() * 8)},
             "gpu_launches": int(launches),
@@ -323,35 +340,34 @@ FORCE_PASS_BYTES = {  # algorithmic bytes per node of each FP32 pass of the bond
 }
 
 
-def run_force(args):
-    import numpy as np
+def force_point(n, steps, warmup, tuning_arg="", no_autotune=False, e2e=True):
+    """One FP32 bond-model force evaluation (pd_force) on an n^3 box: median
+    event time over `steps` evaluations (L2 flushed between them), per-pass
+    event times and their algorithmic-byte fractions of the measured peak."""
     import torch
 
-    from paper_2105_06055_gb300 import build as pd_build
     from paper_2105_06055_gb300 import inputs, pd
 
-    pd_build.build()
     dev = torch.device("cuda")
-    n = args.n
     shape = (n, n, n)
     N = n ** 3
     chi = inputs.cube_with_ball_mask(n)
     u = inputs.separable_modes(shape, 4, max(n // 16, 2), 1e-3, seed=n, kmin=max(n // 32, 1)) * chi
     plan = pd.Plan(pd.Problem(shape=shape, delta=DELTA, fp64=False), torch.tensor(chi, device=dev))
-    if args.tuning:
-        plan.set_tuning(*[int(v) for v in args.tuning.split(",")])
+    if tuning_arg:
+        plan.set_tuning(*[int(v) for v in tuning_arg.split(",")])
         tuning = plan.tuning
     else:
-        tuning = None if args.no_autotune else plan.autotune()
+        tuning = None if no_autotune else plan.autotune()
     ud = torch.tensor(u, device=dev)
     L = torch.empty_like(ud)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         plan.force(ud, L=L)
     torch.cuda.synchronize()
     plan.profile(True)
-    for _ in range(max(args.steps, 3)):
+    for _ in range(max(steps, 3)):
         plan.force(ud, L=L)
     torch.cuda.synchronize()
     prof = plan.profile_read()
@@ -360,7 +376,7 @@ def run_force(args):
     sampler = ClockSampler(None)
     sampler.start()
     times = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.fill_(1.0)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -380,21 +396,44 @@ def run_force(args):
         per = ms / cnt
         byt = FORCE_PASS_BYTES[k] * N + (44 * nb if k == "rows_inv" else 0)
         passes[k] = {"us": 1e3 * per, "algorithmic_bytes": byt, "frac_of_measured_peak": byt / (per * 1e-3) / 1e9 / peak}
-    dom = max(passes, key=lambda k: passes[k]["us"] * (2 if k == "cols_x2" else 1))
     t_ms = statistics.median(times)
-    # end to end: host u -> device, force, device L -> host
-    u_host = torch.tensor(u).pin_memory()
-    L_host = torch.empty_like(u_host).pin_memory()
-    e2e = []
-    for _ in range(3):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ud.copy_(u_host, non_blocking=True)
-        plan.force(ud, L=L)
-        L_host.copy_(L, non_blocking=True)
-        torch.cuda.synchronize()
-        e2e.append(time.perf_counter() - t0)
-    out = {
+    out = {"n": n, "ms_per_eval": t_ms, "node_evals_per_s": N / (t_ms * 1e-3), "passes": passes,
+           "m2_end_to_end_hbm_frac": 25.0 * N / (t_ms * 1e-3) / (peak * 1e9), "gpu_launches": int(launches),
+           "clocks": clocks, "tuning": tuning, "boundary_nodes": nb, "peak": peak, "peak_source": peak_kind}
+    if e2e:
+        # end to end: host u -> device, force, device L -> host
+        u_host = torch.tensor(u).pin_memory()
+        L_host = torch.empty_like(u_host).pin_memory()
+        ts = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ud.copy_(u_host, non_blocking=True)
+            plan.force(ud, L=L)
+            L_host.copy_(L, non_blocking=True)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        out["e2e"] = {"value": N / statistics.median(ts), "unit": UNIT, "h2d_bytes_per_step": int(u_host.numel() * 4),
+                      "d2h_bytes_per_step": int(L_host.numel() * 4)}
+    plan.close()
+    del flush
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_force(args):
+    from paper_2105_06055_gb300 import build as pd_build
+
+    pd_build.build()
+    n = args.n
+    N = n ** 3
+    pt = force_point(n, args.steps, args.warmup, args.tuning, args.no_autotune)
+    passes = pt["passes"]
+    dom = max(passes, key=lambda k: passes[k]["us"] * (2 if k == "cols_x2" else 1))
+    traffic = MEASURED_TRAFFIC.get(f"force{n}_{dom}", (None, None))
+    t_ms = pt["ms_per_eval"]
+    return {
         "metric": f"PD force evals x nodes/sec (3D bond force evaluation, {n}^3)",
         "value": N / (t_ms * 1e-3),
         "unit": UNIT,
@@ -412,18 +451,16 @@ def run_force(args):
                    "l2": "256 MB L2 flush between steps"},
         "passes": passes,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": passes[dom]["algorithmic_bytes"] /
-                     (passes[dom]["us"] * 1e-6) / 1e9, "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
-                     "frac": passes[dom]["frac_of_measured_peak"], "traffic": None},
-        "m2_end_to_end_hbm_frac": 25.0 * N / (t_ms * 1e-3) / (peak * 1e9),
-        "e2e": {"value": N / statistics.median(e2e), "unit": UNIT, "h2d_bytes_per_step": int(u_host.numel() * 4),
-                "d2h_bytes_per_step": int(L_host.numel() * 4)},
-        "gpu_launches": int(launches),
-        "clocks": clocks,
-        "tuning": tuning,
-        "boundary_nodes": nb,
+                     (passes[dom]["us"] * 1e-6) / 1e9, "peak": pt["peak"], "peak_source": pt["peak_source"],
+                     "unit": "GB/s", "frac": passes[dom]["frac_of_measured_peak"], "traffic": traffic[0],
+                     "traffic_source": traffic[1]},
+        "m2_end_to_end_hbm_frac": pt["m2_end_to_end_hbm_frac"],
+        "e2e": pt["e2e"],
+        "gpu_launches": pt["gpu_launches"],
+        "clocks": pt["clocks"],
+        "tuning": pt["tuning"],
+        "boundary_nodes": pt["boundary_nodes"],
     }
-    plan.close()
-    return out
 
 
 def run_batched(args):
@@ -550,6 +587,8 @@ def main():
     ap.add_argument("--tuning", default="", metavar="ROWS,WX2,WLAST,SCHED[,STAGES[,STAGES_INV]]",
                     help="pin a pass configuration instead of autotuning (e.g. the one a tuned run reported)")
     ap.add_argument("--specimens", type=int, default=64)
+    ap.add_argument("--no-sweep", dest="sweep", action="store_false",
+                    help="skip the 256^3 / 512^3 force-evaluation keys of the default run")
     ap.add_argument("--profile-solve", type=int, default=0, metavar="K",
                     help="no timing: build the workload and run one solve capped at K CG iterations "
                          "(a short, deterministic target for ncu captures)")
@@ -632,6 +671,15 @@ def main():
     if world > 1:
         torch.distributed.init_process_group("nccl")
     result, cfg = run_native(args, rank, world)
+    if rank == 0 and args.sweep:
+        # the force evaluation at the larger grids of the scale sweep (extra keys;
+        # the headline stays the static solve)
+        sweep = {}
+        for n in (256, 512):
+            pt = force_point(n, 5, 3, "", args.no_autotune, e2e=False)
+            sweep[f"{n}^3"] = {k: pt[k] for k in ("ms_per_eval", "node_evals_per_s", "passes",
+                                                  "m2_end_to_end_hbm_frac", "tuning")}
+        result["force_sweep"] = sweep
     if rank == 0:
         if not args.no_cpu_baseline:
             v, cores, dt = oracle_sample(args.n, 2, min_seconds=2.0)

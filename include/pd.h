@@ -168,6 +168,21 @@ pd_status pd_step_verlet(pd_plan *plan, void *u, void *v, uint8_t *lambda, const
                          void *stream);
 
 /*
+ * pd_step_verlet_ramp -- pd_step_verlet with a time-varying volume constraint
+ * (Eq. 78, 83: the values prescribed on Gamma change with time), linear in
+ * time: the step that ends at time t = t0 + (n + 1) dt (n = 0 .. nsteps - 1)
+ * sets u = w0 + t w1 on Gamma. This is displacement-controlled loading at a
+ * constant rate, run on the device with no per-step host work; a general
+ * w(t) is applied by calling pd_step_verlet once per step (or per chunk) with
+ * the current field. t0 is the time at the start of the call.
+ * w0: device d x N or NULL (= 0); w1: device d x N (required).
+ * Other arguments and the result as for pd_step_verlet.
+ */
+pd_status pd_step_verlet_ramp(pd_plan *plan, void *u, void *v, uint8_t *lambda, const void *b, const void *w0,
+                              const void *w1, double t0, double dt, int nsteps, int64_t *n_broken_out,
+                              void *stream);
+
+/*
  * pd_plan_set_energy_mode -- how pd_step_verlet evaluates the strain energy
  * density W that decides bond breaking (Eq. 63):
  *   0 (default): the paper's convolution form, Eq. 102 (three FFT

@@ -17,6 +17,7 @@
 // exceeds Wc once fragments have moved far (|u| ~ 10-100 grid units), while
 // the direct sum errs by about eps |u(x)| / |eta| relative to W, locally.
 #include <algorithm>
+#include <cmath>
 
 #include "pd_ops.cuh"
 #include "pd_plan.cuh"
@@ -35,10 +36,11 @@ struct VerletCounters {
     int changed;
 };
 
+// Gamma values at the end of the step: w + t_next w1 (w1 null: w, constant)
 template <typename T>
-__global__ void k_kick_drift(T *u, T *v, uint8_t *lam, const T *L, const T *b, const T *w, const T *W,
-                             const uint8_t *chi, const uint8_t *co, int d, int64_t N, T hdt_rho, T dt, T Wc,
-                             int breaking, VerletCounters *cnt)
+__global__ void k_kick_drift(T *u, T *v, uint8_t *lam, const T *L, const T *b, const T *w, const T *w1, T t_next,
+                             const T *W, const uint8_t *chi, const uint8_t *co, int d, int64_t N, T hdt_rho, T dt,
+                             T Wc, int breaking, VerletCounters *cnt)
 {
     unsigned long long flips = 0;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
@@ -46,7 +48,9 @@ __global__ void k_kick_drift(T *u, T *v, uint8_t *lam, const T *L, const T *b, c
             const int64_t q = i * N + p;
             const T vh = v[q] + hdt_rho * (L[q] + b[q]);
             v[q] = vh;
-            u[q] = co[q] ? (u[q] + dt * vh) : (w ? w[q] : T(0));
+            T g = w ? w[q] : T(0);
+            if (w1) g = g + t_next * w1[q];
+            u[q] = co[q] ? (u[q] + dt * vh) : g;
         }
         if (breaking && chi[p] && lam[p] && !(W[p] <= Wc)) {
             lam[p] = 0;
@@ -182,8 +186,8 @@ pd_status step_force(pd_plan *p, const T *u, const uint8_t *lam, const T *G, T *
 }
 
 template <typename T>
-pd_status verlet_impl(pd_plan *p, T *u, T *v, uint8_t *lam, const T *b, const T *w, double dt, int nsteps,
-                      int64_t *n_broken_out, cudaStream_t st)
+pd_status verlet_impl(pd_plan *p, T *u, T *v, uint8_t *lam, const T *b, const T *w, const T *w1, double t0,
+                      double dt, int nsteps, int64_t *n_broken_out, cudaStream_t st)
 {
     const int d = p->dim;
     const int64_t N = p->N;
@@ -204,8 +208,9 @@ pd_status verlet_impl(pd_plan *p, T *u, T *v, uint8_t *lam, const T *b, const T 
     const unsigned ng = (unsigned)std::min<int64_t>(4 * p->nsm, (N + 255) / 256);
     const unsigned ngv = (unsigned)std::min<int64_t>(4 * p->nsm, (d * N + 255) / 256);
     for (int s = 0; s < nsteps; ++s) {
-        k_kick_drift<T><<<ng, 256, 0, st>>>(u, v, lam, L, b, w, W, p->chi, p->chi_om, d, N, hdt, (T)dt,
-                                            (T)p->wc, breaking, cnt);
+        const T t_next = (T)(t0 + (double)(s + 1) * dt);
+        k_kick_drift<T><<<ng, 256, 0, st>>>(u, v, lam, L, b, w, w1, t_next, W, p->chi, p->chi_om, d, N, hdt,
+                                            (T)dt, (T)p->wc, breaking, cnt);
         PD_LAUNCH_CHECK();
         p->launches++;
         if (breaking) {
@@ -233,27 +238,45 @@ pd_status verlet_impl(pd_plan *p, T *u, T *v, uint8_t *lam, const T *b, const T 
 
 using namespace pd;
 
-extern "C" pd_status pd_step_verlet(pd_plan *p, void *u, void *v, uint8_t *lambda, const void *b, const void *w,
-                                    double dt, int nsteps, int64_t *n_broken_out, void *stream)
+static pd_status verlet_entry(pd_plan *p, void *u, void *v, uint8_t *lambda, const void *b, const void *w,
+                              const void *w1, double t0, double dt, int nsteps, int64_t *n_broken_out, void *stream,
+                              const char *who)
 {
     if (!p || !u || !v || !b) {
-        set_error("pd_step_verlet: null plan, u, v or b");
+        set_error("%s: null plan, u, v or b", who);
         return PD_ERR_ARG;
     }
-    if (!(dt > 0) || nsteps < 0 || !(p->prob.rho > 0)) {
-        set_error("pd_step_verlet: dt and rho must be positive, nsteps >= 0");
+    if (!(dt > 0) || nsteps < 0 || !(p->prob.rho > 0) || !std::isfinite(t0)) {
+        set_error("%s: dt and rho must be positive, nsteps >= 0, t0 finite", who);
         return PD_ERR_ARG;
     }
     if (p->state_based) {
-        set_error("pd_step_verlet: the dynamic driver uses the bond model");
+        set_error("%s: the dynamic driver uses the bond model", who);
         return PD_ERR_ARG;
     }
     cudaStream_t st = (cudaStream_t)stream;
     if (p->prob.fp64)
-        return verlet_impl<double>(p, (double *)u, (double *)v, lambda, (const double *)b, (const double *)w, dt,
-                                   nsteps, n_broken_out, st);
-    return verlet_impl<float>(p, (float *)u, (float *)v, lambda, (const float *)b, (const float *)w, dt, nsteps,
-                              n_broken_out, st);
+        return verlet_impl<double>(p, (double *)u, (double *)v, lambda, (const double *)b, (const double *)w,
+                                   (const double *)w1, t0, dt, nsteps, n_broken_out, st);
+    return verlet_impl<float>(p, (float *)u, (float *)v, lambda, (const float *)b, (const float *)w,
+                              (const float *)w1, t0, dt, nsteps, n_broken_out, st);
+}
+
+extern "C" pd_status pd_step_verlet(pd_plan *p, void *u, void *v, uint8_t *lambda, const void *b, const void *w,
+                                    double dt, int nsteps, int64_t *n_broken_out, void *stream)
+{
+    return verlet_entry(p, u, v, lambda, b, w, nullptr, 0.0, dt, nsteps, n_broken_out, stream, "pd_step_verlet");
+}
+
+extern "C" pd_status pd_step_verlet_ramp(pd_plan *p, void *u, void *v, uint8_t *lambda, const void *b,
+                                         const void *w0, const void *w1, double t0, double dt, int nsteps,
+                                         int64_t *n_broken_out, void *stream)
+{
+    if (!w1) {
+        set_error("pd_step_verlet_ramp: w1 is required (use pd_step_verlet for a constant w)");
+        return PD_ERR_ARG;
+    }
+    return verlet_entry(p, u, v, lambda, b, w0, w1, t0, dt, nsteps, n_broken_out, stream, "pd_step_verlet_ramp");
 }
 
 extern "C" pd_status pd_plan_set_energy_mode(pd_plan *p, int mode)

@@ -31,7 +31,7 @@ EXPORTS = ["pd_plan_create", "pd_plan_destroy", "pd_kernel_spectrum", "pd_force"
            "pd_solve_dr", "pd_plan_create_batched", "pd_batch_size", "pd_batch_plan", "pd_solve_dr_batched",
            "pd_batch_destroy", "pd_plan_autotune", "pd_batch_autotune", "pd_plan_tuning",
            "pd_plan_set_energy_mode", "pd_plan_set_tuning", "pd_plan_autotune_solve", "pd_plan_critical_energy",
-           "pd_plan_inject_stall", "pd_plan_set_affine_split"]
+           "pd_plan_inject_stall", "pd_plan_set_affine_split", "pd_step_verlet_ramp"]
 
 PASS_KINDS = {0: "rows_fwd", 1: "cols_x2", 2: "last_axis", 3: "rows_inv"}
 
@@ -71,6 +71,8 @@ def load():
     lib.pd_force.restype = I
     lib.pd_step_verlet.argtypes = [P, P, P, P, P, P, D, I, ctypes.POINTER(I64), P]
     lib.pd_step_verlet.restype = I
+    lib.pd_step_verlet_ramp.argtypes = [P, P, P, P, P, P, P, D, D, I, ctypes.POINTER(I64), P]
+    lib.pd_step_verlet_ramp.restype = I
     lib.pd_solve_static.argtypes = [P, P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D), P]
     lib.pd_solve_static.restype = I
     lib.pd_force_adjoint.argtypes = [P, P, P, P, P, P, P]
@@ -285,6 +287,22 @@ class Plan:
         _check(load().pd_step_verlet(self._h, _ptr(u), _ptr(v), _ptr(lam), _ptr(b), _ptr(w), float(dt),
                                      int(nsteps), ctypes.byref(nb) if count_broken else None,
                                      _stream(stream)), "pd_step_verlet")
+        return int(nb.value) if count_broken else None
+
+    def step_verlet_ramp(self, u, v, lam, b, w0, w1, t0=0.0, dt=1.0, nsteps=1, count_broken=False, stream=None):
+        """pd_step_verlet_ramp: Gamma values w0 + t w1 at the end of each step."""
+        u = self._field(u, self.dim, "u")
+        v = self._field(v, self.dim, "v")
+        b = self._field(b, self.dim, "b")
+        w0 = self._field(w0, self.dim, "w0", allow_none=True)
+        w1 = self._field(w1, self.dim, "w1")
+        if lam is not None:
+            lam = self._field(lam, 0, "lambda", dtype=torch.uint8)
+        nb = ctypes.c_int64(0)
+        _check(load().pd_step_verlet_ramp(self._h, _ptr(u), _ptr(v), _ptr(lam), _ptr(b), _ptr(w0), _ptr(w1),
+                                          float(t0), float(dt), int(nsteps),
+                                          ctypes.byref(nb) if count_broken else None, _stream(stream)),
+               "pd_step_verlet_ramp")
         return int(nb.value) if count_broken else None
 
     def solve_static(self, u, b, w=None, rtol=1e-8, max_iter=20000, stream=None, raise_on_fail=True):

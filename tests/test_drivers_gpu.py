@@ -255,3 +255,67 @@ def test_static_after_solver_autotune(pdm):
         sols.append(u.cpu().numpy())
         plan.close()
     assert _rel(sols[1], sols[0]) < 1e-6
+
+
+# --------------------------------------------------------------------------
+# Time-varying volume constraints (Eq. 78, 83: w prescribed on Gamma changes with time)
+# --------------------------------------------------------------------------
+
+def _pulled_bar():
+    """2D bar clamped on the left Gamma layers and pulled on the right ones: the
+    prescribed field ramps up in time, so the constraint changes every step."""
+    shape = (32, 128)
+    delta = 3.0
+    chi = inputs.box_mask(shape, (4, 4), (124, 28))
+    x1, x2 = inputs.coords(shape)
+    gam_l = (chi == 1) & (x1 < 7)
+    gam_r = (chi == 1) & (x1 >= 121)
+    co = (chi.astype(bool) & ~gam_l & ~gam_r).astype(np.uint8)
+    w1 = np.zeros((2,) + shape)
+    w1[0][gam_r] = 2e-3   # x-velocity of the right grips
+    w1[1][gam_r] = 5e-4   # and a small shear
+    return shape, delta, chi, np.stack([co, co]), w1
+
+
+@pytest.mark.parametrize("damage", [False, True])
+def test_verlet_time_varying_constraint_matches_oracle(pdm, oracle, damage):
+    """FP64 GPU Verlet with w(t) on Gamma, by the ramp entry point (w = t w1)
+    and by one pd_step_verlet call per step with the current w, against the
+    oracle's Verlet driver with w given as a function of the step."""
+    shape, delta, chi, co, w1 = _pulled_bar()
+    alpha = oracle.alpha_bond(2, 1.0, delta)
+    wc = oracle.wc_from_stretch(2, 1.0, delta, alpha, 1e-3) if damage else 0.0
+    plan = pdm.Plan(pdm.Problem(shape=shape, delta=delta, rho=1.0, Wc=wc, fp64=True), _t(chi, torch.uint8),
+                    _t(co, torch.uint8))
+    dt = 0.5 * plan.stable_dt
+    nsteps = 120
+    lam0 = chi.copy()
+    b = np.zeros((2,) + shape)
+    uo, vo, lo, flo = oracle.verlet_damage(np.zeros((2,) + shape), np.zeros((2,) + shape), lam0, chi, co, b,
+                                           lambda n: (n * dt) * w1, 1.0, delta, alpha, 1.0, dt,
+                                           wc if damage else 1e300, nsteps)
+    if damage:
+        assert flo > 0  # the pulled grips break bonds within the run
+    gam = (chi == 1) & (co[0] == 0)
+    assert np.allclose(uo[0][gam & (w1[0] > 0)], nsteps * dt * 2e-3)
+    # (1) the ramp entry point, in two calls (t0 carries the time over)
+    u = torch.zeros((2,) + shape, dtype=torch.float64, device=DEV)
+    v = torch.zeros_like(u)
+    lam = _t(lam0, torch.uint8) if damage else None
+    n1 = 50
+    nb = plan.step_verlet_ramp(u, v, lam, _t(b), None, _t(w1), t0=0.0, dt=dt, nsteps=n1, count_broken=True)
+    nb += plan.step_verlet_ramp(u, v, lam, _t(b), None, _t(w1), t0=n1 * dt, dt=dt, nsteps=nsteps - n1,
+                                count_broken=True)
+    assert _rel(u.cpu().numpy(), uo) < 1e-10 and _rel(v.cpu().numpy(), vo) < 1e-10
+    if damage:
+        assert nb == flo and np.array_equal(lam.cpu().numpy(), lo)
+    # (2) one call per step with the current prescribed field
+    u.zero_()
+    v.zero_()
+    lam = _t(lam0, torch.uint8) if damage else None
+    for n in range(nsteps):
+        plan.step_verlet(u, v, lam, _t(b), _t(((n + 1) * dt) * w1), dt=dt, nsteps=1)
+    assert _rel(u.cpu().numpy(), uo) < 1e-10 and _rel(v.cpu().numpy(), vo) < 1e-10
+    if damage:
+        assert np.array_equal(lam.cpu().numpy(), lo)
+    plan.close()

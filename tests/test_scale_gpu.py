@@ -57,3 +57,29 @@ def test_bond_force_large_sampled(pdm, oracle, n, fp64):
     Lo = oracle.force_bond_at(u.astype(np.float64), chi, 1.0, 3.0, alpha, nodes)
     rel = float(np.linalg.norm(Lg - Lo) / np.linalg.norm(Lo))
     assert rel < (1e-11 if fp64 else 1e-5), rel
+
+
+@pytest.mark.parametrize("n", [256, 512])
+def test_static_solve_large(pdm, oracle, n):
+    """The config-2 static solve (state-based, nu = 1/4, cube minus a centred
+    ball, clamp and load layers) at 256^3 and 512^3: FP32 FFT CG with FP64
+    refinement to a relative residual of 1e-8, the returned u checked with the
+    oracle's FP64 state-based operator on every node (a full direct sum)."""
+    cfg = inputs.cube_with_cavity(n=n)
+    shape = cfg["shape"]
+    prob = pdm.Problem(shape=shape, delta=3.0, model=pdm.PD_LIN_STATE, nu=0.25, fp64=False)
+    plan = pdm.Plan(prob, torch.tensor(cfg["chi"], device=DEV), torch.tensor(cfg["chi_omega"], device=DEV))
+    b = torch.tensor(cfg["b"], dtype=torch.float64, device=DEV)
+    u = torch.zeros((3,) + shape, dtype=torch.float64, device=DEV)
+    it, rel, st = plan.solve_static(u, b, None, rtol=1e-8, max_iter=100000)
+    assert st == 0 and rel <= 1e-8 and it > 0
+    del b
+    ug = u.cpu().numpy()
+    del u
+    plan.close()
+    torch.cuda.empty_cache()
+    ka, cb, _ = oracle.lps_constants(1.0, 0.25, 1.0, 3.0)
+    res = oracle.static_residual(ug, cfg["chi"], cfg["chi_omega"], cfg["b"], 1.0, 3.0, ("lps", ka, cb))
+    bn = np.linalg.norm(cfg["chi_omega"] * cfg["b"])
+    assert np.linalg.norm(res) / bn <= 1.5e-8
+    assert np.all(ug[:, cfg["chi_omega"][0] == 0] == 0)
