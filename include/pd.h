@@ -34,6 +34,9 @@
  *   PD_LIN_STATE (3D): linearized state-based solid (Eq. 33-39, 92-97) with
  *     kappa = E/(3(1-2nu)), mu = E/(2(1+nu)), bulk m0 = Σ_H omega|xi|^2 dV
  *     in the kernels (Eq. 37) and the nodal m(x) of Eq. 94 in the dilatation.
+ *   PD_NONLIN_BOND (2D/3D): bond force c/2 (|xi+eta|^2 - |xi|^2)(xi+eta) with
+ *     c = alpha/|xi|^3 and the alpha of PD_LIN_BOND (§3.2, Eq. 19-22): exactly
+ *     invariant under finite rigid motions; its small-eta limit is Eq. 17.
  */
 #ifndef PD_H
 #define PD_H
@@ -57,7 +60,9 @@ typedef enum {
 
 typedef enum {
     PD_LIN_BOND = 0,   /* linearized bond-based solid, Eq. 17-18            */
-    PD_LIN_STATE = 1   /* linearized state-based (LPS) solid, Eq. 33-39, 3D */
+    PD_LIN_STATE = 1,  /* linearized state-based (LPS) solid, Eq. 33-39, 3D */
+    PD_NONLIN_BOND = 2 /* nonlinear rotation-invariant bond model, Eq. 19-26
+                          (pd_force only; its linearization is PD_LIN_BOND)  */
 } pd_model;
 
 typedef struct {
@@ -143,6 +148,16 @@ pd_status pd_kernel_spectrum(pd_plan *plan, double *out, void *stream);
  * W:  device, N, or NULL: strain energy density of Eq. 47 / 102 with bond
  *     factor v v' (bond model only).
  * u and L must not overlap.
+ * PD_NONLIN_BOND (s and W must be NULL): the force of Eq. 21 with the chi_B
+ * cut, L_i = chi Σ_H chi' c/2 (|xi+eta|^2 - |xi|^2)(xi_i+eta_i) dV, evaluated as
+ * the correlations of Eq. 26 (the paper's Eq. 59 prints one of its terms
+ * without the factor u_i; the form used here is Eq. 26's): forward transforms
+ * of chi u_j, chi u_i u_j and chi |u|^2 u_i (2D: 7 fields, 3D: 12), one
+ * spectral combination with the kernels C_ij = c xi_i xi_j, a_i = c xi_i and c
+ * (2D: 11 inverse fields, 3D: 21), and a per-node epilogue with plan-time
+ * boundary fields. The body mean of u is removed first (the model is exactly
+ * translation invariant), which keeps the FP32 rounding at the level of the
+ * deformation instead of |u|^3.
  */
 pd_status pd_force(pd_plan *plan, const void *u, const void *s, void *L, void *W, void *stream);
 

@@ -200,8 +200,8 @@ extern "C" pd_status pd_force_adjoint(pd_plan *p, const void *u, const void *s, 
         set_error("pd_force_adjoint: null plan, u or gL");
         return PD_ERR_ARG;
     }
-    if (p->state_based) {
-        set_error("pd_force_adjoint: bond model only");
+    if (p->state_based || p->nonlinear) {
+        set_error("pd_force_adjoint: linearized bond model only");
         return PD_ERR_ARG;
     }
     if (!gu && !gs) return PD_OK;

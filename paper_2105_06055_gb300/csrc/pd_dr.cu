@@ -808,6 +808,10 @@ extern "C" pd_status pd_solve_dr(pd_plan *p, double *u, const double *b, const d
         set_error("pd_solve_dr: null plan, u or b");
         return PD_ERR_ARG;
     }
+    if (p->nonlinear) {
+        set_error("pd_solve_dr: the nonlinear bond model is available through pd_force only");
+        return PD_ERR_ARG;
+    }
     PD_TRY(check_dr_args("pd_solve_dr", rtol, max_iter));
     DrRunner R;
     PD_TRY(R.init({p}));

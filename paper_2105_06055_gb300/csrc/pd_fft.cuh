@@ -570,7 +570,8 @@ struct ColGeom {
 // Tensor maps: tmt covers all slots of the spectrum buffer as
 // [outer * slots][L][2 * inner] scalars with box (2w, lb, 1); tmm the same with
 // box (4, lb, 1) for the mirror column.
-// Shared memory: [L] twiddles, [max(kFin,kFout)][L][w] tiles, [kFin][L][2] mirror, mbarrier.
+// Shared memory: [L] twiddles, [max(kFin,kFout)][L][w] tiles, [max(kFin,kFout)][L][2] mirror,
+// the table slice, mbarrier.
 template <typename T, class Op>
 __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__restrict__ tw, int axis_is_z,
                                               const __grid_constant__ CUtensorMap tmt,
@@ -579,7 +580,8 @@ __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__r
     extern __shared__ __align__(128) unsigned char smem_raw[];
     constexpr int FI = Op::kFin, FO = Op::kFout, MODE = Op::kMode;
     constexpr int FB = FI > FO ? FI : FO;
-    static_assert(MODE != 2 || FO <= FI, "combine writes its outputs over its inputs");
+    // the combine reads all inputs of a mode before it writes that mode's
+    // outputs, so outputs may outnumber inputs (the tile holds max(kFin, kFout))
     const int L = 1 << g.lgl;
     const int w = g.w, ncol = w + g.mirror;  // threads: ncol x (L / kV)
     const int col = threadIdx.x % ncol, jt = threadIdx.x / ncol;
@@ -600,7 +602,7 @@ __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__r
     constexpr int NTAB = (MODE == 2) ? Op::kTab : 0;
     // table slice [comp][fold row][kx]; the kx = n1/2 column only where the tile holds kx = 0
     const int trows = L / 2 + 1, tcols = w + (g.tmode == 1 ? 0 : 1), tcs = trows * tcols;
-    T *tab = reinterpret_cast<T *>(mir + (g.mirror ? FI * L * 2 : 0));
+    T *tab = reinterpret_cast<T *>(mir + (g.mirror ? FB * L * 2 : 0));  // mirror: inputs in, parked outputs out
     unsigned long long *mbar = reinterpret_cast<unsigned long long *>(tab + ((NTAB * tcs + 1) & ~1));
 
     // mirror column (3D last axis): kx = 0 of k2' = (n2 - k2) mod n2

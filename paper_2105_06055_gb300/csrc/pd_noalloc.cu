@@ -242,7 +242,7 @@ extern "C" pd_status pd_force2d_noalloc(const pd_problem *pr, const uint8_t *chi
     k_na_fold<<<(unsigned)((fold + 127) / 128), 128, 0, st>>>(n1, n2, h, off, cc, cnt, 1.0 / (double)N, mh, fold);
     k_na_twiddle<<<(L2 + 255) / 256, 256, 0, st>>>(tw, L2);
     PD_LAUNCH_CHECK();
-    HorizonDev hd{off, cc, nullptr, nullptr, cnt};
+    HorizonDev hd{off, cc, nullptr, nullptr, nullptr, cnt};
     k_gfield<float, double, double><<<(unsigned)((N + 127) / 128), 128, 0, st>>>(n1, n2, 1, hd, 3, chi_B,
                                                                                (const double *)nullptr, G, N);
     PD_LAUNCH_CHECK();

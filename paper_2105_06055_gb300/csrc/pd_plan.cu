@@ -145,8 +145,9 @@ template Model<double> model_view<double>(const pd_plan *);
 //   mhat_c(k) = (1/N) Σ_H C_c(xi) dV (cos(theta) - 1) = -(2/N) Σ C_c dV sin^2(theta/2)
 //   ghat_i(k) = (1/N) Σ_H g_i(xi) dV sin(theta)
 // theta = 2 pi Σ_a k_a o_a / n_a, reduced exactly with integer arithmetic.
+//   chat(k)   = (1/N) Σ_H c(xi) dV (cos(theta) - 1)   (nonlinear bond model, when chat is given)
 __global__ void k_fold_tables(int dim, int n1, int n2, int n3, int h, HorizonDev hz, int ncomp,
-                              double invN, double *mhat, double *ghat, int64_t fold_sz)
+                              double invN, double *mhat, double *ghat, int64_t fold_sz, double *chat = nullptr)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= fold_sz) return;
@@ -155,7 +156,7 @@ __global__ void k_fold_tables(int dim, int n1, int n2, int n3, int h, HorizonDev
     const int kz = (int)(t / ((int64_t)(h + 1) * (n2 / 2 + 1)));
     const int nmax = max(n1, max(n2, n3));
     const int s1 = nmax / n1, s2 = nmax / n2, s3 = nmax / n3;
-    double accm[6] = {0, 0, 0, 0, 0, 0}, accg[3] = {0, 0, 0};
+    double accm[6] = {0, 0, 0, 0, 0, 0}, accg[3] = {0, 0, 0}, accc = 0.0;
     for (int c = 0; c < hz.cnt; ++c) {
         const int o1 = hz.off[3 * c], o2 = hz.off[3 * c + 1], o3 = hz.off[3 * c + 2];
         long long num = (long long)kx * o1 * s1 + (long long)ky * o2 * s2 + (long long)kz * o3 * s3;
@@ -165,12 +166,14 @@ __global__ void k_fold_tables(int dim, int n1, int n2, int n3, int h, HorizonDev
         const double sh = sinpi(frac);                   // sin(theta / 2)
         const double one_minus_cos = 2.0 * sh * sh;
         for (int q = 0; q < ncomp; ++q) accm[q] -= hz.c[q * hz.cnt + c] * one_minus_cos;
+        if (chat) accc -= hz.cs[c] * one_minus_cos;
         if (ghat) {
             const double sn = sinpi(2.0 * frac);
             for (int i = 0; i < 3; ++i) accg[i] += hz.g[i * hz.cnt + c] * sn;
         }
     }
     for (int q = 0; q < ncomp; ++q) mhat[q * fold_sz + t] = accm[q] * invN;
+    if (chat) chat[t] = accc * invN;
     if (ghat)
         for (int i = 0; i < 3; ++i) ghat[i * fold_sz + t] = accg[i] * invN;
     (void)dim;
@@ -410,6 +413,32 @@ __global__ void k_aff_table(int n1, int n2, int n3, HorizonDev hz, int nc, int d
     for (int v = 0; v < nc * dim; ++v) tab[k * nc * dim + v] = (T)acc[v];
 }
 
+// Nonlinear bond model, per boundary entry: S(a_j, chi) = Σ_H a_j(xi) dV chi(x+xi)
+// and S(c, chi) - c^(0) chi = Σ_H c(xi) dV (chi(x+xi) - 1) (both vanish in the
+// delta-interior: a is odd, and there every chi(x+xi) = 1)
+template <typename T>
+__global__ void k_nl_bfields(int n1, int n2, int n3, HorizonDev hz, int dim, const uint8_t *chi,
+                             const GEntry<double> *gent, int64_t ngent, T *out)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ngent) return;
+    const int64_t p = gent[k].p;
+    int i1, i2, i3;
+    node_coords(p, n1, n2, i1, i2, i3);
+    double sa[3] = {0, 0, 0}, sc = 0.0;
+    for (int c = 0; c < hz.cnt; ++c) {
+        const int a = (i1 + hz.off[3 * c]) & (n1 - 1), b = (i2 + hz.off[3 * c + 1]) & (n2 - 1),
+                  e = (i3 + hz.off[3 * c + 2]) & (n3 - 1);
+        if (chi[((int64_t)e * n2 + b) * n1 + a]) {
+            for (int j = 0; j < dim; ++j) sa[j] += hz.g[j * hz.cnt + c];
+        } else {
+            sc -= hz.cs[c];
+        }
+    }
+    for (int j = 0; j < 3; ++j) out[4 * k + j] = (T)sa[j];
+    out[4 * k + 3] = (T)sc;
+}
+
 template <typename Tout>
 __global__ void k_convert(const double *in, Tout *out, int64_t n)
 {
@@ -446,7 +475,7 @@ pd_status dalloc(pd_plan *p, P **ptr, size_t bytes)
 
 struct HostHorizon {
     std::vector<int> off;
-    std::vector<double> c, g, w2;
+    std::vector<double> c, g, w2, cs;
     int cnt = 0;
 };
 
@@ -497,6 +526,8 @@ HostHorizon make_horizon(const pd_plan *p, double kc)
     h.c.assign((size_t)nc * h.cnt, 0.0);
     h.g.assign((size_t)3 * h.cnt, 0.0);
     h.w2.assign((size_t)h.cnt, 0.0);
+    h.cs.assign((size_t)h.cnt, 0.0);
+    const bool nl = p->prob.model == PD_NONLIN_BOND;
     static const int ci[6] = {0, 1, 2, 0, 0, 1}, cj[6] = {0, 1, 2, 1, 2, 2};
     static const int ci2[3] = {0, 1, 0}, cj2[3] = {0, 1, 1};
     for (int c = 0; c < h.cnt; ++c) {
@@ -507,8 +538,10 @@ HostHorizon make_horizon(const pd_plan *p, double kc)
             const int a = dim == 3 ? ci[q] : ci2[q], b = dim == 3 ? cj[q] : cj2[q];
             h.c[(size_t)q * h.cnt + c] = kc * x[a] * x[b] / (rr * rr * rr) * w;
         }
-        for (int i = 0; i < 3; ++i) h.g[(size_t)i * h.cnt + c] = x[i] / rr * w;
+        // state-based: g_i = omega xi_i w; nonlinear bond model: a_i = kc xi_i / |xi|^3 w
+        for (int i = 0; i < 3; ++i) h.g[(size_t)i * h.cnt + c] = nl ? kc * x[i] / (rr * rr * rr) * w : x[i] / rr * w;
         h.w2[c] = rr * w;
+        h.cs[c] = kc / (rr * rr * rr) * w;
     }
     return h;
 }
@@ -610,7 +643,7 @@ void pd_plan_destroy(pd_plan *p)
 {
     if (!p) return;
     void *ptrs[] = {p->chi, p->chi_om, p->mbits, p->hoff, p->mhat64, p->mhat32, p->ghat64, p->ghat32, p->G64, p->G32,
-                    p->goff, p->gidx, p->gent64, p->gent32, p->aff_tab, p->aff_coef,
+                    p->goff, p->gidx, p->gent64, p->gent32, p->aff_tab, p->aff_coef, p->chat64, p->chat32, p->nlb,
                     p->qt64, p->m3inv64, p->qt32, p->m3inv32, p->tw64, p->tw32, p->spec32, p->spec64,
                     p->work, p->red};
     for (void *q : ptrs)
@@ -679,6 +712,7 @@ static pd_status affine_setup(pd_plan *p, cudaStream_t st)
         p->aff_emax[k] = k < dim ? (double)std::max(p->aff_c[k], n[k] - 1 - p->aff_c[k]) : 0.0;
     }
     PD_TRY(moments(p->aff_c[0], p->aff_c[1], p->aff_c[2]));
+    p->body_count = mom[0];
     // normal matrix [[S0, Se^T], [Se, See]] and its inverse (Gauss-Jordan, partial pivoting)
     const int M = dim + 1;
     const int sidx[3][3] = {{4, 7, 8}, {7, 5, 9}, {8, 9, 6}};
@@ -739,7 +773,7 @@ static pd_status plan_create_impl(const pd_problem *pr, const uint8_t *chi_B, co
         set_error("dim must be 2 or 3 (got %d)", dim);
         return PD_ERR_ARG;
     }
-    if (pr->model != PD_LIN_BOND && pr->model != PD_LIN_STATE) {
+    if (pr->model != PD_LIN_BOND && pr->model != PD_LIN_STATE && pr->model != PD_NONLIN_BOND) {
         set_error("unknown model %d", pr->model);
         return PD_ERR_ARG;
     }
@@ -798,7 +832,8 @@ static pd_status plan_create_impl(const pd_problem *pr, const uint8_t *chi_B, co
     p->lgl = ilog2(std::max(n1, std::max(n2, n3)));
     p->dV = dim == 3 ? pr->dx[0] * pr->dx[1] * pr->dx[2] : pr->dx[0] * pr->dx[1];
     const double d = pr->delta;
-    if (pr->model == PD_LIN_BOND) {
+    p->nonlinear = pr->model == PD_NONLIN_BOND ? 1 : 0;
+    if (pr->model == PD_LIN_BOND || pr->model == PD_NONLIN_BOND) {
         p->alpha = dim == 2 ? 9.0 * pr->E / (M_PI * d * d * d) : 12.0 * pr->E / (M_PI * d * d * d * d);
         p->ka = 0.0;
         p->m0 = 0.0;
@@ -852,8 +887,8 @@ static pd_status plan_create_impl(const pd_problem *pr, const uint8_t *chi_B, co
     PD_LAUNCH_CHECK();
     // horizon tables on device (one buffer: ints, then doubles)
     int *d_off = nullptr;
-    double *d_c = nullptr, *d_g = nullptr, *d_w2 = nullptr;
-    PD_TRY(dalloc(p, &p->hoff, sizeof(int) * 3 * hz.cnt + sizeof(double) * ((size_t)(nc + 4) * hz.cnt) + 64));
+    double *d_c = nullptr, *d_g = nullptr, *d_w2 = nullptr, *d_cs = nullptr;
+    PD_TRY(dalloc(p, &p->hoff, sizeof(int) * 3 * hz.cnt + sizeof(double) * ((size_t)(nc + 5) * hz.cnt) + 64));
     d_off = p->hoff;
     {
         char *base = (char *)p->hoff;
@@ -861,12 +896,14 @@ static pd_status plan_create_impl(const pd_problem *pr, const uint8_t *chi_B, co
         d_c = (double *)(base + o);
         d_g = d_c + (size_t)nc * hz.cnt;
         d_w2 = d_g + (size_t)3 * hz.cnt;
+        d_cs = d_w2 + (size_t)hz.cnt;
     }
     PD_CUDA_TRY(cudaMemcpyAsync(d_off, hz.off.data(), sizeof(int) * 3 * hz.cnt, cudaMemcpyHostToDevice, st));
     PD_CUDA_TRY(cudaMemcpyAsync(d_c, hz.c.data(), sizeof(double) * nc * hz.cnt, cudaMemcpyHostToDevice, st));
     PD_CUDA_TRY(cudaMemcpyAsync(d_g, hz.g.data(), sizeof(double) * 3 * hz.cnt, cudaMemcpyHostToDevice, st));
     PD_CUDA_TRY(cudaMemcpyAsync(d_w2, hz.w2.data(), sizeof(double) * hz.cnt, cudaMemcpyHostToDevice, st));
-    HorizonDev hd{d_off, d_c, d_g, d_w2, hz.cnt};
+    PD_CUDA_TRY(cudaMemcpyAsync(d_cs, hz.cs.data(), sizeof(double) * hz.cnt, cudaMemcpyHostToDevice, st));
+    HorizonDev hd{d_off, d_c, d_g, d_w2, p->nonlinear ? d_cs : nullptr, hz.cnt};
     p->hdev = hd;
 
     // reduction scratch; the last 64 bytes hold the device status word
@@ -904,15 +941,23 @@ static pd_status plan_create_impl(const pd_problem *pr, const uint8_t *chi_B, co
     const int64_t fs = p->fold_sz;
     PD_TRY(dalloc(p, &p->mhat64, sizeof(double) * nc * fs));
     PD_TRY(dalloc(p, &p->mhat32, sizeof(float) * nc * fs));
-    if (pr->model == PD_LIN_STATE) {
+    if (pr->model == PD_NONLIN_BOND) {
+        PD_TRY(dalloc(p, &p->chat64, sizeof(double) * fs));
+        PD_TRY(dalloc(p, &p->chat32, sizeof(float) * fs));
+    }
+    if (pr->model == PD_LIN_STATE || pr->model == PD_NONLIN_BOND) {
         PD_TRY(dalloc(p, &p->ghat64, sizeof(double) * 3 * fs));
         PD_TRY(dalloc(p, &p->ghat32, sizeof(float) * 3 * fs));
     }
     k_fold_tables<<<nblk(fs, 128), 128, 0, st>>>(dim, n1, n2, n3, p->h, hd, nc, 1.0 / (double)N, p->mhat64,
-                                                p->ghat64, fs);
+                                                p->ghat64, fs, p->chat64);
     PD_LAUNCH_CHECK();
     k_convert<float><<<nblk(nc * fs), 256, 0, st>>>(p->mhat64, p->mhat32, nc * fs);
     PD_LAUNCH_CHECK();
+    if (p->chat64) {
+        k_convert<float><<<nblk(fs), 256, 0, st>>>(p->chat64, p->chat32, fs);
+        PD_LAUNCH_CHECK();
+    }
     if (p->ghat64) {
         k_convert<float><<<nblk(3 * fs), 256, 0, st>>>(p->ghat64, p->ghat32, 3 * fs);
         PD_LAUNCH_CHECK();
@@ -970,7 +1015,23 @@ static pd_status plan_create_impl(const pd_problem *pr, const uint8_t *chi_B, co
         PD_LAUNCH_CHECK();
         PD_CUDA_TRY(cudaStreamSynchronize(st));
     }
-    if (pr->model == PD_LIN_BOND) PD_TRY(affine_setup(p, st));
+    if (pr->model == PD_LIN_BOND || pr->model == PD_NONLIN_BOND) PD_TRY(affine_setup(p, st));
+    if (pr->model == PD_NONLIN_BOND) {
+        const int64_t ng = std::max<int64_t>(p->ngent, 1);
+        if (pr->fp64) {
+            PD_TRY(dalloc(p, &p->nlb, sizeof(double) * 4 * ng));
+            k_nl_bfields<double><<<nblk(ng, 128), 128, 0, st>>>(n1, n2, n3, hd, dim, p->chi,
+                                                               (const GEntry<double> *)p->gent64, p->ngent,
+                                                               (double *)p->nlb);
+        } else {
+            PD_TRY(dalloc(p, &p->nlb, sizeof(float) * 4 * ng));
+            k_nl_bfields<float><<<nblk(ng, 128), 128, 0, st>>>(n1, n2, n3, hd, dim, p->chi,
+                                                              (const GEntry<double> *)p->gent64, p->ngent,
+                                                              (float *)p->nlb);
+        }
+        PD_LAUNCH_CHECK();
+        PD_CUDA_TRY(cudaStreamSynchronize(st));
+    }
     if (pr->model == PD_LIN_STATE) {
         PD_TRY(dalloc(p, &p->qt64, sizeof(double) * 3 * N));
         PD_TRY(dalloc(p, &p->m3inv64, sizeof(double) * N));
@@ -1021,11 +1082,13 @@ static pd_status plan_create_impl(const pd_problem *pr, const uint8_t *chi_B, co
     PD_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_fork[1], cudaEventDisableTiming));
 
     // spectra and scratch
+    // the 3D nonlinear bond model's last-axis pass reads 12 and writes 21 spectra (out of place)
+    const int slots = (pr->model == PD_NONLIN_BOND && dim == 3) ? 33 : kMaxSpecFields;
     if (!pr->fp64) {
-        p->spec32_slots = kMaxSpecFields;
+        p->spec32_slots = slots;
         PD_TRY(dalloc(p, &p->spec32, sizeof(float) * (size_t)p->spec32_slots * N));
     }
-    p->spec64_slots = pr->fp64 ? kMaxSpecFields : 8;
+    p->spec64_slots = pr->fp64 ? slots : 8;
     PD_TRY(dalloc(p, &p->spec64, sizeof(double) * (size_t)p->spec64_slots * N));
     {
         const size_t tb = pr->fp64 ? sizeof(double) : sizeof(float);

@@ -49,8 +49,10 @@ struct Model {
 struct HorizonDev {
     const int *off;   // 3 x cnt
     const double *c;  // ncomp x cnt: C_ij(xi) dV
-    const double *g;  // 3 x cnt: g_i(xi) dV = omega xi_i dV (state-based)
+    const double *g;  // 3 x cnt: g_i(xi) dV = omega xi_i dV (state-based), or
+                      // a_i(xi) dV = alpha xi_i / |xi|^3 dV (nonlinear bond model)
     const double *w2; // cnt: omega |xi|^2 dV
+    const double *cs; // cnt: c(xi) dV = alpha / |xi|^3 dV (nonlinear bond model), or null
     int cnt;
 };
 
@@ -133,7 +135,13 @@ struct pd_plan {
     int *hoff = nullptr;           // 3 x hcount integer offsets
     double *mhat64 = nullptr;      // ncomp x fold_sz
     float *mhat32 = nullptr;
-    double *ghat64 = nullptr;      // 3 x fold_sz (state-based)
+    double *ghat64 = nullptr;      // 3 x fold_sz (state-based; nonlinear bond model: the a_i spectrum)
+    double *chat64 = nullptr;      // fold_sz: (c^(k) - c^(0)) / N (nonlinear bond model)
+    float *chat32 = nullptr;
+    void *nlb = nullptr;           // nonlinear bond model: per boundary entry S(a_j, chi) (d values) and
+                                   // S(c, chi) - c^(0) chi (slot 3), [ngent][4] in the plan's precision
+    int nonlinear = 0;             // model == PD_NONLIN_BOND
+    double body_count = 0.0;       // Σ chi
     float *ghat32 = nullptr;
     int64_t fold_sz = 0;
     double *G64 = nullptr;         // ncomp x N
@@ -281,7 +289,7 @@ inline void col_cfg(const pd_plan *p, int axis, bool last, int FB, int FI, int N
     auto smem_of = [&](int w, int mir, int tc) {
         const size_t tab = (((size_t)NTAB * (L / 2 + 1) * tc + 1) & ~(size_t)1) * sizeof(T);
         return (size_t)L * sizeof(cx<T>) + (size_t)FB * L * w * sizeof(cx<T>) +
-               (mir ? (size_t)FI * L * 2 * sizeof(cx<T>) : 0) + tab + 16;
+               (mir ? (size_t)FB * L * 2 * sizeof(cx<T>) : 0) + tab + 16;
     };
     int w = p->tune_w[last ? 1 : 0] > 0 ? p->tune_w[last ? 1 : 0] : 32;
     while (w > 2 && ((w + wmirror) * nt > 512 || smem_of(w, wmirror, w + 1) > 100 * 1024 || (H % w))) w >>= 1;

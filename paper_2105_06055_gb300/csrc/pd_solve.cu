@@ -557,6 +557,10 @@ extern "C" pd_status pd_solve_static(pd_plan *p, double *u, const double *b, con
         set_error("pd_solve_static: rtol must be > 0 and max_iter >= 1");
         return PD_ERR_ARG;
     }
+    if (p->nonlinear) {
+        set_error("pd_solve_static: the nonlinear bond model is available through pd_force only");
+        return PD_ERR_ARG;
+    }
     // The solve runs on the plan's own stream (CUDA graphs cannot be captured
     // on the legacy default stream), ordered after the caller's stream.
     cudaStream_t caller = (cudaStream_t)stream;

@@ -29,6 +29,8 @@ extern "C" int pd_batch_size(const pd_batch *B);
 
 namespace pd {
 pd_status time_cg_chunk(pd_plan *p, cudaEvent_t e0, cudaEvent_t e1, float *ms_out);
+template <typename T>
+pd_status force_nl(pd_plan *p, const T *u, T *L, cudaStream_t st);
 }
 
 namespace {
@@ -48,11 +50,12 @@ pd_status time_force(pd_plan *p, cudaEvent_t e0, cudaEvent_t e1, float *ms_out)
     cudaStream_t st = p->own_stream;
     const T *u = (const T *)p->cg_e;
     T *L = (T *)p->cg_q;
-    for (int k = 0; k < 3; ++k) PD_TRY(force_plain<T>(p, u, nullptr, L, nullptr, st));
+    auto eval = [&]() { return p->nonlinear ? force_nl<T>(p, u, L, st) : force_plain<T>(p, u, nullptr, L, nullptr, st); };
+    for (int k = 0; k < 3; ++k) PD_TRY(eval());
     std::vector<float> t;
     for (int k = 0; k < 9; ++k) {
         PD_CUDA_TRY(cudaEventRecord(e0, st));
-        PD_TRY(force_plain<T>(p, u, nullptr, L, nullptr, st));
+        PD_TRY(eval());
         PD_CUDA_TRY(cudaEventRecord(e1, st));
         PD_CUDA_TRY(cudaEventSynchronize(e1));
         float ms = 0.f;
@@ -161,6 +164,11 @@ extern "C" pd_status pd_plan_autotune_solve(pd_plan *p, void *stream)
         set_error("pd_plan_autotune_solve: null plan");
         return PD_ERR_ARG;
     }
+    if (p->nonlinear) {
+        set_error("pd_plan_autotune_solve: the nonlinear bond model is available through pd_force only");
+        return PD_ERR_ARG;
+    }
+
     return tune_plan(p, (cudaStream_t)stream, 1);
 }
 

@@ -250,8 +250,8 @@ static pd_status verlet_entry(pd_plan *p, void *u, void *v, uint8_t *lambda, con
         set_error("%s: dt and rho must be positive, nsteps >= 0, t0 finite", who);
         return PD_ERR_ARG;
     }
-    if (p->state_based) {
-        set_error("%s: the dynamic driver uses the bond model", who);
+    if (p->state_based || p->nonlinear) {
+        set_error("%s: the dynamic driver uses the linearized bond model", who);
         return PD_ERR_ARG;
     }
     cudaStream_t st = (cudaStream_t)stream;

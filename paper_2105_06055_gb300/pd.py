@@ -20,6 +20,7 @@ _lib = None
 
 PD_LIN_BOND = 0
 PD_LIN_STATE = 1
+PD_NONLIN_BOND = 2
 
 STATUS = {0: "PD_OK", -1: "PD_ERR_ARG", -2: "PD_ERR_SIZE", -3: "PD_ERR_NOMEM", -4: "PD_ERR_CUDA",
           -5: "PD_ERR_NOT_CONVERGED", -6: "PD_ERR_TIMEOUT", -7: "PD_ERR_NONFINITE"}
