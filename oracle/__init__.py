@@ -77,6 +77,7 @@ def _load():
             lib.or_horizon.restype = I
             lib.or_force_bond.argtypes = [I, P, P, D, D, P, P, P, P]
             lib.or_energy_bond.argtypes = [I, P, P, D, D, P, P, P, P]
+            lib.or_energy_bond_w.argtypes = [I, P, P, D, D, P, P, P, P]
             lib.or_force_nl.argtypes = [I, P, P, D, D, P, P, P, P]
             lib.or_energy_nl.argtypes = [I, P, P, D, D, P, P, P, P]
             lib.or_force_bond_at.argtypes = [I, P, P, D, D, P, P, P, ctypes.c_int64, P]
@@ -240,13 +241,19 @@ def force_bond_at(u, chi, dx, delta, alpha, nodes):
     return L
 
 
-def energy_bond(u, chi, dx, delta, alpha, lam=None):
-    """W = 1/2 chi lam Σ chi' lam' eta.C.eta dV (Eq. 47, 102)."""
+def energy_bond(u, chi, dx, delta, alpha, lam=None, s=None):
+    """W = 1/2 chi lam Σ chi' lam' eta.C.eta dV (Eq. 47, 102); with a real node
+    weight s the bond factor is (s lam)(s' lam') (reading R17)."""
     chi = _u8(chi)
     dim, n = _grid(chi.shape)
     u = _f64(u)
-    lam = None if lam is None else _u8(lam)
     W = np.empty(chi.shape, dtype=np.float64)
+    if s is not None:
+        w = _f64(s) * (1.0 if lam is None else _u8(lam).astype(np.float64))
+        _load().or_energy_bond_w(dim, _p(n), _p(_dx(dim, dx)), float(delta), float(alpha),
+                                 _p(chi), _p(np.ascontiguousarray(w)), _p(u), _p(W))
+        return W
+    lam = None if lam is None else _u8(lam)
     _load().or_energy_bond(dim, _p(n), _p(_dx(dim, dx)), float(delta), float(alpha),
                            _p(chi), _p(lam), _p(u), _p(W))
     return W
@@ -334,7 +341,7 @@ def symbol_bond(shape, dx, delta, alpha, k):
 # Drivers in the paper's order
 # ----------------------------------------------------------------------------
 
-def verlet_damage(u, v, lam, chi, chi_omega, b, w, dx, delta, alpha, rho, dt, wc, nsteps):
+def verlet_damage(u, v, lam, chi, chi_omega, b, w, dx, delta, alpha, rho, dt, wc, nsteps, s=None, b0=None):
     """Velocity-Verlet with embedded constraint and energy-based bond breaking.
 
     Order per step n -> n+1 (Eq. 83-84 for the kinematics, Eq. 63 and reading R8
@@ -348,6 +355,9 @@ def verlet_damage(u, v, lam, chi, chi_omega, b, w, dx, delta, alpha, rho, dt, wc
     time-varying volume constraint w may instead be a function of the step
     index giving the prescribed field at the end of that step: u^{n+1} takes
     w(n + 1) on Gamma (t = (n + 1) dt).
+    With a node weight s (a spatially varying micromodulus c = c0 s^2, reading
+    R17) the bond factor in L and W is (s lam)(s' lam'). b0, if given, is an
+    extra body force in a^0 only (an impulse on the first step).
     Returns (u, v, lam, flips) with flips = nodes whose lam went 1 -> 0.
     """
     u = _f64(u).copy()
@@ -356,17 +366,25 @@ def verlet_damage(u, v, lam, chi, chi_omega, b, w, dx, delta, alpha, rho, dt, wc
     co = np.asarray(chi_omega, dtype=np.float64)
     b = _f64(b)
     w_at = w if callable(w) else (lambda n, w0=_f64(w): w0)
-    L = force_bond(u, chi, dx, delta, alpha, s=lam.astype(np.float64))
-    W = energy_bond(u, chi, dx, delta, alpha, lam=lam)
+    sw = np.ones(chi.shape) if s is None else _f64(s)
+
+    def force_energy(u, lam):
+        L = force_bond(u, chi, dx, delta, alpha, s=sw * lam.astype(np.float64))
+        W = energy_bond(u, chi, dx, delta, alpha, lam=lam) if s is None else \
+            energy_bond(u, chi, dx, delta, alpha, lam=lam, s=sw)
+        return L, W
+
+    L, W = force_energy(u, lam)
     flips = 0
     for n in range(nsteps):
         a0 = L + b
+        if n == 0 and b0 is not None:
+            a0 = a0 + _f64(b0)
         u = co * (u + dt * (v + dt / (2.0 * rho) * a0)) + (1.0 - co) * _f64(w_at(n + 1))
         new_lam = (lam.astype(bool) & (W <= wc)).astype(np.uint8)
         flips += int(np.sum(lam.astype(np.int64) - new_lam.astype(np.int64)))
         lam = new_lam
-        L = force_bond(u, chi, dx, delta, alpha, s=lam.astype(np.float64))
-        W = energy_bond(u, chi, dx, delta, alpha, lam=lam)
+        L, W = force_energy(u, lam)
         v = co * (v + dt / (2.0 * rho) * (a0 + L + b))
     return u, v, lam, flips
 
@@ -496,13 +514,15 @@ PINS = {
     "force_bond": "translation/rotation null space, affine interior, symbol, reciprocity, "
                   "all-pairs brute force, dense operator spectrum",
     "force_bond_at": "all-pairs brute force at sampled nodes (3D); equals force_bond at those nodes",
-    "energy_bond": "energy identity Σ W dV = -<u, L u> dV; isotropic-stretch closed form",
+    "energy_bond": "energy identity Σ W dV = -<u, L u> dV (also with a real node weight s); isotropic-stretch "
+                   "closed form; all-pairs brute force with the weight s s'",
     "damage": "integer counts vs brute force; intact body d = 0",
     "force_lps": "translation/rotation null space, affine 2-delta interior, dilatation of "
                  "isotropic stretch = 3 s, nu = 1/4 reduces to bond form, reciprocity",
     "force_bond_grad_s": "central finite differences of force_bond",
     "symbol_bond": "single-mode displacement through force_bond",
-    "verlet_damage": "energy conservation without damage, time reversibility",
+    "verlet_damage": "energy conservation without damage (also with a node weight s), time reversibility, "
+                     "s = 1 reduces to the unweighted driver, a first-step impulse equals an initial velocity",
     "cg_static": "FP64 residual of the returned solution",
     "force_nonlinear": "finite rigid rotations give zero force (the linearized model does not), small-"
                        "displacement limit = force_bond, -grad of the total energy, total force zero, all-pairs "

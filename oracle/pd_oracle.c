@@ -267,6 +267,39 @@ void or_energy_bond(int dim, const int *n, const double *dx, double delta, doubl
 }
 
 /*
+ * W of Eq. 47 with a real node weight s in place of the integrity index
+ * (bond factor s s' instead of lam lam', Eq. 44; reading R17 for a spatially
+ * varying micromodulus c = c0 s^2):
+ *   W(x) = 1/2 chi s Σ_xi chi' s' eta.C(xi).eta dV.
+ */
+void or_energy_bond_w(int dim, const int *n, const double *dx, double delta, double alpha,
+                      const uint8_t *chi, const double *s, const double *u, double *W)
+{
+    horizon_t h;
+    build_horizon(dim, dx, delta, &h);
+    const int64_t N = (int64_t)n[0] * n[1] * n[2];
+    const double dV = dvol(dim, dx);
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < N; ++p) {
+        int i1 = (int)(p % n[0]), i2 = (int)((p / n[0]) % n[1]), i3 = (int)(p / ((int64_t)n[0] * n[1]));
+        double acc = 0.0;
+        if (chi[p]) {
+            for (int c = 0; c < h.cnt; ++c) {
+                int64_t q = wrap_index(n, i1, i2, i3, &h.o[3 * c]);
+                if (!chi[q]) continue;
+                const double *xi = &h.xi[3 * c];
+                double r = h.len[c];
+                double xe = 0.0;
+                for (int j = 0; j < dim; ++j) xe += xi[j] * (u[j * N + q] - u[j * N + p]);
+                acc += s[q] * alpha * (1.0 / r) / (r * r) * h.vol[c] * xe * xe;
+            }
+        }
+        W[p] = 0.5 * s[p] * acc * dV;
+    }
+    free_horizon(&h);
+}
+
+/*
  * Nonlinear, rotation-invariant bond model (§3.2, Eq. 19-22) with the
  * embedded-constraint cut (Eq. 75) and a bond factor lam lam' (Eq. 44):
  *   f(xi, eta) = alpha omega |xi| (s + 3/2 s^2 + 1/2 s^3) (xi + eta)/|xi + eta|,

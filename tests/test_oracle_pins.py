@@ -670,3 +670,89 @@ def test_mirror_constraints_reproduce_a_uniform_stretch(oracle):
             wn[c][gam[c]] = 2 * g[c][gam[c]] - ff[c][mir[c][gam[c]]]
         w = 0.5 * (w + wn)
     assert np.max(np.abs(uf - u)) < 1e-8 * np.max(np.abs(u))
+
+
+# --------------------------------------------------------------------------
+# Node weight s (spatially varying micromodulus, reading R17) in W and Verlet
+# --------------------------------------------------------------------------
+
+def test_weighted_energy_identity_and_reductions(oracle):
+    """With the bond factor (s lam)(s' lam'): Σ_x W(x) = -Σ_x u.L(x) (the R9
+    identity with weights), s = lam as reals reproduces the lam form exactly,
+    and a constant s = k scales W by k^2."""
+    shape = (26, 30)
+    chi = _blob(shape, 5)
+    g = inputs.rng(31)
+    lam = (g.random(shape) < 0.9).astype(np.uint8)
+    s = 0.5 + g.random(shape)
+    u = g.normal(size=(2,) + shape)
+    delta = 3.0
+    alpha = oracle.alpha_bond(2, 1.0, delta)
+    W = oracle.energy_bond(u, chi, 1.0, delta, alpha, lam=lam, s=s)
+    L = oracle.force_bond(u, chi, 1.0, delta, alpha, s=s * lam)
+    assert abs(W.sum() + np.sum(u * L)) < 1e-12 * W.sum()
+    W0 = oracle.energy_bond(u, chi, 1.0, delta, alpha, lam=lam)
+    assert np.array_equal(oracle.energy_bond(u, chi, 1.0, delta, alpha, s=lam.astype(float)), W0)
+    assert np.allclose(oracle.energy_bond(u, chi, 1.0, delta, alpha, lam=lam, s=np.full(shape, 1.5)), 2.25 * W0,
+                       rtol=1e-13, atol=0)
+
+
+def test_weighted_energy_brute_force(oracle):
+    """All-pairs sum over minimum-image offsets, written from Eq. 47 with the bond factor s s'."""
+    shape = (9, 11)
+    g = inputs.rng(33)
+    chi = (g.random(shape) < 0.85).astype(np.uint8)
+    s = 0.3 + g.random(shape)
+    u = g.normal(size=(2,) + shape)
+    delta, alpha = 2.6, 0.7
+    W = oracle.energy_bond(u, chi, 1.0, delta, alpha, s=s)
+    n2, n1 = shape
+    ref = np.zeros(shape)
+    for a2 in range(n2):
+        for a1 in range(n1):
+            if not chi[a2, a1]:
+                continue
+            for b2 in range(n2):
+                for b1 in range(n1):
+                    d1 = (b1 - a1 + n1 // 2) % n1 - n1 // 2
+                    d2 = (b2 - a2 + n2 // 2) % n2 - n2 // 2
+                    r = math.hypot(d1, d2)
+                    if r == 0 or r > delta or not chi[b2, b1]:
+                        continue
+                    eta = u[:, b2, b1] - u[:, a2, a1]
+                    ref[a2, a1] += 0.5 * s[a2, a1] * s[b2, b1] * alpha / r ** 3 * (d1 * eta[0] + d2 * eta[1]) ** 2
+    assert np.max(np.abs(W - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_weighted_verlet_reduces_and_conserves_energy(oracle):
+    """s = 1 reproduces the unweighted driver bit for bit; with a varying s
+    and no breaking, 1/2 Σ rho v^2 + 1/2 Σ W(s) is conserved to O(dt^2); an
+    impulse b0 acts on the first step only (equal to starting from v0 = dt b0 / 2 rho)."""
+    shape = (24, 24)
+    chi = inputs.box_mask(shape, (4, 4), (20, 20))
+    delta, rho = 3.0, 1.0
+    alpha = oracle.alpha_bond(2, 1.0, delta)
+    co = np.stack([chi, chi])
+    u0 = inputs.sine_modes(shape, 3, 1e-3, 2, 5) * chi
+    z = np.zeros_like(u0)
+    s = inputs.smooth_positive_field(shape, 4) ** 0.5
+    M = oracle.symbol_bond(shape, 1.0, delta, alpha, (12, 12))
+    dt = 0.2 * 2 * math.sqrt(rho / (1.44 * np.linalg.eigvalsh(M).max()))
+    a = oracle.verlet_damage(u0, z, chi, chi, co, z, z, 1.0, delta, alpha, rho, dt, 1e300, 10)
+    b = oracle.verlet_damage(u0, z, chi, chi, co, z, z, 1.0, delta, alpha, rho, dt, 1e300, 10, s=np.ones(shape))
+    assert all(np.array_equal(x, y) for x, y in zip(a[:3], b[:3]))
+
+    def energy(u, v):
+        return 0.5 * rho * np.sum(v * v) + 0.5 * oracle.energy_bond(u, chi, 1.0, delta, alpha, s=s).sum()
+
+    e0 = energy(u0, z)
+    errs = []
+    for k in (1, 2):
+        uk, vk, _, _ = oracle.verlet_damage(u0, z, chi, chi, co, z, z, 1.0, delta, alpha, rho, dt / k, 1e300, 40 * k,
+                                            s=s)
+        errs.append(abs(energy(uk, vk) / e0 - 1))
+    assert errs[0] < 1e-2 and 3.0 < errs[0] / errs[1] < 5.0
+    imp = inputs.gaussian_impulse(shape, 3.0, 2) * chi
+    c1 = oracle.verlet_damage(z, z, chi, chi, co, z, z, 1.0, delta, alpha, rho, dt, 1e300, 5, s=s, b0=imp)
+    c2 = oracle.verlet_damage(z, dt / (2 * rho) * imp, chi, chi, co, z, z, 1.0, delta, alpha, rho, dt, 1e300, 5, s=s)
+    assert np.allclose(c1[0], c2[0], rtol=1e-12, atol=1e-18)
