@@ -334,6 +334,37 @@ pd_status pd_force_adjoint(pd_plan *plan, const void *u, const void *s, const vo
                            void *gu, void *gs, void *stream);
 
 /*
+ * pd_verlet_loss_grad -- differentiable FCBM-EC dynamics with bond breaking:
+ * a loss on the final state of velocity Verlet (Eq. 83-84 with w = 0) and its
+ * gradient with respect to a spatially varying micromodulus c(x). The paper
+ * has no adjoint; this differentiates the same discrete dynamics.
+ * Dynamics: bond model with bond factor (s lam)(s' lam'), s = sqrt(c_rel)
+ * (c = c_rel times the plan's micromodulus), energy-based breaking of Eq. 63
+ * when the plan has Wc > 0 (W of Eq. 47 with the same bond factor);
+ *   a^n = L(u^n) + b [+ b0 at n = 0],  v^h = v^n + dt/(2 rho) a^n,
+ *   u^{n+1} = chi_O (u^n + dt v^h),  lam^{n+1} = lam^n [W^n <= Wc],
+ *   v^{n+1} = chi_O (v^h + dt/(2 rho) a^{n+1}),   n = 0 .. nsteps - 1;
+ * loss J = Σ_nodes,components (u^N - u_target)^2.
+ * Gradient: dJ/dc_rel with the breaking history held fixed (the decisions
+ * are piecewise constant in c: this is the derivative wherever none of them
+ * changes), by a reverse sweep of adjoint force passes (pd_force_adjoint's)
+ * over states recomputed from checkpoints of (u, v, lam) every
+ * checkpoint_every steps.
+ * c_rel: device N (> 0, else PD_ERR_ARG). lambda0: device N bytes or NULL (1).
+ * u0, v0, b, b0: device d x N or NULL (0). u_target: device d x N.
+ * work: device, at least pd_verlet_adjoint_workspace(plan, nsteps,
+ *   checkpoint_every) bytes, 256-byte aligned; the caller owns it.
+ * loss_out: host (may be NULL). grad_c: device N or NULL (no reverse sweep).
+ * u_final (device d x N) and lambda_final (device N) may be NULL.
+ * Plan precision for every field. Synchronises the stream.
+ */
+int64_t pd_verlet_adjoint_workspace(const pd_plan *plan, int nsteps, int checkpoint_every);
+pd_status pd_verlet_loss_grad(pd_plan *plan, const void *c_rel, const uint8_t *lambda0, const void *u0,
+                              const void *v0, const void *b, const void *b0, const void *u_target, double dt,
+                              int nsteps, int checkpoint_every, void *work, int64_t work_bytes, double *loss_out,
+                              void *grad_c, void *u_final, uint8_t *lambda_final, void *stream);
+
+/*
  * pd_damage -- broken-bond counts and damage index (Eq. 12, 44, 48-49, 65):
  *   beta(x) = chi Σ_H chi',  nb(x) = chi Σ_H chi' (1 - lam lam'),  d = nb / beta.
  * Counts are exact integers (direct integer sums over the horizon).

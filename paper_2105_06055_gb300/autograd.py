@@ -1,24 +1,24 @@
-"""PyTorch autograd over the C ABI: the weighted bond force and its adjoint.
+"""PyTorch autograd over the C ABI: the weighted bond force and its adjoint,
+and the loss of a dynamic run with its micromodulus gradient.
 
 ``PDForce`` wraps ``pd_force`` (forward) and ``pd_force_adjoint`` (backward) of a
 plan, so any torch computation built from force evaluations differentiates
 through the library's kernels: the backward of L = F(u, s) is one fused
 FFT-convolution pass that returns both (dL/du)^T gL and (dL/ds)^T gL.
 
-``verlet_loss`` is the inverse-problem driver: velocity-Verlet dynamics
-(Eq. 67; with chi_Omega = chi_B and w = 0 the EC update of Eq. 83-84 reduces to
-it) under a spatially varying micromodulus c(x) = c0 s(x)^2 (bond factor
-s s' = sqrt(c c')/c0), and a loss on the final displacement. Gradients with
-respect to c go through ``PDForce``; activations are recomputed per segment of
-``checkpoint_every`` steps (torch.utils.checkpoint), so memory holds one
-(u, v) pair per segment instead of one per step.
+``verlet_loss`` is the inverse-problem driver: ``pd_verlet_loss_grad`` runs the
+velocity-Verlet dynamics (Eq. 83-84 with w = 0) under a spatially varying
+micromodulus c(x) (bond factor s s' with s = sqrt(c), c relative to the plan's
+micromodulus; with bond breaking when the plan has a critical energy), the
+loss ||u(T) - u_target||^2, and, in the same call, the reverse sweep over
+states recomputed from checkpoints every ``checkpoint_every`` steps. The
+function here only marshals the tensors; every step runs in the library.
 """
 from __future__ import annotations
 
 from typing import Optional
 
 import torch
-from torch.utils.checkpoint import checkpoint
 
 from . import pd as _pd
 
@@ -58,35 +58,32 @@ def pd_force(plan: "_pd.Plan", u: torch.Tensor, s: Optional[torch.Tensor] = None
     return PDForce.apply(u, s, plan)
 
 
-def verlet_loss(plan: "_pd.Plan", c: torch.Tensor, u_target: torch.Tensor, impulse: torch.Tensor, dt: float,
-                nsteps: int, rho: float = 1.0, c0: float = 1.0, checkpoint_every: int = 10) -> torch.Tensor:
+class VerletLoss(torch.autograd.Function):
+    """J = pd_verlet_loss_grad(plan, c, ...); dJ/dc from the same call."""
+
+    @staticmethod
+    def forward(ctx, c: torch.Tensor, plan: "_pd.Plan", u_target: torch.Tensor, impulse: Optional[torch.Tensor],
+                b: Optional[torch.Tensor], lam0: Optional[torch.Tensor], dt: float, nsteps: int,
+                checkpoint_every: int):
+        loss, grad = plan.verlet_loss_grad(c.contiguous(), u_target.contiguous(), dt, nsteps,
+                                           checkpoint_every=checkpoint_every, lam0=lam0, b=b, b0=impulse,
+                                           want_grad=ctx.needs_input_grad[0])
+        ctx.save_for_backward(grad if grad is not None else torch.empty(0, device=c.device))
+        return torch.tensor(loss, dtype=c.dtype, device=c.device)
+
+    @staticmethod
+    def backward(ctx, gJ: torch.Tensor):
+        (grad,) = ctx.saved_tensors
+        return grad * gJ, None, None, None, None, None, None, None, None
+
+
+def verlet_loss(plan: "_pd.Plan", c: torch.Tensor, u_target: torch.Tensor, impulse: Optional[torch.Tensor],
+                dt: float, nsteps: int, checkpoint_every: int = 10, b: Optional[torch.Tensor] = None,
+                lam0: Optional[torch.Tensor] = None) -> torch.Tensor:
     """Loss ||u(T) - u_target||^2 after nsteps of velocity Verlet from rest.
 
-    The body force is ``impulse`` on the first step and zero afterwards. The
-    micromodulus field enters as the node weight s = sqrt(c / c0).
-    """
-    s = torch.sqrt(c / c0)
-    u = torch.zeros_like(u_target)
-    v = torch.zeros_like(u_target)
-    h = dt / (2.0 * rho)
-
-    def segment(u, v, s, k0, k1):
-        a = pd_force(plan, u, s)
-        if k0 == 0:
-            a = a + impulse
-        for k in range(k0, k1):
-            v = v + h * a
-            u = u + dt * v
-            a = pd_force(plan, u, s)
-            v = v + h * a
-        return u, v
-
-    k = 0
-    while k < nsteps:
-        k1 = min(nsteps, k + checkpoint_every)
-        if checkpoint_every > 0 and torch.is_grad_enabled():
-            u, v = checkpoint(segment, u, v, s, k, k1, use_reentrant=False)
-        else:
-            u, v = segment(u, v, s, k, k1)
-        k = k1
-    return ((u - u_target) ** 2).sum()
+    ``impulse`` is a body force on the first step only, ``b`` a constant one;
+    c is the micromodulus field relative to the plan's (bond factor
+    sqrt(c c')); ``lam0`` an initial integrity index (bond breaking follows the
+    plan's critical energy density)."""
+    return VerletLoss.apply(c, plan, u_target, impulse, b, lam0, dt, nsteps, checkpoint_every)

@@ -189,6 +189,21 @@ pd_status adjoint_any(pd_plan *p, const T *u, const T *s, const T *pv, T *gu, T 
 }
 
 }  // namespace
+
+// The adjoint passes for node weight s with its boundary field G given (the
+// dynamic adjoint keeps G current as the integrity index changes).
+template <typename T>
+pd_status adjoint_weighted(pd_plan *p, const T *u, const T *s, const T *pv, const T *G, T *gu, T *gs,
+                           cudaStream_t st)
+{
+    if (p->dim == 2) return adjoint_pipeline<T, 2>(p, u, s, pv, G, gu, gs, st);
+    return adjoint_pipeline<T, 3>(p, u, s, pv, G, gu, gs, st);
+}
+template pd_status adjoint_weighted<float>(pd_plan *, const float *, const float *, const float *, const float *,
+                                           float *, float *, cudaStream_t);
+template pd_status adjoint_weighted<double>(pd_plan *, const double *, const double *, const double *,
+                                            const double *, double *, double *, cudaStream_t);
+
 }  // namespace pd
 
 using namespace pd;

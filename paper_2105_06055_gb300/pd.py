@@ -32,7 +32,8 @@ EXPORTS = ["pd_plan_create", "pd_plan_destroy", "pd_kernel_spectrum", "pd_force"
            "pd_solve_dr", "pd_plan_create_batched", "pd_batch_size", "pd_batch_plan", "pd_solve_dr_batched",
            "pd_batch_destroy", "pd_plan_autotune", "pd_batch_autotune", "pd_plan_tuning",
            "pd_plan_set_energy_mode", "pd_plan_set_tuning", "pd_plan_autotune_solve", "pd_plan_critical_energy",
-           "pd_plan_inject_stall", "pd_plan_set_affine_split", "pd_step_verlet_ramp"]
+           "pd_plan_inject_stall", "pd_plan_set_affine_split", "pd_step_verlet_ramp",
+           "pd_verlet_adjoint_workspace", "pd_verlet_loss_grad"]
 
 PASS_KINDS = {0: "rows_fwd", 1: "cols_x2", 2: "last_axis", 3: "rows_inv"}
 
@@ -74,6 +75,10 @@ def load():
     lib.pd_step_verlet.restype = I
     lib.pd_step_verlet_ramp.argtypes = [P, P, P, P, P, P, P, D, D, I, ctypes.POINTER(I64), P]
     lib.pd_step_verlet_ramp.restype = I
+    lib.pd_verlet_adjoint_workspace.argtypes = [P, I, I]
+    lib.pd_verlet_adjoint_workspace.restype = I64
+    lib.pd_verlet_loss_grad.argtypes = [P, P, P, P, P, P, P, P, D, I, I, P, I64, ctypes.POINTER(D), P, P, P, P]
+    lib.pd_verlet_loss_grad.restype = I
     lib.pd_solve_static.argtypes = [P, P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D), P]
     lib.pd_solve_static.restype = I
     lib.pd_force_adjoint.argtypes = [P, P, P, P, P, P, P]
@@ -305,6 +310,34 @@ class Plan:
                                           ctypes.byref(nb) if count_broken else None, _stream(stream)),
                "pd_step_verlet_ramp")
         return int(nb.value) if count_broken else None
+
+    def verlet_loss_grad(self, c_rel, u_target, dt, nsteps, checkpoint_every=10, lam0=None, u0=None, v0=None,
+                         b=None, b0=None, want_grad=True, want_final=False, stream=None):
+        """pd_verlet_loss_grad: returns (loss, grad_c or None[, u_final, lambda_final])."""
+        lib = load()
+        c_rel = self._field(c_rel, 0, "c_rel")
+        u_target = self._field(u_target, self.dim, "u_target")
+        u0 = self._field(u0, self.dim, "u0", allow_none=True)
+        v0 = self._field(v0, self.dim, "v0", allow_none=True)
+        b = self._field(b, self.dim, "b", allow_none=True)
+        b0 = self._field(b0, self.dim, "b0", allow_none=True)
+        if lam0 is not None:
+            lam0 = self._field(lam0, 0, "lambda0", dtype=torch.uint8)
+        nbytes = int(lib.pd_verlet_adjoint_workspace(self._h, int(nsteps), int(checkpoint_every)))
+        if nbytes < 0:
+            raise PDError(-1, "pd_verlet_adjoint_workspace")
+        work = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        grad = torch.empty_like(c_rel) if want_grad else None
+        uf = torch.empty_like(u_target) if want_final else None
+        lf = torch.empty(self.shape, dtype=torch.uint8, device=self.device) if want_final else None
+        loss = ctypes.c_double(0.0)
+        _check(lib.pd_verlet_loss_grad(self._h, _ptr(c_rel), _ptr(lam0), _ptr(u0), _ptr(v0), _ptr(b), _ptr(b0),
+                                       _ptr(u_target), float(dt), int(nsteps), int(checkpoint_every), _ptr(work),
+                                       nbytes, ctypes.byref(loss), _ptr(grad), _ptr(uf), _ptr(lf),
+                                       _stream(stream)), "pd_verlet_loss_grad")
+        if want_final:
+            return loss.value, grad, uf, lf
+        return loss.value, grad
 
     def solve_static(self, u, b, w=None, rtol=1e-8, max_iter=20000, stream=None, raise_on_fail=True):
         u = self._field(u, self.dim, "u", dtype=torch.float64)

@@ -75,17 +75,10 @@ def test_verlet_loss_directional_fd(mods):
 
 
 def _final_state(ag, plan, c, imp, dt, nsteps):
-    """u(T) from rest under the weighted force (no autograd)."""
-    s = torch.sqrt(c)
-    u = torch.zeros_like(imp)
-    v = torch.zeros_like(imp)
-    a = ag.pd_force(plan, u, s) + imp
-    for _ in range(nsteps):
-        v = v + 0.5 * dt * a
-        u = u + dt * v
-        a = ag.pd_force(plan, u, s)
-        v = v + 0.5 * dt * a
-    return u
+    """u(T) from rest under the weighted force (the library's dynamics, no gradient)."""
+    _, _, uf, _ = plan.verlet_loss_grad(c, torch.zeros_like(imp), dt, nsteps, b0=imp, want_grad=False,
+                                        want_final=True)
+    return uf
 
 
 def test_verlet_loss_matches_oracle(mods, oracle):
@@ -100,15 +93,9 @@ def test_verlet_loss_matches_oracle(mods, oracle):
     nsteps = 12
 
     def oracle_final(cn):
-        s = np.sqrt(cn)
-        u = np.zeros((3,) + shape)
-        v = np.zeros_like(u)
-        a = oracle.force_bond(u, chi, 1.0, delta, alpha, s=s) + imp.cpu().numpy()
-        for _ in range(nsteps):
-            v = v + 0.5 * dt * a
-            u = u + dt * v
-            a = oracle.force_bond(u, chi, 1.0, delta, alpha, s=s)
-            v = v + 0.5 * dt * a
+        z = np.zeros((3,) + shape)
+        u, _, _, _ = oracle.verlet_damage(z, z, chi, chi, np.stack([chi] * 3), z, z, 1.0, delta, alpha, 1.0, dt,
+                                          1e300, nsteps, s=np.sqrt(cn), b0=imp.cpu().numpy())
         return u
 
     cn, ctn = c.cpu().numpy(), ct.cpu().numpy()
