@@ -256,6 +256,28 @@ pd_status pd_solve_dr(pd_plan *plan, double *u, const double *b, const double *w
                       double rtol, int max_iter, int *iters_out, double *relres_out, void *stream);
 
 /*
+ * pd_solve_mirror -- the static problem of §5.1 with mirror-based volume
+ * constraints instead of the naive ones: every node of Gamma (chi_B = 1,
+ * chi_O = 0 for a component) takes u = 2 g - u(mirror) from the local boundary
+ * value g and the solution at its mirror node inside Omega, while
+ * chi_O (L(u) + b) = 0 holds on Omega (Eq. 89). The paper describes the method
+ * but its appendix is not in the text; this solves the coupled problem at
+ * once: in the Omega values e, u = E e + h with E e = chi_O e - (1 - chi_O)
+ * e(mirror) and h = 2 (1 - chi_O) g, and A e = -chi_O L(E e) = chi_O (L(h) + b)
+ * is solved by BiCGStab (A is not symmetric), one FFT force evaluation per
+ * product, FP64 (FP64 plans only).
+ * u:      device d x N FP64, out: the solution (E e + h).
+ * b, g:   device d x N FP64 or NULL (0); g is read on Gamma.
+ * mirror: device d x N int32: for each component the flat node index of the
+ *         mirror node of a Gamma node (ignored elsewhere); PD_ERR_ARG unless
+ *         every Gamma node has one inside Omega for that component.
+ * Stops when ||r|| <= rtol ||r0||, r0 = chi_O (L(h) + b); relres_out is the
+ * recomputed FP64 residual of u relative to ||r0||. Synchronises the stream.
+ */
+pd_status pd_solve_mirror(pd_plan *plan, double *u, const double *b, const double *g, const int32_t *mirror,
+                          double rtol, int max_iter, int *iters_out, double *relres_out, void *stream);
+
+/*
  * Batched specimens: nspec independent problems (each its own grid, horizon,
  * masks and material) solved together. pd_plan_create_batched creates one plan
  * per specimen (same rules and arguments as pd_plan_create, element i of each

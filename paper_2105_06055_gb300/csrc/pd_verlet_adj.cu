@@ -384,14 +384,17 @@ pd_status loss_grad_impl(pd_plan *p, const T *c_rel, const uint8_t *lam0, const 
             k_adj_scale<T><<<R.ngv, 256, 0, st>>>(R.vbar, R.v, dN, kf);  // R.v: the cotangent k v~
             PD_LAUNCH_CHECK();
             p->launches += 2;
-            // weight and boundary field of lam^n
-            PD_TRY(R.copy(R.lam, R.sg_lam(n - k0), (size_t)N));
-            k_adj_weight<T><<<R.ng, 256, 0, st>>>(R.s, R.lam, R.seff, N);
-            k_adj_flag<<<1, 1, 0, st>>>(R.cnt, 1);
-            k_adj_gfield<T><<<R.nbl, 128, 0, st>>>(p->n1, p->n2, p->n3, p->hdev, p->ncomp, p->chi, R.seff, R.G,
-                                                   N, R.cnt);
-            PD_LAUNCH_CHECK();
-            p->launches += 3;
+            // weight and boundary field of lam^n (without breaking lam never
+            // changes: the ones of the recomputed segment are current)
+            if (R.breaking) {
+                PD_TRY(R.copy(R.lam, R.sg_lam(n - k0), (size_t)N));
+                k_adj_weight<T><<<R.ng, 256, 0, st>>>(R.s, R.lam, R.seff, N);
+                k_adj_flag<<<1, 1, 0, st>>>(R.cnt, 1);
+                k_adj_gfield<T><<<R.nbl, 128, 0, st>>>(p->n1, p->n2, p->n3, p->hdev, p->ncomp, p->chi, R.seff,
+                                                       R.G, N, R.cnt);
+                PD_LAUNCH_CHECK();
+                p->launches += 3;
+            }
             PD_TRY(adjoint_weighted<T>(p, R.sg_u(n - k0), R.seff, R.v, R.G, R.gu, R.gs, st));
             k_adj_acc<T><<<R.ng, 256, 0, st>>>(R.ubar, R.gu, R.sbar, R.gs, R.lam, p->chi_om, p->dim, N);
             PD_LAUNCH_CHECK();

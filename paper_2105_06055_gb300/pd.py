@@ -33,7 +33,7 @@ EXPORTS = ["pd_plan_create", "pd_plan_destroy", "pd_kernel_spectrum", "pd_force"
            "pd_batch_destroy", "pd_plan_autotune", "pd_batch_autotune", "pd_plan_tuning",
            "pd_plan_set_energy_mode", "pd_plan_set_tuning", "pd_plan_autotune_solve", "pd_plan_critical_energy",
            "pd_plan_inject_stall", "pd_plan_set_affine_split", "pd_step_verlet_ramp",
-           "pd_verlet_adjoint_workspace", "pd_verlet_loss_grad"]
+           "pd_verlet_adjoint_workspace", "pd_verlet_loss_grad", "pd_solve_mirror"]
 
 PASS_KINDS = {0: "rows_fwd", 1: "cols_x2", 2: "last_axis", 3: "rows_inv"}
 
@@ -75,6 +75,8 @@ def load():
     lib.pd_step_verlet.restype = I
     lib.pd_step_verlet_ramp.argtypes = [P, P, P, P, P, P, P, D, D, I, ctypes.POINTER(I64), P]
     lib.pd_step_verlet_ramp.restype = I
+    lib.pd_solve_mirror.argtypes = [P, P, P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D), P]
+    lib.pd_solve_mirror.restype = I
     lib.pd_verlet_adjoint_workspace.argtypes = [P, I, I]
     lib.pd_verlet_adjoint_workspace.restype = I64
     lib.pd_verlet_loss_grad.argtypes = [P, P, P, P, P, P, P, P, D, I, I, P, I64, ctypes.POINTER(D), P, P, P, P]
@@ -349,6 +351,20 @@ class Plan:
                                     ctypes.byref(it), ctypes.byref(rr), _stream(stream))
         if st != 0 and (raise_on_fail or st != -5):
             raise PDError(st, "pd_solve_static")
+        return int(it.value), float(rr.value), st
+
+    def solve_mirror(self, u, b, g, mirror, rtol=1e-10, max_iter=20000, stream=None, raise_on_fail=True):
+        """pd_solve_mirror: mirror-based volume constraints (FP64 plans)."""
+        u = self._field(u, self.dim, "u", dtype=torch.float64)
+        b = self._field(b, self.dim, "b", dtype=torch.float64, allow_none=True)
+        g = self._field(g, self.dim, "g", dtype=torch.float64, allow_none=True)
+        mirror = self._field(mirror, self.dim, "mirror", dtype=torch.int32)
+        it = ctypes.c_int(0)
+        rr = ctypes.c_double(0.0)
+        st = load().pd_solve_mirror(self._h, _ptr(u), _ptr(b), _ptr(g), _ptr(mirror), float(rtol), int(max_iter),
+                                    ctypes.byref(it), ctypes.byref(rr), _stream(stream))
+        if st != 0 and (raise_on_fail or st != -5):
+            raise PDError(st, "pd_solve_mirror")
         return int(it.value), float(rr.value), st
 
     def solve_dr(self, u, b, w=None, rtol=1e-8, max_iter=200000, stream=None, raise_on_fail=True):

@@ -319,3 +319,87 @@ def test_verlet_time_varying_constraint_matches_oracle(pdm, oracle, damage):
     if damage:
         assert np.array_equal(lam.cpu().numpy(), lo)
     plan.close()
+
+
+# --------------------------------------------------------------------------
+# Mirror-based volume constraints (§5.1)
+# --------------------------------------------------------------------------
+
+def _mirror_bar(shape, margin2):
+    """Bar along x1 with Gamma layers of three nodes at both ends; mirror planes
+    halfway between the last Gamma and the first Omega layer (component 0 at
+    both ends, the others at the left end only)."""
+    dim = len(shape)
+    n1 = shape[-1]
+    lo = (3,) + (margin2,) * (dim - 1)
+    hi = (n1 - 3,) + tuple(s - margin2 for s in shape[::-1][1:])
+    chi = inputs.box_mask(shape, lo, hi)
+    x = inputs.coords(shape)
+    x1 = x[0]
+    left = (x1 >= 3) & (x1 < 6) & (chi == 1)
+    right = (x1 >= n1 - 6) & (x1 < n1 - 3) & (chi == 1)
+    xl, xr = 5.5, n1 - 6.5
+    co = [chi.copy() for _ in range(dim)]
+    co[0][left | right] = 0
+    for c in range(1, dim):
+        co[c][left] = 0
+    node = np.arange(chi.size, dtype=np.int64).reshape(shape)
+    mir = -np.ones((dim,) + shape, dtype=np.int64)
+    ml = node + (2 * xl - 2 * x1).astype(np.int64)
+    mr = node + (2 * xr - 2 * x1).astype(np.int64)
+    for c in range(dim):
+        mir[c][left] = ml[left]
+    mir[0][right] = mr[right]
+    return chi, np.stack(co), mir, x1, left, right, xl, xr
+
+
+@pytest.mark.parametrize("shape,model,nu", [((32, 64), 0, 0.25), ((16, 16, 32), 0, 0.25),
+                                            ((16, 16, 32), 1, 0.4)])
+def test_mirror_constraints_match_oracle(pdm, oracle, shape, model, nu):
+    """The coupled mirror-constraint solve (BiCGStab over FFT force
+    evaluations) against the oracle's coupled solve (GMRES over its direct
+    sums): displacement to 1e-8, and the mirror relation u = 2 g - u(mirror)
+    on Gamma to rounding."""
+    dim = len(shape)
+    chi, co, mir, x1, left, right, xl, xr = _mirror_bar(shape, 4)
+    eps = 1e-3
+    g = np.zeros((dim,) + shape)
+    g[0][right] = eps * (xr - xl)
+    g[1][left] = 2e-4  # a shear on the left grip
+    b = np.zeros_like(g)
+    b[dim - 1][(chi == 1) & (x1 > 20) & (x1 < 30)] = -1e-5
+    delta = 3.0
+    if model == 0:
+        op = ("bond", oracle.alpha_bond(dim, 1.0, delta))
+    else:
+        ka, cb, _ = oracle.lps_constants(1.0, nu, 1.0, delta)
+        op = ("lps", ka, cb)
+    uo, ito, relo = oracle.static_mirror(chi, co, b, g, mir, 1.0, delta, op, rtol=1e-13)
+    assert relo < 1e-11
+    plan = pdm.Plan(pdm.Problem(shape=shape, delta=delta, model=model, nu=nu, fp64=True), _t(chi, torch.uint8),
+                    _t(co, torch.uint8))
+    u = torch.zeros((dim,) + shape, dtype=torch.float64, device=DEV)
+    it, rel, st = plan.solve_mirror(u, _t(b), _t(g), _t(mir, torch.int32), rtol=1e-12, max_iter=20000)
+    assert st == 0 and rel <= 2e-12 and it > 0
+    ug = u.cpu().numpy()
+    assert _rel(ug, uo) < 1e-8
+    gam = (co == 0) & chi.astype(bool)[None]
+    flat = ug.reshape(dim, -1)
+    for c in range(dim):
+        want = 2 * g[c][gam[c]] - flat[c][mir[c][gam[c]]]
+        assert np.max(np.abs(ug[c][gam[c]] - want)) <= 1e-15 * np.max(np.abs(ug))
+    plan.close()
+
+
+def test_mirror_solve_rejects_bad_mirrors(pdm):
+    shape = (32, 64)
+    chi, co, mir, *_ = _mirror_bar(shape, 4)
+    plan = pdm.Plan(pdm.Problem(shape=shape, delta=3.0, fp64=True), _t(chi, torch.uint8), _t(co, torch.uint8))
+    bad = mir.copy()
+    idx = np.argwhere(co[0] == 0)
+    idx = [tuple(i) for i in idx if chi[tuple(i)] == 1][0]
+    bad[(0,) + idx] = -1
+    u = torch.zeros((2,) + shape, dtype=torch.float64, device=DEV)
+    with pytest.raises(pdm.PDError, match="PD_ERR_ARG"):
+        plan.solve_mirror(u, None, None, _t(bad, torch.int32))
+    plan.close()
