@@ -463,6 +463,45 @@ def run_force(args):
     }
 
 
+def fracture_point(steps=200, warmup=50):
+    """The 2D dynamic-fracture workload (1024 x 512 nodes, delta = 4, pre-notch,
+    traction layers, critical stretch s0 = 1e-3 given to the library, FP32,
+    W by the horizon sum): milliseconds per velocity-Verlet step with bond
+    breaking, timed with CUDA events over `steps` steps after `warmup`."""
+    import torch
+
+    from paper_2105_06055_gb300 import inputs, pd
+
+    dev = torch.device("cuda")
+    cfg = inputs.notched_plate(n1=1024, n2=512, delta=4.0, sigma=1.0)
+    shape = cfg["shape"]
+    plan = pd.Plan(pd.Problem(shape=shape, delta=4.0, rho=1.0, s0=1e-3, nu=1.0 / 3.0, fp64=False),
+                   torch.tensor(cfg["chi"], device=dev))
+    plan.set_energy_mode(True)
+    b = torch.tensor(cfg["b"] * (0.242 * math.sqrt(plan.critical_energy)), dtype=torch.float32, device=dev)
+    u = torch.zeros((2,) + shape, dtype=torch.float32, device=dev)
+    v = torch.zeros_like(u)
+    lam = torch.tensor(cfg["lam"], device=dev)
+    dt = 0.8 * plan.stable_dt
+    plan.step_verlet(u, v, lam, b, None, dt=dt, nsteps=warmup)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = plan.launch_count
+    torch.cuda.synchronize()
+    e0.record(stream)
+    broken = plan.step_verlet(u, v, lam, b, None, dt=dt, nsteps=steps, count_broken=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    N = shape[0] * shape[1]
+    out = {"ms_per_step": ms, "node_steps_per_s": N / (ms * 1e-3), "steps": steps, "after_warmup_steps": warmup,
+           "broken_nodes_in_timed_steps": broken, "launches_per_step": (plan.launch_count - l0) / steps,
+           "workload": "1024x512 pre-notched plate, delta=4, s0=1e-3, FP32, W by horizon sum"}
+    plan.close()
+    return out
+
+
 def run_batched(args):
     import numpy as np
     import torch
@@ -680,6 +719,13 @@ def main():
             sweep[f"{n}^3"] = {k: pt[k] for k in ("ms_per_eval", "node_evals_per_s", "passes",
                                                   "m2_end_to_end_hbm_frac", "tuning")}
         result["force_sweep"] = sweep
+        result["fracture_step"] = fracture_point()
+        # the batched workload (64 uneven 2D specimens, one graph launch per solve), one timed solve
+        bargs = argparse.Namespace(specimens=args.specimens, warmup=1, steps=1)
+        bt = run_batched(bargs)
+        result["batched"] = {k: bt[k] for k in ("value", "unit", "ms_per_step", "relaxation_steps_per_solve",
+                                                "final_rel_residual_max", "autotune_s", "gpu_launches")}
+        result["batched"]["config"] = bt["config"]
     if rank == 0:
         if not args.no_cpu_baseline:
             v, cores, dt = oracle_sample(args.n, 2, min_seconds=2.0)

@@ -336,10 +336,6 @@ struct op_node_acc<Op, std::void_t<decltype(Op::kNodeAcc)>> : std::bool_constant
 template <class Op, class = void>
 struct op_min_blocks : std::integral_constant<int, 1> {
 };
-template <class Op>
-struct op_min_blocks<Op, std::void_t<decltype(Op::kMinBlocks)>> : std::integral_constant<int, Op::kMinBlocks> {
-};
-
 template <typename T, class Op>
 __global__ void __launch_bounds__(256, op_min_blocks<Op>::value) k_rows(RowGeom g, Op op,
                                                                        const cx<T> *__restrict__ tw)

@@ -198,6 +198,11 @@ struct EpiCG {
     static constexpr bool kSparse = false;
     static constexpr int kMinBlocks = 4;  // <= 64 registers: more resident warps
     using Acc = CgAcc;
+    // loads of one node pair: p, r and its boundary-list indices (read-only in this pass)
+    struct EmitIn {
+        typename vec2<T>::type pp[D], rr[D];
+        int2 gi;
+    };
     const T *pv, *r;
     const uint8_t *bits;
     const GEntry<T> *gent;
@@ -223,18 +228,31 @@ struct EpiCG {
         }
     }
     __device__ void sparse(const RowCtx<T> &, int, int) const {}
+    __device__ __forceinline__ void load_emit(const RowCtx<T> &c, int rl, int i1, EmitIn &in) const
+    {
+        using V = typename vec2<T>::type;
+        const int64_t p = (c.row0 + rl) * n1 + i1;
+        in.gi = __ldg(reinterpret_cast<const int2 *>(gidx + p));
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            in.pp[i] = __ldg(reinterpret_cast<const V *>(pv + i * N + p));
+            in.rr[i] = __ldg(reinterpret_cast<const V *>(r + i * N + p));
+        }
+    }
     __device__ __forceinline__ void emit(const RowCtx<T> &c, int rl, int i1, const T *s0, const T *s1,
                                          CgAcc &acc) const
     {
+        EmitIn in;
+        load_emit(c, rl, i1, in);
+        emit_loaded(c, rl, i1, s0, s1, acc, in);
+    }
+    __device__ __forceinline__ void emit_loaded(const RowCtx<T> &c, int rl, int i1, const T *s0, const T *s1,
+                                                CgAcc &acc, const EmitIn &in) const
+    {
         const int64_t p = (c.row0 + rl) * n1 + i1;
         const unsigned b0 = c.b(0, rl, i1), b1 = c.b(0, rl, i1 + 1);
-        const int2 gi = *reinterpret_cast<const int2 *>(gidx + p);
-        typename vec2<T>::type pp[D], rr[D];
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-            pp[i] = load2(pv + i * N + p);
-            rr[i] = load2(r + i * N + p);
-        }
+        const int2 gi = in.gi;
+        const typename vec2<T>::type *pp = in.pp, *rr = in.rr;
         T L0[D], L1[D];
 #pragma unroll
         for (int i = 0; i < D; ++i) {
