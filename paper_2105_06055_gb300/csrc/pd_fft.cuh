@@ -34,8 +34,11 @@
 
 namespace pd {
 
-constexpr int kV = 8;    // complex values per thread and FFT stage
-constexpr int kLgV = 3;  // log2(kV)
+#ifndef PD_FFT_LGV
+#define PD_FFT_LGV 3
+#endif
+constexpr int kLgV = PD_FFT_LGV;  // log2(kV)
+constexpr int kV = 1 << kLgV;     // complex values per thread and FFT stage
 
 __host__ __device__ constexpr int bit_reverse(int i, int bits)
 {
@@ -195,7 +198,7 @@ __device__ __forceinline__ void fft_fields(cx<T> *s, int fstride, int stride, in
 }
 // column passes: grouped sweeps pay for the spectral-combine passes; the plain
 // transforms keep one field per sweep (fewer registers, more resident warps)
-constexpr int kCombFieldGroup = 3;
+constexpr int kCombFieldGroup = kV == 8 ? 3 : 1;
 
 // ---------------------------------------------------------------------------
 // Compensated FP32 accumulation (Knuth two-sum): sums of FP32 products carried
@@ -335,6 +338,9 @@ struct op_node_acc<Op, std::void_t<decltype(Op::kNodeAcc)>> : std::bool_constant
 // compiler must allow, i.e. a register cap of 256 / kMinBlocks per thread).
 template <class Op, class = void>
 struct op_min_blocks : std::integral_constant<int, 1> {
+};
+template <class Op>
+struct op_min_blocks<Op, std::void_t<decltype(Op::kMinBlocks)>> : std::integral_constant<int, Op::kMinBlocks> {
 };
 template <typename T, class Op>
 __global__ void __launch_bounds__(256, op_min_blocks<Op>::value) k_rows(RowGeom g, Op op,

@@ -185,6 +185,8 @@ struct ProCG {
     __device__ void block_done(DSum &acc) const { write_partial(red, acc.value()); }
 };
 
+static_assert(op_min_blocks<ProCG<float, 3>>::value == 1, "ProCG declares no register cap");
+
 struct CgAcc {
     DSum pq, rq, qq;
 };
@@ -309,6 +311,9 @@ struct EpiCG {
         }
     }
 };
+
+static_assert(op_min_blocks<EpiCG<float, 3>>::value == EpiCG<float, 3>::kMinBlocks,
+              "the row kernel must apply the epilogue's register cap");
 
 struct Solver {
     pd_plan *p;
