@@ -172,6 +172,9 @@ __device__ __forceinline__ void fft_smem(cx<T> *s, int fstride, int stride, int 
         const bool first = (lgns == 0), last = (rem == lr);
         const bool ci = cin && first, co = cout && last;
         switch (lr) {
+            case 4:
+                if constexpr (kV >= 16) fft_stage<T, 16, F>(s, fstride, stride, n, ns, lgns + 4, jt, nt, tw, lgl, ci, co);
+                break;
             case 3: fft_stage<T, 8, F>(s, fstride, stride, n, ns, lgns + 3, jt, nt, tw, lgl, ci, co); break;
             case 2: fft_stage<T, 4, F>(s, fstride, stride, n, ns, lgns + 2, jt, nt, tw, lgl, ci, co); break;
             default: fft_stage<T, 2, F>(s, fstride, stride, n, ns, lgns + 1, jt, nt, tw, lgl, ci, co); break;
@@ -201,9 +204,12 @@ __device__ __forceinline__ void fft_fields(cx<T> *s, int fstride, int stride, in
 constexpr int kCombFieldGroup = kV == 8 ? 3 : 1;
 
 // ---------------------------------------------------------------------------
-// Compensated FP32 accumulation (Knuth two-sum): sums of FP32 products carried
-// as an unevaluated pair (hi, lo), accurate to about FP32^2, so reductions run
-// on FP32 units and only the block totals are combined in FP64.
+// Compensated FP32 accumulation (Knuth two-sum): sums carried as an
+// unevaluated pair (hi, lo), accurate to about FP32^2, so reductions run on
+// FP32 units and only the block totals are combined in FP64. Inner products
+// take each FP32 product exactly (the FMA residual a b - fl(a b) is itself a
+// float, the error-free two-product), so a dot product of FP32 vectors is
+// accumulated to about FP64 accuracy without FP64 arithmetic per element.
 // ---------------------------------------------------------------------------
 struct DSum {
     float hi = 0.f, lo = 0.f;
@@ -216,6 +222,14 @@ struct DSum {
         hi = s;
     }
     __device__ __forceinline__ void add(double x) { d += x; }
+    // += a b with the product's rounding error kept
+    __device__ __forceinline__ void add_prod(float a, float b)
+    {
+        const float p = a * b;
+        lo += __fmaf_rn(a, b, -p);
+        add(p);
+    }
+    __device__ __forceinline__ void add_prod(double a, double b) { d += a * b; }
     __device__ __forceinline__ double value() const { return d + (double)hi + (double)lo; }
 };
 

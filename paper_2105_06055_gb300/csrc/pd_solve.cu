@@ -80,7 +80,7 @@ __global__ void k_cg_init(const double *r64, T *r, T *pp, T *e, T *q, int64_t n,
         pp[i] = T(0);
         e[i] = T(0);
         q[i] = T(0);
-        acc.add(v * v);
+        acc.add_prod(v, v);
     }
     write_partial(red, acc.value());
 }
@@ -104,8 +104,8 @@ __global__ void k_cg_update(T *e, T *r, const T *pp, const T *q, int64_t n, doub
         rv.y -= a * qv.y;
         reinterpret_cast<V *>(e)[i] = ev;
         reinterpret_cast<V *>(r)[i] = rv;
-        acc.add(rv.x * rv.x);
-        acc.add(rv.y * rv.y);
+        acc.add_prod(rv.x, rv.x);
+        acc.add_prod(rv.y, rv.y);
     }
     write_partial(red, acc.value());
 }
@@ -127,7 +127,7 @@ __global__ void k_cg_q(T *q, const T *pp, const uint8_t *co, int64_t n, double *
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const T v = co[i] ? -q[i] : T(0);
         q[i] = v;
-        acc.add(pp[i] * v);
+        acc.add_prod(pp[i], v);
     }
     write_partial(red, acc.value());
 }
@@ -171,8 +171,8 @@ struct ProCG {
             store2(e + j * N + p, ee[j].x + alpha * pp[j].x, ee[j].y + alpha * pp[j].y);
             const T ra = rr[j].x - alpha * qq[j].x, rb = rr[j].y - alpha * qq[j].y;
             store2(r + j * N + p, ra, rb);
-            acc.add(ra * ra);
-            acc.add(rb * rb);
+            acc.add_prod(ra, ra);
+            acc.add_prod(rb, rb);
             const T a = ra + beta * pp[j].x;
             const T b = rb + beta * pp[j].y;
             store2(pv + j * N + p, a, b);
@@ -290,12 +290,12 @@ struct EpiCG {
             const T a = ((b0 >> (1 + i)) & 1) ? -L0[i] : T(0);
             const T b = ((b1 >> (1 + i)) & 1) ? -L1[i] : T(0);
             store2(q + i * N + p, a, b);
-            acc.pq.add(pp[i].x * a);
-            acc.pq.add(pp[i].y * b);
-            acc.rq.add(rr[i].x * a);
-            acc.rq.add(rr[i].y * b);
-            acc.qq.add(a * a);
-            acc.qq.add(b * b);
+            acc.pq.add_prod(pp[i].x, a);
+            acc.pq.add_prod(pp[i].y, b);
+            acc.rq.add_prod(rr[i].x, a);
+            acc.rq.add_prod(rr[i].y, b);
+            acc.qq.add_prod(a, a);
+            acc.qq.add_prod(b, b);
         }
     }
     __device__ void block_done(CgAcc &acc) const
