@@ -214,10 +214,6 @@ struct pd_plan {
     int tune_stages = 0;   // row-pass pipeline stages (1 or 2; 0: 2)
     int tune_stages_inv = 0;  // the same for the inverse row passes (0: as tune_stages)
     int energy_direct = 0; // pd_step_verlet: W by a direct horizon sum (pd_plan_set_energy_mode)
-#ifndef PD_VERLET_UNFUSED
-#define PD_VERLET_UNFUSED 0
-#endif
-    int verlet_unfused = PD_VERLET_UNFUSED;  // 1: separate kick/drift kernels around pd_force's passes
     int64_t prof_n[kKinds] = {};
 };
 

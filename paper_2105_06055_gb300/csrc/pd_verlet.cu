@@ -36,147 +36,6 @@ struct VerletCounters {
     int changed;
 };
 
-// ---------------------------------------------------------------------------
-// Fused step: the first half of the step (kick, drift, integrity update) runs
-// in the forward row pass that transforms the new state, the second kick in
-// the inverse row pass that forms the new force, so no separate elementwise
-// pass touches u, v and L:
-//   prologue: v^h = v + h (L + b); u = chi_O (u + dt v^h) + (1 - chi_O) (w + t w1);
-//             lam <- lam [W <= Wc]; forward fields of u with weight chi lam
-//   epilogue: L, W of the new state (weight chi lam, dense G of that weight);
-//             v = chi_O (v^h + h (L + b))
-// ---------------------------------------------------------------------------
-struct VerletArgs {
-    const void *b, *w, *w1;
-    void *v;
-    const void *Lold, *Wold;
-    double h, dt, t_next, wc;
-    int breaking;
-};
-
-template <typename T, int D, bool ENERGY>
-struct ProVerlet {
-    static constexpr int kFin = 0, kFout = D + (ENERGY ? Sym<D>::n : 0);
-    static constexpr int kNF = D, kNB = 2, kStage = 0;  // u; bits (chi, chi_O), lam
-    static constexpr bool kSparse = false;
-    T *u;
-    uint8_t *lam;
-    const uint8_t *bits;
-    const T *b, *w, *w1, *Lold, *Wold;
-    T *v;
-    T h, dt, t_next, wc;
-    int breaking;
-    VerletCounters *cnt;
-    int64_t N;
-    int n1;
-    cx<T> *spec;
-    int64_t fstride;
-    __device__ const cx<T> *spec_in(int) const { return nullptr; }
-    __device__ cx<T> *spec_out(int f) const { return spec + f * fstride; }
-    __device__ const T *nf_src(int k) const { return u + k * N; }
-    __device__ const uint8_t *nb_src(int k) const { return k == 0 ? bits : lam; }
-    __device__ __forceinline__ void node1(const RowCtx<T> &c, int rl, int i1, T *out) const
-    {
-        const int64_t p = (c.row0 + rl) * n1 + i1;
-        const unsigned bt = c.b(0, rl, i1);
-        uint8_t lm = c.b(1, rl, i1);
-        T uu[D];
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-            const int64_t q = j * N + p;
-            const T vh = v[q] + h * (Lold[q] + b[q]);
-            v[q] = vh;
-            T g = w ? w[q] : T(0);
-            if (w1) g = g + t_next * w1[q];
-            uu[j] = ((bt >> (1 + j)) & 1) ? c.f(j, rl, i1) + dt * vh : g;
-            u[q] = uu[j];
-        }
-        if (breaking && (bt & 1) && lm && !(Wold[p] <= wc)) {
-            lm = 0;
-            lam[p] = 0;
-            atomicAdd(&cnt->flips, 1ull);
-            atomicExch(&cnt->changed, 1);
-        }
-        const T wt = ((bt & 1) && lm) ? T(1) : T(0);
-#pragma unroll
-        for (int j = 0; j < D; ++j) out[j] = wt * uu[j];
-        if constexpr (ENERGY) {
-#pragma unroll
-            for (int q = 0; q < Sym<D>::n; ++q) out[D + q] = wt * uu[Sym<D>::i(q)] * uu[Sym<D>::j(q)];
-        }
-    }
-    __device__ __forceinline__ void node2(const RowCtx<T> &c, int rl, int i1, const T *, const T *, T *o0,
-                                          T *o1) const
-    {
-        node1(c, rl, i1, o0);
-        node1(c, rl, i1 + 1, o1);
-    }
-    __device__ void sparse(const RowCtx<T> &, int, int) const {}
-    __device__ void emit(const RowCtx<T> &, int, int, const T *, const T *, DSum &) const {}
-    __device__ void block_done(DSum &) const {}
-};
-
-template <typename T, int D, bool ENERGY>
-struct EpiVerlet {
-    static constexpr int NC = Sym<D>::n;
-    static constexpr int kFin = D + (ENERGY ? 1 : 0), kFout = 0, kStage = 0;
-    static constexpr int kNF = D + NC, kNB = 2;  // u, G; bits, lam
-    static constexpr bool kSparse = false;
-    const T *u;
-    const uint8_t *lam, *bits;
-    const T *G, *b;
-    T *L, *W, *v;
-    T h;
-    int64_t N;
-    int n1;
-    const cx<T> *spec;
-    int64_t fstride;
-    __device__ const cx<T> *spec_in(int f) const { return spec + f * fstride; }
-    __device__ cx<T> *spec_out(int) const { return nullptr; }
-    __device__ const T *nf_src(int k) const { return k < D ? u + k * N : G + (k - D) * N; }
-    __device__ const uint8_t *nb_src(int k) const { return k == 0 ? bits : lam; }
-    __device__ __forceinline__ void node1(const RowCtx<T> &c, int rl, int i1, const T *in) const
-    {
-        const int64_t p = (c.row0 + rl) * n1 + i1;
-        const unsigned bt = c.b(0, rl, i1);
-        const T wt = ((bt & 1) && c.b(1, rl, i1)) ? T(1) : T(0);
-        T uu[D], g[NC], Gu[D];
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-            uu[j] = c.f(j, rl, i1);
-            Gu[j] = T(0);
-        }
-#pragma unroll
-        for (int q = 0; q < NC; ++q) g[q] = (wt != T(0)) ? c.f(D + q, rl, i1) : T(0);
-        sym_apply<T, D>(g, uu, Gu);
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-            const int64_t q = i * N + p;
-            const T Li = wt * (in[i] - Gu[i]);
-            L[q] = Li;
-            v[q] = ((bt >> (1 + i)) & 1) ? v[q] + h * (Li + b[q]) : T(0);
-        }
-        if constexpr (ENERGY) {
-            T uc = T(0), ugu = T(0);
-#pragma unroll
-            for (int i = 0; i < D; ++i) {
-                uc += uu[i] * in[i];
-                ugu += uu[i] * Gu[i];
-            }
-            W[p] = T(0.5) * wt * (in[D] - T(2) * uc + ugu);
-        }
-    }
-    __device__ __forceinline__ void node2(const RowCtx<T> &c, int rl, int i1, const T *in0, const T *in1, T *,
-                                          T *) const
-    {
-        node1(c, rl, i1, in0);
-        node1(c, rl, i1 + 1, in1);
-    }
-    __device__ void sparse(const RowCtx<T> &, int, int) const {}
-    __device__ void emit(const RowCtx<T> &, int, int, const T *, const T *, DSum &) const {}
-    __device__ void block_done(DSum &) const {}
-};
-
 // Gamma values at the end of the step: w + t_next w1 (w1 null: w, constant)
 template <typename T>
 __global__ void k_kick_drift(T *u, T *v, uint8_t *lam, const T *L, const T *b, const T *w, const T *w1, T t_next,
@@ -314,50 +173,6 @@ pd_status energy_direct(pd_plan *p, const T *u, const uint8_t *lam, T *W, cudaSt
     return PD_OK;
 }
 
-// One fused step (see ProVerlet / EpiVerlet): forward pass with the first half
-// of the step, the boundary field of the new weight if lam changed, the
-// column passes, inverse pass with the force, W and the second kick.
-template <typename T, int D, bool ENERGY>
-pd_status verlet_step_fused(pd_plan *p, T *u, T *v, uint8_t *lam, const T *b, const T *w, const T *w1, double t_next,
-                            double h, double dt, int breaking, T *L, T *W, T *G, VerletCounters *cnt,
-                            cudaStream_t st)
-{
-    cx<T> *spec = reinterpret_cast<cx<T> *>(spec_buf<T>(p));
-    const int64_t fs = p->N / 2;
-    constexpr int FI = D + (ENERGY ? Sym<D>::n : 0), FO = D + (ENERGY ? 1 : 0);
-    ProVerlet<T, D, ENERGY> pro{u,  lam,   p->mbits,    b,      w,  w1,  L, W, v, (T)h, (T)dt, (T)t_next, (T)p->wc,
-                                breaking, cnt, p->N, p->n1, spec, fs};
-    PD_TRY(launch_rows<T>(p, pro, st));
-    if (breaking) {
-        const unsigned nbl = (unsigned)((p->N + 127) / 128);
-        k_gfield_lam<T><<<nbl, 128, 0, st>>>(p->n1, p->n2, p->n3, p->hdev, p->ncomp, p->chi, lam, G, p->N, cnt, 0);
-        k_clear_changed<<<1, 1, 0, st>>>(cnt);
-        PD_LAUNCH_CHECK();
-        p->launches += 2;
-    }
-    if (D == 3) PD_TRY((col_pass<T, FI>(p, 0, false, st)));
-    const int ob = D == 3 ? FI : 0;
-    CombForce<T, D, ENERGY> cmb{model_view<T>(p), ob};
-    PD_TRY(launch_cols<T>(p, cmb, D == 3 ? 2 : 1, true, FI, st));
-    if (D == 3) PD_TRY((col_pass<T, FO>(p, ob, true, st)));
-    EpiVerlet<T, D, ENERGY> epi{u, lam, p->mbits, G, b, L, W, v, (T)h, p->N, p->n1, spec + ob * fs, fs};
-    PD_TRY(launch_rows<T>(p, epi, st));
-    return PD_OK;
-}
-
-template <typename T>
-pd_status verlet_step_fused_any(pd_plan *p, T *u, T *v, uint8_t *lam, const T *b, const T *w, const T *w1,
-                                double t_next, double h, double dt, int breaking, bool energy, T *L, T *W, T *G,
-                                VerletCounters *cnt, cudaStream_t st)
-{
-    if (p->dim == 2)
-        return energy ? verlet_step_fused<T, 2, true>(p, u, v, lam, b, w, w1, t_next, h, dt, breaking, L, W, G, cnt, st)
-                      : verlet_step_fused<T, 2, false>(p, u, v, lam, b, w, w1, t_next, h, dt, breaking, L, W, G, cnt,
-                                                       st);
-    return energy ? verlet_step_fused<T, 3, true>(p, u, v, lam, b, w, w1, t_next, h, dt, breaking, L, W, G, cnt, st)
-                  : verlet_step_fused<T, 3, false>(p, u, v, lam, b, w, w1, t_next, h, dt, breaking, L, W, G, cnt, st);
-}
-
 // one force evaluation of the step, with W in the plan's energy mode
 template <typename T>
 pd_status step_force(pd_plan *p, const T *u, const uint8_t *lam, const T *G, T *L, T *W, int breaking,
@@ -392,18 +207,6 @@ pd_status verlet_impl(pd_plan *p, T *u, T *v, uint8_t *lam, const T *b, const T 
     const T hdt = (T)(0.5 * dt / p->prob.rho);
     const unsigned ng = (unsigned)std::min<int64_t>(4 * p->nsm, (N + 255) / 256);
     const unsigned ngv = (unsigned)std::min<int64_t>(4 * p->nsm, (d * N + 255) / 256);
-    if (!p->verlet_unfused) {
-        // the step's elementwise work lives in the passes (lam NULL: weight chi, no breaking)
-        uint8_t *lw = lam ? lam : p->chi;
-        const bool energy = breaking && !p->energy_direct;
-        const double h = 0.5 * dt / p->prob.rho;
-        for (int s = 0; s < nsteps; ++s) {
-            PD_TRY(verlet_step_fused_any<T>(p, u, v, lw, b, w, w1, t0 + (double)(s + 1) * dt, h, dt, breaking, energy,
-                                            L, W, G, cnt, st));
-            if (breaking && p->energy_direct) PD_TRY(energy_direct<T>(p, u, lam, W, st));
-        }
-        nsteps = 0;
-    }
     for (int s = 0; s < nsteps; ++s) {
         const T t_next = (T)(t0 + (double)(s + 1) * dt);
         k_kick_drift<T><<<ng, 256, 0, st>>>(u, v, lam, L, b, w, w1, t_next, W, p->chi, p->chi_om, d, N, hdt,
