@@ -126,9 +126,12 @@ class ClockSampler:
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
 # committed ncu summaries; None when the kernel changed after the capture.
 MEASURED_TRAFFIC = {
-    "rows_inv": (99.3e6, "profiles/k_rows_EpiCG_static_solve_128cube.md"),
+    "rows_inv": (99.6e6, "profiles/k_rows_EpiCG_static_solve_128cube.md"),
     "last_axis": (42.3e6, "profiles/k_rows_EpiCG_static_solve_128cube.md"),
-    "rows_fwd": (145.2e6, "profiles/k_rows_EpiCG_static_solve_128cube.md"),
+    "rows_fwd": (145.0e6, "profiles/k_rows_EpiCG_static_solve_128cube.md"),
+    "force256_rows_fwd": (367.5e6, "profiles/force_eval_256cube.md"),
+    "force256_last_axis": (495.1e6, "profiles/force_eval_256cube.md"),
+    "force256_rows_inv": (562.3e6, "profiles/force_eval_256cube.md"),
 }
 
 
@@ -396,6 +399,11 @@ def force_point(n, steps, warmup, tuning_arg="", no_autotune=False, e2e=True):
         per = ms / cnt
         byt = FORCE_PASS_BYTES[k] * N + (44 * nb if k == "rows_inv" else 0)
         passes[k] = {"us": 1e3 * per, "algorithmic_bytes": byt, "frac_of_measured_peak": byt / (per * 1e-3) / 1e9 / peak}
+        meas = MEASURED_TRAFFIC.get(f"force{n}_{k}")
+        if meas:
+            # DRAM bytes of a committed capture of this pass at this size, over the live event time
+            passes[k]["dram_bytes_measured"] = meas[0]
+            passes[k]["frac_measured_bytes"] = meas[0] / (per * 1e-3) / 1e9 / peak
     t_ms = statistics.median(times)
     out = {"n": n, "ms_per_eval": t_ms, "node_evals_per_s": N / (t_ms * 1e-3), "passes": passes,
            "m2_end_to_end_hbm_frac": 25.0 * N / (t_ms * 1e-3) / (peak * 1e9), "gpu_launches": int(launches),
