@@ -37,8 +37,9 @@ def test_empty_and_bondless_bodies_give_zero_force(pdm, fp64, dim):
     u = inputs.rng(3).normal(size=(dim,) + shape)
     chi = np.zeros(shape, dtype=np.uint8)
     assert np.all(_force(pdm, shape, chi, u, 3.0, fp64) == 0)
-    # isolated nodes farther apart than the horizon: no bond has both ends in the body
-    chi[(slice(8, -8, 8),) * dim] = 1
+    # isolated nodes 8 apart (delta = 3) and 4 from the faces (margin 3): no bond
+    # has both ends in the body
+    chi[tuple(slice(4, n - 3, 8) for n in shape)] = 1
     assert chi.sum() > 1
     L = _force(pdm, shape, chi, u, 3.0, fp64)
     assert np.max(np.abs(L)) <= (1e-14 if fp64 else 1e-6) * np.max(np.abs(u))
