@@ -228,13 +228,13 @@ struct DrAcc {
 
 __device__ __forceinline__ void write_partial3(double *red, const DrAcc &acc)
 {
-    const double a = block_sum_d(acc.num.value());
-    const double b = block_sum_d(acc.den.value());
-    const double f = block_sum_d(acc.ff.value());
+    const DSum *a[3] = {&acc.num, &acc.den, &acc.ff};
+    double t[3];
+    block_sums<3>(a, t);
     if (threadIdx.x == 0) {
-        red[kRedPart + 3 * blockIdx.x] = a;
-        red[kRedPart + 3 * blockIdx.x + 1] = b;
-        red[kRedPart + 3 * blockIdx.x + 2] = f;
+        red[kRedPart + 3 * blockIdx.x] = t[0];
+        red[kRedPart + 3 * blockIdx.x + 1] = t[1];
+        red[kRedPart + 3 * blockIdx.x + 2] = t[2];
     }
 }
 

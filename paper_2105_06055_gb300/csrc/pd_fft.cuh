@@ -94,13 +94,28 @@ __device__ __forceinline__ void dft_reg(cx<T> *v)
     }
 }
 
+// Swizzled element order between the first and second stage: element e is
+// stored at e ^ ((e >> sh) & 7) (an involution for sh >= 3). The first
+// radix-8 stage writes the 8 outputs of one butterfly to consecutive
+// elements, so in natural order the lanes of a warp store 8 elements apart
+// and pile onto two of the 16 eight-byte bank pairs; XOR-ing the element's
+// low three bits with the butterfly index spreads them over all pairs. With
+// 8 butterflies per row (rows 8 bank pairs apart) sh = 3 is conflict-free,
+// with 16 or more sh = 4. Row passes use it; in the column tiles the lanes of
+// a warp differ first in the column, the conflicts are at most 2-way at the
+// tile widths the passes run with, and the extra index arithmetic on the
+// strided addresses cost more than it saved (measured).
+__device__ __forceinline__ int swz(int e, int sh) { return e ^ ((e >> sh) & 7); }
+
 // One radix-R Stockham stage of F length-n transforms, field f stored at
 // s[f * fstride + e * stride]. Thread jt (of nt = n/kV) handles butterflies
 // j = jt + b nt, b < kV/R, of every field (the twiddles are loaded once for
-// all fields). tw[i] = e^{-2 pi i i / 2^lgl}. Ends with a block-wide barrier.
-template <typename T, int R, int F>
+// all fields). tw[i] = e^{-2 pi i i / 2^lgl}. SI / SO: read / write in the
+// swizzled order of shift sh. Ends with a block-wide barrier.
+template <typename T, int R, int F, bool SI = false, bool SO = false>
 __device__ __forceinline__ void fft_stage(cx<T> *s, int fstride, int stride, int n, int ns, int lgnsr, int jt,
-                                          int nt, const cx<T> *__restrict__ tw, int lgl, bool cin, bool cout)
+                                          int nt, const cx<T> *__restrict__ tw, int lgl, bool cin, bool cout,
+                                          int sh = 0)
 {
     static_assert(R <= kV, "radix larger than the values per thread");
     constexpr int B = kV / R;
@@ -113,7 +128,9 @@ __device__ __forceinline__ void fft_stage(cx<T> *s, int fstride, int stride, int
             const int j = jt + b * nt;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const cx<T> x = s[f * fstride + (j + r * q) * stride];
+                int e = j + r * q;
+                if constexpr (SI) e = swz(e, sh);
+                const cx<T> x = s[f * fstride + e * stride];
                 v[f][b * R + r] = cin ? conjg(x) : x;
             }
         }
@@ -131,7 +148,11 @@ __device__ __forceinline__ void fft_stage(cx<T> *s, int fstride, int stride, int
             }
             dft_reg<T, R>(&v[0][b * R]);
 #pragma unroll
-            for (int r = 0; r < R; ++r) s[(o + r * ns) * stride] = cout ? conjg(v[0][b * R + r]) : v[0][b * R + r];
+            for (int r = 0; r < R; ++r) {
+                int e = o + r * ns;
+                if constexpr (SO) e = swz(e, sh);
+                s[e * stride] = cout ? conjg(v[0][b * R + r]) : v[0][b * R + r];
+            }
         } else {
             cx<T> w[R];
             if (ns > 1) {
@@ -146,8 +167,11 @@ __device__ __forceinline__ void fft_stage(cx<T> *s, int fstride, int stride, int
                 }
                 dft_reg<T, R>(&v[f][b * R]);
 #pragma unroll
-                for (int r = 0; r < R; ++r)
-                    s[f * fstride + (o + r * ns) * stride] = cout ? conjg(v[f][b * R + r]) : v[f][b * R + r];
+                for (int r = 0; r < R; ++r) {
+                    int e = o + r * ns;
+                    if constexpr (SO) e = swz(e, sh);
+                    s[f * fstride + e * stride] = cout ? conjg(v[f][b * R + r]) : v[f][b * R + r];
+                }
             }
         }
     }
@@ -159,44 +183,102 @@ __device__ __forceinline__ void fft_stage(cx<T> *s, int fstride, int stride, int
 // radix 4 or 2 for the remainder, which comes last (schedule 0) or first
 // (schedule 1). With cin the input is conjugated as it is read, with cout the
 // output as it is written (IDFT(x) = conj(DFT(conj(x))) costs no extra pass).
+// sh > 0: a first stage of radix 8 hands its outputs to the second stage in
+// the swizzled order of shift sh (input and output stay in natural order).
 template <typename T, int F = 1>
 __device__ __forceinline__ void fft_smem(cx<T> *s, int fstride, int stride, int lgn, int jt,
                                          const cx<T> *__restrict__ tw, int lgl, bool cin = false,
-                                         bool cout = false, int sched = 0)
+                                         bool cout = false, int sched = 0, int sh = 0)
 {
     const int n = 1 << lgn, nt = n >> kLgV;
     int ns = 1, lgns = 0, rem = lgn;
     const int rm = lgn % kLgV;
+    bool sw_in = false;  // this stage reads the swizzled order
     while (rem > 0) {
         const int lr = (sched && lgns == 0 && rm) ? rm : (rem >= kLgV ? kLgV : rem);
         const bool first = (lgns == 0), last = (rem == lr);
         const bool ci = cin && first, co = cout && last;
+        const bool sw_out = kV == 8 && sh > 0 && first && !last && lr == 3;
         switch (lr) {
             case 4:
                 if constexpr (kV >= 16) fft_stage<T, 16, F>(s, fstride, stride, n, ns, lgns + 4, jt, nt, tw, lgl, ci, co);
                 break;
-            case 3: fft_stage<T, 8, F>(s, fstride, stride, n, ns, lgns + 3, jt, nt, tw, lgl, ci, co); break;
-            case 2: fft_stage<T, 4, F>(s, fstride, stride, n, ns, lgns + 2, jt, nt, tw, lgl, ci, co); break;
-            default: fft_stage<T, 2, F>(s, fstride, stride, n, ns, lgns + 1, jt, nt, tw, lgl, ci, co); break;
+            case 3:
+                if (sw_out)
+                    fft_stage<T, 8, F, false, true>(s, fstride, stride, n, ns, lgns + 3, jt, nt, tw, lgl, ci, co, sh);
+                else if (sw_in)
+                    fft_stage<T, 8, F, true, false>(s, fstride, stride, n, ns, lgns + 3, jt, nt, tw, lgl, ci, co, sh);
+                else
+                    fft_stage<T, 8, F>(s, fstride, stride, n, ns, lgns + 3, jt, nt, tw, lgl, ci, co);
+                break;
+            case 2:
+                if (sw_in)
+                    fft_stage<T, 4, F, true, false>(s, fstride, stride, n, ns, lgns + 2, jt, nt, tw, lgl, ci, co, sh);
+                else
+                    fft_stage<T, 4, F>(s, fstride, stride, n, ns, lgns + 2, jt, nt, tw, lgl, ci, co);
+                break;
+            default:
+                if (sw_in)
+                    fft_stage<T, 2, F, true, false>(s, fstride, stride, n, ns, lgns + 1, jt, nt, tw, lgl, ci, co, sh);
+                else
+                    fft_stage<T, 2, F>(s, fstride, stride, n, ns, lgns + 1, jt, nt, tw, lgl, ci, co);
+                break;
         }
+        sw_in = sw_out;
         ns <<= lr;
         lgns += lr;
         rem -= lr;
     }
 }
 
+// fft_smem for a length 2^LGN, stage schedule SCHED and swizzle shift SH
+// (0: none) fixed at compile time: the stage sequence unrolls, so the lengths,
+// strides, twiddle shifts and conjugation flags fft_stage derives from it are
+// constants (shared-memory offsets fold into the load and store instructions
+// and no stage dispatch runs). Same arithmetic as fft_smem.
+template <typename T, int F, int LGN, int SCHED, int SH, int LGNS = 0, bool SWIN = false>
+__device__ __forceinline__ void fft_ct(cx<T> *s, int fstride, int stride, int jt, const cx<T> *__restrict__ tw,
+                                       int lgl, bool cin, bool cout)
+{
+    constexpr int REM = LGN - LGNS, RM = LGN % kLgV;
+    constexpr int LR = (SCHED && LGNS == 0 && RM) ? RM : (REM >= kLgV ? kLgV : REM);
+    constexpr bool FIRST = LGNS == 0, LAST = REM == LR;
+    constexpr bool SWOUT = kV == 8 && SH > 0 && FIRST && !LAST && LR == 3;
+    fft_stage<T, (1 << LR), F, SWIN, SWOUT>(s, fstride, stride, 1 << LGN, 1 << LGNS, LGNS + LR, jt,
+                                            (1 << LGN) >> kLgV, tw, lgl, cin && FIRST, cout && LAST, SH);
+    if constexpr (!LAST) fft_ct<T, F, LGN, SCHED, SH, LGNS + LR, SWOUT>(s, fstride, stride, jt, tw, lgl, cin, cout);
+}
+
+// Hooks of fft_fields, called with the index of a sweep's first field and
+// its field count before and after the sweep (by all threads).
+struct NoHook {
+    __device__ __forceinline__ void operator()(int, int) const {}
+};
+
 // F transforms in sweeps of up to MG fields at a time (one barrier pair per
 // stage and sweep instead of per stage and field; MG x 8 complex values live
-// per thread)
-template <typename T, int F, int MG>
+// per thread). f0 numbers the first field for the hooks.
+template <typename T, int F, int MG, class Before = NoHook, class After = NoHook>
 __device__ __forceinline__ void fft_fields(cx<T> *s, int fstride, int stride, int lgn, int jt,
-                                           const cx<T> *__restrict__ tw, int lgl, bool cin, bool cout, int sched)
+                                           const cx<T> *__restrict__ tw, int lgl, bool cin, bool cout, int sched,
+                                           int f0 = 0, const Before &before = {}, const After &after = {})
 {
-    if constexpr (F > 0) {
+    if constexpr (MG == 1) {
+        // one field per sweep: a loop (one copy of the transform code)
+#pragma unroll 1
+        for (int f = 0; f < F; ++f) {
+            before(f0 + f, 1);
+            fft_smem<T, 1>(s + f * fstride, fstride, stride, lgn, jt, tw, lgl, cin, cout, sched);
+            after(f0 + f, 1);
+        }
+    } else if constexpr (F > 0) {
         constexpr int G = F < MG ? F : MG;
+        before(f0, G);
         fft_smem<T, G>(s, fstride, stride, lgn, jt, tw, lgl, cin, cout, sched);
+        after(f0, G);
         if constexpr (F > G)
-            fft_fields<T, F - G, MG>(s + G * fstride, fstride, stride, lgn, jt, tw, lgl, cin, cout, sched);
+            fft_fields<T, F - G, MG>(s + G * fstride, fstride, stride, lgn, jt, tw, lgl, cin, cout, sched, f0 + G,
+                                     before, after);
     }
 }
 // column passes: grouped sweeps pay for the spectral-combine passes; the plain
@@ -247,6 +329,46 @@ __device__ __forceinline__ double block_sum_d(double v)
     if (wid == 0)
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     return v;  // valid in thread 0
+}
+
+// Block sums of NV compensated accumulators (valid in thread 0; whole warps).
+// The FP32 pairs (hi, lo) are merged across each warp by the two-sum of the
+// hi parts, their rounding errors going to lo, so only one lane per warp
+// converts to FP64: FP64 runs at a small fraction of the FP32 rate, and a
+// per-thread FP64 reduction kept that pipe busy for several microseconds of
+// every row pass. FP64 parts are summed in FP64 only in warps that hold any.
+template <int NV>
+__device__ __forceinline__ void block_sums(const DSum *const (&a)[NV], double (&out)[NV])
+{
+    __shared__ double sh_bn[NV][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();  // a previous call may still be reading sh_bn
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        float hi = a[v]->hi, lo = a[v]->lo;
+        double d = a[v]->d;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+            const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+            const float s = hi + h2, bb = s - hi;
+            lo += l2 + ((hi - (s - bb)) + (h2 - bb));
+            hi = s;
+        }
+        if (__any_sync(0xffffffffu, d != 0.0))
+            for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        if (lane == 0) sh_bn[v][wid] = d + (double)hi + (double)lo;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            double t = 0.0;
+            for (int k = 0; k < nw; ++k) t += sh_bn[v][k];
+            out[v] = t;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -356,7 +478,9 @@ struct op_min_blocks : std::integral_constant<int, 1> {
 template <class Op>
 struct op_min_blocks<Op, std::void_t<decltype(Op::kMinBlocks)>> : std::integral_constant<int, Op::kMinBlocks> {
 };
-template <typename T, class Op>
+// LG > 0: compiled for packed rows of 2^LG complex values (g.lgh == LG) and
+// stage schedule SCHED (g.sched == SCHED); LG = 0 reads both from g.
+template <typename T, class Op, int LG = 0, int SCHED = 0>
 __global__ void __launch_bounds__(256, op_min_blocks<Op>::value) k_rows(RowGeom g, Op op,
                                                                        const cx<T> *__restrict__ tw)
 {
@@ -366,7 +490,8 @@ __global__ void __launch_bounds__(256, op_min_blocks<Op>::value) k_rows(RowGeom 
     constexpr int FB = FI > KO ? FI : KO;
     static_assert(!(FO > 0 && ST > 0), "an op either stages outputs or transforms forward");
     constexpr bool kLoad = FI > 0 || NF > 0 || NB > 0;
-    const int H = 1 << g.lgh, n1 = 2 * H, nt = H >> kLgV, lg1 = g.lgh + 1;
+    const int lgh = LG > 0 ? LG : g.lgh;
+    const int H = 1 << lgh, n1 = 2 * H, nt = H >> kLgV, lg1 = lgh + 1;
     const int rows = g.rows, pitch = g.pitch;
     const int64_t ntiles = g.nrows / rows;
     // forward passes (FI = 0) load no spectra: one transform workspace, and
@@ -425,6 +550,13 @@ __global__ void __launch_bounds__(256, op_min_blocks<Op>::value) k_rows(RowGeom 
     if (kLoad && threadIdx.x == 0 && t < ntiles && !stall) issue(t, 0);
     unsigned phase = 0;  // bit s: parity of the next completion of stage s
     const int jt = threadIdx.x % nt, rf = threadIdx.x / nt;  // FFT mapping: nt threads per row
+    const int rsh = nt >= 16 ? 4 : 3;                        // swizzle shift of the first stage (fft_smem)
+    auto row_fft = [&](cx<T> *z) {
+        if constexpr (LG > 0)
+            fft_ct<T, 1, LG, SCHED, (LG - kLgV >= 4 ? 4 : 3)>(z, 0, 1, jt, tws, LG + 1, false, false);
+        else
+            fft_smem<T>(z, 0, 1, g.lgh, jt, tws, lg1, false, false, g.sched, rsh);
+    };
     typename op_acc<Op>::type acc;
 
     for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
@@ -475,12 +607,12 @@ __global__ void __launch_bounds__(256, op_min_blocks<Op>::value) k_rows(RowGeom 
             __syncthreads();
 #pragma unroll 1
             for (int f = 0; f < FI; ++f)
-                fft_smem<T>(spec + (f * rows + rf) * pitch, 0, 1, g.lgh, jt, tws, lg1, false, false, g.sched);
+                row_fft(spec + (f * rows + rf) * pitch);
         }
 
         // per-node work, lanes over consecutive packed slots (2 nodes each)
         for (int idx = threadIdx.x; idx < rows * H; idx += blockDim.x) {
-            const int rl = idx >> g.lgh, n = idx & (H - 1);
+            const int rl = idx >> lgh, n = idx & (H - 1);
             T in0[FI > 0 ? FI : 1], in1[FI > 0 ? FI : 1];
             T o0[KO > 0 ? KO : 1], o1[KO > 0 ? KO : 1];
 #pragma unroll
@@ -504,7 +636,7 @@ __global__ void __launch_bounds__(256, op_min_blocks<Op>::value) k_rows(RowGeom 
         }
         if constexpr (ST > 0) {
             for (int idx = threadIdx.x; idx < rows * H; idx += blockDim.x) {
-                const int rl = idx >> g.lgh, n = idx & (H - 1);
+                const int rl = idx >> lgh, n = idx & (H - 1);
                 T s0[ST], s1[ST];
 #pragma unroll
                 for (int f = 0; f < ST; ++f) {
@@ -519,7 +651,7 @@ __global__ void __launch_bounds__(256, op_min_blocks<Op>::value) k_rows(RowGeom 
         if constexpr (FO > 0) {
 #pragma unroll 1
             for (int f = 0; f < FO; ++f)
-                fft_smem<T>(spec + (f * rows + rf) * pitch, 0, 1, g.lgh, jt, tws, lg1, false, false, g.sched);
+                row_fft(spec + (f * rows + rf) * pitch);
             const T half = T(0.5);
 #pragma unroll
             for (int f = 0; f < FO; ++f) {
@@ -587,7 +719,7 @@ struct ColGeom {
 // [outer * slots][L][2 * inner] scalars with box (2w, lb, 1); tmm the same with
 // box (4, lb, 1) for the mirror column.
 // Shared memory: [L] twiddles, [max(kFin,kFout)][L][w] tiles, [max(kFin,kFout)][L][2] mirror,
-// the table slice, mbarrier.
+// the table slice, mbarriers (one per field for the plain transforms, else one).
 template <typename T, class Op>
 __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__restrict__ tw, int axis_is_z,
                                               const __grid_constant__ CUtensorMap tmt,
@@ -598,7 +730,8 @@ __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__r
     constexpr int FB = FI > FO ? FI : FO;
     // the combine reads all inputs of a mode before it writes that mode's
     // outputs, so outputs may outnumber inputs (the tile holds max(kFin, kFout))
-    const int L = 1 << g.lgl;
+    const int lgl = g.lgl;
+    const int L = 1 << lgl;
     const int w = g.w, ncol = w + g.mirror;  // threads: ncol x (L / kV)
     const int col = threadIdx.x % ncol, jt = threadIdx.x / ncol;
     const int H = 1 << g.lgh;
@@ -625,8 +758,14 @@ __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__r
     int mcol = -1;
     if (g.mirror && (c0 & (H - 1)) == 0) mcol = ((g.n2 - (c0 >> g.lgh)) & (g.n2 - 1)) << g.lgh;
 
-    if (threadIdx.x == 0) mbar_init(mbar, 1);
-    for (int i = threadIdx.x; i < L; i += nthreads) tws[i] = tw[i << (g.lgtw - g.lgl)];
+    // every field has its own barrier: a sweep of fields is transformed as
+    // soon as they have arrived while the later ones are still in flight,
+    // and outputs leave sweep by sweep while the next sweep is transformed
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int f = 0; f < FI; ++f) mbar_init(&mbar[f], 1);
+    }
+    for (int i = threadIdx.x; i < L; i += nthreads) tws[i] = tw[i << (g.lgtw - lgl)];
     __syncthreads();
     // kernel-table slice of this tile (plan constants: fetched before the wait
     // for the preceding pass, overlapping its tail)
@@ -652,34 +791,62 @@ __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__r
     pdl_trigger();
     if (threadIdx.x == 0) {
         pdl_wait();  // the tiles are the preceding pass's output; only thread 0 touches global data
-        const unsigned bytes = (unsigned)(FI * fsz * sizeof(cx<T>) + (mcol >= 0 ? FI * L * 2 * sizeof(cx<T>) : 0));
-        mbar_expect_tx(mbar, bytes);
+        const unsigned fbytes = (unsigned)(fsz * sizeof(cx<T>) + (mcol >= 0 ? L * 2 * sizeof(cx<T>) : 0));
 #pragma unroll
         for (int f = 0; f < FI; ++f) {
+            mbar_expect_tx(&mbar[f], fbytes);
             const int z = o + op.slot_in(f) * g.outer;
             for (int l0 = 0; l0 < L; l0 += g.lb) {
-                tma_load_3d(tile + f * fsz + l0 * w, &tmt, 2 * c0, l0, z, mbar);
-                if (mcol >= 0) tma_load_3d(mir + f * L * 2 + l0 * 2, &tmm, 2 * mcol, l0, z, mbar);
+                tma_load_3d(tile + f * fsz + l0 * w, &tmt, 2 * c0, l0, z, &mbar[f]);
+                if (mcol >= 0) tma_load_3d(mir + f * L * 2 + l0 * 2, &tmm, 2 * mcol, l0, z, &mbar[f]);
             }
         }
     }
-    if (!mbar_wait(mbar, 0, g.err)) return;
-    if constexpr (NTAB > 0) __syncthreads();
 
     // per-thread transform: a tile column, or the mirror column
     const bool is_m = col >= w;
     const int cstride = is_m ? 2 : w;
     auto colbase = [&](int f) -> cx<T> * { return is_m ? (mir + f * L * 2) : (tile + f * fsz + col); };
+    const int fstr = is_m ? L * 2 : fsz;  // field stride of this thread's column
 
     constexpr int FPRE = (MODE == 2) ? Op::kPre : 0;
-    const int fstr = is_m ? L * 2 : fsz;  // field stride of this thread's column
-    fft_fields<T, FI - FPRE, MODE == 2 ? kCombFieldGroup : 1>(colbase(FPRE), fstr, cstride, g.lgl, jt, tws, g.lgl,
-                                                              MODE == 1, MODE == 1, g.sched);
+    constexpr int GF = MODE == 2 ? kCombFieldGroup : 1;  // fields per sweep
+    // A bounded wait that runs out marks the block failed (all threads agree):
+    // it stores nothing, and before it exits it lets the copies in flight land.
+    bool failed = false;
+    int narrived = 0;  // fields waited for
+    auto arrive = [&](int f0, int n) {
+        const int upto = f0 + n;
+        bool ok = true;
+        if (!failed)
+            for (int f = narrived; f < upto; ++f) ok = ok && mbar_wait(&mbar[f], 0, g.err);
+        narrived = upto;
+        failed = __syncthreads_or(failed || !ok);
+    };
+    auto emit = [&](int f0, int n) {  // store output fields [f0, f0 + n)
+        fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0 && !failed) {
+            for (int f = f0; f < f0 + n; ++f)
+                for (int l0 = 0; l0 < L; l0 += g.lb)
+                    tma_store_3d(&tmt, 2 * c0, l0, o + op.slot_out(f) * g.outer, tile + f * fsz + l0 * w);
+            bulk_commit();
+        }
+    };
+
+    if constexpr (MODE != 2) {
+        fft_fields<T, FI, 1>(colbase(0), fstr, cstride, lgl, jt, tws, lgl, MODE == 1, MODE == 1, g.sched, 0, arrive,
+                             emit);
+    } else {
+        if constexpr (FI == FPRE) arrive(0, FI);
+        fft_fields<T, FI - FPRE, GF>(colbase(FPRE), fstr, cstride, lgl, jt, tws, lgl, false, false, g.sched, FPRE,
+                                     arrive);
+    }
 
     if constexpr (MODE == 2 && Op::kStoreIn) {
         fence_proxy_async();
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && !failed) {
 #pragma unroll
             for (int f = FPRE; f < FI; ++f)
                 for (int l0 = 0; l0 < L; l0 += g.lb)
@@ -780,19 +947,12 @@ __global__ void __launch_bounds__(512) k_cols(ColGeom g, Op op, const cx<T> *__r
             }
             __syncthreads();
         }
-        fft_fields<T, FO, kCombFieldGroup>(colbase(0), fstr, cstride, g.lgl, jt, tws, g.lgl, false, true, g.sched);
+        fft_fields<T, FO, GF>(colbase(0), fstr, cstride, lgl, jt, tws, lgl, false, true, g.sched, 0, NoHook{}, emit);
     }
 
-    // ---- store
-    constexpr int FS = (MODE == 2) ? FO : FI;
-    fence_proxy_async();
-    __syncthreads();
     if (threadIdx.x == 0) {
-#pragma unroll
-        for (int f = 0; f < FS; ++f)
-            for (int l0 = 0; l0 < L; l0 += g.lb)
-                tma_store_3d(&tmt, 2 * c0, l0, o + op.slot_out(f) * g.outer, tile + f * fsz + l0 * w);
-        bulk_commit();
+        if (failed)
+            for (int f = 0; f < FI; ++f) mbar_wait(&mbar[f], 0, nullptr);
         bulk_wait_read_all();
     }
 }

@@ -95,6 +95,7 @@ struct ProForce {
     static constexpr int kFin = 0, kFout = D + (ENERGY ? Sym<D>::n : 0);
     static constexpr int kNF = D + (WM == W_S ? 1 : 0), kNB = 1 + (WM == W_LAM ? 1 : 0), kStage = 0;
     static constexpr bool kSparse = false;
+    static constexpr bool kFixedLength = std::is_same_v<T, float> && !ENERGY && WM == W_NONE;
     const T *u;
     const T *s;
     const uint8_t *lam;
@@ -186,6 +187,7 @@ struct EpiForceSparse {
     static constexpr int kFin = D + (ENERGY ? 1 : 0), kFout = 0, kStage = D + (ENERGY ? 1 : 0);
     static constexpr int kNF = ENERGY ? D : 0, kNB = 1;
     static constexpr bool kSparse = false;
+    static constexpr bool kFixedLength = std::is_same_v<T, float> && !ENERGY;
     const T *u;
     const uint8_t *chi;
     const GEntry<T> *gent;

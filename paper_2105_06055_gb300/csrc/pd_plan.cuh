@@ -289,7 +289,7 @@ inline void col_cfg(const pd_plan *p, int axis, bool last, int FB, int FI, int N
     auto smem_of = [&](int w, int mir, int tc) {
         const size_t tab = (((size_t)NTAB * (L / 2 + 1) * tc + 1) & ~(size_t)1) * sizeof(T);
         return (size_t)L * sizeof(cx<T>) + (size_t)FB * L * w * sizeof(cx<T>) +
-               (mir ? (size_t)FB * L * 2 * sizeof(cx<T>) : 0) + tab + 16;
+               (mir ? (size_t)FB * L * 2 * sizeof(cx<T>) : 0) + tab + 8 * ((size_t)FB + 1);
     };
     int w = p->tune_w[last ? 1 : 0] > 0 ? p->tune_w[last ? 1 : 0] : 32;
     while (w > 2 && ((w + wmirror) * nt > 512 || smem_of(w, wmirror, w + 1) > 100 * 1024 || (H % w))) w >>= 1;
@@ -383,6 +383,32 @@ inline pd_status launch_k(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 bloc
     return PD_OK;
 }
 
+// Row ops that declare kFixedLength = true also get row kernels compiled for
+// the packed row lengths of the 128^3 to 512^3 boxes (64 to 256 values), one
+// per stage schedule where the schedule matters; other lengths use the kernel
+// that reads the length at run time.
+template <class Op, class = void>
+struct op_fixed_len : std::false_type {
+};
+template <class Op>
+struct op_fixed_len<Op, std::void_t<decltype(Op::kFixedLength)>> : std::bool_constant<Op::kFixedLength> {
+};
+
+template <typename T, class Op>
+auto rows_kernel(int lgh, int sched)
+{
+    using K = decltype(&k_rows<T, Op>);
+    if constexpr (op_fixed_len<Op>::value) {
+        switch (lgh) {
+            case 6: return (K)&k_rows<T, Op, 6, 0>;
+            case 7: return sched ? (K)&k_rows<T, Op, 7, 1> : (K)&k_rows<T, Op, 7, 0>;
+            case 8: return sched ? (K)&k_rows<T, Op, 8, 1> : (K)&k_rows<T, Op, 8, 0>;
+            default: break;
+        }
+    }
+    return (K)&k_rows<T, Op>;
+}
+
 // Persistent row pass: as many blocks as fit on the GPU at once (at most one
 // per tile). *grid_out receives the block count (the number of block partial
 // sums an op with a block accumulator writes).
@@ -394,14 +420,15 @@ pd_status launch_rows(pd_plan *p, const Op &op, cudaStream_t st, unsigned *grid_
     constexpr int KO = Op::kFout > Op::kStage ? Op::kFout : Op::kStage;
     constexpr int FB = Op::kFin > KO ? Op::kFin : KO;
     row_cfg<T>(p, Op::kFin, FB, Op::kNF, Op::kNB, g, c);
-    PD_TRY(set_smem_attr((const void *)k_rows<T, Op>, c.smem));
+    const auto kern = rows_kernel<T, Op>(g.lgh, g.sched);
+    PD_TRY(set_smem_attr((const void *)kern, c.smem));
     int per_sm = 0;
-    PD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows<T, Op>, (int)c.block.x, c.smem));
+    PD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)c.block.x, c.smem));
     const int64_t cap = (int64_t)std::max(per_sm, 1) * p->nsm;
     if ((int64_t)c.grid.x > cap) c.grid.x = (unsigned)cap;
     if (grid_out) *grid_out = c.grid.x;
     PD_TRY(prof_begin(p, Op::kFin > 0 ? PASS_ROWS_INV : PASS_ROWS_FWD, st));
-    PD_TRY(launch_k(p->pdl != 0, k_rows<T, Op>, c.grid, c.block, c.smem, st, g, op, tw_buf<T>(p)));
+    PD_TRY(launch_k(p->pdl != 0, kern, c.grid, c.block, c.smem, st, g, op, tw_buf<T>(p)));
     PD_TRY(prof_end(p, st));
     p->launches++;
     return PD_OK;

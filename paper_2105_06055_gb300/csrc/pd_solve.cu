@@ -82,7 +82,7 @@ __global__ void k_cg_init(const double *r64, T *r, T *pp, T *e, T *q, int64_t n,
         q[i] = T(0);
         acc.add_prod(v, v);
     }
-    write_partial(red, acc.value());
+    write_partial(red, acc);
 }
 
 // e += alpha p ; r -= alpha q ; partial r.r   (n a multiple of 2)
@@ -107,7 +107,7 @@ __global__ void k_cg_update(T *e, T *r, const T *pp, const T *q, int64_t n, doub
         acc.add_prod(rv.x, rv.x);
         acc.add_prod(rv.y, rv.y);
     }
-    write_partial(red, acc.value());
+    write_partial(red, acc);
 }
 
 // p = r + beta p (state-based path, unfused)
@@ -129,7 +129,7 @@ __global__ void k_cg_q(T *q, const T *pp, const uint8_t *co, int64_t n, double *
         q[i] = v;
         acc.add_prod(pp[i], v);
     }
-    write_partial(red, acc.value());
+    write_partial(red, acc);
 }
 
 // rows, forward: pending update e += alpha p, r -= alpha q, then
@@ -139,6 +139,7 @@ template <typename T, int D>
 struct ProCG {
     static constexpr int kFin = 0, kFout = D, kNF = 0, kNB = 1, kStage = 0;
     static constexpr bool kSparse = false, kNodeAcc = true;
+    static constexpr bool kFixedLength = std::is_same_v<T, float>;
     T *e, *r, *pv;
     const T *q;
     const uint8_t *bits;
@@ -182,7 +183,7 @@ struct ProCG {
     }
     __device__ void sparse(const RowCtx<T> &, int, int) const {}
     __device__ void emit(const RowCtx<T> &, int, int, const T *, const T *, DSum &) const {}
-    __device__ void block_done(DSum &acc) const { write_partial(red, acc.value()); }
+    __device__ void block_done(DSum &acc) const { write_partial(red, acc); }
 };
 
 static_assert(op_min_blocks<ProCG<float, 3>>::value == 1, "ProCG declares no register cap");
@@ -198,6 +199,7 @@ template <typename T, int D>
 struct EpiCG {
     static constexpr int kFin = D, kFout = 0, kStage = D, kNF = 0, kNB = 1;
     static constexpr bool kSparse = false;
+    static constexpr bool kFixedLength = std::is_same_v<T, float>;
     static constexpr int kMinBlocks = 4;  // <= 64 registers: more resident warps
     using Acc = CgAcc;
     // loads of one node pair: p, r and its boundary-list indices (read-only in this pass)
@@ -300,14 +302,14 @@ struct EpiCG {
     }
     __device__ void block_done(CgAcc &acc) const
     {
-        const double x = block_sum_d(acc.pq.value());
-        const double y = block_sum_d(acc.rq.value());
-        const double z = block_sum_d(acc.qq.value());
+        const DSum *a[3] = {&acc.pq, &acc.rq, &acc.qq};
+        double t[3];
+        block_sums<3>(a, t);
         if (threadIdx.x == 0) {
             double *o = red + kRedPart + kPartB + 3 * blockIdx.x;
-            o[0] = x;
-            o[1] = y;
-            o[2] = z;
+            o[0] = t[0];
+            o[1] = t[1];
+            o[2] = t[2];
         }
     }
 };

@@ -50,6 +50,15 @@ __device__ __forceinline__ void write_partial(double *red, double v)
     if (threadIdx.x == 0) red[kRedPart + blockIdx.x] = t;
 }
 
+// the same for a compensated accumulator (FP32 pairs merged per warp)
+__device__ __forceinline__ void write_partial(double *red, const DSum &acc)
+{
+    const DSum *a[1] = {&acc};
+    double t[1];
+    block_sums<1>(a, t);
+    if (threadIdx.x == 0) red[kRedPart + blockIdx.x] = t[0];
+}
+
 // Final reduction of nparts block partials into scalar `dst`, then:
 //   0: store only; 1: alpha = rr / pq; 2: beta = rrnew / rr, rr = rrnew
 __global__ void k_finish(double *red, int nparts, int dst, int what)
