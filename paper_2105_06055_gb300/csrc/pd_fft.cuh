@@ -470,6 +470,16 @@ struct op_node_acc<Op, std::void_t<decltype(Op::kNodeAcc)>> : std::bool_constant
 // the next tile are in flight while the current one is transformed. Twiddles
 // are copied to shared memory once; outputs leave through coalesced stores.
 // Block accumulators (acc) run over all tiles of the block.
+// Row ops may declare l2_prefetch(row0, rows): called by the thread that
+// issues a tile's bulk copies, right after them, to start the node fields the
+// op reads with plain loads later (after the tile's transforms) towards L2.
+template <class Op, class = void>
+struct op_has_l2_prefetch : std::false_type {
+};
+template <class Op>
+struct op_has_l2_prefetch<Op, std::void_t<decltype(&Op::l2_prefetch)>> : std::true_type {
+};
+
 // Row ops may declare kMinBlocks (resident 256-thread blocks per SM the
 // compiler must allow, i.e. a register cap of 256 / kMinBlocks per thread).
 template <class Op, class = void>
@@ -528,6 +538,7 @@ __global__ void __launch_bounds__(256, op_min_blocks<Op>::value) k_rows(RowGeom 
             bulk_load(nf + k * rows * n1, op.nf_src(k) + r0 * n1, rows * n1 * sizeof(T), &mbar[s]);
 #pragma unroll
         for (int k = 0; k < NB; ++k) bulk_load(nb + k * rows * n1, op.nb_src(k) + r0 * n1, rows * n1, &mbar[s]);
+        if constexpr (op_has_l2_prefetch<Op>::value) op.l2_prefetch(r0, rows);
     };
 
     if (kLoad && threadIdx.x == 0) {

@@ -152,6 +152,19 @@ struct ProCG {
     __device__ cx<T> *spec_out(int f) const { return spec + f * fstride; }
     __device__ const T *nf_src(int) const { return nullptr; }
     __device__ const uint8_t *nb_src(int) const { return bits; }
+    // e, r, p and q of the tile's rows start towards L2 while its mask bytes arrive
+    __device__ __forceinline__ void l2_prefetch(int64_t row0, int rows) const
+    {
+        const int64_t base = row0 * n1;
+        const unsigned bytes = (unsigned)(rows * n1 * sizeof(T));
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            bulk_prefetch_l2(e + j * N + base, bytes);
+            bulk_prefetch_l2(r + j * N + base, bytes);
+            bulk_prefetch_l2(pv + j * N + base, bytes);
+            bulk_prefetch_l2(q + j * N + base, bytes);
+        }
+    }
     __device__ __forceinline__ void node2(const RowCtx<T> &c, int rl, int i1, const T *, const T *, T *o0,
                                           T *o1, DSum &acc) const
     {
@@ -221,6 +234,19 @@ struct EpiCG {
     __device__ cx<T> *spec_out(int) const { return nullptr; }
     __device__ const T *nf_src(int) const { return nullptr; }
     __device__ const uint8_t *nb_src(int) const { return bits; }
+    // p, r and the boundary index of the tile's rows start towards L2 while
+    // the tile's spectra arrive and are transformed (one bulk prefetch each)
+    __device__ __forceinline__ void l2_prefetch(int64_t row0, int rows) const
+    {
+        const int64_t base = row0 * n1;
+        const unsigned bytes = (unsigned)(rows * n1 * sizeof(T));
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            bulk_prefetch_l2(pv + j * N + base, bytes);
+            bulk_prefetch_l2(r + j * N + base, bytes);
+        }
+        bulk_prefetch_l2(gidx + base, (unsigned)(rows * n1 * sizeof(int)));
+    }
     __device__ __forceinline__ void node2(const RowCtx<T> &c, int rl, int i1, const T *in0, const T *in1, T *o0,
                                           T *o1) const
     {

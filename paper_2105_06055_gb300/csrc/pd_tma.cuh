@@ -93,6 +93,13 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned b
                  : "memory");
 }
 
+// Bulk prefetch of [src, src + bytes) into L2 (16-byte aligned address, size a
+// multiple of 16; no shared memory, no completion to wait for)
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // 1D bulk copy shared -> global
 __device__ __forceinline__ void bulk_store(void *dst, const void *src, unsigned bytes)
 {
