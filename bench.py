@@ -126,12 +126,12 @@ class ClockSampler:
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
 # committed ncu summaries; None when the kernel changed after the capture.
 MEASURED_TRAFFIC = {
-    "rows_inv": (99.6e6, "profiles/k_rows_EpiCG_static_solve_128cube.md"),
+    "rows_inv": (100.9e6, "profiles/k_rows_EpiCG_static_solve_128cube.md"),
     "last_axis": (42.3e6, "profiles/k_rows_EpiCG_static_solve_128cube.md"),
-    "rows_fwd": (145.0e6, "profiles/k_rows_EpiCG_static_solve_128cube.md"),
-    "force256_rows_fwd": (367.5e6, "profiles/force_eval_256cube.md"),
-    "force256_last_axis": (495.1e6, "profiles/force_eval_256cube.md"),
-    "force256_rows_inv": (562.3e6, "profiles/force_eval_256cube.md"),
+    "rows_fwd": (146.4e6, "profiles/k_rows_EpiCG_static_solve_128cube.md"),
+    "force256_rows_fwd": (368.0e6, "profiles/force_eval_256cube.md"),
+    "force256_last_axis": (495.4e6, "profiles/force_eval_256cube.md"),
+    "force256_rows_inv": (563.5e6, "profiles/force_eval_256cube.md"),
 }
 
 
@@ -160,14 +160,18 @@ def pass_bytes(kind, N, nbound, d=3, nc=6):
       last_axis: read + write d spectra, folded kernel table (nc floats per
                  folded mode, (n/2+1)^3 ~ N/8 modes)
       rows_inv : read d spectra (4d), p, r (8d), mask bits (1); write q (4d);
-                 boundary list (32 B per boundary node) and p there (4d)"""
+                 boundary list (32 B per boundary node) and p there (4d)
+      plane_fwd, plane_inv: the same bytes as rows_fwd, rows_inv (their x2
+                 transforms stay in shared memory)"""
     per_node = {
         "rows_fwd": 32 * d + 1,
+        "plane_fwd": 32 * d + 1,
         "cols_x2": 8 * d,
         "last_axis": 8 * d + nc * 4 / 8.0,
         "rows_inv": 16 * d + 1,
+        "plane_inv": 16 * d + 1,
     }[kind]
-    extra = (32 + 4 * d) * nbound if kind == "rows_inv" else 0
+    extra = (32 + 4 * d) * nbound if kind in ("rows_inv", "plane_inv") else 0
     return per_node * N + extra
 
 
@@ -191,6 +195,8 @@ def run_native(args, rank, world):
     chi = torch.tensor(cfg["chi"], device=dev)
     chi_om = torch.tensor(cfg["chi_omega"], device=dev)
     plan = pd.Plan(prob, chi, chi_om)
+    if args.plane_mask is not None:
+        plan.set_plane_passes(args.plane_mask)
     if args.tuning:
         plan.set_tuning(*[int(v) for v in args.tuning.split(",")])
         tuning = plan.tuning
@@ -219,7 +225,8 @@ def run_native(args, rank, world):
     calib = plan.profile_read()
     plan.profile(False)
     dom_name = max(calib.items(), key=lambda kv: kv[1][0])[0]
-    evals_per_solve = calib["rows_inv"][1]  # one inverse row pass per force evaluation
+    # one inverse row or plane pass per force evaluation
+    evals_per_solve = calib["rows_inv"][1] + calib.get("plane_inv", (0.0, 0))[1]
 
     uuid = None
     try:
@@ -330,6 +337,8 @@ def run_native(args, rank, world):
             "gpu_launches": int(launches),
             "clocks": clocks,
             "tuning": tuning,
+            # halves of the CG iteration that ran as plane passes (bit 0 forward, bit 1 inverse)
+            "plane_passes": (1 if calib.get("plane_fwd", (0, 0))[1] else 0) | (2 if calib.get("plane_inv", (0, 0))[1] else 0),
         }
     plan.close()
     return result, cfg
@@ -631,6 +640,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="static", choices=["static", "batched", "force"])
     ap.add_argument("--no-autotune", action="store_true", help="skip the pass autotuner (built-in tile heuristic)")
+    ap.add_argument("--plane-mask", type=int, default=None, metavar="M",
+                    help="static solve: halves of the CG iteration run as fused x1-x2 plane passes (bit 0 forward, "
+                         "bit 1 inverse; 0 = row and column passes; default: the library's)")
     ap.add_argument("--tuning", default="", metavar="ROWS,WX2,WLAST,SCHED[,STAGES[,STAGES_INV]]",
                     help="pin a pass configuration instead of autotuning (e.g. the one a tuned run reported)")
     ap.add_argument("--specimens", type=int, default=64)
@@ -651,6 +663,8 @@ def main():
         dev = torch.device("cuda")
         plan = pd.Plan(pd.Problem(shape=cfg["shape"], delta=DELTA, model=pd.PD_LIN_STATE, nu=0.25, fp64=False),
                        torch.tensor(cfg["chi"], device=dev), torch.tensor(cfg["chi_omega"], device=dev))
+        if args.plane_mask is not None:
+            plan.set_plane_passes(args.plane_mask)
         if args.tuning:
             plan.set_tuning(*[int(v) for v in args.tuning.split(",")])
         elif not args.no_autotune:

@@ -444,9 +444,28 @@ double pd_plan_critical_energy(const pd_plan *plan);
 pd_status pd_plan_set_affine_split(pd_plan *plan, int on);
 
 /*
+ * pd_plan_set_plane_passes -- pass layout of the FP32 CG iteration of
+ * pd_solve_static on cubes of 32^3, 64^3 and 128^3. Bit 0 of mask: the
+ * forward half (CG update, x1 and x2 transforms), bit 1: the inverse half
+ * (x2 and x1 inverse transforms, CG epilogue) run as plane passes, where the
+ * transforms of one field of one x1-x2 plane run in one block
+ * (pd_plan_profile kinds 4 and 5) and the spectra make no round trip between
+ * them; a clear bit runs that half as a row pass and a column pass along x2
+ * (kinds 0, 1, 3), as on every other shape. Same operator either way (the
+ * transforms and epilogues do the same arithmetic). Default 1: on the 128^3
+ * cube with cavity the forward plane pass is faster than its row and column
+ * passes, while the inverse plane pass is slower (its blocks of the planes
+ * inside the body's faces carry a whole plane of boundary nodes each);
+ * pd_plan_autotune_solve times 1, 0 and 3 and keeps the fastest. PD_ERR_ARG
+ * for a null plan or a mask outside 0..3.
+ */
+pd_status pd_plan_set_plane_passes(pd_plan *plan, int mask);
+
+/*
  * pd_plan_inject_stall -- test hook for the failure handling of bounded
- * device waits. The next row pass of the given kind launched on the plan
- * (0: forward, 3: inverse; see pd_plan_profile) has its first block issue none
+ * device waits. The next pass of the given kind launched on the plan
+ * (0: forward row pass, 3: inverse row pass, 5: inverse plane pass of the
+ * FP32 CG; see pd_plan_profile) has its first block issue none
  * of its bulk copies, so that block's wait on its copy barrier gives up after
  * the library's limit (2 s), sets the plan's device status word and the block
  * exits; the rest of the pass runs normally. pd_solve_static then returns
@@ -484,6 +503,9 @@ int64_t pd_plan_boundary_nodes(const pd_plan *plan);
  *   1 column pass along x2 (3D), forward or inverse
  *   2 last-axis pass (forward transform, spectral combine, inverse transform)
  *   3 row pass, inverse (x1 transform + epilogue)
+ *   4 plane pass, forward (CG prologue + x1 and x2 transforms; FP32 CG on cubes
+ *     of 32^3, 64^3 and 128^3, whose x1-x2 plane of one field fits in shared memory)
+ *   5 plane pass, inverse (x2 and x1 transforms + CG epilogue; same cubes)
  * Reading synchronises on the recorded events. Enabling resets the counters.
  */
 pd_status pd_plan_profile(pd_plan *plan, int mask);

@@ -570,8 +570,9 @@ pd_status pd_plan_set_affine_split(pd_plan *p, int on)
 
 pd_status pd_plan_inject_stall(pd_plan *p, int kind)
 {
-    if (!p || (kind != 0 && kind != 3)) {
-        set_error("pd_plan_inject_stall: null plan or kind not 0 (forward row pass) or 3 (inverse row pass)");
+    if (!p || (kind != 0 && kind != 3 && kind != 5)) {
+        set_error("pd_plan_inject_stall: null plan or kind not 0 (forward row pass), 3 (inverse row pass) or 5 "
+                  "(inverse plane pass)");
         return PD_ERR_ARG;
     }
     const int v = kind + 1;

@@ -186,7 +186,7 @@ struct pd_plan {
     pd::HorizonDev hdev;  // device horizon tables (views into hoff)
     // per-pass timing (diagnostics): event pairs around each FFT-pass launch
     static constexpr int kEvPool = 1024;
-    static constexpr int kKinds = 4;
+    static constexpr int kKinds = 6;
     cudaEvent_t ev[2 * kEvPool] = {};
     int ev_kind[kEvPool] = {};
     int ev_used = 0;
@@ -206,6 +206,8 @@ struct pd_plan {
     cudaEvent_t ev_fork[2] = {nullptr, nullptr};
     int no_fork = 0;  // set while capturing into conditional-node bodies (single stream there)
     int pdl = 1;      // pass kernels launched as programmatic dependents (griddepcontrol)
+    int plane_passes = 1;  // FP32 CG on cubes up to 128^3: halves of the iteration whose x1 and x2
+                           // transforms run fused in plane passes (bit 0 forward, bit 1 inverse)
     double prof_ms[kKinds] = {};
     // pass configuration picked by pd_plan_autotune (0: built-in heuristic)
     int tune_rows = 0;     // rows per row-pass block
@@ -315,7 +317,7 @@ inline void col_cfg(const pd_plan *p, int axis, bool last, int FB, int FI, int N
 pd_status set_smem_attr(const void *func, size_t smem);
 
 // pass kinds for the timing facility
-enum PassKind { PASS_ROWS_FWD = 0, PASS_COLS = 1, PASS_LAST = 2, PASS_ROWS_INV = 3 };
+enum PassKind { PASS_ROWS_FWD = 0, PASS_COLS = 1, PASS_LAST = 2, PASS_ROWS_INV = 3, PASS_PLANE_FWD = 4, PASS_PLANE_INV = 5 };
 pd_status prof_harvest(pd_plan *p);
 pd_status prof_harvest_range(pd_plan *p, int b, int e);
 

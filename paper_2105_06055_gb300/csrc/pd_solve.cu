@@ -13,7 +13,9 @@
 // runs in FP64. CG inner products are accumulated per thread in compensated
 // FP32 (two-sum) and per block in FP64.
 //
-// One CG iteration is five fused passes and one small kernel; the vector
+// One CG iteration is five fused passes and one small kernel (three passes
+// and the small kernel on cubes of up to 128^3 in FP32, where the plane passes
+// of pd_plane.cuh fuse the x1 and x2 transforms); the vector
 // updates of iteration i are applied in the first pass of iteration i+1, so
 // all reductions of an iteration happen in one place (r.q and q.q give the
 // next r.r before r is updated: (r - alpha q).(r - alpha q) = rr - 2 alpha rq
@@ -39,6 +41,14 @@ namespace {
 
 constexpr int kChunk = 16;       // CG iterations per graph replay
 constexpr int kPartB = 14400;    // fused iteration: r.r partials below, (p.q, r.q, q.q) triples above
+}  // namespace
+}  // namespace pd
+
+#include "pd_plane.cuh"
+
+namespace pd {
+namespace {
+
 constexpr int kHostStatus = 32;  // slot of the pinned host scalars that receives the device status word
 
 // rr = sum of the first pass's partials; alpha, beta from the second pass's triples
@@ -343,6 +353,30 @@ struct EpiCG {
 static_assert(op_min_blocks<EpiCG<float, 3>>::value == EpiCG<float, 3>::kMinBlocks,
               "the row kernel must apply the epilogue's register cap");
 
+// log2(n1 / 2) when the plane passes apply (FP32 cubes of 32^3, 64^3 or 128^3:
+// one field of an x1-x2 plane fits in shared memory), else 0
+template <typename T, int D>
+int plane_lgh(const pd_plan *p)
+{
+    if (!std::is_same_v<T, float> || D != 3 || p->dim != 3 || p->n1 != p->n2 || !p->plane_passes) return 0;
+    if (D * p->n3 > kPartB) return 0;
+    return p->n1 == 32 ? 4 : p->n1 == 64 ? 5 : p->n1 == 128 ? 6 : 0;
+}
+
+template <typename T, int D, int LGH>
+pd_status launch_plane(pd_plan *p, bool fwd, const PlaneArgs<T> &pa, cudaStream_t st)
+{
+    using S = PlaneShape<T, LGH, LGH + 1>;
+    const auto kern = fwd ? k_plane_cg_fwd<T, D, LGH, LGH + 1> : k_plane_cg_inv<T, D, LGH, LGH + 1>;
+    PD_TRY(set_smem_attr((const void *)kern, S::smem));
+    PD_TRY(prof_begin(p, fwd ? PASS_PLANE_FWD : PASS_PLANE_INV, st));
+    PD_TRY(launch_k(p->pdl != 0, kern, dim3((unsigned)(D * p->n3)), dim3(S::THREADS), S::smem, st, pa,
+                    tw_buf<T>(p)));
+    PD_TRY(prof_end(p, st));
+    p->launches++;
+    return PD_OK;
+}
+
 struct Solver {
     pd_plan *p;
     cudaStream_t st;
@@ -394,6 +428,21 @@ struct Solver {
         return PD_OK;
     }
 
+    template <typename T, int D>
+    pd_status plane_pass(int lgh, bool fwd, const PlaneArgs<T> &pa)
+    {
+        if constexpr (std::is_same_v<T, float> && D == 3) {
+            switch (lgh) {
+                case 4: return launch_plane<T, D, 4>(p, fwd, pa, st);
+                case 5: return launch_plane<T, D, 5>(p, fwd, pa, st);
+                case 6: return launch_plane<T, D, 6>(p, fwd, pa, st);
+                default: break;
+            }
+        }
+        set_error("plane pass for an unsupported shape");
+        return PD_ERR_SIZE;
+    }
+
     // one CG iteration (enqueued; no host synchronisation)
     template <typename T, int D>
     pd_status iteration()
@@ -417,15 +466,29 @@ struct Solver {
         const int64_t fs = p->N / 2;
         const Model<T> m = model_view<T>(p);
         unsigned gpro = 0, gepi = 0;
-        ProCG<T, D> pro{e, r, pv, q, p->mbits, p->red, p->N, p->n1, spec, fs};
-        PD_TRY(launch_rows<T>(p, pro, st, &gpro));
-        if (D == 3) PD_TRY((col_pass<T, D>(p, 0, false, st)));
         const int ob = D == 3 ? D : 0;
+        const int lgh = plane_lgh<T, D>(p);
+        const bool plane_fwd = lgh && (p->plane_passes & 1), plane_inv = lgh && (p->plane_passes & 2);
+        const PlaneArgs<T> pa{e, r, pv, q, p->mbits, spec, fs, p->N, p->red, m.gent, p->goff, p->lgl,
+                              p->dev_status, p->inject};
+        if (plane_fwd) {
+            PD_TRY((plane_pass<T, D>(lgh, true, pa)));
+            gpro = (unsigned)(D * p->n3);
+        } else {
+            ProCG<T, D> pro{e, r, pv, q, p->mbits, p->red, p->N, p->n1, spec, fs};
+            PD_TRY(launch_rows<T>(p, pro, st, &gpro));
+            if (D == 3) PD_TRY((col_pass<T, D>(p, 0, false, st)));
+        }
         CombForce<T, D, false> cmb{m, ob};
         PD_TRY(launch_cols<T>(p, cmb, D == 3 ? 2 : 1, true, D, st));
-        if (D == 3) PD_TRY((col_pass<T, D>(p, ob, true, st)));
-        EpiCG<T, D> epi{pv, r, p->mbits, m.gent, p->gidx, q, p->red, p->N, p->n1, spec + ob * fs, fs};
-        PD_TRY(launch_rows<T>(p, epi, st, &gepi));
+        if (plane_inv) {
+            PD_TRY((plane_pass<T, D>(lgh, false, pa)));
+            gepi = (unsigned)(D * p->n3);
+        } else {
+            if (D == 3) PD_TRY((col_pass<T, D>(p, ob, true, st)));
+            EpiCG<T, D> epi{pv, r, p->mbits, m.gent, p->gidx, q, p->red, p->N, p->n1, spec + ob * fs, fs};
+            PD_TRY(launch_rows<T>(p, epi, st, &gepi));
+        }
         if (gpro > (unsigned)kPartB || gepi > (unsigned)kPartB) {
             set_error("pd_solve_static: %u / %u row blocks exceed the reduction buffer", gpro, gepi);
             return PD_ERR_SIZE;

@@ -5,8 +5,9 @@
 // force evaluation (pd_plan_autotune) or a chunk of its static solver's CG
 // iterations (pd_plan_autotune_solve) on its workspace with CUDA events.
 //
-// The search covers rows x stages jointly, then the inverse passes' stages,
-// the schedule, the last-axis width and the x2 width one at a time; each candidate is timed as
+// The search covers (for the solver on FP32 cubes up to 128^3) the plane-pass
+// layout of the CG iteration, then rows x stages jointly, the inverse passes'
+// stages, the schedule, the last-axis width and the x2 width one at a time; each candidate is timed as
 // the median of nine force evaluations after three untimed ones. Candidates
 // are limited to the shapes the passes accept (powers of two; at least one
 // warp per row block; shared memory within the pass's own limit, which the
@@ -106,6 +107,12 @@ pd_status tune_plan(pd_plan *p, cudaStream_t caller, int target = 0)
         }
         *knob = best;
     };
+    // static solve on an FP32 cube with plane passes: which halves of the CG
+    // iteration run as plane passes (bit 0 forward, bit 1 inverse) first, as
+    // the row knobs below only act on the halves that stay row passes
+    if (target == 1 && p->dim == 3 && !p->prob.fp64 && !p->state_based && p->n1 == p->n2 &&
+        (p->n1 == 32 || p->n1 == 64 || p->n1 == 128))
+        best_of(&p->plane_passes, {1, 0, 3});
     // rows per tile and pipeline depth jointly (they interact through shared
     // memory), then the schedule and the column widths one at a time
     const int H = p->h;
@@ -213,6 +220,17 @@ extern "C" pd_status pd_batch_autotune(pd_batch *B, void *stream)
         }
     }
     pd_batch_invalidate(B);
+    return PD_OK;
+}
+
+extern "C" pd_status pd_plan_set_plane_passes(pd_plan *p, int on)
+{
+    if (!p || on < 0 || on > 3) {
+        set_error("pd_plan_set_plane_passes: null plan or mask not in 0..3");
+        return PD_ERR_ARG;
+    }
+    p->plane_passes = on;
+    drop_graphs(p);
     return PD_OK;
 }
 

@@ -32,10 +32,10 @@ EXPORTS = ["pd_plan_create", "pd_plan_destroy", "pd_kernel_spectrum", "pd_force"
            "pd_solve_dr", "pd_plan_create_batched", "pd_batch_size", "pd_batch_plan", "pd_solve_dr_batched",
            "pd_batch_destroy", "pd_plan_autotune", "pd_batch_autotune", "pd_plan_tuning",
            "pd_plan_set_energy_mode", "pd_plan_set_tuning", "pd_plan_autotune_solve", "pd_plan_critical_energy",
-           "pd_plan_inject_stall", "pd_plan_set_affine_split", "pd_step_verlet_ramp",
+           "pd_plan_inject_stall", "pd_plan_set_affine_split", "pd_plan_set_plane_passes", "pd_step_verlet_ramp",
            "pd_verlet_adjoint_workspace", "pd_verlet_loss_grad", "pd_solve_mirror"]
 
-PASS_KINDS = {0: "rows_fwd", 1: "cols_x2", 2: "last_axis", 3: "rows_inv"}
+PASS_KINDS = {0: "rows_fwd", 1: "cols_x2", 2: "last_axis", 3: "rows_inv", 4: "plane_fwd", 5: "plane_inv"}
 
 
 class PDError(RuntimeError):
@@ -101,6 +101,8 @@ def load():
     lib.pd_plan_inject_stall.restype = I
     lib.pd_plan_set_affine_split.argtypes = [P, I]
     lib.pd_plan_set_affine_split.restype = I
+    lib.pd_plan_set_plane_passes.argtypes = [P, I]
+    lib.pd_plan_set_plane_passes.restype = I
     lib.pd_plan_profile.argtypes = [P, I]
     lib.pd_plan_profile.restype = I
     lib.pd_plan_profile_read.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(I64)]
@@ -456,14 +458,22 @@ class Plan:
     def boundary_nodes(self):
         return int(load().pd_plan_boundary_nodes(self._h))
 
+    def set_plane_passes(self, mask):
+        """FP32 CG on 32^3 / 64^3 / 128^3 cubes: which halves of the iteration run as
+        fused x1-x2 plane passes (bit 0 forward, bit 1 inverse; True = both, False =
+        neither: row and column passes) (pd_plan_set_plane_passes)."""
+        m = 3 if mask is True else 0 if mask is False else int(mask)
+        _check(load().pd_plan_set_plane_passes(self._h, m), "pd_plan_set_plane_passes")
+
     def set_affine_split(self, on: bool):
         """pd_force on fields with a large affine part: transform u - a (a the
         least-squares affine fit) and add the exact force of a (pd_plan_set_affine_split)."""
         _check(load().pd_plan_set_affine_split(self._h, 1 if on else 0), "pd_plan_set_affine_split")
 
     def inject_stall(self, kind: int):
-        """Failure-handling test hook (pd_plan_inject_stall): the next row pass
-        of this kind (0 forward, 3 inverse) has one block whose wait runs out."""
+        """Failure-handling test hook (pd_plan_inject_stall): the next pass of
+        this kind (0 forward row pass, 3 inverse row pass, 5 inverse plane pass)
+        has one block whose wait runs out."""
         _check(load().pd_plan_inject_stall(self._h, int(kind)), "pd_plan_inject_stall")
 
     @property

@@ -77,6 +77,39 @@ def test_static_2d_bond_fp64_with_prescribed_w(pdm, oracle):
     plan.close()
 
 
+@pytest.mark.parametrize("n", [32, 64])
+def test_plane_passes_match_row_passes(pdm, oracle, n):
+    """FP32 CG on a cube: every combination of fused x1-x2 plane passes and
+    row/column passes for the two halves of the iteration gives the same refined
+    solution; each meets the oracle's residual, and the profile shows which
+    passes ran."""
+    cfg = inputs.cube_with_cavity(n=n, radius_frac=0.2)
+    shape = cfg["shape"]
+    prob = pdm.Problem(shape=shape, delta=3.0, model=pdm.PD_LIN_STATE, nu=0.25, fp64=False)
+    ka, cb, _ = oracle.lps_constants(1.0, 0.25, 1.0, 3.0)
+    bn = np.linalg.norm(cfg["chi_omega"] * cfg["b"])
+    sols = {}
+    for mask in (3, 1, 2, 0):  # bit 0: forward half as a plane pass, bit 1: inverse half
+        plan = pdm.Plan(prob, _t(cfg["chi"], torch.uint8), _t(cfg["chi_omega"], torch.uint8))
+        plan.set_plane_passes(mask)
+        plan.profile(True)
+        u = torch.zeros((3,) + shape, dtype=torch.float64, device=DEV)
+        it, rel, st = plan.solve_static(u, _t(cfg["b"]), None, rtol=1e-9, max_iter=5000)
+        prof = plan.profile_read()
+        plan.close()
+        assert st == 0 and rel <= 1e-9
+        assert prof["plane_fwd"][1] == (it if mask & 1 else 0)
+        assert prof["plane_inv"][1] == (it if mask & 2 else 0)
+        # x2 column passes: one per CG half that is not a plane pass (plus the FP64 residuals')
+        assert prof["cols_x2"][1] >= (2 - (mask & 1) - (mask >> 1)) * it
+        ug = u.cpu().numpy()
+        res = oracle.static_residual(ug, cfg["chi"], cfg["chi_omega"], cfg["b"], 1.0, 3.0, ("lps", ka, cb))
+        assert np.linalg.norm(res) / bn <= 1.5e-9
+        sols[mask] = ug
+    for mask in (1, 2, 0):
+        assert _rel(sols[mask], sols[3]) < 1e-8
+
+
 def test_static_config2_full_size(pdm, oracle):
     """128^3 cube with spherical cavity, FP32 FFTs + FP64 refinement to 1e-8;
     the returned u is checked with the oracle's FP64 operator (residual) and

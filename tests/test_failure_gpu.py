@@ -2,7 +2,8 @@
 traps or hangs the GPU):
 
 * a bounded device wait that runs out: pd_plan_inject_stall makes one block of
-  the next row pass issue no copies, so its wait on the copy barrier gives up
+  the next row pass (or inverse plane pass of the FP32 CG) issue no copies, so
+  its wait on the copy barrier gives up
   after the library's limit and records the time-out in the plan's status
   word; pd_solve_static must return PD_ERR_TIMEOUT and the same plan must then
   solve normally;
@@ -53,9 +54,11 @@ def _solve_ok(pdm, plan, cfg, oracle):
     assert np.linalg.norm(res) / np.linalg.norm(cfg["chi_omega"] * cfg["b"]) <= 1.5e-8
 
 
-@pytest.mark.parametrize("kind", [0, 3])
+@pytest.mark.parametrize("kind", [0, 3, 5])
 def test_wait_time_out_is_reported_and_plan_stays_usable(pdm, oracle, kind):
     cfg, plan = _cube(pdm, fp64=False)
+    if kind == 5:
+        plan.set_plane_passes(3)  # the inverse half of the CG iteration as a plane pass
     plan.inject_stall(kind)
     u = torch.zeros((3,) + cfg["shape"], dtype=torch.float64, device=DEV)
     with pytest.raises(pdm.PDError, match="PD_ERR_TIMEOUT"):
