@@ -361,6 +361,13 @@ __global__ void k_gfill(int n1, int64_t nrows, const uint8_t *chi, const double 
     }
 }
 
+// gnode[e] = node of boundary entry e
+__global__ void k_gnode(const GEntry<float> *g, int64_t n, int *gnode)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) gnode[e] = (int)g[e].p;
+}
+
 // Body moments about the node (c0, c1, c2): Σ chi, Σ chi e_k, Σ chi e_k e_l
 // (e = i - c; order S0, e1, e2, e3, 11, 22, 33, 12, 13, 23), block partials.
 // The sums are of integers below 2^53, so they are exact in FP64.
@@ -644,7 +651,7 @@ void pd_plan_destroy(pd_plan *p)
 {
     if (!p) return;
     void *ptrs[] = {p->chi, p->chi_om, p->mbits, p->hoff, p->mhat64, p->mhat32, p->ghat64, p->ghat32, p->G64, p->G32,
-                    p->goff, p->gidx, p->gent64, p->gent32, p->aff_tab, p->aff_coef, p->chat64, p->chat32, p->nlb,
+                    p->goff, p->gidx, p->gnode, p->gpe, p->gent64, p->gent32, p->aff_tab, p->aff_coef, p->chat64, p->chat32, p->nlb,
                     p->qt64, p->m3inv64, p->qt32, p->m3inv32, p->tw64, p->tw32, p->spec32, p->spec64,
                     p->work, p->red};
     for (void *q : ptrs)
@@ -1014,6 +1021,14 @@ static pd_status plan_create_impl(const pd_problem *pr, const uint8_t *chi_B, co
         k_gfill<<<nblk(nr, 128), 128, 0, st>>>(n1, nr, p->chi, p->G64, nc, N, p->goff, (GEntry<double> *)p->gent64,
                                               (GEntry<float> *)p->gent32, p->gidx);
         PD_LAUNCH_CHECK();
+        if (dim == 3 && !pr->fp64 && n1 == n2 && (n1 == 32 || n1 == 64 || n1 == 128)) {
+            // FP32 cubes with plane passes: entry -> node, and the per-entry (G p) buffer
+            const int64_t ng = std::max<int64_t>(acc, 1);
+            PD_TRY(dalloc(p, &p->gnode, sizeof(int) * (size_t)ng));
+            PD_TRY(dalloc(p, &p->gpe, sizeof(float) * 3 * (size_t)ng));
+            k_gnode<<<nblk(ng, 256), 256, 0, st>>>((const GEntry<float> *)p->gent32, acc, p->gnode);
+            PD_LAUNCH_CHECK();
+        }
         PD_CUDA_TRY(cudaStreamSynchronize(st));
     }
     if (pr->model == PD_LIN_BOND || pr->model == PD_NONLIN_BOND) PD_TRY(affine_setup(p, st));

@@ -148,6 +148,9 @@ struct pd_plan {
     float *G32 = nullptr;
     int *goff = nullptr;           // nrows + 1: boundary-node list offsets per row
     int *gidx = nullptr;           // N: entry of the node in the boundary list, or -1
+    int *gnode = nullptr;          // [ngent] node of each boundary entry (plane-pass cubes only)
+    void *gpe = nullptr;           // [3][ngent] FP32 (G p) per boundary entry, written by the CG iteration
+                                   // while its last-axis pass runs (plane-pass cubes only)
     void *gent64 = nullptr;        // GEntry<double>[ngent]
     void *gent32 = nullptr;        // GEntry<float>[ngent]
     // affine split of pd_force (pd_plan_set_affine_split): per boundary entry the

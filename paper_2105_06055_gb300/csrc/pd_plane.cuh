@@ -8,15 +8,21 @@
 // shared memory, so each CG iteration is
 //   plane forward  : CG vector update, chi p, x1 R2C, x2 FFT      (one kernel)
 //   last axis      : x3 FFT, spectral multiply, inverse x3 FFT   (k_cols)
-//   plane inverse  : x2 inverse FFT, x1 C2R, L, q, inner products (one kernel)
+//   G p            : (G p) per boundary-list entry   (k_gp_entries, beside the last axis)
+//   plane inverse  : x2 inverse FFT, x1 C2R, L = chi y - G p, q, inner products
 //   finish         : alpha, beta
 // and the two column passes along x2 (a read and a write of every spectrum
 // each) disappear. A block's field is one displacement component j: the CG
 // vector updates act per component and the inner products are sums over
 // components, so a block adds its component's share to the partial sums. The
-// boundary term G p couples the components at boundary nodes only; the
-// inverse block walks its plane's part of the boundary list and reads the
-// other components of p there.
+// boundary term G p couples the components at boundary nodes only. It is
+// computed per entry of the boundary list on the plan's second stream while
+// the last-axis pass runs (p is final once the forward half is done), and the
+// inverse block only reads its plane's entries (node, (G p)_j): the boundary
+// nodes are far from evenly spread over the planes (every body node of the
+// planes inside the body's faces is one), and with the dependent loads of the
+// entry and of p at its node inside the inverse blocks, the blocks of those
+// planes held up the whole pass.
 //
 // Same arithmetic as the row ops ProCG / EpiCG and the column passes: the same
 // transforms (fft_ct), unpacking formulas and compensated sums.
@@ -37,8 +43,10 @@ struct PlaneArgs {
                             // 0..D-1, the inverse pass reads slots D..2D-1
     int64_t fs, N;
     double *red;            // reduction buffer: partials and scalars
-    const GEntry<T> *gent;  // boundary list, ordered by node
-    const int *goff;        // per row: first boundary-list entry of the row (nrows + 1 offsets)
+    const T *gpe;           // [D][nent] (G p) per boundary-list entry (k_gp_entries)
+    const int *gnode;       // [nent] node of each entry
+    const int *goff;        // per row: first entry of the row (nrows + 1 offsets; the list is ordered by node)
+    int64_t nent;
     int lgl;                // log2 of the plan's twiddle table length
     int *err;               // device status word
     int *inject;            // failure-handling test hook (see k_rows): kind 5 stalls the inverse plane pass
@@ -194,7 +202,6 @@ __global__ void __launch_bounds__(PlaneShape<T, LGH, LG2>::THREADS, 3)
 {
     using S = PlaneShape<T, LGH, LG2>;
     using V = typename vec2<T>::type;
-    static_assert(sizeof(GEntry<T>) % 16 == 0, "boundary entries are prefetched in 16-byte units");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     cx<T> *tws = reinterpret_cast<cx<T> *>(smem_raw);
     cx<T> *pl = reinterpret_cast<cx<T> *>(smem_raw + S::kTw);
@@ -220,16 +227,12 @@ __global__ void __launch_bounds__(PlaneShape<T, LGH, LG2>::THREADS, 3)
     const bool ok = mbar_wait(mbar, 0, a.err);
     if (__syncthreads_or(!ok)) return;  // no copy in flight: the stalled block issued none
     if (tid == 0) {
-        // p_j, r_j, the mask bytes and the plane's boundary entries towards L2
-        // while the plane is transformed (issued once the spectrum is in, so
-        // they do not compete with it)
+        // p_j, r_j and the mask bytes towards L2 while the plane is transformed
+        // (issued once the spectrum is in, so they do not compete with it)
         const unsigned nb = (unsigned)(S::n2 * S::n1 * sizeof(T));
         bulk_prefetch_l2(a.pv + (int64_t)j * a.N + pbase, nb);
         bulk_prefetch_l2(a.r + (int64_t)j * a.N + pbase, nb);
         bulk_prefetch_l2(a.bits + pbase, (unsigned)(S::n2 * S::n1));
-        const int e0 = a.goff[z * S::n2], e1 = a.goff[(z + 1) * S::n2];
-        for (int e = e0; e < e1; e += 2048)  // 64 KB pieces (32-byte entries)
-            bulk_prefetch_l2(a.gent + e, (unsigned)((e1 - e < 2048 ? e1 - e : 2048) * sizeof(GEntry<T>)));
     }
 
     // x2: inverse FFTs along the columns (IDFT = conj DFT conj)
@@ -252,48 +255,20 @@ __global__ void __launch_bounds__(PlaneShape<T, LGH, LG2>::THREADS, 3)
                                             false, false);
     }
 
-    // boundary term: (G p)_j of the plane's boundary nodes (entries of its
-    // rows are contiguous in the list) subtracted from y_j in shared memory;
-    // the two nodes of a packed slot are its two halves, so no two entries
-    // write the same word. Entries go in batches of kB per thread, every load
-    // of a batch issued before any is used (an entry's p loads depend on its
-    // node index).
+    // boundary term: (G p)_j of the plane's boundary entries (contiguous in the
+    // list) subtracted from y_j in shared memory; the two nodes of a packed slot
+    // are its two halves, so no two entries write the same word
     {
-        constexpr int kB = 4;
         const int e0 = a.goff[z * S::n2], e1 = a.goff[(z + 1) * S::n2];
-#pragma unroll 1
-        for (int eb = e0 + tid; eb < e1; eb += kB * S::THREADS) {
-            GEntry<T> ge[kB];
-#pragma unroll
-            for (int u = 0; u < kB; ++u) {
-                const int e = eb + u * S::THREADS;
-                if (e < e1) ge[u] = a.gent[e];
-            }
-            T x[kB][D];
-#pragma unroll
-            for (int u = 0; u < kB; ++u)
-                if (eb + u * S::THREADS < e1) {
-#pragma unroll
-                    for (int k = 0; k < D; ++k) x[u][k] = a.pv[(int64_t)k * a.N + ge[u].p];
-                }
-#pragma unroll
-            for (int u = 0; u < kB; ++u) {
-                if (eb + u * S::THREADS >= e1) break;
-                T y[D];
-#pragma unroll
-                for (int k = 0; k < D; ++k) y[k] = T(0);
-                sym_apply<T, D>(ge[u].g, x[u], y);
-                T gj = T(0);
-#pragma unroll
-                for (int k = 0; k < D; ++k)
-                    if (k == j) gj = y[k];  // unrolled: no indexing by the run-time j
-                const int nd = (int)(ge[u].p - pbase);  // node within the plane
-                cx<T> &w = pl[(nd >> (LGH + 1)) * S::PITCH + ((nd & (S::n1 - 1)) >> 1)];
-                if (nd & 1)
-                    w.y += gj;  // the odd node of the slot holds -Im w
-                else
-                    w.x -= gj;
-            }
+        const T *gj = a.gpe + (int64_t)j * a.nent;
+        for (int e = e0 + tid; e < e1; e += S::THREADS) {
+            const int nd = (int)(a.gnode[e] - pbase);  // node within the plane
+            const T g = gj[e];
+            cx<T> &w = pl[(nd >> (LGH + 1)) * S::PITCH + ((nd & (S::n1 - 1)) >> 1)];
+            if (nd & 1)
+                w.y += g;  // the odd node of the slot holds -Im w
+            else
+                w.x -= g;
         }
         __syncthreads();
     }
@@ -331,6 +306,26 @@ __global__ void __launch_bounds__(PlaneShape<T, LGH, LG2>::THREADS, 3)
         o[0] = t[0];
         o[1] = t[1];
         o[2] = t[2];
+    }
+}
+
+// (G p) of every boundary-list entry, component-major: gpe[j nent + e] (the
+// same products and order as the row passes' boundary term).
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_gp_entries(const GEntry<T> *__restrict__ gent, int64_t nent,
+                                                    const T *__restrict__ pv, int64_t N, T *__restrict__ gpe)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nent; e += (int64_t)gridDim.x * blockDim.x) {
+        const GEntry<T> ge = gent[e];
+        T x[D], y[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            x[k] = pv[(int64_t)k * N + ge.p];
+            y[k] = T(0);
+        }
+        sym_apply<T, D>(ge.g, x, y);
+#pragma unroll
+        for (int k = 0; k < D; ++k) gpe[(int64_t)k * nent + e] = y[k];
     }
 }
 

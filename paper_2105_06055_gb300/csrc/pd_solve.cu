@@ -358,7 +358,8 @@ static_assert(op_min_blocks<EpiCG<float, 3>>::value == EpiCG<float, 3>::kMinBloc
 template <typename T, int D>
 int plane_lgh(const pd_plan *p)
 {
-    if (!std::is_same_v<T, float> || D != 3 || p->dim != 3 || p->n1 != p->n2 || !p->plane_passes) return 0;
+    if (!std::is_same_v<T, float> || D != 3 || p->dim != 3 || p->n1 != p->n2 || !p->plane_passes || !p->gnode)
+        return 0;
     if (D * p->n3 > kPartB) return 0;
     return p->n1 == 32 ? 4 : p->n1 == 64 ? 5 : p->n1 == 128 ? 6 : 0;
 }
@@ -469,8 +470,8 @@ struct Solver {
         const int ob = D == 3 ? D : 0;
         const int lgh = plane_lgh<T, D>(p);
         const bool plane_fwd = lgh && (p->plane_passes & 1), plane_inv = lgh && (p->plane_passes & 2);
-        const PlaneArgs<T> pa{e, r, pv, q, p->mbits, spec, fs, p->N, p->red, m.gent, p->goff, p->lgl,
-                              p->dev_status, p->inject};
+        const PlaneArgs<T> pa{e, r, pv, q, p->mbits, spec, fs, p->N, p->red, (const T *)p->gpe, p->gnode, p->goff,
+                              p->ngent, p->lgl, p->dev_status, p->inject};
         if (plane_fwd) {
             PD_TRY((plane_pass<T, D>(lgh, true, pa)));
             gpro = (unsigned)(D * p->n3);
@@ -478,6 +479,20 @@ struct Solver {
             ProCG<T, D> pro{e, r, pv, q, p->mbits, p->red, p->N, p->n1, spec, fs};
             PD_TRY(launch_rows<T>(p, pro, st, &gpro));
             if (D == 3) PD_TRY((col_pass<T, D>(p, 0, false, st)));
+        }
+        if (plane_inv && p->ngent > 0) {
+            // (G p) per boundary entry for the inverse plane pass, on the second
+            // stream beside the last-axis pass (joined by that pass's join)
+            const bool fork = p->aux_stream && !p->no_fork;
+            cudaStream_t gs = fork ? p->aux_stream : st;
+            if (fork) {
+                PD_CUDA_TRY(cudaEventRecord(p->ev_fork[0], st));
+                PD_CUDA_TRY(cudaStreamWaitEvent(gs, p->ev_fork[0], 0));
+            }
+            const unsigned gb = (unsigned)std::min<int64_t>((p->ngent + 255) / 256, 4 * (int64_t)p->nsm);
+            k_gp_entries<T, D><<<gb, 256, 0, gs>>>(m.gent, p->ngent, (const T *)pv, p->N, (T *)p->gpe);
+            PD_LAUNCH_CHECK();
+            p->launches++;
         }
         CombForce<T, D, false> cmb{m, ob};
         PD_TRY(launch_cols<T>(p, cmb, D == 3 ? 2 : 1, true, D, st));
