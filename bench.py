@@ -126,9 +126,10 @@ class ClockSampler:
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
 # committed ncu summaries; None when the kernel changed after the capture.
 MEASURED_TRAFFIC = {
-    "rows_inv": (100.9e6, "profiles/k_rows_EpiCG_static_solve_128cube.md"),
-    "last_axis": (42.3e6, "profiles/k_rows_EpiCG_static_solve_128cube.md"),
-    "rows_fwd": (146.4e6, "profiles/k_rows_EpiCG_static_solve_128cube.md"),
+    "plane_fwd": (143.2e6, "profiles/cg_iteration_kernels_static_solve_128cube.md"),
+    "rows_inv": (101.2e6, "profiles/cg_iteration_kernels_static_solve_128cube.md"),
+    "last_axis": (42.3e6, "profiles/cg_iteration_kernels_static_solve_128cube.md"),
+    "rows_fwd": (146.4e6, "profiles/cg_iteration_kernels_static_solve_128cube.md"),
     "force256_rows_fwd": (368.0e6, "profiles/force_eval_256cube.md"),
     "force256_last_axis": (495.4e6, "profiles/force_eval_256cube.md"),
     "force256_rows_inv": (563.5e6, "profiles/force_eval_256cube.md"),
