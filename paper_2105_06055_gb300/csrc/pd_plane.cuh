@@ -141,25 +141,35 @@ __global__ void __launch_bounds__(PlaneShape<T, LGH, LG2>::THREADS, 3)
 
     const int64_t base = (int64_t)z * S::n2 * S::n1 + (int64_t)j * a.N;
     const T alpha = (T)a.red[kRedScal + S_ALPHA], beta = (T)a.red[kRedScal + S_BETA];
-    T *e = a.e + base, *r = a.r + base, *pv = a.pv + base;
-    const T *q = a.q + base;
-    const uint8_t *bits = a.bits + (int64_t)z * S::n2 * S::n1;
+    T *__restrict__ e = a.e + base;
+    T *__restrict__ r = a.r + base;
+    T *__restrict__ pv = a.pv + base;
+    const T *__restrict__ q = a.q + base;
+    const uint8_t *__restrict__ bits = a.bits + (int64_t)z * S::n2 * S::n1;
     DSum acc;
-    // nodes 2 idx, 2 idx + 1 of the plane (row idx >> LGH, packed slot idx & (H - 1))
+    // nodes 4 k ... 4 k + 3 of the plane: packed slots 2 k, 2 k + 1 of row 2 k >> LGH
+    static_assert(std::is_same_v<T, float>, "16-byte vector accesses of FP32 fields");
 #pragma unroll 2
-    for (int idx = tid; idx < S::n2 * S::H; idx += S::THREADS) {
-        const int i = 2 * idx;
-        const uchar2 b = *reinterpret_cast<const uchar2 *>(bits + i);
-        const V ee = load2(e + i), rr = load2(r + i), pp = load2(pv + i), qq = load2(q + i);
-        store2(e + i, ee.x + alpha * pp.x, ee.y + alpha * pp.y);
-        const T ra = rr.x - alpha * qq.x, rb = rr.y - alpha * qq.y;
-        store2(r + i, ra, rb);
-        acc.add_prod(ra, ra);
-        acc.add_prod(rb, rb);
-        const T pa = ra + beta * pp.x, pb = rb + beta * pp.y;
-        store2(pv + i, pa, pb);
-        pl[(idx >> LGH) * S::PITCH + (idx & (S::H - 1))] =
-            mk((b.x & 1) ? pa : T(0), (b.y & 1) ? pb : T(0));
+    for (int k = tid; k < S::n2 * S::H / 2; k += S::THREADS) {
+        const int i = 4 * k;
+        const uchar4 b = *reinterpret_cast<const uchar4 *>(bits + i);
+        const float4 ee = *reinterpret_cast<const float4 *>(e + i), rr = *reinterpret_cast<const float4 *>(r + i);
+        const float4 pp = *reinterpret_cast<const float4 *>(pv + i), qq = *reinterpret_cast<const float4 *>(q + i);
+        *reinterpret_cast<float4 *>(e + i) =
+            make_float4(ee.x + alpha * pp.x, ee.y + alpha * pp.y, ee.z + alpha * pp.z, ee.w + alpha * pp.w);
+        const float4 rn = make_float4(rr.x - alpha * qq.x, rr.y - alpha * qq.y, rr.z - alpha * qq.z,
+                                      rr.w - alpha * qq.w);
+        *reinterpret_cast<float4 *>(r + i) = rn;
+        acc.add_prod(rn.x, rn.x);
+        acc.add_prod(rn.y, rn.y);
+        acc.add_prod(rn.z, rn.z);
+        acc.add_prod(rn.w, rn.w);
+        const float4 pn = make_float4(rn.x + beta * pp.x, rn.y + beta * pp.y, rn.z + beta * pp.z,
+                                      rn.w + beta * pp.w);
+        *reinterpret_cast<float4 *>(pv + i) = pn;
+        const int slot = 2 * k;
+        *reinterpret_cast<float4 *>(&pl[(slot >> LGH) * S::PITCH + (slot & (S::H - 1))]) =
+            make_float4((b.x & 1) ? pn.x : 0.f, (b.y & 1) ? pn.y : 0.f, (b.z & 1) ? pn.z : 0.f, (b.w & 1) ? pn.w : 0.f);
     }
     __syncthreads();
 
