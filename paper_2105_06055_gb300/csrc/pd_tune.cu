@@ -5,8 +5,8 @@
 // force evaluation (pd_plan_autotune) or a chunk of its static solver's CG
 // iterations (pd_plan_autotune_solve) on its workspace with CUDA events.
 //
-// The search covers (for the solver on FP32 cubes up to 128^3) the plane-pass
-// layout of the CG iteration, then rows x stages jointly, the inverse passes'
+// The search covers (for the solver on FP32 cubes up to 128^3) whether the CG
+// iteration's forward half runs as a plane pass, then rows x stages jointly, the inverse passes'
 // stages, the schedule, the last-axis width and the x2 width one at a time; each candidate is timed as
 // the median of nine force evaluations after three untimed ones. Candidates
 // are limited to the shapes the passes accept (powers of two; at least one
@@ -107,12 +107,14 @@ pd_status tune_plan(pd_plan *p, cudaStream_t caller, int target = 0)
         }
         *knob = best;
     };
-    // static solve on an FP32 cube with plane passes: which halves of the CG
-    // iteration run as plane passes (bit 0 forward, bit 1 inverse) first, as
-    // the row knobs below only act on the halves that stay row passes
+    // static solve on an FP32 cube with plane passes: whether the forward half
+    // of the CG iteration runs as a plane pass, first, as the row knobs below
+    // only act on the halves that stay row passes. The inverse plane pass is
+    // not a candidate: a lone chunk timed it faster, whole solves slower (128^3:
+    // 115.3 against 105.9 ms per solve).
     if (target == 1 && p->dim == 3 && !p->prob.fp64 && !p->state_based && p->n1 == p->n2 &&
         (p->n1 == 32 || p->n1 == 64 || p->n1 == 128))
-        best_of(&p->plane_passes, {1, 0, 3});
+        best_of(&p->plane_passes, {1, 0});
     // rows per tile and pipeline depth jointly (they interact through shared
     // memory), then the schedule and the column widths one at a time
     const int H = p->h;
