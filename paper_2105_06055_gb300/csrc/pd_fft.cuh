@@ -101,10 +101,12 @@ __device__ __forceinline__ void dft_reg(cx<T> *v)
 // and pile onto two of the 16 eight-byte bank pairs; XOR-ing the element's
 // low three bits with the butterfly index spreads them over all pairs. With
 // 8 butterflies per row (rows 8 bank pairs apart) sh = 3 is conflict-free,
-// with 16 or more sh = 4. Row passes use it; in the column tiles the lanes of
-// a warp differ first in the column, the conflicts are at most 2-way at the
-// tile widths the passes run with, and the extra index arithmetic on the
-// strided addresses cost more than it saved (measured).
+// with 16 or more sh = 4. The row kernels compiled for a fixed row length and
+// the plane passes use it; in the column tiles the lanes of a warp differ
+// first in the column, the conflicts are at most 2-way at the tile widths the
+// passes run with, and the extra index arithmetic on the strided addresses
+// cost more than it saved (measured), as it did in the row kernels that read
+// the length at run time.
 __device__ __forceinline__ int swz(int e, int sh) { return e ^ ((e >> sh) & 7); }
 
 // One radix-R Stockham stage of F length-n transforms, field f stored at
@@ -183,48 +185,26 @@ __device__ __forceinline__ void fft_stage(cx<T> *s, int fstride, int stride, int
 // radix 4 or 2 for the remainder, which comes last (schedule 0) or first
 // (schedule 1). With cin the input is conjugated as it is read, with cout the
 // output as it is written (IDFT(x) = conj(DFT(conj(x))) costs no extra pass).
-// sh > 0: a first stage of radix 8 hands its outputs to the second stage in
-// the swizzled order of shift sh (input and output stay in natural order).
 template <typename T, int F = 1>
 __device__ __forceinline__ void fft_smem(cx<T> *s, int fstride, int stride, int lgn, int jt,
                                          const cx<T> *__restrict__ tw, int lgl, bool cin = false,
-                                         bool cout = false, int sched = 0, int sh = 0)
+                                         bool cout = false, int sched = 0)
 {
     const int n = 1 << lgn, nt = n >> kLgV;
     int ns = 1, lgns = 0, rem = lgn;
     const int rm = lgn % kLgV;
-    bool sw_in = false;  // this stage reads the swizzled order
     while (rem > 0) {
         const int lr = (sched && lgns == 0 && rm) ? rm : (rem >= kLgV ? kLgV : rem);
         const bool first = (lgns == 0), last = (rem == lr);
         const bool ci = cin && first, co = cout && last;
-        const bool sw_out = kV == 8 && sh > 0 && first && !last && lr == 3;
         switch (lr) {
             case 4:
                 if constexpr (kV >= 16) fft_stage<T, 16, F>(s, fstride, stride, n, ns, lgns + 4, jt, nt, tw, lgl, ci, co);
                 break;
-            case 3:
-                if (sw_out)
-                    fft_stage<T, 8, F, false, true>(s, fstride, stride, n, ns, lgns + 3, jt, nt, tw, lgl, ci, co, sh);
-                else if (sw_in)
-                    fft_stage<T, 8, F, true, false>(s, fstride, stride, n, ns, lgns + 3, jt, nt, tw, lgl, ci, co, sh);
-                else
-                    fft_stage<T, 8, F>(s, fstride, stride, n, ns, lgns + 3, jt, nt, tw, lgl, ci, co);
-                break;
-            case 2:
-                if (sw_in)
-                    fft_stage<T, 4, F, true, false>(s, fstride, stride, n, ns, lgns + 2, jt, nt, tw, lgl, ci, co, sh);
-                else
-                    fft_stage<T, 4, F>(s, fstride, stride, n, ns, lgns + 2, jt, nt, tw, lgl, ci, co);
-                break;
-            default:
-                if (sw_in)
-                    fft_stage<T, 2, F, true, false>(s, fstride, stride, n, ns, lgns + 1, jt, nt, tw, lgl, ci, co, sh);
-                else
-                    fft_stage<T, 2, F>(s, fstride, stride, n, ns, lgns + 1, jt, nt, tw, lgl, ci, co);
-                break;
+            case 3: fft_stage<T, 8, F>(s, fstride, stride, n, ns, lgns + 3, jt, nt, tw, lgl, ci, co); break;
+            case 2: fft_stage<T, 4, F>(s, fstride, stride, n, ns, lgns + 2, jt, nt, tw, lgl, ci, co); break;
+            default: fft_stage<T, 2, F>(s, fstride, stride, n, ns, lgns + 1, jt, nt, tw, lgl, ci, co); break;
         }
-        sw_in = sw_out;
         ns <<= lr;
         lgns += lr;
         rem -= lr;
@@ -561,12 +541,15 @@ __global__ void __launch_bounds__(256, op_min_blocks<Op>::value) k_rows(RowGeom 
     if (kLoad && threadIdx.x == 0 && t < ntiles && !stall) issue(t, 0);
     unsigned phase = 0;  // bit s: parity of the next completion of stage s
     const int jt = threadIdx.x % nt, rf = threadIdx.x / nt;  // FFT mapping: nt threads per row
-    const int rsh = nt >= 16 ? 4 : 3;                        // swizzle shift of the first stage (fft_smem)
+    // the kernels compiled for a row length exchange the first stage's outputs
+    // in swizzled order (constant index arithmetic); with the run-time length
+    // the extra index arithmetic cost more than the bank conflicts it removes
+    // (2D rows of 256 to 1024 nodes: relaxation steps 26% slower)
     auto row_fft = [&](cx<T> *z) {
         if constexpr (LG > 0)
             fft_ct<T, 1, LG, SCHED, (LG - kLgV >= 4 ? 4 : 3)>(z, 0, 1, jt, tws, LG + 1, false, false);
         else
-            fft_smem<T>(z, 0, 1, g.lgh, jt, tws, lg1, false, false, g.sched, rsh);
+            fft_smem<T>(z, 0, 1, g.lgh, jt, tws, lg1, false, false, g.sched);
     };
     typename op_acc<Op>::type acc;
 
