@@ -69,11 +69,16 @@ def test_reference_arm_under_torchrun_two_ranks():
 
 def test_pass_bytes_match_the_per_node_figures():
     """The roofline's algorithmic bytes per launch: 97 / 24 / 27 / 49 B per node
-    for the forward row, x2, last-axis and inverse row passes of the FP32 CG
-    iteration (d = 3), plus 44 B per boundary node in the inverse row pass."""
+    for the forward row (or plane), x2, last-axis and inverse row (or plane)
+    passes of the FP32 CG iteration (d = 3), plus 44 B per boundary node in the
+    inverse pass."""
     import bench
     N = 128 ** 3
     assert bench.pass_bytes("rows_fwd", N, 0) == 97 * N
     assert bench.pass_bytes("cols_x2", N, 0) == 24 * N
     assert bench.pass_bytes("last_axis", N, 0) == 27 * N
     assert bench.pass_bytes("rows_inv", N, 1000) == 49 * N + 44 * 1000
+    # the plane passes move the bytes of the row passes they replace (their x2
+    # transform stays in shared memory)
+    assert bench.pass_bytes("plane_fwd", N, 0) == bench.pass_bytes("rows_fwd", N, 0)
+    assert bench.pass_bytes("plane_inv", N, 1000) == bench.pass_bytes("rows_inv", N, 1000)
