@@ -126,7 +126,7 @@ class ClockSampler:
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the
 # committed ncu summaries; None when the kernel changed after the capture.
 MEASURED_TRAFFIC = {
-    "plane_fwd": (143.2e6, "profiles/cg_iteration_kernels_static_solve_128cube.md"),
+    "plane_fwd": (143.3e6, "profiles/cg_iteration_kernels_static_solve_128cube.md"),
     "rows_inv": (101.2e6, "profiles/cg_iteration_kernels_static_solve_128cube.md"),
     "last_axis": (42.3e6, "profiles/cg_iteration_kernels_static_solve_128cube.md"),
     "rows_fwd": (146.4e6, "profiles/cg_iteration_kernels_static_solve_128cube.md"),
