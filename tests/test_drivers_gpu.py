@@ -77,14 +77,29 @@ def test_static_2d_bond_fp64_with_prescribed_w(pdm, oracle):
     plan.close()
 
 
-@pytest.mark.parametrize("n", [32, 64])
-def test_plane_passes_match_row_passes(pdm, oracle, n):
-    """FP32 CG on a cube: every combination of fused x1-x2 plane passes and
-    row/column passes for the two halves of the iteration gives the same refined
-    solution; each meets the oracle's residual, and the profile shows which
-    passes ran."""
-    cfg = inputs.cube_with_cavity(n=n, radius_frac=0.2)
-    shape = cfg["shape"]
+def _block_with_cavity(shape, margin=3, layers=3, sigma=1e-3, delta=3.0):
+    """The cube-with-cavity case on a box whose sides may differ (C-order shape):
+    body = the box minus a margin and a centred ball, clamped at the x1-low face,
+    loaded at the x1-high face."""
+    x1, x2, x3 = inputs.coords(shape, 1.0)
+    n3, n2, n1 = shape
+    chi = inputs.box_mask(shape, (margin,) * 3, (n1 - margin, n2 - margin, n3 - margin))
+    r = 0.2 * min(shape)
+    chi[(x1 - (n1 - 1) / 2) ** 2 + (x2 - (n2 - 1) / 2) ** 2 + (x3 - (n3 - 1) / 2) ** 2 < r * r] = 0
+    chi_om = chi.copy()
+    chi_om[(x1 < margin + layers) & (chi == 1)] = 0
+    b = np.zeros((3,) + shape)
+    b[0][(x1 >= n1 - margin - layers) & (chi == 1)] = sigma / delta
+    return dict(shape=shape, chi=chi, chi_omega=np.stack([chi_om] * 3), b=b)
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (64, 64, 64), (32, 64, 64)])
+def test_plane_passes_match_row_passes(pdm, oracle, shape):
+    """FP32 CG on boxes with n1 = n2 (the plane passes' condition; n3 free):
+    every combination of fused x1-x2 plane passes and row/column passes for the
+    two halves of the iteration gives the same refined solution; each meets the
+    oracle's residual, and the profile shows which passes ran."""
+    cfg = _block_with_cavity(shape)
     prob = pdm.Problem(shape=shape, delta=3.0, model=pdm.PD_LIN_STATE, nu=0.25, fp64=False)
     ka, cb, _ = oracle.lps_constants(1.0, 0.25, 1.0, 3.0)
     bn = np.linalg.norm(cfg["chi_omega"] * cfg["b"])
